@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark: multiplicative-update sweeps per second of the fused sweep.
+
+Workload: dense CP 'ir,jr,kr->ijk' 512 x 512 x 512 (134,217,728 entries),
+rank 64, Y = Poisson counts from Gamma(0.3, 1) ground-truth factors (seed 0),
+no missing entries, KL loss ((alpha, beta) = (1, 0) of App. B), init
+U(0.5, 1.5).  One step = one sweep of Algorithm 1 (three factor updates).
+Y (537 MB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+Arms:
+  --impl ours       the tensor-core (BF16 operands, FP32 accumulation) sweep,
+                    plus the plain FP32 CUDA-core sweep as a variant
+  --impl reference  the FP64 CPU oracle on the host cores (a bounded slab of the
+                    same workload per step, scaled to sweeps/s)
+
+Multi-GPU (torchrun): every rank fits its own replica of the workload (the
+problems are independent; no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MU sweeps/sec at oracle-matched loss; % of HBM/tensor roofline; mixed vs plain FP32"
+UNIT = "sweeps/s"
+WORKLOAD = "cp ir,jr,kr->ijk 512x512x512 rank 64, KL (alpha,beta)=(1,0), Poisson/Gamma(0.3,1), no mask"
+N_ENTRIES = 512 ** 3
+SLAB_ROWS = 16          # rows of factor A updated per reference step
+CPU_BASELINE_ROWS = 64  # rows of factor A updated by the cpu_baseline leg
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="cube side (512 = the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_view_tc.cuh", "k_view_tc.cu", "k_view_tc_inst.cuh"):
+        with open(os.path.join(ROOT, "paper_2602_02759_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM bytes per launch of the fused pass from the committed ncu summary,
+    or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "fused_pass_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("kernel_hash") == kernel_hash():
+            return float(d["bytes_per_launch_full"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle legs
+
+def oracle_slab_seconds(p, rows):
+    """Time the oracle's update of rows [0, rows) of factor A: that update only
+    involves Y[0:rows], A[0:rows], B and C, so it is exactly those rows of the
+    full update."""
+    import numpy as np
+    from oracle import OracleModel
+    import oracle
+    dims = dict(p.dims)
+    dims["i"] = rows
+    m = OracleModel(p.model_str, dims)
+    y = np.ascontiguousarray(p.y[:rows], dtype=np.float64)
+    init = [np.ascontiguousarray(p.inits[0][0][:rows], np.float64),
+            p.inits[0][1].astype(np.float64), p.inits[0][2].astype(np.float64)]
+    t0 = time.perf_counter()
+    m.update_factor(0, y, None, init, p.alpha, p.beta)
+    return time.perf_counter() - t0, oracle.num_threads()
+
+
+def sweep_fraction(rows, n):
+    # a sweep updates 3 factors of n rows each
+    return rows / (3.0 * n)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    p = synth.config2(n=args.n)
+    rows = min(SLAB_ROWS, args.n)
+    for _ in range(args.warmup):
+        oracle_slab_seconds(p, rows)
+    ts = []
+    cores = 1
+    for _ in range(args.steps):
+        t, cores = oracle_slab_seconds(p, rows)
+        ts.append(t)
+    total = sum(ts)
+    value = args.steps * sweep_fraction(rows, args.n) / total
+    sample = (f"per step: oracle update of rows 0..{rows - 1} of factor A (Y[0:{rows}], exact rows "
+              f"of the full update) = {sweep_fraction(rows, args.n):.5f} sweep")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2_flush": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2602_02759_gb300 as nef
+    import synth
+
+    p = synth.config2(n=args.n)
+    # cpu_baseline before any heavy GPU work (rank 0, N = 1 only)
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = min(CPU_BASELINE_ROWS, args.n)
+        t, cores = oracle_slab_seconds(p, rows)
+        cpu_base = {"value": sweep_fraction(rows, args.n) / t, "unit": UNIT, "cores": cores,
+                    "kind": "oracle",
+                    "sample": f"oracle update of rows 0..{rows - 1} of factor A (exact rows of the "
+                              f"full update) = {sweep_fraction(rows, args.n):.5f} sweep, {t:.1f} s"}
+
+    dims = p.dims
+    stream = torch.cuda.current_stream()
+    Y = torch.from_numpy(p.y).cuda()
+    init = [torch.from_numpy(f).cuda() for f in p.inits[0]]
+
+    def fresh():
+        return [f.clone() for f in init]
+
+    plan = nef.Plan(p.model_str, dims, precision="bf16", profile=True, stream=stream)
+    fs = fresh()
+    for _ in range(args.warmup):
+        plan.fit(Y, None, fs, p.alpha, p.beta, 1)
+    plan.check()
+    plan.profile(reset=True)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.fit(Y, None, fs, p.alpha, p.beta, 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    plan.check()
+    ms = ev0.elapsed_time(ev1)
+    prof = plan.profile(reset=True)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel: the tensor-core fused pass
+    hbm, bf16, src = load_peaks()
+    tc_ms, tc_n = prof["tcgen05"]
+    roof = None
+    if tc_n:
+        avg_s = tc_ms / tc_n / 1e3
+        alg_bytes = 4.0 * p.y.size   # one FP32 read of Y per pass
+        ach = alg_bytes / avg_s / 1e9
+        traffic = load_traffic()
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
+                "kernel": "k_view_tc (tcgen05 fused pass)", "avg_launch_us": avg_s * 1e6,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "share_of_step": tc_ms / ms}
+    launches_per_sweep = plan.launches(False)
+    loss_bf16 = plan.loss(Y, None, fs, p.alpha, p.beta)[0]
+
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        # plain FP32 CUDA-core sweep from the same start, same number of sweeps
+        plan32 = nef.Plan(p.model_str, dims, precision="fp32", profile=True, stream=stream)
+        g = fresh()
+        for _ in range(args.warmup):
+            plan32.fit(Y, None, g, p.alpha, p.beta, 1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan32.fit(Y, None, g, p.alpha, p.beta, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan32.check()
+        ms32 = e0.elapsed_time(e1)
+        loss32 = plan32.loss(Y, None, g, p.alpha, p.beta)[0]
+        variants["fp32_plain"] = {"value": args.steps / (ms32 / 1e3), "unit": UNIT,
+                                  "ms_per_step": ms32 / args.steps, "loss": loss32}
+        variants["bf16_vs_fp32_speedup"] = (args.steps / (ms / 1e3)) / variants["fp32_plain"]["value"]
+        variants["loss_check"] = {"bf16": loss_bf16, "fp32": loss32,
+                                  "rel_diff": abs(loss_bf16 - loss32) / loss32,
+                                  "sweeps": args.warmup + args.steps,
+                                  "note": "the FP32 sweep matches the FP64 oracle to 1e-5 (parity tests)"}
+        del plan32
+
+    e2e = None
+    if not args.no_e2e:
+        Yh = torch.from_numpy(p.y).pin_memory()
+        Fh = [f.clone().cpu().pin_memory() for f in init]
+        Fo = [torch.empty_like(f).pin_memory() for f in Fh]
+        Yd = torch.empty_like(Y)
+        fd = fresh()
+        torch.cuda.synchronize()
+        h2d = Yh.numel() * 4 + sum(f.numel() * 4 for f in Fh)
+        d2h = sum(f.numel() * 4 for f in Fo)
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            Yd.copy_(Yh, non_blocking=True)
+            for a, b in zip(fd, Fh):
+                a.copy_(b, non_blocking=True)
+            plan.fit(Yd, None, fd, p.alpha, p.beta, 1)
+            for a, b in zip(Fo, fd):
+                a.copy_(b, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+        del Yd, Yh
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands, fp32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "bf16 (tcgen05)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2_flush": "inputs larger than L2 (Y = 537 MB)"},
+            "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e,
+            "gpu_launches": launches_per_sweep * args.steps,
+            "clocks": clocks, "loss": loss_bf16, "variants": variants,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

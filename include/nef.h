@@ -1,0 +1,170 @@
+/*
+ * nef.h -- C ABI of the GB300 (sm_103a) nonnegative einsum factorization engine.
+ *
+ * The engine fits  Yhat = einsum(model_str, Theta^(1), ..., Theta^(L))  to a
+ * nonnegative tensor Y by the multiplicative update of NNEinFact:
+ *   model family and model string ............ Sec. 2, Eq. 2.1-2.3
+ *   objective with the floor eps ............. Sec. 3, Eq. 3.1
+ *   update  Theta <- max(eps, Theta * g^{-1}(num/den)) ... Thm. 3.1, Eq. 3.4
+ *   num/den as einsum(einstr_l, ...) ......... Eq. 3.5-3.8
+ *   the sweep (Gauss-Seidel over factors) .... Algorithm 1
+ *   (alpha,beta)-divergence, a, b and g ...... App. B
+ *   missing data (mask) ...................... Sec. 6.5 (experimental design)
+ *
+ * Conventions shared by every entry point
+ *   - Letters are lowercase a-z.  Letters on the right of "->" are observed
+ *     (the modes of Y, in that order); letters that appear only on the left are
+ *     latent (contracted), numbered in order of first appearance.
+ *   - Y is row-major over the observed letters in right-hand-side order.
+ *   - Factor l is row-major over the letters of the l-th term, in term order.
+ *   - mask, when given, holds one byte per entry of Y (nonzero = observed).
+ *   - Device pointers are CUDA global-memory pointers on the current device;
+ *     the caller owns Y, mask and the factors.  Host pointers are marked.
+ *   - Element type: double for NEF_FP64 plans, float otherwise (NEF_FP32 and
+ *     NEF_BF16 keep FP32 data and FP32 master factors; NEF_BF16 feeds the
+ *     tensor cores BF16 operands with FP32 accumulation).
+ *   - Work is ordered on opt.stream (a cudaStream_t; NULL = legacy stream).
+ *     nef_fit and nef_update return once the work is enqueued; nef_loss
+ *     synchronises the stream.
+ *   - No call throws or aborts: each returns a nef_status, and
+ *     nef_last_error() gives a message for the last failure on this thread.
+ *   - The plan owns a device workspace sized at nef_plan time; a plan may be
+ *     used by one thread at a time.
+ */
+#ifndef NEF_H
+#define NEF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nef_plan_s* nef_plan_t;
+
+typedef enum {
+    NEF_OK = 0,
+    NEF_EINVAL = 1,        /* bad argument: null pointer, size, option or factor index   */
+    NEF_EPARSE = 2,        /* malformed model string (Eq. 2.2 grammar)                    */
+    NEF_EUNSUPPORTED = 3,  /* alpha == 0 with beta != 1 (no decomposition, App. B), or a  */
+                           /* plan the requested precision cannot run                     */
+    NEF_ENOMEM = 4,        /* device workspace allocation failed                          */
+    NEF_ECUDA = 5,         /* a CUDA runtime or driver call failed                        */
+    NEF_EDATA = 6,         /* Y holds a negative or non-finite entry (checked on request) */
+    NEF_ETIMEOUT = 7       /* a bounded device-side wait gave up; the context is intact   */
+} nef_status;
+
+enum {
+    NEF_FP32 = 0,  /* CUDA-core FP32 fused sweep (the plain FP32 path)                */
+    NEF_BF16 = 1,  /* tcgen05 tensor cores: BF16 operands, FP32 TMEM accumulation     */
+    NEF_FP64 = 2   /* CUDA-core FP64 fused sweep                                      */
+};
+
+typedef struct {
+    int precision;      /* NEF_FP32, NEF_BF16 or NEF_FP64                                   */
+    double eps;         /* floor of Eq. 3.1 (paper: "a very small eps > 0"); default 1e-10  */
+    int check_data;     /* nonzero: nef_fit/nef_update first check Y >= 0 and finite        */
+    int force_generic;  /* nonzero: use the unfused path (yhat, a, b materialised)          */
+    int profile;        /* nonzero: time every fused-pass launch with CUDA events on the    */
+                        /* plan's stream (read back with nef_plan_profile)                  */
+    void* stream;       /* cudaStream_t used by every call on the plan                      */
+} nef_options;
+
+/* Fill *opt with the defaults: NEF_FP32, eps = 1e-10, no data check, fused, no
+ * profiling, stream NULL. */
+void nef_default_options(nef_options* opt);
+
+/*
+ * nef_plan -- parse model_str (Eq. 2.2), check it, and build the per-factor
+ * pass plans of Algorithm 1 (including swap(model_str, l) of Eq. 3.8).
+ *   model_str : NUL-terminated, e.g. "ir,jr,kr->ijk" (host)
+ *   shapes    : n_obs dimensions of Y in right-hand-side order (host)
+ *   ranks     : n_lat latent dimensions in order of first appearance (host)
+ *   opt       : options (host; NULL = defaults); copied into the plan
+ *   out       : receives the plan handle (host)
+ * Errors: NEF_EPARSE for a malformed string or a repeated letter within a
+ * term or on the right; NEF_EINVAL for a count mismatch or a dimension < 1;
+ * NEF_ENOMEM / NEF_ECUDA from workspace allocation.  On error *out is NULL.
+ */
+nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs,
+                    const int64_t* ranks, int n_lat, const nef_options* opt,
+                    nef_plan_t* out);
+
+/* Release the plan and its workspace (NULL is ignored). */
+void nef_plan_destroy(nef_plan_t plan);
+
+/*
+ * nef_fit -- run `iters` sweeps of Algorithm 1: for l = 1..L in string order,
+ * rebuild Yhat from the current factors, form num and den (Eq. 3.6-3.8) with
+ * the masked weights a(Y,Yhat), b(Y,Yhat) of App. B, and apply Eq. 3.4.
+ *   Y       : device, N elements (see conventions), not modified
+ *   mask    : device, N bytes, or NULL (every entry observed)
+ *   factors : host array of L device pointers, updated in place
+ *   alpha, beta : the (alpha,beta)-divergence parameters of App. B
+ *   iters   : number of sweeps (0 is a no-op)
+ * Errors: NEF_EUNSUPPORTED for alpha == 0 with beta != 1; NEF_EINVAL for a
+ * null pointer or iters < 0; NEF_EDATA if check_data found a bad Y entry
+ * (factors untouched); NEF_ECUDA for a failed launch.
+ */
+nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask,
+                   void* const* factors, double alpha, double beta, int iters);
+
+/*
+ * nef_update -- one inner step of Algorithm 1: update factor l only, with the
+ * other factors held fixed.  Arguments as nef_fit; l in [0, L).
+ */
+nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask,
+                      void* const* factors, double alpha, double beta);
+
+/*
+ * nef_loss -- sum over observed entries of D_{alpha,beta}(y, yhat) (Eq. 3.1
+ * with the five-case definition of App. B), with FP64 accumulation.
+ *   out : host, 2 doubles: out[0] = the sum, out[1] = the number of observed
+ *         entries (so out[0]/out[1] is the mean of Sec. 6.5's metric).
+ * Synchronises the plan's stream.  Errors as nef_fit.
+ */
+nef_status nef_loss(nef_plan_t plan, const void* Y, const uint8_t* mask,
+                    void* const* factors, double alpha, double beta, double* out);
+
+/*
+ * nef_plan_info -- human-readable description of the per-factor passes the
+ * planner chose (row/column view, bond letters, operand sources, kernels).
+ * Writes at most cap bytes (NUL-terminated) into buf (host).  Returns the
+ * length the full text needs.
+ */
+int nef_plan_info(nef_plan_t plan, char* buf, int cap);
+
+/*
+ * nef_plan_launches -- number of kernel launches one sweep of nef_fit enqueues
+ * for the given mask presence (used to report launch counts).
+ */
+int nef_plan_launches(nef_plan_t plan, int has_mask);
+
+/*
+ * nef_plan_profile -- with opt.profile set: synchronise the plan's stream and
+ * return (host) the summed device time in milliseconds and the number of the
+ * fused-pass launches recorded since the last reset, per kernel family:
+ *   ms[0], count[0] : tensor-core (tcgen05) fused passes
+ *   ms[1], count[1] : CUDA-core fused passes
+ * reset != 0 clears the record afterwards.  Errors: NEF_EINVAL without
+ * profiling; NEF_ECUDA from the event queries.
+ */
+nef_status nef_plan_profile(nef_plan_t plan, double* ms, int* count, int reset);
+
+/*
+ * nef_check -- synchronise the plan's stream and report device-side errors
+ * raised by earlier calls on this plan: NEF_ETIMEOUT if a bounded wait inside
+ * a kernel gave up (the kernel then exits cleanly, the results of that call
+ * are invalid, the context stays usable), NEF_ECUDA for an asynchronous CUDA
+ * error.  Clears the device flag.
+ */
+nef_status nef_check(nef_plan_t plan);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* nef_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEF_H */

@@ -1,0 +1,215 @@
+"""ctypes binding of the C ABI in include/nef.h (argument marshalling only).
+
+Every step of the sweep runs in libnef.so's CUDA kernels; torch only provides
+device memory and the stream.  The library is built in-tree by
+``paper_2602_02759_gb300.build`` (or ``__graft_entry__.build()``); if it is
+missing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libnef.so")
+
+NEF_FP32, NEF_BF16, NEF_FP64 = 0, 1, 2
+STATUS = {0: "NEF_OK", 1: "NEF_EINVAL", 2: "NEF_EPARSE", 3: "NEF_EUNSUPPORTED", 4: "NEF_ENOMEM",
+          5: "NEF_ECUDA", 6: "NEF_EDATA", 7: "NEF_ETIMEOUT"}
+PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
+
+# every symbol include/nef.h declares
+EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_update",
+           "nef_loss", "nef_plan_info", "nef_plan_launches", "nef_plan_profile", "nef_check",
+           "nef_last_error"]
+# every symbol include/nef_debug.h declares
+DEBUG_EXPORTS = ["nef_tc_probe"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double),
+                ("check_data", ctypes.c_int), ("force_generic", ctypes.c_int),
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class NefError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libnef.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libnef.so not built at {path}; run paper_2602_02759_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    lib.nef_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.nef_plan.argtypes = [ctypes.c_char_p, i64p, ctypes.c_int, i64p, ctypes.c_int,
+                             ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.nef_plan.restype = ctypes.c_int
+    lib.nef_plan_destroy.argtypes = [vp]
+    lib.nef_fit.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int]
+    lib.nef_fit.restype = ctypes.c_int
+    lib.nef_update.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(vp), ctypes.c_double,
+                               ctypes.c_double]
+    lib.nef_update.restype = ctypes.c_int
+    lib.nef_loss.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double, dp]
+    lib.nef_loss.restype = ctypes.c_int
+    lib.nef_plan_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_int]
+    lib.nef_plan_info.restype = ctypes.c_int
+    lib.nef_plan_launches.argtypes = [vp, ctypes.c_int]
+    lib.nef_plan_launches.restype = ctypes.c_int
+    lib.nef_plan_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.c_int]
+    lib.nef_plan_profile.restype = ctypes.c_int
+    lib.nef_check.argtypes = [vp]
+    lib.nef_check.restype = ctypes.c_int
+    lib.nef_last_error.restype = ctypes.c_char_p
+    lib.nef_tc_probe.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+    lib.nef_tc_probe.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != 0:
+        msg = load().nef_last_error().decode(errors="replace")
+        raise NefError(status, msg)
+
+
+def split_model(model_str: str):
+    """Observed letters (RHS order) and latent letters (order of first appearance)."""
+    s = model_str.replace(" ", "")
+    lhs, rhs = s.split("->")
+    latent = []
+    for ch in lhs.replace(",", ""):
+        if ch not in rhs and ch not in latent:
+            latent.append(ch)
+    return list(rhs), latent, lhs.split(",")
+
+
+class Plan:
+    """A plan for one model string and shape (nef_plan).
+
+    ``dims`` maps letters to sizes (observed dims and latent ranks).  ``stream``
+    is a torch.cuda.Stream (or a raw cudaStream_t integer); None uses torch's
+    current stream at plan time.
+    """
+
+    def __init__(self, model_str: str, dims: dict, precision: str = "fp32", eps: float = 1e-10,
+                 check_data: bool = False, force_generic: bool = False, profile: bool = False,
+                 stream=None):
+        lib = load()
+        obs, lat, terms = split_model(model_str)
+        self.model_str = model_str
+        self.terms = terms
+        self.dims = dict(dims)
+        self.precision = precision
+        shapes = (ctypes.c_int64 * max(1, len(obs)))(*[int(dims[c]) for c in obs])
+        ranks = (ctypes.c_int64 * max(1, len(lat)))(*[int(dims[c]) for c in lat])
+        opt = Options()
+        lib.nef_default_options(ctypes.byref(opt))
+        opt.precision = PRECISIONS[precision]
+        opt.eps = float(eps)
+        opt.check_data = int(bool(check_data))
+        opt.force_generic = int(bool(force_generic))
+        opt.profile = int(bool(profile))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        h = ctypes.c_void_p()
+        check(lib.nef_plan(model_str.encode(), shapes, len(obs), ranks, len(lat),
+                           ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nef_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ----------------------------------------------------------- helpers
+    @staticmethod
+    def _ptr(t):
+        return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+    def _facs(self, factors):
+        arr = (ctypes.c_void_p * len(factors))()
+        for k, f in enumerate(factors):
+            arr[k] = f.data_ptr()
+        return arr
+
+    def _check_args(self, Y, mask, factors):
+        import torch
+        want = torch.float64 if self.precision == "fp64" else torch.float32
+        if Y.dtype != want or not Y.is_contiguous() or not Y.is_cuda:
+            raise ValueError(f"Y must be a contiguous CUDA {want} tensor")
+        if mask is not None and (mask.dtype != torch.uint8 or not mask.is_contiguous()
+                                 or mask.numel() != Y.numel() or not mask.is_cuda):
+            raise ValueError("mask must be a contiguous CUDA uint8 tensor shaped like Y")
+        if len(factors) != len(self.terms):
+            raise ValueError("wrong number of factors")
+        for t, f in zip(self.terms, factors):
+            shp = tuple(int(self.dims[c]) for c in t)
+            if f.dtype != want or not f.is_contiguous() or tuple(f.shape) != shp or not f.is_cuda:
+                raise ValueError(f"factor {t} must be a contiguous CUDA {want} tensor of shape {shp}")
+
+    # -------------------------------------------------------------- ABI
+    def fit(self, Y, mask, factors, alpha, beta, iters):
+        self._check_args(Y, mask, factors)
+        check(load().nef_fit(self._h, self._ptr(Y), self._ptr(mask), self._facs(factors),
+                             float(alpha), float(beta), int(iters)))
+
+    def update(self, l, Y, mask, factors, alpha, beta):
+        self._check_args(Y, mask, factors)
+        check(load().nef_update(self._h, int(l), self._ptr(Y), self._ptr(mask),
+                                self._facs(factors), float(alpha), float(beta)))
+
+    def loss(self, Y, mask, factors, alpha, beta):
+        self._check_args(Y, mask, factors)
+        out = (ctypes.c_double * 2)()
+        check(load().nef_loss(self._h, self._ptr(Y), self._ptr(mask), self._facs(factors),
+                              float(alpha), float(beta), out))
+        return float(out[0]), int(out[1])
+
+    def check(self):
+        """Synchronise and raise if a kernel reported a bounded-wait timeout."""
+        check(load().nef_check(self._h))
+
+    def profile(self, reset: bool = True):
+        """Summed device ms and launch counts of the fused passes since the last reset:
+        {"tcgen05": (ms, n), "simt": (ms, n)}."""
+        ms = (ctypes.c_double * 2)()
+        cnt = (ctypes.c_int * 2)()
+        check(load().nef_plan_profile(self._h, ms, cnt, int(bool(reset))))
+        return {"tcgen05": (ms[0], cnt[0]), "simt": (ms[1], cnt[1])}
+
+    def info(self) -> str:
+        n = load().nef_plan_info(self._h, None, 0)
+        buf = ctypes.create_string_buffer(n)
+        load().nef_plan_info(self._h, buf, n)
+        return buf.value.decode()
+
+    def launches(self, has_mask: bool) -> int:
+        return int(load().nef_plan_launches(self._h, int(bool(has_mask))))

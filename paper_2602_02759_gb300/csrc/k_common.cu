@@ -1,0 +1,336 @@
+// k_common.cu -- small kernels of the sweep: the generic einsum used for operand
+// preparation and epilogues (Eq. 3.8 with S in place of the weighted tensor),
+// mask packing, the data check, split reductions, the update of Eq. 3.4, and the
+// unfused fallback that materialises yhat, a(Y,Yhat), b(Y,Yhat) (Algorithm 1 as
+// written) for model strings the fused view cannot express.
+#include <algorithm>
+
+#include "nef_device.cuh"
+#include "nef_internal.h"
+
+namespace nef {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__global__ void k_einsum_part(EinDesc d, int64_t chunk, T* partial) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sp = blockIdx.y;
+    if (o >= d.n_out_el) return;
+    int64_t off[kMaxEinOps];
+    for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
+    int64_t rem = o;
+    for (int q = d.n_out - 1; q >= 0; --q) {
+        int64_t v = rem % d.dim[q];
+        rem /= d.dim[q];
+        for (int k = 0; k < d.n_ops; ++k) off[k] += v * d.ost[k][q];
+    }
+    const int64_t f0 = (int64_t)sp * chunk;
+    const int64_t f1 = min(f0 + chunk, d.n_free_el);
+    int64_t idx[kMaxEinLet];
+    rem = f0;
+    for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
+        idx[q] = rem % d.dim[q];
+        rem /= d.dim[q];
+        for (int k = 0; k < d.n_ops; ++k) off[k] += idx[q] * d.ost[k][q];
+    }
+    T acc = T(0);
+    for (int64_t f = f0; f < f1; ++f) {
+        T p = T(1);
+        for (int k = 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
+        acc += p;
+        for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
+            idx[q] += 1;
+            for (int k = 0; k < d.n_ops; ++k) off[k] += d.ost[k][q];
+            if (idx[q] < d.dim[q]) break;
+            for (int k = 0; k < d.n_ops; ++k) off[k] -= d.ost[k][q] * d.dim[q];
+            idx[q] = 0;
+        }
+    }
+    partial[(int64_t)sp * d.n_out_el + o] = acc;
+}
+
+// Single-split contraction written straight to the destination layout.
+template <typename T>
+__global__ void k_einsum_direct(EinDesc d) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= d.n_out_el) return;
+    int64_t off[kMaxEinOps];
+    for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
+    int64_t dst = 0, rem = o;
+    for (int q = d.n_out - 1; q >= 0; --q) {
+        const int64_t v = rem % d.dim[q];
+        rem /= d.dim[q];
+        dst += v * d.out_st[q];
+        for (int k = 0; k < d.n_ops; ++k) off[k] += v * d.ost[k][q];
+    }
+    int64_t idx[kMaxEinLet];
+    for (int q = d.n_out; q < d.n_out + d.n_free; ++q) idx[q] = 0;
+    T acc = T(0);
+    for (int64_t f = 0; f < d.n_free_el; ++f) {
+        T p = T(1);
+        for (int k = 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
+        acc += p;
+        for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
+            idx[q] += 1;
+            for (int k = 0; k < d.n_ops; ++k) off[k] += d.ost[k][q];
+            if (idx[q] < d.dim[q]) break;
+            for (int k = 0; k < d.n_ops; ++k) off[k] -= d.ost[k][q] * d.dim[q];
+            idx[q] = 0;
+        }
+    }
+    T* out = static_cast<T*>(d.out);
+    out[dst] = d.accumulate ? out[dst] + acc : acc;
+}
+
+template <typename T>
+__global__ void k_einsum_final(EinDesc d, int n_split, const T* partial) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= d.n_out_el) return;
+    T acc = T(0);
+    for (int s = 0; s < n_split; ++s) acc += partial[(int64_t)s * d.n_out_el + o];
+    int64_t dst = 0, rem = o;
+    for (int q = d.n_out - 1; q >= 0; --q) {
+        dst += (rem % d.dim[q]) * d.out_st[q];
+        rem /= d.dim[q];
+    }
+    T* out = static_cast<T*>(d.out);
+    out[dst] = d.accumulate ? out[dst] + acc : acc;
+}
+
+__global__ void k_pack_mask(const uint8_t* __restrict__ m, int64_t n, uint32_t* __restrict__ bits) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = (n + 31) >> 5;
+    if (w >= nw) return;
+    uint32_t v = 0;
+    const int64_t e0 = w << 5;
+    for (int b = 0; b < 32; ++b) {
+        const int64_t e = e0 + b;
+        if (e < n && m[e]) v |= (1u << b);
+    }
+    bits[w] = v;
+}
+
+template <typename T>
+__global__ void k_check_data(const T* __restrict__ y, int64_t n, int* flag) {
+    int bad = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        T v = y[e];
+        if (!(v >= T(0)) || isinf((double)v)) bad = 1;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+template <typename T>
+__global__ void k_reduce_splits(const T* __restrict__ part, int n_split, int64_t n, T* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    T acc = T(0);
+    for (int s = 0; s < n_split; ++s) acc += part[(int64_t)s * n + e];
+    out[e] = acc;
+}
+
+template <typename T>
+__global__ void k_update(T* __restrict__ theta, const T* __restrict__ num, const T* __restrict__ den,
+                         int64_t n, UpdateSpec u) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    theta[e] = mu_update(theta[e], num[e], den[e], u);
+}
+
+template <typename T>
+__global__ void k_fill(T* p, int64_t n, T v) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) p[e] = v;
+}
+
+__global__ void k_sum_f64(const double* __restrict__ part, int n, double* out) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += part[k];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) out[0] = v;
+    }
+}
+
+__global__ void k_convert_bf16(const float* __restrict__ src, int64_t n, uint16_t* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    // round to nearest even
+    uint32_t u = __float_as_uint(src[e]);
+    uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);
+    dst[e] = (uint16_t)(r >> 16);
+}
+
+// Unfused path: yhat at every entry by a loop over all latent combinations,
+// then the masked weights and (optionally) the divergence.
+template <typename T>
+__global__ void k_generic_weights(GenericRecon g, const T* __restrict__ y, const uint32_t* mbits,
+                                  WeightSpec w, T* __restrict__ wa, T* __restrict__ wb,
+                                  int has_loss, LossSpec L, double* loss_part) {
+    __shared__ double sh_loss[kThreads / 32];
+    __shared__ double sh_cnt[kThreads / 32];
+    double lsum = 0.0, lcnt = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t idx[kMaxLet];
+        int64_t rem = e;
+        for (int m = g.n_obs - 1; m >= 0; --m) {
+            idx[m] = rem % g.dim[m];
+            rem /= g.dim[m];
+        }
+        int64_t off[kMaxFac];
+        for (int f = 0; f < g.n_fac; ++f) {
+            off[f] = 0;
+            for (int m = 0; m < g.n_obs; ++m) off[f] += idx[m] * g.fst[f][m];
+        }
+        for (int x = g.n_obs; x < g.n_let; ++x) idx[x] = 0;
+        T yh = T(0);
+        for (int64_t c = 0; c < g.n_lat_el; ++c) {
+            T p = T(1);
+            for (int f = 0; f < g.n_fac; ++f) p *= static_cast<const T*>(g.fac[f])[off[f]];
+            yh += p;
+            for (int x = g.n_let - 1; x >= g.n_obs; --x) {
+                idx[x] += 1;
+                for (int f = 0; f < g.n_fac; ++f) off[f] += g.fst[f][x];
+                if (idx[x] < g.dim[x]) break;
+                for (int f = 0; f < g.n_fac; ++f) off[f] -= g.fst[f][x] * g.dim[x];
+                idx[x] = 0;
+            }
+        }
+        const int obs = mbits ? mask_bit(mbits, e) : 1;
+        const T yv = y[e];
+        T a = T(0), b = T(0);
+        if (obs) {
+            ab_weights(yv, yh, w, a, b);
+            if (has_loss) {
+                lsum += (double)divergence(yv, yh, L);
+                lcnt += 1.0;
+            }
+        }
+        if (wa) wa[e] = a;
+        if (wb) wb[e] = b;
+    }
+    if (has_loss) {
+        lsum = warp_sum(lsum);
+        lcnt = warp_sum(lcnt);
+        if ((threadIdx.x & 31) == 0) {
+            sh_loss[threadIdx.x >> 5] = lsum;
+            sh_cnt[threadIdx.x >> 5] = lcnt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0, c = 0.0;
+            for (int k = 0; k < kThreads / 32; ++k) { s += sh_loss[k]; c += sh_cnt[k]; }
+            loss_part[blockIdx.x] = s;
+            loss_part[gridDim.x + blockIdx.x] = c;
+        }
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int threads = kThreads) {
+    return (unsigned)((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cudaStream_t st) {
+    if (d.n_out_el <= 0) return cudaSuccess;
+    // split the free combinations so that the grid has enough threads
+    const int64_t want = (int64_t)152 * 2048;
+    int64_t n_split = 1;
+    if (d.n_free_el > 64 && d.n_out_el < want && partial_cap >= 2 * d.n_out_el) {
+        n_split = std::min<int64_t>((want + d.n_out_el - 1) / d.n_out_el, d.n_free_el / 32);
+        n_split = std::min<int64_t>(n_split, 65535);
+        n_split = std::min<int64_t>(n_split, partial_cap / d.n_out_el);
+        n_split = std::max<int64_t>(n_split, 1);
+    }
+    if (n_split == 1) {
+        // one pass straight into the destination
+        k_einsum_direct<T><<<blocks_for(d.n_out_el), kThreads, 0, st>>>(d);
+        return cudaGetLastError();
+    }
+    const int64_t chunk = (d.n_free_el + n_split - 1) / n_split;
+    dim3 grid(blocks_for(d.n_out_el), (unsigned)n_split);
+    k_einsum_part<T><<<grid, kThreads, 0, st>>>(d, chunk, partial);
+    k_einsum_final<T><<<blocks_for(d.n_out_el), kThreads, 0, st>>>(d, (int)n_split, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_mask(const uint8_t* mask, int64_t n, uint32_t* bits, cudaStream_t st) {
+    const int64_t nw = (n + 31) >> 5;
+    k_pack_mask<<<blocks_for(nw), kThreads, 0, st>>>(mask, n, bits);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_check_data(const T* y, int64_t n, int* flag, cudaStream_t st) {
+    unsigned nb = (unsigned)std::min<int64_t>(blocks_for(n), 152 * 8);
+    k_check_data<T><<<nb, kThreads, 0, st>>>(y, n, flag);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce_splits(const T* part, int n_split, int64_t n, T* out, cudaStream_t st) {
+    k_reduce_splits<T><<<blocks_for(n), kThreads, 0, st>>>(part, n_split, n, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
+                          cudaStream_t st) {
+    k_update<T><<<blocks_for(n), kThreads, 0, st>>>(theta, num, den, n, u);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fill(T* p, int64_t n, T v, cudaStream_t st) {
+    k_fill<T><<<blocks_for(n), kThreads, 0, st>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_f64(const double* part, int n, double* out, cudaStream_t st) {
+    k_sum_f64<<<1, 1024, 0, st>>>(part, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st) {
+    k_convert_bf16<<<blocks_for(n), kThreads, 0, st>>>(src, n, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint32_t* mbits,
+                                   const WeightSpec& w, T* wa, T* wb, const LossSpec* loss,
+                                   double* loss_part, int n_part, cudaStream_t st) {
+    const unsigned nb = loss ? (unsigned)n_part : (unsigned)std::min<int64_t>(blocks_for(g.n), 152 * 16);
+    LossSpec L{};
+    if (loss) L = *loss;
+    k_generic_weights<T><<<nb, kThreads, 0, st>>>(g, y, mbits, w, wa, wb, loss ? 1 : 0, L, loss_part);
+    return cudaGetLastError();
+}
+
+#define NEF_INST(T)                                                                          \
+    template cudaError_t launch_einsum<T>(const EinDesc&, T*, int64_t, cudaStream_t);        \
+    template cudaError_t launch_check_data<T>(const T*, int64_t, int*, cudaStream_t);        \
+    template cudaError_t launch_reduce_splits<T>(const T*, int, int64_t, T*, cudaStream_t);  \
+    template cudaError_t launch_update<T>(T*, const T*, const T*, int64_t, const UpdateSpec&, \
+                                          cudaStream_t);                                     \
+    template cudaError_t launch_fill<T>(T*, int64_t, T, cudaStream_t);                       \
+    template cudaError_t launch_generic_weights<T>(const GenericRecon&, const T*,             \
+                                                   const uint32_t*, const WeightSpec&, T*, T*, \
+                                                   const LossSpec*, double*, int, cudaStream_t);
+
+NEF_INST(float)
+NEF_INST(double)
+
+}  // namespace nef

@@ -1,0 +1,46 @@
+// k_view_tc_inst.cuh -- instantiation helper: one translation unit per bond width.
+#pragma once
+#include "k_view_tc.cuh"
+
+namespace nef {
+namespace tc {
+
+template <int BP, bool DEN, int WK>
+cudaError_t launch_one(const CUtensorMap& map, const Params& p, int grid, cudaStream_t st) {
+    auto kern = k_view_tc<BP, DEN, WK>;
+    const int sm = Layout<BP, DEN>::kAlloc;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kThreads, sm, st>>>(map, p);
+    return cudaGetLastError();
+}
+
+template <int BP>
+cudaError_t launch_bp(const CUtensorMap& map, const Params& p, int den, int wk, int grid, cudaStream_t st) {
+    if (den) {
+        switch (wk) {
+            case WK_KL: return launch_one<BP, true, WK_KL>(map, p, grid, st);
+            case WK_B05: return launch_one<BP, true, WK_B05>(map, p, grid, st);
+            case WK_HEL: return launch_one<BP, true, WK_HEL>(map, p, grid, st);
+            default: return launch_one<BP, true, WK_GEN>(map, p, grid, st);
+        }
+    }
+    switch (wk) {
+        case WK_KL: return launch_one<BP, false, WK_KL>(map, p, grid, st);
+        case WK_HEL: return launch_one<BP, false, WK_HEL>(map, p, grid, st);
+        default: return launch_one<BP, false, WK_GEN>(map, p, grid, st);
+    }
+}
+
+}  // namespace tc
+}  // namespace nef
+
+#define NEF_TC_INSTANCE(BP)                                                                  \
+    namespace nef {                                                                          \
+    namespace tc {                                                                           \
+    cudaError_t launch_bp##BP(const CUtensorMap& map, const Params& p, int den, int wk,      \
+                              int grid, cudaStream_t st) {                                   \
+        return launch_bp<BP>(map, p, den, wk, grid, st);                                     \
+    }                                                                                        \
+    }                                                                                        \
+    }

@@ -1,0 +1,111 @@
+// nef_device.cuh -- device-side helpers: the App. B weights, divergence and
+// update in float and double, with specialised powers.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "nef_internal.h"
+
+namespace nef {
+
+__device__ __forceinline__ float pw_code(float x, int code, double e) {
+    switch (code) {
+        case POW_ONE: return 1.0f;
+        case POW_ID: return x;
+        case POW_RCP: return 1.0f / x;
+        case POW_RSQRT: return rsqrtf(x);
+        case POW_SQRT: return sqrtf(x);
+        case POW_SQ: return x * x;
+        case POW_RSQRT3: { float r = rsqrtf(x); return r * r * r; }
+        case POW_RCP2: { float r = 1.0f / x; return r * r; }
+        default: return powf(x, (float)e);
+    }
+}
+
+__device__ __forceinline__ double pw_code(double x, int code, double e) {
+    switch (code) {
+        case POW_ONE: return 1.0;
+        case POW_ID: return x;
+        case POW_RCP: return 1.0 / x;
+        case POW_RSQRT: return 1.0 / sqrt(x);
+        case POW_SQRT: return sqrt(x);
+        case POW_SQ: return x * x;
+        case POW_RSQRT3: { double r = 1.0 / sqrt(x); return r * r * r; }
+        case POW_RCP2: { double r = 1.0 / x; return r * r; }
+        default: return pow(x, e);
+    }
+}
+
+// x^p with 0^p = 0 for p > 0, 0^0 = 1 (the convention of App. B at x = 0).
+template <typename T>
+__device__ __forceinline__ T powz(T x, double p) {
+    if (x == T(0)) return p > 0.0 ? T(0) : (p == 0.0 ? T(1) : T(INFINITY));
+    return pw_code(x, POW_GENERAL, p);
+}
+
+// Masked weights of App. B (mask handled by the caller).
+template <typename T>
+__device__ __forceinline__ void ab_weights(T y, T yh, const WeightSpec& w, T& wa, T& wb) {
+    if (w.log_case) {
+        wa = log(y / yh);
+        wb = T(1);
+        return;
+    }
+    T ya;
+    if (y == T(0)) ya = (w.e_y > 0.0) ? T(0) : (w.e_y == 0.0 ? T(1) : T(INFINITY));
+    else ya = pw_code(y, w.y_code, w.e_y);
+    wa = ya * pw_code(yh, w.a_code, w.e_a);
+    wb = pw_code(yh, w.b_code, w.e_b);
+}
+
+// D_{alpha,beta}(x, y): the five cases of App. B.
+template <typename T>
+__device__ __forceinline__ T divergence(T x, T y, const LossSpec& L) {
+    const double al = L.alpha, be = L.beta;
+    switch (L.kase) {
+        case 1: {  // beta = 0
+            T xa = powz(x, al);
+            T t = (x == T(0)) ? T(0) : T(al) * xa * log(x / y);
+            return T(1.0 / (al * al)) * (powz(y, al) - xa + t);
+        }
+        case 2:  // alpha = -beta
+            return T(1.0 / (al * al)) * (powz(x, al) / powz(y, al) - T(1) + T(al) * log(y / x));
+        case 3:  // alpha = 0
+            return T(1.0 / (be * be)) *
+                   (T(be) * powz(y, be) * log(y / x) - powz(y, be) + powz(x, be));
+        case 4: {  // alpha = beta = 0
+            T d = log(x) - log(y);
+            return T(0.5) * d * d;
+        }
+        default: {
+            const double ab = al + be;
+            return T(1.0 / (al * be)) *
+                   (T(al / ab) * powz(x, ab) + T(be / ab) * powz(y, ab) - powz(x, al) * powz(y, be));
+        }
+    }
+}
+
+// Eq. 3.4 for one element; den == 0 keeps theta.
+template <typename T>
+__device__ __forceinline__ T mu_update(T theta, T num, T den, const UpdateSpec& u) {
+    if (den == T(0)) return theta;
+    T z = num / den;
+    T g = u.log_case ? exp(z) : pw_code(z, u.eta_code, u.eta);
+    T v = theta * g;
+    return v > T(u.eps) ? v : T(u.eps);
+}
+
+// Bit e of a packed mask (bit e%32 of word e/32).
+__device__ __forceinline__ int mask_bit(const uint32_t* bits, int64_t e) {
+    return (bits[e >> 5] >> (e & 31)) & 1u;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace nef

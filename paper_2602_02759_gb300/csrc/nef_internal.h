@@ -1,0 +1,156 @@
+// nef_internal.h -- descriptors shared by the host planner and the CUDA kernels.
+//
+// A factor update (one inner step of Algorithm 1) runs as a "view pass":
+// Y is viewed as a matrix Y[row, col] where the rows are a contiguous run of
+// observed letters containing the updated factor's observed letters and the
+// columns are the remaining observed letters:
+//     element (row, col = co*c_in + ci) lives at  co*rows*c_in + row*c_in + ci.
+// The reconstruction factorises through a set of latent "bond" letters,
+//     yhat[row, col] = sum_b P[row, b] * Q[col, b]                  (Eq. 2.1)
+// and the numerator of Eq. 3.6-3.8 is  S_a[row, b] = sum_col W_a[row,col] Q[col,b]
+// followed by a small "epilogue" einsum of S_a with the other row-side factors.
+// P and Q are Hadamard products of rows gathered from canonical [n x ld]
+// operand matrices ("sources").
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nef {
+
+constexpr int kMaxLet = 26;
+constexpr int kMaxFac = 16;
+constexpr int kMaxSrc = 4;    // gathered sources per operand side
+constexpr int kMaxTerm = 3;   // index terms per source
+constexpr int kMaxEinOps = 8; // operands of a small einsum
+constexpr int kMaxEinLet = 12;
+
+// Specialised evaluation of x^e for the weights of App. B.
+enum PowCode : int {
+    POW_ONE = 0,      // x^0
+    POW_ID = 1,       // x^1
+    POW_RCP = 2,      // x^-1
+    POW_RSQRT = 3,    // x^-1/2
+    POW_SQRT = 4,     // x^1/2
+    POW_SQ = 5,       // x^2
+    POW_RSQRT3 = 6,   // x^-3/2
+    POW_GENERAL = 7,  // exp2(e * log2 x)
+    POW_RCP2 = 8      // x^-2
+};
+
+// Weights of App. B: wa = M * y^alpha * yhat^(beta-1), wb = M * yhat^(alpha+beta-1)
+// (alpha != 0), or wa = M * log(y/yhat), wb = M (alpha = 0, beta = 1).
+struct WeightSpec {
+    int log_case;       // 1 for (alpha, beta) = (0, 1)
+    int y_code;         // PowCode of y^alpha
+    int a_code;         // PowCode of yhat^(beta-1)
+    int b_code;         // PowCode of yhat^(alpha+beta-1)
+    double alpha, beta;
+    double e_y, e_a, e_b;  // exponents (used by POW_GENERAL)
+};
+
+// Loss cases of App. B.
+struct LossSpec {
+    int kase;           // 0 generic, 1 beta=0, 2 alpha=-beta, 3 alpha=0, 4 alpha=beta=0
+    double alpha, beta;
+};
+
+// Update of Eq. 3.4: theta <- max(eps, theta * ginv(num/den)).
+struct UpdateSpec {
+    int log_case;       // g = log -> exp
+    int eta_code;       // PowCode of z^eta
+    double eta;
+    double eps;
+};
+
+struct SrcDesc {
+    const void* ptr;              // canonical [n x ld] matrix (operand element type)
+    int64_t ld;                   // elements per row (= bond_pad)
+    int nterm;
+    int64_t div[kMaxTerm], mod[kMaxTerm], mul[kMaxTerm];  // row = sum ((i/div)%mod)*mul
+};
+
+struct SideDesc {
+    int nsrc;
+    SrcDesc src[kMaxSrc];
+};
+
+struct ViewDesc {
+    int64_t c_out, rows, c_in;    // Y viewed as [c_out][rows][c_in]
+    int bond, bond_pad;           // real and padded bond size
+    SideDesc P, Q;
+};
+
+// Small generic einsum: out[o] = sum over free combos of prod_k op_k[...].
+// Letters are compact ids 0..n_let-1: out letters first, then free letters.
+struct EinDesc {
+    int n_ops;
+    const void* op[kMaxEinOps];
+    int64_t ost[kMaxEinOps][kMaxEinLet];  // per-letter strides of each operand (0 = absent)
+    int n_out, n_free;
+    int64_t dim[kMaxEinLet];
+    int64_t out_st[kMaxEinLet];           // destination strides for the out letters
+    int64_t n_out_el, n_free_el;
+    void* out;
+    int accumulate;                        // 1: out += result, 0: out = result
+};
+
+// ------------------------------------------------------------- launchers
+// All launchers return cudaGetLastError() after enqueueing on `st`.
+
+template <typename T>
+cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cudaStream_t st);
+
+cudaError_t launch_pack_mask(const uint8_t* mask, int64_t n, uint32_t* bits, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_check_data(const T* y, int64_t n, int* flag, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_view_simt(const T* y, const uint32_t* mbits, const ViewDesc& v,
+                             const WeightSpec& w, int need_den, int n_split,
+                             T* s_num, T* s_den, const LossSpec* loss, double* loss_part,
+                             cudaStream_t st, int* n_ctas_out);
+
+template <typename T>
+cudaError_t launch_reduce_splits(const T* part, int n_split, int64_t n, T* out, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_update(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
+                          cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_fill(T* p, int64_t n, T v, cudaStream_t st);
+
+cudaError_t launch_sum_f64(const double* part, int n, double* out, cudaStream_t st);
+
+// Generic (unfused) path: materialise yhat, then W_a, W_b and optionally the loss.
+struct GenericRecon {
+    int n_obs, n_let, n_fac;
+    int64_t dim[kMaxLet];
+    int64_t y_st[kMaxLet];                   // strides of Y per observed letter
+    int64_t fst[kMaxFac][kMaxLet];           // strides of each factor per letter
+    const void* fac[kMaxFac];
+    int64_t n, n_lat_el;
+};
+
+template <typename T>
+cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint32_t* mbits,
+                                   const WeightSpec& w, T* wa, T* wb, const LossSpec* loss,
+                                   double* loss_part, int n_part, cudaStream_t st);
+
+// tcgen05 path (BF16 operands, FP32 accumulators in TMEM).
+struct TcLaunchInfo {
+    int n_ctas;
+    int smem_bytes;
+};
+
+cudaError_t launch_convert_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st);
+
+cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v,
+                           const WeightSpec& w, int need_den, int n_split, float* s_num,
+                           float* s_den, int* err_flag, cudaStream_t st, TcLaunchInfo* info);
+
+bool tc_view_supported(const ViewDesc& v, int need_den);
+
+}  // namespace nef

@@ -1,0 +1,1236 @@
+// plan.cpp -- einsum contraction planner, workspace, sweep driver and C ABI.
+//
+// Parsing follows the model-string grammar of Eq. 2.2; swap(model_str, l) of
+// Eq. 3.8 is represented by the per-factor pass plan below.  For every factor
+// l the planner looks for a "view" of Y (rows = a contiguous run of observed
+// letters holding l's observed letters, columns = the other observed letters)
+// through which the reconstruction factorises over a small set of latent bond
+// letters (Eq. 2.1):  yhat[row, col] = sum_b P[row, b] Q[col, b].
+// The numerator/denominator of Eq. 3.6-3.8 then become
+//     S[row, b] = sum_col W[row, col] Q[col, b]            (fused pass kernel)
+//     num_l = einsum(S, the other row-side factors -> l)   (small epilogue)
+// If no view exists (a factor straddles rows and columns, e.g. the many-body
+// model), the pass falls back to Algorithm 1 as written: materialise yhat,
+// a(Y,Yhat), b(Y,Yhat) and contract with einstr_l.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nef.h"
+#include "nef_internal.h"
+
+using namespace nef;
+
+namespace {
+
+thread_local std::string g_err;
+
+nef_status fail(nef_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define NEF_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(NEF_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                \
+    } while (0)
+
+// ------------------------------------------------------------------ model
+struct Model {
+    int M = 0, K = 0, L = 0;                 // observed, latent letters; factors
+    std::vector<char> letter;                 // id -> char
+    std::vector<int64_t> dim;                 // id -> size
+    std::vector<std::vector<int>> term;       // factor -> letter ids in term order
+    int64_t N = 1;                            // entries of Y
+    bool is_obs(int x) const { return x < M; }
+    int64_t fac_size(int f) const {
+        int64_t n = 1;
+        for (int x : term[f]) n *= dim[x];
+        return n;
+    }
+    bool fac_has(int f, int x) const {
+        return std::find(term[f].begin(), term[f].end(), x) != term[f].end();
+    }
+    int64_t fac_stride(int f, int x) const {  // stride of letter x in factor f (0 if absent)
+        int64_t s = 1;
+        for (int p = (int)term[f].size() - 1; p >= 0; --p) {
+            if (term[f][p] == x) return s;
+            s *= dim[term[f][p]];
+        }
+        return 0;
+    }
+    int64_t y_stride(int x) const {
+        if (x >= M) return 0;
+        int64_t s = 1;
+        for (int m = M - 1; m > x; --m) s *= dim[m];
+        return s;
+    }
+};
+
+nef_status parse_model(const char* str, const int64_t* shapes, int n_obs, const int64_t* ranks,
+                       int n_lat, Model& md) {
+    if (!str) return fail(NEF_EINVAL, "model string is NULL");
+    std::string s;
+    for (const char* p = str; *p; ++p)
+        if (*p != ' ') s.push_back(*p);
+    size_t arrow = s.find("->");
+    if (arrow == std::string::npos || s.find("->", arrow + 2) != std::string::npos)
+        return fail(NEF_EPARSE, "model string needs exactly one '->'");
+    std::string lhs = s.substr(0, arrow), rhs = s.substr(arrow + 2);
+    std::vector<std::string> terms;
+    size_t start = 0;
+    while (true) {
+        size_t c = lhs.find(',', start);
+        terms.push_back(lhs.substr(start, c == std::string::npos ? std::string::npos : c - start));
+        if (c == std::string::npos) break;
+        start = c + 1;
+    }
+    auto ok_letter = [](char ch) { return ch >= 'a' && ch <= 'z'; };
+    int id_of[128];
+    for (int& v : id_of) v = -1;
+    for (char ch : rhs) {
+        if (!ok_letter(ch)) return fail(NEF_EPARSE, "bad output letter '%c'", ch);
+        if (id_of[(int)ch] >= 0) return fail(NEF_EPARSE, "repeated output letter '%c'", ch);
+        id_of[(int)ch] = (int)md.letter.size();
+        md.letter.push_back(ch);
+    }
+    md.M = (int)md.letter.size();
+    if (md.M == 0) return fail(NEF_EPARSE, "no observed letters");
+    if ((int)terms.size() > kMaxFac) return fail(NEF_EPARSE, "too many factors (max %d)", kMaxFac);
+    for (auto& t : terms) {
+        std::vector<int> ids;
+        for (char ch : t) {
+            if (!ok_letter(ch)) return fail(NEF_EPARSE, "bad letter '%c' in term '%s'", ch, t.c_str());
+            if (id_of[(int)ch] < 0) {
+                id_of[(int)ch] = (int)md.letter.size();
+                md.letter.push_back(ch);
+            }
+            int id = id_of[(int)ch];
+            if (std::find(ids.begin(), ids.end(), id) != ids.end())
+                return fail(NEF_EPARSE, "repeated letter '%c' in term '%s'", ch, t.c_str());
+            ids.push_back(id);
+        }
+        md.term.push_back(ids);
+    }
+    md.L = (int)md.term.size();
+    md.K = (int)md.letter.size() - md.M;
+    if ((int)md.letter.size() > kMaxLet) return fail(NEF_EPARSE, "too many letters");
+    for (int m = 0; m < md.M; ++m) {
+        bool seen = false;
+        for (auto& t : md.term)
+            if (std::find(t.begin(), t.end(), m) != t.end()) seen = true;
+        if (!seen) return fail(NEF_EPARSE, "output letter '%c' appears in no term", md.letter[m]);
+    }
+    if (n_obs != md.M) return fail(NEF_EINVAL, "model has %d observed letters, got %d shapes", md.M, n_obs);
+    if (n_lat != md.K) return fail(NEF_EINVAL, "model has %d latent letters, got %d ranks", md.K, n_lat);
+    if (md.M > 0 && !shapes) return fail(NEF_EINVAL, "shapes is NULL");
+    if (md.K > 0 && !ranks) return fail(NEF_EINVAL, "ranks is NULL");
+    md.dim.resize(md.letter.size());
+    for (int m = 0; m < md.M; ++m) md.dim[m] = shapes[m];
+    for (int k = 0; k < md.K; ++k) md.dim[md.M + k] = ranks[k];
+    for (size_t x = 0; x < md.dim.size(); ++x)
+        if (md.dim[x] < 1) return fail(NEF_EINVAL, "dimension of '%c' must be >= 1", md.letter[x]);
+    md.N = 1;
+    for (int m = 0; m < md.M; ++m) md.N *= md.dim[m];
+    return NEF_OK;
+}
+
+// -------------------------------------------------------------- the plan
+// An einsum recipe over global letter ids; pointers are bound at run time.
+struct EinOpRef {
+    int kind;        // 0 factor f, 1 workspace buffer
+    int index;       // factor index or buffer id
+    std::vector<int64_t> st;  // per global letter stride (size n_letters)
+};
+
+struct EinRecipe {
+    std::vector<int> out_let, free_let;   // global ids
+    std::vector<int64_t> out_st;          // destination strides (aligned with out_let)
+    std::vector<EinOpRef> ops;
+    int out_kind = 1, out_index = 0;      // destination: 0 factor, 1 buffer
+    int64_t n_out_el = 1, n_free_el = 1;
+};
+
+enum BufId { B_NUM = 0, B_DEN, B_SNUM, B_SDEN, B_SPART_N, B_SPART_D, B_DENVEC, B_COLSUM0,
+             B_WA = 20, B_WB, B_SRC0 = 32 };
+
+struct SourcePlan {
+    EinRecipe build;       // writes the canonical [n x ld] matrix into buffer src_buf
+    int buf;               // buffer id (>= B_SRC0)
+    int64_t n_rows;        // rows of the canonical matrix
+    SrcDesc desc;          // index terms (ptr bound at run time)
+};
+
+struct PassPlan {
+    int l = 0;
+    bool generic = false;
+    // view
+    int run_s = 0, run_e = 0;
+    std::vector<int> bond;            // global latent ids
+    ViewDesc view{};
+    SourcePlan P;
+    std::vector<SourcePlan> Q;
+    bool q_gathered = false;
+    EinRecipe epi_num, epi_den;       // S -> num_l, den_l
+    bool den_closed = false;          // b == 1 and no mask: den via column sums of Q
+    std::vector<EinRecipe> colsum;    // per Q source: [ld] column sums into B_COLSUM0+k
+    EinRecipe den_prod;               // product of the column sums -> B_DENVEC
+    EinRecipe epi_den_closed;         // den_l from the broadcast den vector
+    int n_split = 1;
+    int64_t cost = 0;
+    std::string desc;
+    // generic
+    EinRecipe gen_num, gen_den;
+};
+
+struct Buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct nef_plan_s {
+    Model md;
+    nef_options opt{};
+    int prec = NEF_FP32;
+    size_t esz = 4;
+    std::vector<PassPlan> pass;
+    std::vector<Buffer> buf;          // indexed by BufId
+    // fixed workspace
+    void* ein_partial = nullptr;
+    int64_t ein_partial_cap = 0;      // elements
+    uint32_t* mask_bits = nullptr;
+    double* loss_part = nullptr;
+    int loss_part_cap = 0;
+    double* loss_out = nullptr;
+    int* flag = nullptr;
+    int* tc_err = nullptr;
+    std::vector<uint16_t*> src_bf16;  // per buffer id >= B_SRC0 (BF16 plans)
+    std::string info;
+    // profiling: event pairs around fused-pass launches, per kernel family
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    size_t ev_next = 0;
+};
+
+namespace {
+
+// ------------------------------------------------------------- planning
+int64_t prod_dims(const Model& md, const std::vector<int>& ids) {
+    int64_t n = 1;
+    for (int x : ids) n *= md.dim[x];
+    return n;
+}
+
+std::string letters_of(const Model& md, const std::vector<int>& ids) {
+    std::string s;
+    for (int x : ids) s.push_back(md.letter[x]);
+    return s;
+}
+
+// Strides of a row-major layout over `ids` with an extra trailing block of `ld`
+// elements for the bond letters (bond letters row-major inside the block).
+void canon_strides(const Model& md, const std::vector<int>& rows, const std::vector<int>& bond,
+                   int64_t ld, std::vector<int64_t>& st_of_letter) {
+    st_of_letter.assign(md.letter.size(), 0);
+    int64_t s = 1;
+    for (int p = (int)bond.size() - 1; p >= 0; --p) {
+        st_of_letter[bond[p]] = s;
+        s *= md.dim[bond[p]];
+    }
+    s = ld;
+    for (int p = (int)rows.size() - 1; p >= 0; --p) {
+        st_of_letter[rows[p]] = s;
+        s *= md.dim[rows[p]];
+    }
+}
+
+EinOpRef factor_op(const Model& md, int f) {
+    EinOpRef o;
+    o.kind = 0;
+    o.index = f;
+    o.st.assign(md.letter.size(), 0);
+    for (int x : md.term[f]) o.st[x] = md.fac_stride(f, x);
+    return o;
+}
+
+void finish_recipe(const Model& md, EinRecipe& r) {
+    r.n_out_el = prod_dims(md, r.out_let);
+    r.n_free_el = prod_dims(md, r.free_let);
+}
+
+// Letters used by a set of factors.
+std::vector<int> letters_used(const Model& md, const std::vector<int>& facs) {
+    std::vector<int> used;
+    for (int f : facs)
+        for (int x : md.term[f])
+            if (std::find(used.begin(), used.end(), x) == used.end()) used.push_back(x);
+    std::sort(used.begin(), used.end());
+    return used;
+}
+
+bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, PassPlan& out, int& next_buf) {
+    const Model& md = p.md;
+    std::vector<int> run, cols;
+    for (int m = 0; m < md.M; ++m) (m >= s && m < e ? run : cols).push_back(m);
+    if (cols.empty() || run.empty()) return false;
+    auto in_run = [&](int x) { return x >= s && x < e; };
+    // classify factors
+    std::vector<int> cls(md.L);  // 0 row, 1 col, 2 latent-only
+    for (int f = 0; f < md.L; ++f) {
+        int nr = 0, nc = 0;
+        for (int x : md.term[f])
+            if (md.is_obs(x)) (in_run(x) ? nr : nc)++;
+        if (nr && nc) return false;  // straddles the split
+        cls[f] = nr ? 0 : (nc ? 1 : 2);
+    }
+    if (cls[l] == 1) return false;
+    std::vector<int> lat_only;
+    for (int f = 0; f < md.L; ++f)
+        if (cls[f] == 2 && f != l) lat_only.push_back(f);
+    if (lat_only.size() > 6) return false;
+    if (assign >= (1 << lat_only.size())) return false;
+    int64_t best_bond = -1;
+    std::vector<int> best_row, best_col, best_bondv;
+    {
+        const int mask = assign;
+        std::vector<int> rowf, colf;
+        for (int f = 0; f < md.L; ++f) {
+            if (cls[f] == 0 || f == l) rowf.push_back(f);
+            else if (cls[f] == 1) colf.push_back(f);
+        }
+        for (size_t q = 0; q < lat_only.size(); ++q)
+            ((mask >> q) & 1 ? colf : rowf).push_back(lat_only[q]);
+        if (colf.empty()) return false;
+        std::vector<int> rl, cl, bond;
+        for (int x : letters_used(md, rowf)) if (!md.is_obs(x)) rl.push_back(x);
+        for (int x : letters_used(md, colf)) if (!md.is_obs(x)) cl.push_back(x);
+        for (int x : rl)
+            if (std::find(cl.begin(), cl.end(), x) != cl.end()) bond.push_back(x);
+        best_bond = prod_dims(md, bond);
+        best_row = rowf;
+        best_col = colf;
+        best_bondv = bond;
+    }
+    const std::vector<int>& rowf = best_row;
+    const std::vector<int>& colf = best_col;
+    const std::vector<int>& bond = best_bondv;
+    const int64_t bsz = best_bond;
+    int64_t bond_pad;
+    if (p.prec == NEF_FP64) bond_pad = bsz <= 32 ? 32 : (bsz <= 64 ? 64 : -1);
+    else if (p.prec == NEF_BF16) bond_pad = bsz <= 16 ? 16 : (bsz <= 32 ? 32 : (bsz <= 64 ? 64 : (bsz <= 128 ? 128 : -1)));
+    else bond_pad = bsz <= 16 ? 16 : (bsz <= 32 ? 32 : (bsz <= 64 ? 64 : -1));
+    if (bond_pad < 0) return false;
+    if (p.prec == NEF_BF16 && bond_pad > 64) return false;  // SIMT fallback must cover it too
+
+    PassPlan pp;
+    pp.l = l;
+    pp.run_s = s;
+    pp.run_e = e;
+    pp.bond = bond;
+    const int64_t rows = prod_dims(md, run);
+    const int64_t ncols = prod_dims(md, cols);
+    int64_t c_out = 1, c_in = 1;
+    for (int m = 0; m < s; ++m) c_out *= md.dim[m];
+    for (int m = e; m < md.M; ++m) c_in *= md.dim[m];
+    pp.view.c_out = c_out;
+    pp.view.rows = rows;
+    pp.view.c_in = c_in;
+    pp.view.bond = (int)bsz;
+    pp.view.bond_pad = (int)bond_pad;
+
+    // ---- P: canonical [rows x bond_pad] over the run letters, summing row-private latents
+    {
+        SourcePlan sp;
+        sp.buf = next_buf++;
+        sp.n_rows = rows;
+        EinRecipe& r = sp.build;
+        std::vector<int64_t> cst;
+        canon_strides(md, run, bond, bond_pad, cst);
+        r.out_let = run;
+        for (int x : bond) r.out_let.push_back(x);
+        for (int x : r.out_let) r.out_st.push_back(cst[x]);
+        for (int x : letters_used(md, rowf))
+            if (std::find(r.out_let.begin(), r.out_let.end(), x) == r.out_let.end())
+                r.free_let.push_back(x);
+        for (int f : rowf) r.ops.push_back(factor_op(md, f));
+        r.out_kind = 1;
+        r.out_index = sp.buf;
+        finish_recipe(md, r);
+        sp.desc = SrcDesc{};
+        sp.desc.ld = bond_pad;
+        sp.desc.nterm = 1;
+        sp.desc.div[0] = 1;
+        sp.desc.mod[0] = rows;
+        sp.desc.mul[0] = 1;
+        pp.P = sp;
+        // a row letter without any row-side factor cannot happen: every observed letter is in a term
+    }
+    // ---- Q: gathered sources when every column factor carries exactly the bond latents
+    bool gather = true;
+    std::vector<int> seen_obs;
+    for (int f : colf) {
+        std::vector<int> fl;
+        for (int x : md.term[f]) if (!md.is_obs(x)) fl.push_back(x);
+        std::vector<int> sb = bond, sf = fl;
+        std::sort(sb.begin(), sb.end());
+        std::sort(sf.begin(), sf.end());
+        if (sb != sf) gather = false;
+        int nobs = 0;
+        for (int x : md.term[f]) if (md.is_obs(x)) ++nobs;
+        if (nobs == 0 || nobs > kMaxTerm) gather = false;
+        for (int x : md.term[f])
+            if (md.is_obs(x)) {
+                if (std::find(seen_obs.begin(), seen_obs.end(), x) != seen_obs.end()) gather = false;
+                seen_obs.push_back(x);
+            }
+    }
+    if ((int)colf.size() > kMaxSrc) gather = false;
+    if (gather && (int)seen_obs.size() != (int)cols.size()) gather = false;
+    // column index digits: col = mixed radix over `cols` (RHS order)
+    auto col_div = [&](int x) {
+        int64_t d = 1;
+        bool after = false;
+        for (int c : cols) {
+            if (after) d *= md.dim[c];
+            if (c == x) after = true;
+        }
+        return d;
+    };
+    int64_t prep_elems = rows * bond_pad;
+    if (gather) {
+        pp.q_gathered = true;
+        for (int f : colf) {
+            SourcePlan sp;
+            sp.buf = next_buf++;
+            std::vector<int> fobs;
+            for (int x : md.term[f]) if (md.is_obs(x)) fobs.push_back(x);
+            sp.n_rows = prod_dims(md, fobs);
+            std::vector<int64_t> cst;
+            canon_strides(md, fobs, bond, bond_pad, cst);
+            EinRecipe& r = sp.build;
+            r.out_let = fobs;
+            for (int x : bond) r.out_let.push_back(x);
+            for (int x : r.out_let) r.out_st.push_back(cst[x]);
+            r.ops.push_back(factor_op(md, f));
+            r.out_kind = 1;
+            r.out_index = sp.buf;
+            finish_recipe(md, r);
+            sp.desc = SrcDesc{};
+            sp.desc.ld = bond_pad;
+            sp.desc.nterm = (int)fobs.size();
+            for (size_t t = 0; t < fobs.size(); ++t) {
+                sp.desc.div[t] = col_div(fobs[t]);
+                sp.desc.mod[t] = md.dim[fobs[t]];
+                sp.desc.mul[t] = cst[fobs[t]] / bond_pad;
+            }
+            prep_elems += sp.n_rows * bond_pad;
+            pp.Q.push_back(sp);
+        }
+    } else {
+        if (ncols * bond_pad > md.N / 4) return false;
+        SourcePlan sp;
+        sp.buf = next_buf++;
+        sp.n_rows = ncols;
+        std::vector<int64_t> cst;
+        canon_strides(md, cols, bond, bond_pad, cst);
+        EinRecipe& r = sp.build;
+        r.out_let = cols;
+        for (int x : bond) r.out_let.push_back(x);
+        for (int x : r.out_let) r.out_st.push_back(cst[x]);
+        for (int x : letters_used(md, colf))
+            if (std::find(r.out_let.begin(), r.out_let.end(), x) == r.out_let.end())
+                r.free_let.push_back(x);
+        for (int f : colf) r.ops.push_back(factor_op(md, f));
+        r.out_kind = 1;
+        r.out_index = sp.buf;
+        finish_recipe(md, r);
+        sp.desc = SrcDesc{};
+        sp.desc.ld = bond_pad;
+        sp.desc.nterm = 1;
+        sp.desc.div[0] = 1;
+        sp.desc.mod[0] = ncols;
+        sp.desc.mul[0] = 1;
+        prep_elems += ncols * bond_pad;
+        pp.Q.push_back(sp);
+    }
+    // ---- epilogue: num_l = einsum(S[run, bond], other row-side factors -> l)
+    auto make_epi = [&](int s_buf, bool broadcast_rows) {
+        EinRecipe r;
+        r.out_let = md.term[l];
+        for (int x : md.term[l]) r.out_st.push_back(md.fac_stride(l, x));
+        EinOpRef sop;
+        sop.kind = 1;
+        sop.index = s_buf;
+        sop.st.assign(md.letter.size(), 0);
+        std::vector<int64_t> cst;
+        canon_strides(md, run, bond, bond_pad, cst);
+        for (int x : run) sop.st[x] = broadcast_rows ? 0 : cst[x];
+        for (int x : bond) sop.st[x] = cst[x];
+        r.ops.push_back(sop);
+        std::vector<int> used = run;
+        for (int x : bond) used.push_back(x);
+        for (int f : rowf) {
+            if (f == l) continue;
+            r.ops.push_back(factor_op(md, f));
+            for (int x : md.term[f]) used.push_back(x);
+        }
+        std::sort(used.begin(), used.end());
+        used.erase(std::unique(used.begin(), used.end()), used.end());
+        for (int x : used)
+            if (!md.fac_has(l, x)) r.free_let.push_back(x);
+        r.out_kind = 1;
+        r.out_index = -1;  // bound later (B_NUM / B_DEN)
+        finish_recipe(md, r);
+        return r;
+    };
+    pp.epi_num = make_epi(B_SNUM, false);
+    pp.epi_num.out_index = B_NUM;
+    pp.epi_den = make_epi(B_SDEN, false);
+    pp.epi_den.out_index = B_DEN;
+    // closed-form denominator (used when b == 1 and there is no mask)
+    pp.den_closed = pp.q_gathered;
+    if (pp.den_closed) {
+        for (size_t k = 0; k < pp.Q.size(); ++k) {
+            const SourcePlan& sp = pp.Q[k];
+            EinRecipe r;
+            // sum over the canonical rows of source k: treat it as a [n_rows x ld] matrix with
+            // pseudo letters: we reuse the source's own out letters
+            r.out_let = bond;
+            std::vector<int64_t> bst;
+            canon_strides(md, {}, bond, bond_pad, bst);
+            for (int x : bond) r.out_st.push_back(bst[x]);
+            EinOpRef o;
+            o.kind = 1;
+            o.index = sp.buf;
+            o.st.assign(md.letter.size(), 0);
+            for (size_t q = 0; q < sp.build.out_let.size(); ++q) o.st[sp.build.out_let[q]] = sp.build.out_st[q];
+            r.ops.push_back(o);
+            for (int x : sp.build.out_let)
+                if (std::find(bond.begin(), bond.end(), x) == bond.end()) r.free_let.push_back(x);
+            r.out_kind = 1;
+            r.out_index = B_COLSUM0 + (int)k;
+            finish_recipe(md, r);
+            pp.colsum.push_back(r);
+        }
+        EinRecipe pr;
+        pr.out_let = bond;
+        std::vector<int64_t> bst;
+        canon_strides(md, {}, bond, bond_pad, bst);
+        for (int x : bond) pr.out_st.push_back(bst[x]);
+        for (size_t k = 0; k < pp.Q.size(); ++k) {
+            EinOpRef o;
+            o.kind = 1;
+            o.index = B_COLSUM0 + (int)k;
+            o.st.assign(md.letter.size(), 0);
+            for (int x : bond) o.st[x] = bst[x];
+            pr.ops.push_back(o);
+        }
+        pr.out_kind = 1;
+        pr.out_index = B_DENVEC;
+        finish_recipe(md, pr);
+        pp.den_prod = pr;
+        pp.epi_den_closed = make_epi(B_DENVEC, true);
+        pp.epi_den_closed.out_index = B_DEN;
+    }
+    // ---- split of the columns across CTAs
+    const int tm = (p.prec == NEF_FP64) ? 32 : (p.prec == NEF_BF16 ? 128 : 64);
+    const int tn = (p.prec == NEF_FP64) ? 32 : (p.prec == NEF_BF16 ? 128 : 64);
+    const int64_t n_rb = (rows + tm - 1) / tm;
+    const int64_t tiles = (ncols + tn - 1) / tn;
+    const int64_t target = (p.prec == NEF_BF16) ? 148 : 152 * 4;
+    int64_t ns = std::max<int64_t>(1, target / std::max<int64_t>(1, n_rb));
+    ns = std::min<int64_t>(ns, tiles);
+    ns = std::max<int64_t>(ns, 1);
+    pp.n_split = (int)ns;
+    pp.view.P.nsrc = 1;
+    pp.view.Q.nsrc = (int)pp.Q.size();
+    // ---- cost: bytes moved per pass
+    int64_t epi_cost = pp.epi_num.n_out_el * pp.epi_num.n_free_el;
+    pp.cost = md.N * 4 + prep_elems * 8 + ns * rows * bond_pad * 8 + epi_cost / 4 +
+              (gather ? 0 : ncols * bond_pad * 4 * 4);
+    char d[512];
+    snprintf(d, sizeof(d),
+             "factor %d '%s': view rows='%s' (%lld) cols=%lld [c_out=%lld c_in=%lld] bond='%s' "
+             "(%lld->%lld) Q=%s(%d) splits=%d epilogue=%lldx%lld",
+             l, letters_of(md, md.term[l]).c_str(), letters_of(md, run).c_str(), (long long)rows,
+             (long long)ncols, (long long)c_out, (long long)c_in, letters_of(md, bond).c_str(),
+             (long long)bsz, (long long)bond_pad, gather ? "gather" : "dense", (int)pp.Q.size(),
+             pp.n_split, (long long)pp.epi_num.n_out_el, (long long)pp.epi_num.n_free_el);
+    pp.desc = d;
+    out = pp;
+    return true;
+}
+
+void plan_generic(const nef_plan_s& p, int l, PassPlan& pp) {
+    const Model& md = p.md;
+    pp.l = l;
+    pp.generic = true;
+    auto mk = [&](int wbuf, int obuf) {
+        EinRecipe r;
+        r.out_let = md.term[l];
+        for (int x : md.term[l]) r.out_st.push_back(md.fac_stride(l, x));
+        EinOpRef w;
+        w.kind = 1;
+        w.index = wbuf;
+        w.st.assign(md.letter.size(), 0);
+        for (int m = 0; m < md.M; ++m) w.st[m] = md.y_stride(m);
+        r.ops.push_back(w);
+        for (int f = 0; f < md.L; ++f)
+            if (f != l) r.ops.push_back(factor_op(md, f));
+        for (int x = 0; x < (int)md.letter.size(); ++x)
+            if (!md.fac_has(l, x)) r.free_let.push_back(x);
+        r.out_kind = 1;
+        r.out_index = obuf;
+        finish_recipe(md, r);
+        return r;
+    };
+    pp.gen_num = mk(B_WA, B_NUM);
+    pp.gen_den = mk(B_WB, B_DEN);
+    char d[256];
+    snprintf(d, sizeof(d), "factor %d '%s': generic (yhat, a, b materialised; einstr contraction)",
+             l, letters_of(md, md.term[l]).c_str());
+    pp.desc = d;
+}
+
+// ------------------------------------------------------------- run time
+WeightSpec weight_spec(double al, double be) {
+    WeightSpec w{};
+    w.alpha = al;
+    w.beta = be;
+    auto code = [](double e) {
+        if (e == 0.0) return (int)POW_ONE;
+        if (e == 1.0) return (int)POW_ID;
+        if (e == -1.0) return (int)POW_RCP;
+        if (e == -0.5) return (int)POW_RSQRT;
+        if (e == 0.5) return (int)POW_SQRT;
+        if (e == 2.0) return (int)POW_SQ;
+        if (e == -1.5) return (int)POW_RSQRT3;
+        if (e == -2.0) return (int)POW_RCP2;
+        return (int)POW_GENERAL;
+    };
+    if (al == 0.0) {
+        w.log_case = 1;
+        w.y_code = POW_ONE;
+        w.a_code = POW_ONE;
+        w.b_code = POW_ONE;
+        return w;
+    }
+    w.e_y = al;
+    w.e_a = be - 1.0;
+    w.e_b = al + be - 1.0;
+    w.y_code = code(w.e_y);
+    w.a_code = code(w.e_a);
+    w.b_code = code(w.e_b);
+    return w;
+}
+
+LossSpec loss_spec(double al, double be) {
+    LossSpec L{};
+    L.alpha = al;
+    L.beta = be;
+    if (al != 0.0 && be != 0.0 && al + be != 0.0) L.kase = 0;
+    else if (be == 0.0 && al != 0.0) L.kase = 1;
+    else if (al == -be && al != 0.0) L.kase = 2;
+    else if (al == 0.0 && be != 0.0) L.kase = 3;
+    else L.kase = 4;
+    return L;
+}
+
+UpdateSpec update_spec(double al, double be, double eps) {
+    UpdateSpec u{};
+    u.eps = eps;
+    if (al == 0.0 && be == 1.0) {
+        u.log_case = 1;
+        return u;
+    }
+    double q = 1.0 / al - be / al;
+    double pexp = q > 1.0 ? 1.0 - be : (q < 0.0 ? al + be - 1.0 : al);
+    u.eta = 1.0 / pexp;
+    if (u.eta == 1.0) u.eta_code = POW_ID;
+    else if (u.eta == 2.0) u.eta_code = POW_SQ;
+    else if (u.eta == 0.5) u.eta_code = POW_SQRT;
+    else if (u.eta == -1.0) u.eta_code = POW_RCP;
+    else u.eta_code = POW_GENERAL;
+    return u;
+}
+
+void* buf_ptr(nef_plan_t p, int id) { return p->buf[id].ptr; }
+
+EinDesc bind(nef_plan_t p, const EinRecipe& r, void* const* factors) {
+    EinDesc d{};
+    const int nl = (int)(r.out_let.size() + r.free_let.size());
+    d.n_ops = (int)r.ops.size();
+    d.n_out = (int)r.out_let.size();
+    d.n_free = (int)r.free_let.size();
+    std::vector<int> lets = r.out_let;
+    lets.insert(lets.end(), r.free_let.begin(), r.free_let.end());
+    for (int q = 0; q < nl; ++q) d.dim[q] = p->md.dim[lets[q]];
+    for (int k = 0; k < d.n_ops; ++k) {
+        const EinOpRef& o = r.ops[k];
+        d.op[k] = o.kind == 0 ? factors[o.index] : buf_ptr(p, o.index);
+        for (int q = 0; q < nl; ++q) d.ost[k][q] = o.st[lets[q]];
+    }
+    for (int q = 0; q < d.n_out; ++q) d.out_st[q] = r.out_st[q];
+    d.n_out_el = r.n_out_el;
+    d.n_free_el = r.n_free_el;
+    d.out = r.out_kind == 0 ? factors[r.out_index] : buf_ptr(p, r.out_index);
+    d.accumulate = 0;
+    return d;
+}
+
+bool recipe_fits(const EinRecipe& r) {
+    return r.ops.size() <= (size_t)kMaxEinOps && r.out_let.size() + r.free_let.size() <= (size_t)kMaxEinLet;
+}
+
+template <typename T>
+nef_status run_ein(nef_plan_t p, const EinRecipe& r, void* const* factors, cudaStream_t st) {
+    EinDesc d = bind(p, r, factors);
+    NEF_CUDA(launch_einsum<T>(d, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
+    return NEF_OK;
+}
+
+#define NEF_TRY(x)                     \
+    do {                               \
+        nef_status s_ = (x);           \
+        if (s_ != NEF_OK) return s_;   \
+    } while (0)
+
+template <typename T>
+nef_status prepare_sources(nef_plan_t p, PassPlan& pp, void* const* factors, cudaStream_t st) {
+    NEF_TRY(run_ein<T>(p, pp.P.build, factors, st));
+    for (auto& q : pp.Q) NEF_TRY(run_ein<T>(p, q.build, factors, st));
+    return NEF_OK;
+}
+
+ViewDesc bind_view(nef_plan_t p, const PassPlan& pp, bool bf16) {
+    ViewDesc v = pp.view;
+    v.P.nsrc = 1;
+    v.P.src[0] = pp.P.desc;
+    v.P.src[0].ptr = bf16 ? (const void*)p->src_bf16[pp.P.buf] : buf_ptr(p, pp.P.buf);
+    v.Q.nsrc = (int)pp.Q.size();
+    for (size_t k = 0; k < pp.Q.size(); ++k) {
+        v.Q.src[k] = pp.Q[k].desc;
+        v.Q.src[k].ptr = bf16 ? (const void*)p->src_bf16[pp.Q[k].buf] : buf_ptr(p, pp.Q[k].buf);
+    }
+    return v;
+}
+
+// Event pair for one profiled launch (pool grows on demand, reused after reset).
+nef_status prof_begin(nef_plan_t p, cudaStream_t st, cudaEvent_t* a, cudaEvent_t* b) {
+    while (p->ev_next + 2 > p->ev_pool.size()) {
+        cudaEvent_t e;
+        NEF_CUDA(cudaEventCreate(&e));
+        p->ev_pool.push_back(e);
+    }
+    *a = p->ev_pool[p->ev_next++];
+    *b = p->ev_pool[p->ev_next++];
+    NEF_CUDA(cudaEventRecord(*a, st));
+    return NEF_OK;
+}
+
+template <typename T>
+nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbits,
+                    void* const* factors, const WeightSpec& w, const UpdateSpec& u, cudaStream_t st) {
+    const Model& md = p->md;
+    const int64_t nl = md.fac_size(pp.l);
+    T* num = static_cast<T*>(buf_ptr(p, B_NUM));
+    T* den = static_cast<T*>(buf_ptr(p, B_DEN));
+    if (pp.generic) {
+        GenericRecon g{};
+        g.n_obs = md.M;
+        g.n_let = (int)md.letter.size();
+        g.n_fac = md.L;
+        for (int x = 0; x < g.n_let; ++x) g.dim[x] = md.dim[x];
+        for (int f = 0; f < md.L; ++f) {
+            for (int x = 0; x < g.n_let; ++x) g.fst[f][x] = md.fac_stride(f, x);
+            g.fac[f] = factors[f];
+        }
+        g.n = md.N;
+        g.n_lat_el = 1;
+        for (int x = md.M; x < g.n_let; ++x) g.n_lat_el *= md.dim[x];
+        NEF_CUDA(launch_generic_weights<T>(g, y, mbits, w, static_cast<T*>(buf_ptr(p, B_WA)),
+                                           static_cast<T*>(buf_ptr(p, B_WB)), nullptr, nullptr, 0, st));
+        NEF_TRY(run_ein<T>(p, pp.gen_num, factors, st));
+        NEF_TRY(run_ein<T>(p, pp.gen_den, factors, st));
+        NEF_CUDA(launch_update<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, st));
+        return NEF_OK;
+    }
+    const bool b_is_one = (w.log_case || w.b_code == POW_ONE);
+    const bool closed = pp.den_closed && b_is_one && mbits == nullptr;
+    const int need_den = closed ? 0 : 1;
+    NEF_TRY(prepare_sources<T>(p, pp, factors, st));
+    const int64_t sz = pp.view.rows * pp.view.bond_pad;
+    T* spn = static_cast<T*>(buf_ptr(p, B_SPART_N));
+    T* spd = static_cast<T*>(buf_ptr(p, B_SPART_D));
+    bool used_tc = false;
+    if constexpr (sizeof(T) == 4) {
+        if (p->prec == NEF_BF16 && tc_view_supported(pp.view, need_den)) {
+            NEF_CUDA(launch_convert_bf16(static_cast<const float*>(buf_ptr(p, pp.P.buf)),
+                                         pp.P.n_rows * pp.view.bond_pad, p->src_bf16[pp.P.buf], st));
+            for (auto& q : pp.Q)
+                NEF_CUDA(launch_convert_bf16(static_cast<const float*>(buf_ptr(p, q.buf)),
+                                             q.n_rows * pp.view.bond_pad, p->src_bf16[q.buf], st));
+            ViewDesc v = bind_view(p, pp, true);
+            TcLaunchInfo info{};
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (p->opt.profile) NEF_TRY(prof_begin(p, st, &e0, &e1));
+            NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den,
+                                    pp.n_split, reinterpret_cast<float*>(spn),
+                                    reinterpret_cast<float*>(spd), p->tc_err, st, &info));
+            if (p->opt.profile) {
+                NEF_CUDA(cudaEventRecord(e1, st));
+                p->ev_used.push_back({0, {e0, e1}});
+            }
+            used_tc = true;
+        }
+    }
+    int n_split = pp.n_split;
+    if (!used_tc) {
+        ViewDesc v = bind_view(p, pp, false);
+        int n_ctas = 0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (p->opt.profile) NEF_TRY(prof_begin(p, st, &e0, &e1));
+        NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, need_den, n_split, spn, need_den ? spd : nullptr,
+                                     nullptr, nullptr, st, &n_ctas));
+        if (p->opt.profile) {
+            NEF_CUDA(cudaEventRecord(e1, st));
+            p->ev_used.push_back({1, {e0, e1}});
+        }
+    }
+    NEF_CUDA(launch_reduce_splits<T>(spn, n_split, sz, static_cast<T*>(buf_ptr(p, B_SNUM)), st));
+    if (need_den)
+        NEF_CUDA(launch_reduce_splits<T>(spd, n_split, sz, static_cast<T*>(buf_ptr(p, B_SDEN)), st));
+    NEF_TRY(run_ein<T>(p, pp.epi_num, factors, st));
+    if (need_den) {
+        NEF_TRY(run_ein<T>(p, pp.epi_den, factors, st));
+    } else {
+        for (auto& r : pp.colsum) NEF_TRY(run_ein<T>(p, r, factors, st));
+        NEF_TRY(run_ein<T>(p, pp.den_prod, factors, st));
+        NEF_TRY(run_ein<T>(p, pp.epi_den_closed, factors, st));
+    }
+    NEF_CUDA(launch_update<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, st));
+    return NEF_OK;
+}
+
+nef_status check_ab(double al, double be) {
+    if (!std::isfinite(al) || !std::isfinite(be)) return fail(NEF_EINVAL, "alpha/beta must be finite");
+    if (al == 0.0 && be != 1.0)
+        return fail(NEF_EUNSUPPORTED, "alpha == 0 with beta != 1 has no decomposition (App. B)");
+    return NEF_OK;
+}
+
+template <typename T>
+nef_status prologue(nef_plan_t p, const void* Y, const uint8_t* mask, void* const* factors,
+                    cudaStream_t st, const uint32_t** mbits) {
+    if (!Y) return fail(NEF_EINVAL, "Y is NULL");
+    if (!factors) return fail(NEF_EINVAL, "factors is NULL");
+    for (int f = 0; f < p->md.L; ++f)
+        if (!factors[f]) return fail(NEF_EINVAL, "factor %d is NULL", f);
+    *mbits = nullptr;
+    if (mask) {
+        NEF_CUDA(launch_pack_mask(mask, p->md.N, p->mask_bits, st));
+        *mbits = p->mask_bits;
+    }
+    if (p->opt.check_data) {
+        NEF_CUDA(cudaMemsetAsync(p->flag, 0, sizeof(int), st));
+        NEF_CUDA(launch_check_data<T>(static_cast<const T*>(Y), p->md.N, p->flag, st));
+        int h = 0;
+        NEF_CUDA(cudaMemcpyAsync(&h, p->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NEF_CUDA(cudaStreamSynchronize(st));
+        if (h) return fail(NEF_EDATA, "Y holds a negative or non-finite entry");
+    }
+    return NEF_OK;
+}
+
+template <typename T>
+nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* const* factors,
+                    double al, double be, int iters, int only_l) {
+    cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
+    const uint32_t* mbits = nullptr;
+    NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
+    const WeightSpec w = weight_spec(al, be);
+    const UpdateSpec u = update_spec(al, be, p->opt.eps);
+    const T* y = static_cast<const T*>(Y);
+    for (int it = 0; it < iters; ++it) {
+        for (int l = 0; l < p->md.L; ++l) {
+            if (only_l >= 0 && l != only_l) continue;
+            NEF_TRY(run_pass<T>(p, p->pass[l], y, mbits, factors, w, u, st));
+        }
+    }
+    return NEF_OK;
+}
+
+template <typename T>
+nef_status loss_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* const* factors,
+                     double al, double be, double* out) {
+    cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
+    const uint32_t* mbits = nullptr;
+    NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
+    const WeightSpec w = weight_spec(al, be);
+    const LossSpec L = loss_spec(al, be);
+    const T* y = static_cast<const T*>(Y);
+    int n_part = 0;
+    // the first factor with a view serves as the reconstruction route
+    int vl = -1;
+    for (int l = 0; l < p->md.L; ++l)
+        if (!p->pass[l].generic) { vl = l; break; }
+    if (vl >= 0) {
+        PassPlan& pp = p->pass[vl];
+        NEF_TRY(prepare_sources<T>(p, pp, factors, st));
+        ViewDesc v = bind_view(p, pp, false);
+        const int64_t tm = sizeof(T) == 8 ? 32 : 64;
+        const int64_t n_rb = (v.rows + tm - 1) / tm;
+        int ns = (int)std::max<int64_t>(1, std::min<int64_t>(pp.n_split, p->loss_part_cap / 2 / n_rb));
+        NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, 0, ns, nullptr, nullptr, &L, p->loss_part, st, &n_part));
+    } else {
+        GenericRecon g{};
+        const Model& md = p->md;
+        g.n_obs = md.M;
+        g.n_let = (int)md.letter.size();
+        g.n_fac = md.L;
+        for (int x = 0; x < g.n_let; ++x) g.dim[x] = md.dim[x];
+        for (int f = 0; f < md.L; ++f) {
+            for (int x = 0; x < g.n_let; ++x) g.fst[f][x] = md.fac_stride(f, x);
+            g.fac[f] = factors[f];
+        }
+        g.n = md.N;
+        g.n_lat_el = 1;
+        for (int x = md.M; x < g.n_let; ++x) g.n_lat_el *= md.dim[x];
+        n_part = (int)std::min<int64_t>((md.N + 255) / 256, p->loss_part_cap / 2);
+        NEF_CUDA(launch_generic_weights<T>(g, y, mbits, w, nullptr, nullptr, &L, p->loss_part, n_part, st));
+    }
+    NEF_CUDA(launch_sum_f64(p->loss_part, n_part, p->loss_out, st));
+    NEF_CUDA(launch_sum_f64(p->loss_part + n_part, n_part, p->loss_out + 1, st));
+    NEF_CUDA(cudaMemcpyAsync(out, p->loss_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NEF_CUDA(cudaStreamSynchronize(st));
+    return NEF_OK;
+}
+
+nef_status alloc(nef_plan_t p, int id, size_t bytes) {
+    if ((int)p->buf.size() <= id) p->buf.resize(id + 1);
+    if (bytes == 0) bytes = 16;
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NEF_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    NEF_CUDA(cudaMemset(ptr, 0, bytes));
+    p->buf[id].ptr = ptr;
+    p->buf[id].bytes = bytes;
+    return NEF_OK;
+}
+
+void destroy(nef_plan_t p) {
+    if (!p) return;
+    for (auto& b : p->buf)
+        if (b.ptr) cudaFree(b.ptr);
+    for (auto* q : p->src_bf16)
+        if (q) cudaFree(q);
+    if (p->ein_partial) cudaFree(p->ein_partial);
+    if (p->mask_bits) cudaFree(p->mask_bits);
+    if (p->loss_part) cudaFree(p->loss_part);
+    if (p->loss_out) cudaFree(p->loss_out);
+    if (p->flag) cudaFree(p->flag);
+    if (p->tc_err) cudaFree(p->tc_err);
+    for (auto e : p->ev_pool) cudaEventDestroy(e);
+    delete p;
+}
+
+nef_status build_plan(nef_plan_t p) {
+    const Model& md = p->md;
+    int next_buf = B_SRC0;
+    std::string info;
+    for (int l = 0; l < md.L; ++l) {
+        PassPlan best;
+        bool found = false;
+        if (!p->opt.force_generic) {
+            for (int s = 0; s < md.M; ++s)
+                for (int e = s + 1; e <= md.M; ++e) {
+                    bool ok_run = true;
+                    for (int x : md.term[l])
+                        if (md.is_obs(x) && !(x >= s && x < e)) ok_run = false;
+                    if (!ok_run) continue;
+                  for (int assign = 0; assign < 64; ++assign) {
+                    PassPlan cand;
+                    int nb = next_buf;
+                    if (!plan_view(*p, l, s, e, assign, cand, nb)) continue;
+                    bool fits = recipe_fits(cand.P.build) && recipe_fits(cand.epi_num) &&
+                                recipe_fits(cand.epi_den);
+                    for (auto& q : cand.Q) fits = fits && recipe_fits(q.build);
+                    if (cand.den_closed) {
+                        for (auto& r : cand.colsum) fits = fits && recipe_fits(r);
+                        fits = fits && recipe_fits(cand.den_prod) && recipe_fits(cand.epi_den_closed);
+                    }
+                    if (!fits) continue;
+                    if (!found || cand.cost < best.cost) {
+                        best = cand;
+                        found = true;
+                    }
+                  }
+                }
+        }
+        if (found) {
+            // renumber the source buffers of the chosen candidate
+            int remap_base = next_buf;
+            auto renum = [&](SourcePlan& sp) {
+                int nb = remap_base++;
+                sp.buf = nb;
+                sp.build.out_index = nb;
+            };
+            std::vector<int> old_ids;
+            old_ids.push_back(best.P.buf);
+            for (auto& q : best.Q) old_ids.push_back(q.buf);
+            renum(best.P);
+            for (auto& q : best.Q) renum(q);
+            for (size_t k = 0; k < best.colsum.size(); ++k) best.colsum[k].ops[0].index = best.Q[k].buf;
+            next_buf = remap_base;
+            (void)old_ids;
+        } else {
+            plan_generic(*p, l, best);
+            if (!recipe_fits(best.gen_num))
+                return fail(NEF_EUNSUPPORTED, "factor %d: contraction too large for the generic path", l);
+        }
+        if (!best.generic) {
+            bool tc = false;
+            if (p->prec == NEF_BF16) {
+                ViewDesc vv = best.view;
+                vv.P.nsrc = 1;
+                vv.P.src[0] = best.P.desc;
+                vv.Q.nsrc = (int)best.Q.size();
+                for (size_t k = 0; k < best.Q.size(); ++k) vv.Q.src[k] = best.Q[k].desc;
+                tc = tc_view_supported(vv, 1);
+            }
+            best.desc += tc ? " kernel=tcgen05" : (p->prec == NEF_FP64 ? " kernel=simt-fp64" : " kernel=simt-fp32");
+        }
+        info += best.desc + "\n";
+        p->pass.push_back(best);
+    }
+    p->info = info;
+    // ---- workspace
+    size_t es = p->esz;
+    int64_t max_fac = 1, max_s = 16, max_part = 16;
+    bool any_generic = false;
+    int64_t max_bond_pad = 16;
+    for (int l = 0; l < md.L; ++l) max_fac = std::max(max_fac, md.fac_size(l));
+    for (auto& pp : p->pass) {
+        if (pp.generic) { any_generic = true; continue; }
+        max_s = std::max(max_s, pp.view.rows * pp.view.bond_pad);
+        max_part = std::max(max_part, (int64_t)pp.n_split * pp.view.rows * pp.view.bond_pad);
+        max_bond_pad = std::max<int64_t>(max_bond_pad, pp.view.bond_pad);
+    }
+    NEF_TRY(alloc(p, B_NUM, max_fac * es));
+    NEF_TRY(alloc(p, B_DEN, max_fac * es));
+    NEF_TRY(alloc(p, B_SNUM, max_s * es));
+    NEF_TRY(alloc(p, B_SDEN, max_s * es));
+    NEF_TRY(alloc(p, B_SPART_N, max_part * es));
+    NEF_TRY(alloc(p, B_SPART_D, max_part * es));
+    NEF_TRY(alloc(p, B_DENVEC, max_bond_pad * es));
+    for (int k = 0; k < kMaxSrc; ++k) NEF_TRY(alloc(p, B_COLSUM0 + k, max_bond_pad * es));
+    if (any_generic) {
+        NEF_TRY(alloc(p, B_WA, md.N * es));
+        NEF_TRY(alloc(p, B_WB, md.N * es));
+    }
+    p->src_bf16.assign(next_buf + 1, nullptr);
+    for (auto& pp : p->pass) {
+        if (pp.generic) continue;
+        std::vector<SourcePlan*> srcs{&pp.P};
+        for (auto& q : pp.Q) srcs.push_back(&q);
+        for (auto* sp : srcs) {
+            size_t n = (size_t)sp->n_rows * pp.view.bond_pad;
+            NEF_TRY(alloc(p, sp->buf, n * es));
+            if (p->prec == NEF_BF16) {
+                void* q = nullptr;
+                if (cudaMalloc(&q, n * 2) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(NEF_ENOMEM, "cudaMalloc of a BF16 operand failed");
+                }
+                NEF_CUDA(cudaMemset(q, 0, n * 2));
+                p->src_bf16[sp->buf] = static_cast<uint16_t*>(q);
+            }
+        }
+    }
+    p->ein_partial_cap = 1 << 22;
+    NEF_CUDA(cudaMalloc(&p->ein_partial, p->ein_partial_cap * es));
+    NEF_CUDA(cudaMalloc(&p->mask_bits, ((md.N + 31) / 32 + 1) * sizeof(uint32_t)));
+    // loss partials: two doubles per CTA of the loss pass (view of the first viewable factor)
+    int64_t loss_ctas = 152 * 64;
+    for (auto& pp : p->pass) {
+        if (pp.generic) continue;
+        const int64_t tm = p->prec == NEF_FP64 ? 32 : 64;
+        loss_ctas = std::max<int64_t>(loss_ctas, ((pp.view.rows + tm - 1) / tm) * 2);
+        break;
+    }
+    p->loss_part_cap = (int)(2 * loss_ctas);
+    NEF_CUDA(cudaMalloc(&p->loss_part, p->loss_part_cap * sizeof(double)));
+    NEF_CUDA(cudaMalloc(&p->loss_out, 2 * sizeof(double)));
+    NEF_CUDA(cudaMalloc(&p->flag, sizeof(int)));
+    NEF_CUDA(cudaMalloc(&p->tc_err, sizeof(int)));
+    NEF_CUDA(cudaMemset(p->tc_err, 0, sizeof(int)));
+    return NEF_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+void nef_default_options(nef_options* opt) {
+    if (!opt) return;
+    opt->precision = NEF_FP32;
+    opt->eps = 1e-10;
+    opt->check_data = 0;
+    opt->force_generic = 0;
+    opt->profile = 0;
+    opt->stream = nullptr;
+}
+
+nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, const int64_t* ranks,
+                    int n_lat, const nef_options* opt, nef_plan_t* out) {
+    g_err.clear();
+    if (!out) return fail(NEF_EINVAL, "out is NULL");
+    *out = nullptr;
+    nef_plan_t p = new nef_plan_s();
+    if (opt) p->opt = *opt;
+    else nef_default_options(&p->opt);
+    if (p->opt.precision != NEF_FP32 && p->opt.precision != NEF_BF16 && p->opt.precision != NEF_FP64) {
+        delete p;
+        return fail(NEF_EINVAL, "unknown precision %d", p->opt.precision);
+    }
+    if (!(p->opt.eps >= 0.0)) {
+        delete p;
+        return fail(NEF_EINVAL, "eps must be >= 0");
+    }
+    p->prec = p->opt.precision;
+    p->esz = p->prec == NEF_FP64 ? 8 : 4;
+    nef_status s = parse_model(model_str, shapes, n_obs, ranks, n_lat, p->md);
+    if (s != NEF_OK) {
+        delete p;
+        return s;
+    }
+    s = build_plan(p);
+    if (s != NEF_OK) {
+        destroy(p);
+        return s;
+    }
+    *out = p;
+    return NEF_OK;
+}
+
+void nef_plan_destroy(nef_plan_t plan) { destroy(plan); }
+
+nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
+                   double alpha, double beta, int iters) {
+    g_err.clear();
+    if (!plan) return fail(NEF_EINVAL, "plan is NULL");
+    if (iters < 0) return fail(NEF_EINVAL, "iters must be >= 0");
+    NEF_TRY(check_ab(alpha, beta));
+    if (plan->prec == NEF_FP64) return fit_impl<double>(plan, Y, mask, factors, alpha, beta, iters, -1);
+    return fit_impl<float>(plan, Y, mask, factors, alpha, beta, iters, -1);
+}
+
+nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask, void* const* factors,
+                      double alpha, double beta) {
+    g_err.clear();
+    if (!plan) return fail(NEF_EINVAL, "plan is NULL");
+    if (l < 0 || l >= plan->md.L) return fail(NEF_EINVAL, "factor index %d out of range", l);
+    NEF_TRY(check_ab(alpha, beta));
+    if (plan->prec == NEF_FP64) return fit_impl<double>(plan, Y, mask, factors, alpha, beta, 1, l);
+    return fit_impl<float>(plan, Y, mask, factors, alpha, beta, 1, l);
+}
+
+nef_status nef_loss(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
+                    double alpha, double beta, double* out) {
+    g_err.clear();
+    if (!plan) return fail(NEF_EINVAL, "plan is NULL");
+    if (!out) return fail(NEF_EINVAL, "out is NULL");
+    NEF_TRY(check_ab(alpha, beta));
+    if (plan->prec == NEF_FP64) return loss_impl<double>(plan, Y, mask, factors, alpha, beta, out);
+    return loss_impl<float>(plan, Y, mask, factors, alpha, beta, out);
+}
+
+int nef_plan_info(nef_plan_t plan, char* buf, int cap) {
+    if (!plan) return 0;
+    int n = (int)plan->info.size();
+    if (buf && cap > 0) {
+        int c = std::min(n, cap - 1);
+        memcpy(buf, plan->info.data(), c);
+        buf[c] = 0;
+    }
+    return n + 1;
+}
+
+int nef_plan_launches(nef_plan_t plan, int has_mask) {
+    if (!plan) return 0;
+    int total = 0;
+    for (auto& pp : plan->pass) {
+        if (pp.generic) {
+            total += 1 + 2 + 2 + 1;
+            continue;
+        }
+        int n = 2 * (1 + (int)pp.Q.size());            // source einsums
+        if (plan->prec == NEF_BF16) n += 1 + (int)pp.Q.size();  // BF16 conversions
+        n += 1;                                         // view kernel
+        bool closed = pp.den_closed && !has_mask;      // (b == 1 is decided per call)
+        n += closed ? 1 : 2;                            // split reductions
+        n += 2;                                         // epilogue num
+        n += closed ? 2 * ((int)pp.colsum.size() + 2) : 2;
+        n += 1;                                         // update
+        total += n;
+    }
+    return total;
+}
+
+nef_status nef_plan_profile(nef_plan_t plan, double* ms, int* count, int reset) {
+    g_err.clear();
+    if (!plan || !ms || !count) return fail(NEF_EINVAL, "NULL argument");
+    if (!plan->opt.profile) return fail(NEF_EINVAL, "plan was created without opt.profile");
+    cudaStream_t st = static_cast<cudaStream_t>(plan->opt.stream);
+    NEF_CUDA(cudaStreamSynchronize(st));
+    ms[0] = ms[1] = 0.0;
+    count[0] = count[1] = 0;
+    for (auto& u : plan->ev_used) {
+        float t = 0.f;
+        NEF_CUDA(cudaEventElapsedTime(&t, u.second.first, u.second.second));
+        ms[u.first] += t;
+        count[u.first] += 1;
+    }
+    if (reset) {
+        plan->ev_used.clear();
+        plan->ev_next = 0;
+    }
+    return NEF_OK;
+}
+
+nef_status nef_check(nef_plan_t plan) {
+    g_err.clear();
+    if (!plan) return fail(NEF_EINVAL, "plan is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(plan->opt.stream);
+    int h = 0;
+    NEF_CUDA(cudaMemcpyAsync(&h, plan->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NEF_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        NEF_CUDA(cudaMemsetAsync(plan->tc_err, 0, sizeof(int), st));
+        NEF_CUDA(cudaStreamSynchronize(st));
+        return fail(NEF_ETIMEOUT, "a bounded wait in the tensor-core pass gave up (site %d)", h);
+    }
+    return NEF_OK;
+}
+
+const char* nef_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

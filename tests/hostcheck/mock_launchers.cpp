@@ -1,0 +1,213 @@
+// Plain-loop implementations of the launcher interface in nef_internal.h,
+// following each descriptor's documented meaning, so that plan.cpp (the real
+// planner and sweep driver) can be checked against the oracle on a CPU host.
+// TEST INFRASTRUCTURE ONLY: built by tests/hostcheck/build.py into a separate
+// library that the product never loads.  The element math (weights, divergence,
+// update) is the product's own nef_device.cuh compiled for the host.
+#include <cmath>
+#include <vector>
+
+#define __device__
+#define __forceinline__ inline
+#define __shfl_xor_sync(m, v, o) (v)
+static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+using std::isinf;
+#include "nef_device.cuh"
+#include "nef_internal.h"
+
+namespace nef {
+
+template <typename T>
+cudaError_t launch_einsum(const EinDesc& d, T*, int64_t, cudaStream_t) {
+    const int nl = d.n_out + d.n_free;
+    std::vector<int64_t> idx(nl);
+    for (int64_t o = 0; o < d.n_out_el; ++o) {
+        int64_t rem = o, dst = 0;
+        for (int q = d.n_out - 1; q >= 0; --q) {
+            idx[q] = rem % d.dim[q];
+            dst += idx[q] * d.out_st[q];
+            rem /= d.dim[q];
+        }
+        T acc = 0;
+        for (int64_t f = 0; f < d.n_free_el; ++f) {
+            int64_t r2 = f;
+            for (int q = nl - 1; q >= d.n_out; --q) {
+                idx[q] = r2 % d.dim[q];
+                r2 /= d.dim[q];
+            }
+            T p = 1;
+            for (int k = 0; k < d.n_ops; ++k) {
+                int64_t off = 0;
+                for (int q = 0; q < nl; ++q) off += idx[q] * d.ost[k][q];
+                p *= static_cast<const T*>(d.op[k])[off];
+            }
+            acc += p;
+        }
+        T* out = static_cast<T*>(d.out);
+        out[dst] = d.accumulate ? out[dst] + acc : acc;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_pack_mask(const uint8_t* m, int64_t n, uint32_t* bits, cudaStream_t) {
+    for (int64_t w = 0; w < (n + 31) / 32; ++w) {
+        uint32_t v = 0;
+        for (int b = 0; b < 32; ++b)
+            if (w * 32 + b < n && m[w * 32 + b]) v |= 1u << b;
+        bits[w] = v;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_check_data(const T* y, int64_t n, int* flag, cudaStream_t) {
+    for (int64_t e = 0; e < n; ++e)
+        if (!(y[e] >= 0) || std::isinf((double)y[e])) *flag = 1;
+    return cudaSuccess;
+}
+
+template <typename T>
+static T side_value(const SideDesc& sd, int64_t i, int b) {
+    T p = 1;
+    for (int s = 0; s < sd.nsrc; ++s) {
+        const SrcDesc& d = sd.src[s];
+        int64_t r = 0;
+        for (int t = 0; t < d.nterm; ++t) r += ((i / d.div[t]) % d.mod[t]) * d.mul[t];
+        p *= static_cast<const T*>(d.ptr)[r * d.ld + b];
+    }
+    return p;
+}
+
+template <typename T>
+cudaError_t launch_view_simt(const T* y, const uint32_t* mbits, const ViewDesc& v,
+                             const WeightSpec& w, int need_den, int n_split, T* s_num, T* s_den,
+                             const LossSpec* loss, double* loss_part, cudaStream_t, int* n_ctas) {
+    const int64_t ncols = v.c_out * v.c_in;
+    const int BP = v.bond_pad;
+    if (s_num) {
+        for (int64_t e = 0; e < (int64_t)n_split * v.rows * BP; ++e) {
+            s_num[e] = 0;
+            if (need_den) s_den[e] = 0;
+        }
+    }
+    double ls = 0, lc = 0;
+    std::vector<T> P(BP), Q(BP);
+    for (int64_t row = 0; row < v.rows; ++row) {
+        for (int b = 0; b < BP; ++b) P[b] = b < v.bond ? side_value<T>(v.P, row, b) : T(0);
+        for (int64_t col = 0; col < ncols; ++col) {
+            const int64_t idx = (col / v.c_in) * v.rows * v.c_in + row * v.c_in + (col % v.c_in);
+            if (mbits && !mask_bit(mbits, idx)) continue;
+            T yh = 0;
+            for (int b = 0; b < BP; ++b) {
+                Q[b] = b < v.bond ? side_value<T>(v.Q, col, b) : T(0);
+                yh += P[b] * Q[b];
+            }
+            T a, bb;
+            ab_weights(y[idx], yh, w, a, bb);
+            if (loss) { ls += (double)divergence(y[idx], yh, *loss); lc += 1; }
+            if (s_num)
+                for (int b = 0; b < BP; ++b) {
+                    s_num[row * BP + b] += a * Q[b];
+                    if (need_den) s_den[row * BP + b] += bb * Q[b];
+                }
+        }
+    }
+    if (loss) { loss_part[0] = ls; loss_part[1] = lc; }
+    if (n_ctas) *n_ctas = 1;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_reduce_splits(const T* part, int n_split, int64_t n, T* out, cudaStream_t) {
+    for (int64_t e = 0; e < n; ++e) {
+        T acc = 0;
+        for (int s = 0; s < n_split; ++s) acc += part[s * n + e];
+        out[e] = acc;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_update(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
+                          cudaStream_t) {
+    for (int64_t e = 0; e < n; ++e) theta[e] = mu_update(theta[e], num[e], den[e], u);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_fill(T* p, int64_t n, T v, cudaStream_t) {
+    for (int64_t e = 0; e < n; ++e) p[e] = v;
+    return cudaSuccess;
+}
+
+cudaError_t launch_sum_f64(const double* part, int n, double* out, cudaStream_t) {
+    double s = 0;
+    for (int k = 0; k < n; ++k) s += part[k];
+    *out = s;
+    return cudaSuccess;
+}
+
+cudaError_t launch_convert_bf16(const float*, int64_t, uint16_t*, cudaStream_t) {
+    return cudaErrorNotSupported;
+}
+
+template <typename T>
+cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint32_t* mbits,
+                                   const WeightSpec& w, T* wa, T* wb, const LossSpec* loss,
+                                   double* loss_part, int n_part, cudaStream_t) {
+    double ls = 0, lc = 0;
+    std::vector<int64_t> idx(g.n_let);
+    for (int64_t e = 0; e < g.n; ++e) {
+        int64_t rem = e;
+        for (int m = g.n_obs - 1; m >= 0; --m) { idx[m] = rem % g.dim[m]; rem /= g.dim[m]; }
+        T yh = 0;
+        for (int64_t c = 0; c < g.n_lat_el; ++c) {
+            int64_t r2 = c;
+            for (int x = g.n_let - 1; x >= g.n_obs; --x) { idx[x] = r2 % g.dim[x]; r2 /= g.dim[x]; }
+            T p = 1;
+            for (int f = 0; f < g.n_fac; ++f) {
+                int64_t off = 0;
+                for (int x = 0; x < g.n_let; ++x) off += idx[x] * g.fst[f][x];
+                p *= static_cast<const T*>(g.fac[f])[off];
+            }
+            yh += p;
+        }
+        T a = 0, b = 0;
+        if (!mbits || mask_bit(mbits, e)) {
+            ab_weights(y[e], yh, w, a, b);
+            if (loss) { ls += (double)divergence(y[e], yh, *loss); lc += 1; }
+        }
+        if (wa) wa[e] = a;
+        if (wb) wb[e] = b;
+    }
+    if (loss) {
+        for (int k = 0; k < 2 * n_part; ++k) loss_part[k] = 0;
+        loss_part[0] = ls;
+        loss_part[n_part] = lc;
+    }
+    return cudaSuccess;
+}
+
+bool tc_view_supported(const ViewDesc&, int) { return false; }
+cudaError_t launch_view_tc(const float*, const uint32_t*, const ViewDesc&, const WeightSpec&, int,
+                           int, float*, float*, int*, cudaStream_t, TcLaunchInfo*) {
+    return cudaErrorNotSupported;
+}
+
+#define INST(T)                                                                                  \
+    template cudaError_t launch_einsum<T>(const EinDesc&, T*, int64_t, cudaStream_t);            \
+    template cudaError_t launch_check_data<T>(const T*, int64_t, int*, cudaStream_t);            \
+    template cudaError_t launch_view_simt<T>(const T*, const uint32_t*, const ViewDesc&,         \
+                                             const WeightSpec&, int, int, T*, T*,                \
+                                             const LossSpec*, double*, cudaStream_t, int*);      \
+    template cudaError_t launch_reduce_splits<T>(const T*, int, int64_t, T*, cudaStream_t);      \
+    template cudaError_t launch_update<T>(T*, const T*, const T*, int64_t, const UpdateSpec&,     \
+                                          cudaStream_t);                                         \
+    template cudaError_t launch_fill<T>(T*, int64_t, T, cudaStream_t);                           \
+    template cudaError_t launch_generic_weights<T>(const GenericRecon&, const T*,                 \
+                                                   const uint32_t*, const WeightSpec&, T*, T*,     \
+                                                   const LossSpec*, double*, int, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace nef

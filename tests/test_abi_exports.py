@@ -1,0 +1,48 @@
+"""The C-ABI library loads on a CPU-only host and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(nef_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_02759_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_headers_match_binding_lists():
+    import paper_2602_02759_gb300 as nef
+    assert _declared("nef.h") == sorted(nef.EXPORTS)
+    assert _declared("nef_debug.h") == sorted(nef.DEBUG_EXPORTS)
+
+
+@pytest.mark.parametrize("header", ["nef.h", "nef_debug.h"])
+def test_library_exports_every_declared_symbol(lib, header):
+    for name in _declared(header):
+        assert hasattr(lib, name), name
+
+
+def test_defaults_and_errors_without_gpu(lib):
+    """Calls that need no device work return their documented status codes."""
+    import paper_2602_02759_gb300._nef as b
+    L = b.load()
+    o = b.Options()
+    L.nef_default_options(ctypes.byref(o))
+    assert o.precision == 0 and o.eps == pytest.approx(1e-10) and o.force_generic == 0
+    h = ctypes.c_void_p()
+    shapes = (ctypes.c_int64 * 3)(2, 2, 2)
+    ranks = (ctypes.c_int64 * 1)(2)
+    assert L.nef_plan(b"ir,jr,kr", shapes, 3, ranks, 1, None, ctypes.byref(h)) == 2
+    assert b"->" in L.nef_last_error()
+    assert L.nef_plan(b"ir,jr,kr->ijk", shapes, 2, ranks, 1, None, ctypes.byref(h)) == 1
+    assert L.nef_fit(None, None, None, None, 1.0, 0.0, 1) == 1

@@ -1,0 +1,221 @@
+"""Host logic of the C ABI (parser, planner, sweep driver) against the oracle.
+
+plan.cpp is compiled with g++ against a fake CUDA runtime whose "device"
+memory is host memory, with plain-loop launchers that implement each kernel
+descriptor's documented meaning (tests/hostcheck).  This checks the planner's
+views, strides, epilogue einsums, closed-form denominators and the generic
+fallback on a CPU-only host; the kernels themselves are checked on the GPU.
+"""
+import ctypes
+import os
+import sys
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "hostcheck"))
+import build as hostcheck_build  # noqa: E402
+
+from oracle import OracleModel  # noqa: E402
+
+NEF_FP32, NEF_BF16, NEF_FP64 = 0, 1, 2
+
+
+class Opt(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double),
+                ("check_data", ctypes.c_int), ("force_generic", ctypes.c_int),
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lib = ctypes.CDLL(hostcheck_build.build())
+    vp = ctypes.c_void_p
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.nef_plan.argtypes = [ctypes.c_char_p, i64p, ctypes.c_int, i64p, ctypes.c_int,
+                             ctypes.POINTER(Opt), ctypes.POINTER(vp)]
+    lib.nef_fit.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int]
+    lib.nef_update.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(vp), ctypes.c_double,
+                               ctypes.c_double]
+    lib.nef_loss.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                             ctypes.POINTER(ctypes.c_double)]
+    lib.nef_plan_destroy.argtypes = [vp]
+    lib.nef_plan_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_int]
+    lib.nef_last_error.restype = ctypes.c_char_p
+    lib.nef_default_options.argtypes = [ctypes.POINTER(Opt)]
+    return lib
+
+
+def split(model_str):
+    lhs, rhs = model_str.split("->")
+    lat = []
+    for ch in lhs.replace(",", ""):
+        if ch not in rhs and ch not in lat:
+            lat.append(ch)
+    return list(rhs), lat, lhs.split(",")
+
+
+def make_plan(lib, model_str, dims, prec, force_generic=False, eps=1e-10):
+    obs, lat, _ = split(model_str)
+    shapes = (ctypes.c_int64 * max(1, len(obs)))(*[dims[c] for c in obs])
+    ranks = (ctypes.c_int64 * max(1, len(lat)))(*[dims[c] for c in lat])
+    o = Opt()
+    lib.nef_default_options(ctypes.byref(o))
+    o.precision = prec
+    o.eps = eps
+    o.force_generic = int(force_generic)
+    h = ctypes.c_void_p()
+    rc = lib.nef_plan(model_str.encode(), shapes, len(obs), ranks, len(lat), ctypes.byref(o),
+                      ctypes.byref(h))
+    return rc, h
+
+
+def info(lib, h):
+    buf = ctypes.create_string_buffer(8192)
+    lib.nef_plan_info(h, buf, 8192)
+    return buf.value.decode()
+
+
+def facs_arr(fs):
+    arr = (ctypes.c_void_p * len(fs))()
+    for k, f in enumerate(fs):
+        arr[k] = f.ctypes.data
+    return arr
+
+
+MODELS = [
+    ("ir,jr,kr->ijk", dict(i=5, j=6, k=7, r=3)),
+    ("ir,jr->ij", dict(i=7, j=5, r=2)),
+    ("ir,js,kt,rst->ijk", dict(i=4, j=3, k=5, r=2, s=3, t=2)),
+    ("iab,jbc,kca->ijk", dict(i=3, j=4, k=3, a=2, b=2, c=3)),
+    ("ia,ja,ab,kb,lb->ijkl", dict(i=4, j=3, k=5, l=3, a=3, b=2)),
+    ("ij,jk,ik->ijk", dict(i=3, j=4, k=5)),
+    ("i,jr,kr->ijk", dict(i=4, j=3, k=5, r=2)),
+    ("ir,jkr->ijk", dict(i=4, j=3, k=5, r=3)),
+    ("ir,jr,ak,kr,tr->ijat", dict(i=3, j=4, a=3, t=2, k=2, r=3)),
+    ("wr,dr,hr,irk,jrk->wdhij", dict(w=2, d=3, h=2, i=3, j=4, r=2, k=2)),
+    ("ri,jr,kr->ijk", dict(i=4, j=3, k=5, r=3)),
+    ("ir,js,rs->ij", dict(i=5, j=4, r=2, s=3)),
+]
+
+
+@pytest.mark.parametrize("model_str,dims", MODELS)
+@pytest.mark.parametrize("prec", [NEF_FP64, NEF_FP32])
+@pytest.mark.parametrize("ab", [(1.0, 0.0), (0.5, 0.5), (1.0, -0.5), (0.0, 1.0)])
+@pytest.mark.parametrize("masked", [False, True])
+def test_fit_matches_oracle(lib, model_str, dims, prec, ab, masked):
+    a, b = ab
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(hash((model_str, a, b, masked)) % 2**32)
+    dt = np.float64 if prec == NEF_FP64 else np.float32
+    fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)).astype(dt) for l in range(m.n_factors)]
+    y = rng.uniform(0.2, 3.0, size=m.y_shape).astype(dt)
+    mask = (rng.random(m.y_shape) > 0.3).astype(np.uint8) if masked else None
+    rc, h = make_plan(lib, model_str, dims, prec)
+    assert rc == 0, lib.nef_last_error()
+    try:
+        ref = m.fit(y, mask, [f.astype(np.float64) for f in fs], a, b, 2)
+        work = [f.copy() for f in fs]
+        rc = lib.nef_fit(h, y.ctypes.data, None if mask is None else mask.ctypes.data,
+                         facs_arr(work), a, b, 2)
+        assert rc == 0, lib.nef_last_error()
+        tol = 1e-10 if prec == NEF_FP64 else 2e-5
+        for l in range(m.n_factors):
+            rel = np.linalg.norm(work[l] - ref[l]) / np.linalg.norm(ref[l])
+            assert rel < tol, (l, rel, info(lib, h))
+        out = (ctypes.c_double * 2)()
+        rc = lib.nef_loss(h, y.ctypes.data, None if mask is None else mask.ctypes.data,
+                          facs_arr(work), a, b, out)
+        assert rc == 0, lib.nef_last_error()
+        lref, cnt = m.loss(y, mask, [w.astype(np.float64) for w in work], a, b)
+        assert out[1] == cnt
+        assert out[0] == pytest.approx(lref, rel=1e-9 if prec == NEF_FP64 else 1e-5)
+    finally:
+        lib.nef_plan_destroy(h)
+
+
+@pytest.mark.parametrize("model_str,dims", MODELS[:5])
+def test_generic_path_matches_oracle(lib, model_str, dims):
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(3)
+    fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)) for l in range(m.n_factors)]
+    y = rng.uniform(0.2, 3.0, size=m.y_shape)
+    mask = (rng.random(m.y_shape) > 0.3).astype(np.uint8)
+    rc, h = make_plan(lib, model_str, dims, NEF_FP64, force_generic=True)
+    assert rc == 0
+    try:
+        assert "generic" in info(lib, h)
+        ref = m.fit(y, mask, fs, 1.0, 0.0, 1)
+        work = [f.copy() for f in fs]
+        assert lib.nef_fit(h, y.ctypes.data, mask.ctypes.data, facs_arr(work), 1.0, 0.0, 1) == 0
+        for l in range(m.n_factors):
+            np.testing.assert_allclose(work[l], ref[l], rtol=1e-11)
+    finally:
+        lib.nef_plan_destroy(h)
+
+
+def test_update_single_factor(lib):
+    model_str, dims = "ia,ja,ab,kb,lb->ijkl", dict(i=4, j=3, k=5, l=3, a=3, b=2)
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(4)
+    fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)) for l in range(m.n_factors)]
+    y = rng.uniform(0.2, 3.0, size=m.y_shape)
+    rc, h = make_plan(lib, model_str, dims, NEF_FP64)
+    try:
+        for l in range(m.n_factors):
+            ref, _, _ = m.update_factor(l, y, None, fs, 0.5, 0.5)
+            work = [f.copy() for f in fs]
+            assert lib.nef_update(h, l, y.ctypes.data, None, facs_arr(work), 0.5, 0.5) == 0
+            for q in range(m.n_factors):
+                np.testing.assert_allclose(work[q], ref[q], rtol=1e-12)
+    finally:
+        lib.nef_plan_destroy(h)
+
+
+def test_planner_views(lib):
+    """The chosen views for the benchmark shapes: CP uses one row letter per
+    factor with gathered columns; the LR-core custom model uses bond b."""
+    rc, h = make_plan(lib, "ir,jr,kr->ijk", dict(i=16, j=16, k=16, r=8), NEF_FP32)
+    txt = info(lib, h)
+    lib.nef_plan_destroy(h)
+    assert txt.count("gather") == 3 and "generic" not in txt, txt
+    rc, h = make_plan(lib, "ia,ja,ab,kb,lb->ijkl", dict(i=16, j=16, k=8, l=4, a=4, b=2), NEF_FP32)
+    txt = info(lib, h)
+    lib.nef_plan_destroy(h)
+    assert "generic" not in txt, txt
+    rc, h = make_plan(lib, "ij,jk,ik->ijk", dict(i=3, j=4, k=5), NEF_FP32)
+    txt = info(lib, h)
+    lib.nef_plan_destroy(h)
+    assert txt.count("generic") == 3, txt
+
+
+@pytest.mark.parametrize("bad,code", [
+    ("ir,jr,kr", 2), ("ir,jr->ii", 2), ("iir,jr->ij", 2), ("ir,jr->ijk", 2), ("iR,jr->ij", 2),
+])
+def test_parse_errors(lib, bad, code):
+    shapes = (ctypes.c_int64 * 3)(2, 2, 2)
+    ranks = (ctypes.c_int64 * 2)(2, 2)
+    h = ctypes.c_void_p()
+    rc = lib.nef_plan(bad.encode(), shapes, 2, ranks, 1, None, ctypes.byref(h))
+    assert rc == code, (bad, rc, lib.nef_last_error())
+    assert not h.value
+
+
+def test_argument_errors(lib):
+    rc, h = make_plan(lib, "ir,jr->ij", dict(i=3, j=3, r=2), NEF_FP32)
+    assert rc == 0
+    y = np.ones((3, 3), np.float32)
+    fs = [np.ones((3, 2), np.float32), np.ones((3, 2), np.float32)]
+    try:
+        assert lib.nef_fit(h, y.ctypes.data, None, facs_arr(fs), 0.0, 0.5, 1) == 3  # unsupported
+        assert lib.nef_fit(h, None, None, facs_arr(fs), 1.0, 0.0, 1) == 1
+        assert lib.nef_fit(h, y.ctypes.data, None, facs_arr(fs), 1.0, 0.0, -1) == 1
+        assert lib.nef_update(h, 5, y.ctypes.data, None, facs_arr(fs), 1.0, 0.0) == 1
+    finally:
+        lib.nef_plan_destroy(h)
+    shapes = (ctypes.c_int64 * 2)(3, 0)
+    ranks = (ctypes.c_int64 * 1)(2)
+    hh = ctypes.c_void_p()
+    assert lib.nef_plan(b"ir,jr->ij", shapes, 2, ranks, 1, None, ctypes.byref(hh)) == 1
