@@ -53,6 +53,7 @@ k_view_simt(const T* __restrict__ y, const uint32_t* __restrict__ mbits, ViewDes
     T* Wa = Ys + TM * (TN + PAD);                // [TN][TM+PAD]
     T* Wb = Wa + TN * (TM + PAD);                // [TN][TM+PAD]
     int64_t* coff = reinterpret_cast<int64_t*>(Wb + (DEN ? TN * (TM + PAD) : 0));  // [TN]
+    int64_t* qrow = coff + TN;                                                     // [kMaxSrc][TN]
 
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
@@ -85,13 +86,19 @@ k_view_simt(const T* __restrict__ y, const uint32_t* __restrict__ mbits, ViewDes
         __syncthreads();
         if (tid < TN) {
             const int64_t col = c0 + tid;
-            coff[tid] = (col < c_hi) ? (col / v.c_in) * v.rows * v.c_in + (col % v.c_in) : -1;
+            const bool ok = col < c_hi;
+            coff[tid] = ok ? (col / v.c_in) * v.rows * v.c_in + (col % v.c_in) : -1;
+            for (int s = 0; s < v.Q.nsrc; ++s) qrow[s * TN + tid] = ok ? src_row(v.Q.src[s], col) : 0;
         }
+        __syncthreads();
         for (int e = tid; e < TN * BP; e += kThreads) {
             const int c = e / BP, b = e % BP;
-            const int64_t col = c0 + c;
             T q = T(0);
-            if (col < c_hi && b < v.bond) q = side_value<T>(v.Q, col, b);
+            if (coff[c] >= 0 && b < v.bond) {
+                q = T(1);
+                for (int s = 0; s < v.Q.nsrc; ++s)
+                    q *= static_cast<const T*>(v.Q.src[s].ptr)[qrow[s * TN + c] * v.Q.src[s].ld + b];
+            }
             Qb[b * (TN + PAD) + c] = q;
             Qc[c * (BP + PAD) + b] = q;
         }
@@ -203,7 +210,7 @@ size_t smem_bytes(bool den) {
     constexpr int PAD = 4;
     size_t n = (size_t)BP * (TM + PAD) + (size_t)BP * (TN + PAD) + (size_t)TN * (BP + PAD) +
                (size_t)TM * (TN + PAD) + (size_t)TN * (TM + PAD) * (den ? 2 : 1);
-    return n * sizeof(T) + TN * sizeof(int64_t);
+    return n * sizeof(T) + (1 + kMaxSrc) * TN * sizeof(int64_t);
 }
 
 template <typename T, int TM, int TN, int BP, bool DEN, bool GEMM2, bool LOSS>

@@ -778,7 +778,7 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
     T* spd = static_cast<T*>(buf_ptr(p, B_SPART_D));
     bool used_tc = false;
     if constexpr (sizeof(T) == 4) {
-        if (p->prec == NEF_BF16 && tc_view_supported(pp.view, need_den)) {
+        if (p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den)) {
             NEF_CUDA(launch_convert_bf16(static_cast<const float*>(buf_ptr(p, pp.P.buf)),
                                          pp.P.n_rows * pp.view.bond_pad, p->src_bf16[pp.P.buf], st));
             for (auto& q : pp.Q)

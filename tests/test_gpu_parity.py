@@ -158,8 +158,8 @@ def test_bf16_single_updates(model_str, dims, a, b, masked):
     y = rng.poisson(np.einsum(model_str, *truth)).astype(np.float32)
     mask = (rng.random(m.y_shape) > 0.2).astype(np.uint8) if masked else None
     init = [rng.uniform(0.5, 1.5, m.factor_shape(l)) for l in range(m.n_factors)]
-    plan = nef.Plan(model_str, dims, precision="bf16")
-    assert "generic" not in plan.info()
+    plan = nef.Plan(model_str, dims, precision="bf16", profile=True)
+    assert "generic" not in plan.info() and "simt" not in plan.info(), plan.info()
     Y = dev(y)
     M = None if mask is None else dev(mask, torch.uint8)
     for l in range(m.n_factors):
@@ -168,6 +168,7 @@ def test_bf16_single_updates(model_str, dims, a, b, masked):
         plan.update(l, Y, M, fs, a, b)
         plan.check()
         got = fs[l].cpu().numpy()
+        assert plan.profile()["tcgen05"][1] == 1, "the tensor-core pass did not run"
         assert np.all(np.isfinite(got))
         assert rel(got, ref[l]) < 2e-3, (l, rel(got, ref[l]), plan.info())
 
@@ -183,12 +184,13 @@ def test_bf16_fit_loss_matches_oracle(model_str, dims, a, b, masked):
     init = [rng.uniform(0.5, 1.5, m.factor_shape(l)) for l in range(m.n_factors)]
     iters = 15
     ref, trace = m.fit(y, mask, init, a, b, iters, trace=True)
-    plan = nef.Plan(model_str, dims, precision="bf16")
+    plan = nef.Plan(model_str, dims, precision="bf16", profile=True)
     fs = [dev(f) for f in init]
     Y = dev(y)
     M = None if mask is None else dev(mask, torch.uint8)
     plan.fit(Y, M, fs, a, b, iters)
     plan.check()
+    assert plan.profile()["tcgen05"][1] == iters * m.n_factors
     lo, _ = plan.loss(Y, M, fs, a, b)
     assert lo == pytest.approx(trace[-1], rel=1e-3)
 
@@ -203,7 +205,7 @@ def test_config2_sampled_update(prec, beta):
     p = synth.config2(beta=beta)
     m = OracleModel(p.model_str, p.dims)
     init = [f.astype(np.float64) for f in p.inits[0]]
-    plan = nef.Plan(p.model_str, p.dims, precision=prec)
+    plan = nef.Plan(p.model_str, p.dims, precision=prec, profile=True)
     Y = dev(p.y)
     rng = np.random.default_rng(11)
     tol = 2e-3 if prec == "bf16" else 1e-5
@@ -211,6 +213,8 @@ def test_config2_sampled_update(prec, beta):
         fs = [dev(f) for f in init]
         plan.update(l, Y, None, fs, 1.0, beta)
         plan.check()
+        kern = plan.profile()
+        assert kern["tcgen05" if prec == "bf16" else "simt"][1] == 1
         got = fs[l].cpu().numpy()
         rows = rng.choice(512, size=2, replace=False)
         cols = rng.choice(64, size=4, replace=False)
