@@ -160,6 +160,34 @@ nef_status nef_plan_profile(nef_plan_t plan, double* ms, int* count, int reset);
  */
 nef_status nef_check(nef_plan_t plan);
 
+/*
+ * nef_cp3_update_static -- update factor l of the 3-way CP model
+ * "ir,jr,kr->ijk" in place (one inner step of the sweep, FP32, no mask)
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * running while a framework's caching allocator owns the device memory, or
+ * loops that forbid allocation after start-up.
+ *   Y       : device, I*J*K floats, row-major [i][j][k]
+ *   shape   : host, {I, J, K}
+ *   rank    : R; must be 16, 32 or 64
+ *   factors : host array of 3 device pointers: A [I][R], B [J][R], C [K][R];
+ *             factor l is updated in place, the others are read
+ *   alpha, beta, eps : as for nef_fit / nef_options
+ *   stream  : cudaStream_t the work is ordered on
+ * Intermediates live in one fixed 16 MiB device array inside the library
+ * (kept by every GPU that loads it until the process exits), so the updated
+ * factor must satisfy rows x R <= 1,048,576 (rows = I, J or K); larger sizes
+ * return NEF_EINVAL.  Every call shares that array: calls that can overlap on
+ * the GPU (other streams or host threads) race and must be serialised by the
+ * caller.  The first call on each device looks up the array's device address,
+ * so make it before any stream capture.  Returns once the work is enqueued.
+ * Errors: NEF_EINVAL (null pointer, bad rank, factor index or size),
+ * NEF_EUNSUPPORTED (alpha == 0 with beta != 1), NEF_ECUDA (launch failure).
+ */
+nef_status nef_cp3_update_static(const float* Y, const int64_t* shape, int rank,
+                                 float* const* factors, int l, double alpha, double beta,
+                                 double eps, void* stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char* nef_last_error(void);
 

@@ -18,6 +18,7 @@ from ._nef import (  # noqa: F401
     NEF_FP64,
     NefError,
     Plan,
+    cp3_update_static,
     load,
     split_model,
 )

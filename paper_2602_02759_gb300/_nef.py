@@ -21,7 +21,7 @@ PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 # every symbol include/nef.h declares
 EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_update",
            "nef_loss", "nef_plan_info", "nef_plan_launches", "nef_plan_profile", "nef_check",
-           "nef_last_error"]
+           "nef_cp3_update_static", "nef_last_error"]
 # every symbol include/nef_debug.h declares
 DEBUG_EXPORTS = ["nef_tc_probe"]
 
@@ -73,6 +73,9 @@ def load(path: str = LIB_PATH):
     lib.nef_check.argtypes = [vp]
     lib.nef_check.restype = ctypes.c_int
     lib.nef_last_error.restype = ctypes.c_char_p
+    lib.nef_cp3_update_static.argtypes = [vp, i64p, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
+    lib.nef_cp3_update_static.restype = ctypes.c_int
     lib.nef_tc_probe.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.nef_tc_probe.restype = ctypes.c_int
     _lib = lib
@@ -94,6 +97,19 @@ def split_model(model_str: str):
         if ch not in rhs and ch not in latent:
             latent.append(ch)
     return list(rhs), latent, lhs.split(",")
+
+
+def cp3_update_static(Y, factors, l, alpha, beta, eps=1e-10, stream=None):
+    """nef_cp3_update_static: update factor l of 'ir,jr,kr->ijk' in place without any
+    device allocation (see include/nef.h).  Y, factors: contiguous CUDA float32."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    shape = (ctypes.c_int64 * 3)(*[int(s) for s in Y.shape])
+    arr = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in factors])
+    check(load().nef_cp3_update_static(ctypes.c_void_p(Y.data_ptr()), shape, int(factors[0].shape[1]),
+                                       arr, int(l), float(alpha), float(beta), float(eps),
+                                       ctypes.c_void_p(stream.cuda_stream)))
 
 
 class Plan:

@@ -95,6 +95,14 @@ struct EinDesc {
     int accumulate;                        // 1: out += result, 0: out = result
 };
 
+// Message returned by nef_last_error() on this thread.
+void set_last_error(const char* msg);
+
+// Specialisation of the App. B weights, loss and update for given (alpha, beta).
+WeightSpec weight_spec(double alpha, double beta);
+LossSpec loss_spec(double alpha, double beta);
+UpdateSpec update_spec(double alpha, double beta, double eps);
+
 // ------------------------------------------------------------- launchers
 // All launchers return cudaGetLastError() after enqueueing on `st`.
 

@@ -226,6 +226,73 @@ struct nef_plan_s {
     size_t ev_next = 0;
 };
 
+namespace nef {
+
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+WeightSpec weight_spec(double al, double be) {
+    WeightSpec w{};
+    w.alpha = al;
+    w.beta = be;
+    auto code = [](double e) {
+        if (e == 0.0) return (int)POW_ONE;
+        if (e == 1.0) return (int)POW_ID;
+        if (e == -1.0) return (int)POW_RCP;
+        if (e == -0.5) return (int)POW_RSQRT;
+        if (e == 0.5) return (int)POW_SQRT;
+        if (e == 2.0) return (int)POW_SQ;
+        if (e == -1.5) return (int)POW_RSQRT3;
+        if (e == -2.0) return (int)POW_RCP2;
+        return (int)POW_GENERAL;
+    };
+    if (al == 0.0) {
+        w.log_case = 1;
+        w.y_code = POW_ONE;
+        w.a_code = POW_ONE;
+        w.b_code = POW_ONE;
+        return w;
+    }
+    w.e_y = al;
+    w.e_a = be - 1.0;
+    w.e_b = al + be - 1.0;
+    w.y_code = code(w.e_y);
+    w.a_code = code(w.e_a);
+    w.b_code = code(w.e_b);
+    return w;
+}
+
+LossSpec loss_spec(double al, double be) {
+    LossSpec L{};
+    L.alpha = al;
+    L.beta = be;
+    if (al != 0.0 && be != 0.0 && al + be != 0.0) L.kase = 0;
+    else if (be == 0.0 && al != 0.0) L.kase = 1;
+    else if (al == -be && al != 0.0) L.kase = 2;
+    else if (al == 0.0 && be != 0.0) L.kase = 3;
+    else L.kase = 4;
+    return L;
+}
+
+UpdateSpec update_spec(double al, double be, double eps) {
+    UpdateSpec u{};
+    u.eps = eps;
+    if (al == 0.0 && be == 1.0) {
+        u.log_case = 1;
+        return u;
+    }
+    double q = 1.0 / al - be / al;
+    double pexp = q > 1.0 ? 1.0 - be : (q < 0.0 ? al + be - 1.0 : al);
+    u.eta = 1.0 / pexp;
+    if (u.eta == 1.0) u.eta_code = POW_ID;
+    else if (u.eta == 2.0) u.eta_code = POW_SQ;
+    else if (u.eta == 0.5) u.eta_code = POW_SQRT;
+    else if (u.eta == -1.0) u.eta_code = POW_RCP;
+    else u.eta_code = POW_GENERAL;
+    return u;
+}
+
+}  // namespace nef
+
 namespace {
 
 // ------------------------------------------------------------- planning
@@ -607,67 +674,6 @@ void plan_generic(const nef_plan_s& p, int l, PassPlan& pp) {
 }
 
 // ------------------------------------------------------------- run time
-WeightSpec weight_spec(double al, double be) {
-    WeightSpec w{};
-    w.alpha = al;
-    w.beta = be;
-    auto code = [](double e) {
-        if (e == 0.0) return (int)POW_ONE;
-        if (e == 1.0) return (int)POW_ID;
-        if (e == -1.0) return (int)POW_RCP;
-        if (e == -0.5) return (int)POW_RSQRT;
-        if (e == 0.5) return (int)POW_SQRT;
-        if (e == 2.0) return (int)POW_SQ;
-        if (e == -1.5) return (int)POW_RSQRT3;
-        if (e == -2.0) return (int)POW_RCP2;
-        return (int)POW_GENERAL;
-    };
-    if (al == 0.0) {
-        w.log_case = 1;
-        w.y_code = POW_ONE;
-        w.a_code = POW_ONE;
-        w.b_code = POW_ONE;
-        return w;
-    }
-    w.e_y = al;
-    w.e_a = be - 1.0;
-    w.e_b = al + be - 1.0;
-    w.y_code = code(w.e_y);
-    w.a_code = code(w.e_a);
-    w.b_code = code(w.e_b);
-    return w;
-}
-
-LossSpec loss_spec(double al, double be) {
-    LossSpec L{};
-    L.alpha = al;
-    L.beta = be;
-    if (al != 0.0 && be != 0.0 && al + be != 0.0) L.kase = 0;
-    else if (be == 0.0 && al != 0.0) L.kase = 1;
-    else if (al == -be && al != 0.0) L.kase = 2;
-    else if (al == 0.0 && be != 0.0) L.kase = 3;
-    else L.kase = 4;
-    return L;
-}
-
-UpdateSpec update_spec(double al, double be, double eps) {
-    UpdateSpec u{};
-    u.eps = eps;
-    if (al == 0.0 && be == 1.0) {
-        u.log_case = 1;
-        return u;
-    }
-    double q = 1.0 / al - be / al;
-    double pexp = q > 1.0 ? 1.0 - be : (q < 0.0 ? al + be - 1.0 : al);
-    u.eta = 1.0 / pexp;
-    if (u.eta == 1.0) u.eta_code = POW_ID;
-    else if (u.eta == 2.0) u.eta_code = POW_SQ;
-    else if (u.eta == 0.5) u.eta_code = POW_SQRT;
-    else if (u.eta == -1.0) u.eta_code = POW_RCP;
-    else u.eta_code = POW_GENERAL;
-    return u;
-}
-
 void* buf_ptr(nef_plan_t p, int id) { return p->buf[id].ptr; }
 
 EinDesc bind(nef_plan_t p, const EinRecipe& r, void* const* factors) {
