@@ -420,53 +420,80 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
         }
     } else if (warp == 2 || warp == 3) {
         // ------------------------------------------------------ P / Q operand builders
+        // Thread q builds column q of every Q tile.  The gathered source rows of
+        // the next tile are loaded while the current tile is built, so the L2
+        // latency of the gathers overlaps the build and the wait for a free stage.
         const int q = tid - 64;  // 0..63
         constexpr int NCH = BP / 8;  // 16-byte chunks per bond row
         {
             const SrcDesc& ps = v.P.src[0];
             const uint16_t* pbase = static_cast<const uint16_t*>(ps.ptr);
-            for (int rr = q; rr < TM; rr += 64) {
-                const int64_t row = r0 + rr;
+            uint4 pv[2][NCH];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = r0 + q + 64 * h;
                 const bool ok = row < v.rows;
                 const int64_t pr = ok ? src_row_tc(ps, row) : 0;
 #pragma unroll
-                for (int j = 0; j < NCH; ++j) {
-                    uint4 val = make_uint4(0, 0, 0, 0);
-                    if (ok) val = *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8);
-                    *reinterpret_cast<uint4*>(sm + LY::kP + swz<RB>(rr * RB + j * 16)) = val;
-                }
+                for (int j = 0; j < NCH; ++j)
+                    pv[h][j] = ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8)
+                                  : make_uint4(0, 0, 0, 0);
             }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int j = 0; j < NCH; ++j)
+                    *reinterpret_cast<uint4*>(sm + LY::kP + swz<RB>((q + 64 * h) * RB + j * 16)) = pv[h][j];
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(pfull);
         }
-        for (int i = 0; i < T; ++i) {
-            const int sq = i % NSQ;
-            if (!mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8)) break;
+        const int nsrc = v.Q.nsrc;
+        // gathered rows of the first two sources for one tile (further sources are
+        // read while building)
+        auto load_tile = [&](int i, uint4 (&r)[2][NCH], int64_t (&srow)[kMaxSrc], bool& ok) {
             int64_t col0;
             int nvalid, x0, z0;
             tile_info(t_lo + i, col0, nvalid, x0, z0);
-            const bool ok = q < nvalid;
+            ok = q < nvalid;
             const int64_t col = col0 + q;
-            int64_t srow[kMaxSrc];
 #pragma unroll
-            for (int s = 0; s < kMaxSrc; ++s)
-                srow[s] = (ok && s < v.Q.nsrc) ? src_row_tc(v.Q.src[s], col) : 0;
+            for (int s2 = 0; s2 < kMaxSrc; ++s2)
+                srow[s2] = (ok && s2 < nsrc) ? src_row_tc(v.Q.src[s2], col) : 0;
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const uint16_t* sb = static_cast<const uint16_t*>(v.Q.src[s2 < nsrc ? s2 : 0].ptr);
+                const int64_t ld = v.Q.src[s2 < nsrc ? s2 : 0].ld;
+#pragma unroll
+                for (int j = 0; j < NCH; ++j)
+                    r[s2][j] = (ok && s2 < nsrc) ? *reinterpret_cast<const uint4*>(sb + srow[s2] * ld + j * 8)
+                                                 : make_uint4(0, 0, 0, 0);
+            }
+        };
+        auto build_tile = [&](int i, const uint4 (&r)[2][NCH], const int64_t (&srow)[kMaxSrc], bool ok) -> bool {
+            const int sq = i % NSQ;
+            if (!mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8)) return false;
             uint8_t* qdst = sm + LY::kQ + sq * LY::kQStage;
 #pragma unroll
             for (int j = 0; j < NCH; ++j) {
-                float acc[8];
+                float acc[8], f[8];
+                unpack_bf16x8(r[0][j], acc);
+                if (nsrc >= 2) {
+                    unpack_bf16x8(r[1][j], f);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) acc[e] = ok ? 1.0f : 0.0f;
-                if (ok) {
-                    for (int s = 0; s < v.Q.nsrc; ++s) {
-                        const uint16_t* sb = static_cast<const uint16_t*>(v.Q.src[s].ptr);
-                        const uint4 raw = *reinterpret_cast<const uint4*>(sb + srow[s] * v.Q.src[s].ld + j * 8);
-                        float f[8];
-                        unpack_bf16x8(raw, f);
+                    for (int e = 0; e < 8; ++e) acc[e] *= f[e];
+                }
+                for (int s2 = 2; s2 < nsrc; ++s2) {
+                    const uint16_t* sb = static_cast<const uint16_t*>(v.Q.src[s2].ptr);
+                    const uint4 raw = ok ? *reinterpret_cast<const uint4*>(sb + srow[s2] * v.Q.src[s2].ld + j * 8)
+                                         : make_uint4(0, 0, 0, 0);
+                    unpack_bf16x8(raw, f);
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) acc[e] *= f[e];
-                    }
+                    for (int e = 0; e < 8; ++e) acc[e] *= f[e];
+                }
+                if (!ok) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[e] = 0.0f;
                 }
                 uint4 outv;
                 outv.x = pack_bf16(acc[0], acc[1]);
@@ -478,6 +505,18 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(qfull(sq));
+            return true;
+        };
+        uint4 ra[2][NCH], rb[2][NCH];
+        int64_t sa[kMaxSrc], sb2[kMaxSrc];
+        bool oka = false, okb = false;
+        if (T > 0) load_tile(0, ra, sa, oka);
+        for (int i = 0; i < T; i += 2) {
+            if (i + 1 < T) load_tile(i + 1, rb, sb2, okb);
+            if (!build_tile(i, ra, sa, oka)) break;
+            if (i + 1 >= T) break;
+            if (i + 2 < T) load_tile(i + 2, ra, sa, oka);
+            if (!build_tile(i + 1, rb, sb2, okb)) break;
         }
     } else {
         // ------------------------------------------------------ epilogue (thread = row)
