@@ -13,9 +13,12 @@
 // yhat and the weights never leave the chip.  At the end the epilogue warps
 // copy S from TMEM to the per-split partial buffers.
 //
-// Warp roles (256 threads): warp 0 TMA producer + TMEM allocator, warp 1 MMA
-// issuer, warps 2-3 Q/P operand builders, warps 4-7 epilogue (thread = row =
-// TMEM lane).  Every mbarrier wait is bounded: on timeout the CTA raises an
+// Warp roles (448 threads): warp 0 TMA producer + TMEM allocator, warp 1 MMA
+// issuer, warps 2-5 Q/P operand builders (two threads per tile column, each
+// building half of the bond chunks), warps 6-13 epilogue.  Epilogue warp w
+// reads TMEM lanes 32*(w%4).. (one tile row per thread) and owns columns
+// 32*((w-6)/4)..+31 of each tile, so every SM sub-partition runs two epilogue
+// warps that hide each other's latency.  Every mbarrier wait is bounded: on timeout the CTA raises an
 // error flag, drains its own in-flight copies and MMAs, frees TMEM and exits.
 #pragma once
 
@@ -35,7 +38,10 @@ constexpr int TN = 64;         // columns per tile
 constexpr int NSY = 3;         // Y pipeline stages
 constexpr int NSQ = 3;         // Q pipeline stages
 constexpr int NW = 2;          // W buffers and yhat TMEM buffers
-constexpr int kThreads = 256;
+constexpr int kThreads = 448;   // 14 warps
+constexpr int kEpiWarps = 8;
+constexpr int kOpWarps = 4;
+constexpr int kEpiWarp0 = 2 + kOpWarps;  // first epilogue warp
 constexpr int kYStageBytes = TM * TN * 4;   // 32 KB
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -298,15 +304,15 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + LY::kMisc + 4);
 
     if (tid == 0) {
-        for (int s = 0; s < NSY; ++s) { mbar_init(yfull(s), 1); mbar_init(yempty(s), 4); }
-        for (int s = 0; s < NSQ; ++s) { mbar_init(qfull(s), 2); mbar_init(qempty(s), 1); }
+        for (int s = 0; s < NSY; ++s) { mbar_init(yfull(s), 1); mbar_init(yempty(s), kEpiWarps); }
+        for (int s = 0; s < NSQ; ++s) { mbar_init(qfull(s), kOpWarps); mbar_init(qempty(s), 1); }
         for (int b = 0; b < NW; ++b) {
             mbar_init(dfull(b), 1);
-            mbar_init(dempty(b), 4);
-            mbar_init(wfull(b), 4);
+            mbar_init(dempty(b), kEpiWarps);
+            mbar_init(wfull(b), kEpiWarps);
             mbar_init(wempty(b), 1);
         }
-        mbar_init(pfull, 2);
+        mbar_init(pfull, kOpWarps);
         mbar_init(sfull, 1);
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -418,109 +424,104 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             volatile int dummy_abort = 0;
             mbar_wait(drain, 0, &dummy_abort, prm.err, 7);
         }
-    } else if (warp == 2 || warp == 3) {
+    } else if (warp < kEpiWarp0) {
         // ------------------------------------------------------ P / Q operand builders
-        // Thread q builds column q of every Q tile.  The gathered source rows of
-        // the next tile are loaded while the current tile is built, so the L2
-        // latency of the gathers overlaps the build and the wait for a free stage.
-        const int q = tid - 64;  // 0..63
-        constexpr int NCH = BP / 8;  // 16-byte chunks per bond row
+        // Thread q builds bond chunks [hq*NH, hq*NH + NH) of column cq of every Q
+        // tile.  The gathered rows of the next tile are loaded while the current one
+        // is built, so the L2 latency of the gathers overlaps the build and the wait
+        // for a free stage.
+        const int q = tid - 64;                 // 0..127
+        constexpr int NCH = BP / 8;             // 16-byte chunks per bond row
+        constexpr int NH = NCH / 2;             // chunks per thread
+        const int cq = q & 63, hq = q >> 6;
         {
             const SrcDesc& ps = v.P.src[0];
             const uint16_t* pbase = static_cast<const uint16_t*>(ps.ptr);
-            uint4 pv[2][NCH];
+            const int64_t prow = r0 + q;
+            const bool ok = prow < v.rows;
+            const int64_t pr = ok ? src_row_tc(ps, prow) : 0;
+            uint4 pv[NCH];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t row = r0 + q + 64 * h;
-                const bool ok = row < v.rows;
-                const int64_t pr = ok ? src_row_tc(ps, row) : 0;
+            for (int j = 0; j < NCH; ++j)
+                pv[j] = ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-                for (int j = 0; j < NCH; ++j)
-                    pv[h][j] = ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8)
-                                  : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int j = 0; j < NCH; ++j)
-                    *reinterpret_cast<uint4*>(sm + LY::kP + swz<RB>((q + 64 * h) * RB + j * 16)) = pv[h][j];
+            for (int j = 0; j < NCH; ++j)
+                *reinterpret_cast<uint4*>(sm + LY::kP + swz<RB>(q * RB + j * 16)) = pv[j];
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(pfull);
         }
         const int nsrc = v.Q.nsrc;
-        // gathered rows of the first two sources for one tile (further sources are
-        // read while building)
-        auto load_tile = [&](int i, uint4 (&r)[2][NCH], int64_t (&srow)[kMaxSrc], bool& ok) {
+        const uint16_t* s0 = static_cast<const uint16_t*>(v.Q.src[0].ptr);
+        const uint16_t* s1 = static_cast<const uint16_t*>(v.Q.src[nsrc > 1 ? 1 : 0].ptr);
+        const int64_t ld0 = v.Q.src[0].ld, ld1 = v.Q.src[nsrc > 1 ? 1 : 0].ld;
+        uint4 nx0[NH], nx1[NH];
+        int64_t nrow[kMaxSrc];
+        bool nok = false;
+        auto issue = [&](int i) {  // gathered rows of tile i into nx0/nx1
             int64_t col0;
             int nvalid, x0, z0;
             tile_info(t_lo + i, col0, nvalid, x0, z0);
-            ok = q < nvalid;
-            const int64_t col = col0 + q;
+            nok = cq < nvalid;
+            const int64_t col = col0 + cq;
 #pragma unroll
             for (int s2 = 0; s2 < kMaxSrc; ++s2)
-                srow[s2] = (ok && s2 < nsrc) ? src_row_tc(v.Q.src[s2], col) : 0;
+                nrow[s2] = (nok && s2 < nsrc) ? src_row_tc(v.Q.src[s2], col) : 0;
 #pragma unroll
-            for (int s2 = 0; s2 < 2; ++s2) {
-                const uint16_t* sb = static_cast<const uint16_t*>(v.Q.src[s2 < nsrc ? s2 : 0].ptr);
-                const int64_t ld = v.Q.src[s2 < nsrc ? s2 : 0].ld;
-#pragma unroll
-                for (int j = 0; j < NCH; ++j)
-                    r[s2][j] = (ok && s2 < nsrc) ? *reinterpret_cast<const uint4*>(sb + srow[s2] * ld + j * 8)
-                                                 : make_uint4(0, 0, 0, 0);
+            for (int j = 0; j < NH; ++j) {
+                const int jj = hq * NH + j;
+                nx0[j] = nok ? *reinterpret_cast<const uint4*>(s0 + nrow[0] * ld0 + jj * 8) : make_uint4(0, 0, 0, 0);
+                nx1[j] = (nok && nsrc > 1) ? *reinterpret_cast<const uint4*>(s1 + nrow[1] * ld1 + jj * 8)
+                                           : make_uint4(0, 0, 0, 0);
             }
         };
-        auto build_tile = [&](int i, const uint4 (&r)[2][NCH], const int64_t (&srow)[kMaxSrc], bool ok) -> bool {
+        if (T > 0) issue(0);
+#pragma unroll 1
+        for (int i = 0; i < T; ++i) {
+            uint4 c0[NH], c1[NH];
+            int64_t crow[kMaxSrc];
+#pragma unroll
+            for (int j = 0; j < NH; ++j) { c0[j] = nx0[j]; c1[j] = nx1[j]; }
+#pragma unroll
+            for (int s2 = 0; s2 < kMaxSrc; ++s2) crow[s2] = nrow[s2];
+            const bool cok = nok;
+            if (i + 1 < T) issue(i + 1);
             const int sq = i % NSQ;
-            if (!mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8)) return false;
+            if (!mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8)) break;
             uint8_t* qdst = sm + LY::kQ + sq * LY::kQStage;
 #pragma unroll
-            for (int j = 0; j < NCH; ++j) {
+            for (int j = 0; j < NH; ++j) {
+                const int jj = hq * NH + j;
                 float acc[8], f[8];
-                unpack_bf16x8(r[0][j], acc);
-                if (nsrc >= 2) {
-                    unpack_bf16x8(r[1][j], f);
+                unpack_bf16x8(c0[j], acc);
+                if (nsrc > 1) {
+                    unpack_bf16x8(c1[j], f);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) acc[e] *= f[e];
                 }
                 for (int s2 = 2; s2 < nsrc; ++s2) {
                     const uint16_t* sb = static_cast<const uint16_t*>(v.Q.src[s2].ptr);
-                    const uint4 raw = ok ? *reinterpret_cast<const uint4*>(sb + srow[s2] * v.Q.src[s2].ld + j * 8)
-                                         : make_uint4(0, 0, 0, 0);
+                    const uint4 raw = cok ? *reinterpret_cast<const uint4*>(sb + crow[s2] * v.Q.src[s2].ld + jj * 8)
+                                          : make_uint4(0, 0, 0, 0);
                     unpack_bf16x8(raw, f);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) acc[e] *= f[e];
-                }
-                if (!ok) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) acc[e] = 0.0f;
                 }
                 uint4 outv;
                 outv.x = pack_bf16(acc[0], acc[1]);
                 outv.y = pack_bf16(acc[2], acc[3]);
                 outv.z = pack_bf16(acc[4], acc[5]);
                 outv.w = pack_bf16(acc[6], acc[7]);
-                *reinterpret_cast<uint4*>(qdst + swz<RB>(q * RB + j * 16)) = outv;
+                *reinterpret_cast<uint4*>(qdst + swz<RB>(cq * RB + jj * 16)) = outv;
             }
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(qfull(sq));
-            return true;
-        };
-        uint4 ra[2][NCH], rb[2][NCH];
-        int64_t sa[kMaxSrc], sb2[kMaxSrc];
-        bool oka = false, okb = false;
-        if (T > 0) load_tile(0, ra, sa, oka);
-        for (int i = 0; i < T; i += 2) {
-            if (i + 1 < T) load_tile(i + 1, rb, sb2, okb);
-            if (!build_tile(i, ra, sa, oka)) break;
-            if (i + 1 >= T) break;
-            if (i + 2 < T) load_tile(i + 2, ra, sa, oka);
-            if (!build_tile(i + 1, rb, sb2, okb)) break;
         }
     } else {
-        // ------------------------------------------------------ epilogue (thread = row)
-        const int e = tid - 128;                    // 0..127 == TMEM lane == tile row
+        // ------------------------------------------------------ epilogue
+        const int e = ((warp & 3) << 5) + lane;      // tile row == TMEM lane
+        const int h = (warp - kEpiWarp0) >> 2;        // column half of the tile
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         const int64_t row = r0 + e;
         const bool row_ok = row < v.rows;
@@ -529,13 +530,13 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             const bool ok = mbar_wait(bar, par, abort_flag, prm.err, code);
             return __all_sync(0xffffffffu, ok);
         };
+#pragma unroll 1
         for (int i = 0; i < T; ++i) {
             const int b = i & 1, s = i % NSY;
             if (!wwait(dfull(b), (i >> 1) & 1, 9)) break;
             tc_fence_after();
-            uint32_t yh0[32], yh1[32];
-            tmem_ld32(tmem + lane_off + b * TN, yh0);
-            tmem_ld32(tmem + lane_off + b * TN + 32, yh1);
+            uint32_t yh[32];
+            tmem_ld32(tmem + lane_off + b * TN + 32 * h, yh);
             tmem_wait_ld();
             tc_fence_before();
             __syncwarp();
@@ -545,65 +546,59 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             int nvalid, x0, z0;
             tile_info(t_lo + i, col0, nvalid, x0, z0);
             const uint8_t* ys = sm + LY::kY + s * kYStageBytes;
-            float yv[64];
+            float yv[32];
             if (prm.trans) {
 #pragma unroll
-                for (int c = 0; c < 64; ++c) yv[c] = *reinterpret_cast<const float*>(ys + c * (TM * 4) + e * 4);
+                for (int c = 0; c < 32; ++c)
+                    yv[c] = *reinterpret_cast<const float*>(ys + (32 * h + c) * (TM * 4) + e * 4);
             } else {
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float4 f = *reinterpret_cast<const float4*>(
-                            ys + h * (kYStageBytes / 2) + e * 128 + ((j ^ (e & 7)) << 4));
-                        yv[h * 32 + 4 * j + 0] = f.x;
-                        yv[h * 32 + 4 * j + 1] = f.y;
-                        yv[h * 32 + 4 * j + 2] = f.z;
-                        yv[h * 32 + 4 * j + 3] = f.w;
-                    }
+                for (int j = 0; j < 8; ++j) {
+                    const float4 f = *reinterpret_cast<const float4*>(ys + h * (kYStageBytes / 2) + e * 128 +
+                                                                      ((j ^ (e & 7)) << 4));
+                    yv[4 * j + 0] = f.x;
+                    yv[4 * j + 1] = f.y;
+                    yv[4 * j + 2] = f.z;
+                    yv[4 * j + 3] = f.w;
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(yempty(s));
-            // observed columns of this row: bit c of `obs`
-            uint64_t obs = nvalid >= 64 ? ~0ull : ((1ull << nvalid) - 1ull);
-            if (!row_ok) obs = 0;
+            // observed columns of this row within the half: bit c of `obs`
+            const int nv = min(32, max(0, nvalid - 32 * h));
+            uint32_t obs = row_ok ? (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u)) : 0u;
             if (prm.mbits && obs) {
+                const int64_t cbase = col0 + 32 * h;
                 if (prm.trans) {
-                    uint64_t m = 0;
-                    for (int c = 0; c < nvalid; ++c) {
-                        const int64_t idx = (col0 + c) * v.rows + row;
-                        m |= (uint64_t)mask_bit(prm.mbits, idx) << c;
-                    }
+                    uint32_t m = 0;
+                    for (int c = 0; c < nv; ++c)
+                        m |= (uint32_t)mask_bit(prm.mbits, (cbase + c) * v.rows + row) << c;
                     obs &= m;
                 } else {
-                    const int64_t idx0 = (col0 / v.c_in) * v.rows * v.c_in + row * v.c_in + (col0 % v.c_in);
+                    const int64_t idx0 = (cbase / v.c_in) * v.rows * v.c_in + row * v.c_in + (cbase % v.c_in);
                     const int64_t w0 = idx0 >> 5;
                     const int sh = (int)(idx0 & 31);
-                    const uint64_t lo = prm.mbits[w0];
-                    const uint64_t mid = prm.mbits[w0 + 1];
-                    const uint64_t hi = (sh && nvalid > 64 - sh) ? prm.mbits[w0 + 2] : 0ull;
-                    uint64_t m = (lo | (mid << 32)) >> sh;
-                    if (sh) m |= hi << (64 - sh);
-                    obs &= m;
+                    uint64_t m = prm.mbits[w0];
+                    if (sh) m |= (uint64_t)prm.mbits[w0 + 1] << 32;
+                    obs &= (uint32_t)(m >> sh);
                 }
             }
-            uint32_t wa2[32], wb2[32];
+            uint32_t wa2[16], wb2[16];
 #pragma unroll
-            for (int c = 0; c < 64; c += 2) {
-                float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
-                const float h0 = __uint_as_float(c < 32 ? yh0[c] : yh1[c - 32]);
-                const float h1 = __uint_as_float(c + 1 < 32 ? yh0[c + 1] : yh1[c - 31]);
-                if ((obs >> c) & 1ull) tc_weights<WK>(yv[c], h0, w, a0, b0);
-                if ((obs >> (c + 1)) & 1ull) tc_weights<WK>(yv[c + 1], h1, w, a1, b1);
-                wa2[c >> 1] = pack_bf16(a0, a1);
-                if (DEN) wb2[c >> 1] = pack_bf16(b0, b1);
+            for (int c = 0; c < 32; c += 2) {
+                float a0, b0, a1, b1;
+                tc_weights<WK>(yv[c], __uint_as_float(yh[c]), w, a0, b0);
+                tc_weights<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), w, a1, b1);
+                const bool o0 = (obs >> c) & 1u, o1 = (obs >> (c + 1)) & 1u;
+                wa2[c >> 1] = pack_bf16(o0 ? a0 : 0.f, o1 ? a1 : 0.f);
+                if (DEN) wb2[c >> 1] = pack_bf16(o0 ? b0 : 0.f, o1 ? b1 : 0.f);
             }
             if (!wwait(wempty(b), ((i >> 1) & 1) ^ 1, 11)) break;
             uint8_t* wa_dst = sm + LY::kWa + b * LY::kWStage;
             uint8_t* wb_dst = sm + LY::kWb + b * LY::kWStage;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t off = e * 128 + ((j ^ (e & 7)) << 4);
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t off = e * 128 + (((4 * h + j) ^ (e & 7)) << 4);
                 *reinterpret_cast<uint4*>(wa_dst + off) =
                     make_uint4(wa2[4 * j], wa2[4 * j + 1], wa2[4 * j + 2], wa2[4 * j + 3]);
                 if (DEN)
@@ -614,32 +609,28 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             __syncwarp();
             if (lane == 0) mbar_arrive(wfull(b));
         }
-        // ---- S readout (tcgen05.ld is warp-collective: every lane loads, valid rows store)
+        // ---- S readout: the first four epilogue warps copy S_num, the other four S_den
         bool have = (T > 0) && mbar_wait(sfull, 0, abort_flag, prm.err, 12);
         have = __all_sync(0xffffffffu, have);
         tc_fence_after();
-        float* dn = prm.s_num + (sp * v.rows + row) * BP;
-        float* dd = DEN ? prm.s_den + (sp * v.rows + row) * BP : nullptr;
+        if (h == 0 || DEN) {
+            const uint32_t tsrc = (h == 0) ? t_snum : t_sden;
+            float* dst = ((h == 0) ? prm.s_num : prm.s_den) + (sp * v.rows + row) * BP;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BP; c0 += 16) {
+                uint32_t r[16];
 #pragma unroll
-        for (int c0 = 0; c0 < BP; c0 += 16) {
-            uint32_t r[16], rd[16];
+                for (int k = 0; k < 16; ++k) r[k] = 0u;
+                if (have) {
+                    tmem_ld16(tsrc + lane_off + c0, r);
+                    tmem_wait_ld();
+                }
+                if (row_ok) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) { r[k] = 0u; rd[k] = 0u; }
-            if (have) {
-                tmem_ld16(t_snum + lane_off + c0, r);
-                if (DEN) tmem_ld16(t_sden + lane_off + c0, rd);
-                tmem_wait_ld();
-            }
-            if (row_ok) {
-#pragma unroll
-                for (int k = 0; k < 16; k += 4) {
-                    *reinterpret_cast<float4*>(dn + c0 + k) =
-                        make_float4(__uint_as_float(r[k]), __uint_as_float(r[k + 1]),
-                                    __uint_as_float(r[k + 2]), __uint_as_float(r[k + 3]));
-                    if (DEN)
-                        *reinterpret_cast<float4*>(dd + c0 + k) =
-                            make_float4(__uint_as_float(rd[k]), __uint_as_float(rd[k + 1]),
-                                        __uint_as_float(rd[k + 2]), __uint_as_float(rd[k + 3]));
+                    for (int k = 0; k < 16; k += 4)
+                        *reinterpret_cast<float4*>(dst + c0 + k) =
+                            make_float4(__uint_as_float(r[k]), __uint_as_float(r[k + 1]),
+                                        __uint_as_float(r[k + 2]), __uint_as_float(r[k + 3]));
                 }
             }
         }
