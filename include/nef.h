@@ -161,6 +161,37 @@ nef_status nef_plan_profile(nef_plan_t plan, double* ms, int* count, int reset);
 nef_status nef_check(nef_plan_t plan);
 
 /*
+ * nef_fit_batched -- fit many independent CP models "ir,jr,kr->ijk" at once,
+ * each from several starting points (random restarts; the paper's conclusion
+ * notes that the method benefits from multiple random initializations), by
+ * `iters` sweeps of Algorithm 1 per (problem, restart).  All restarts of a
+ * problem share each read of its Y.  The sweep loop is captured in one CUDA
+ * graph and launched once.
+ *   n          : number of problems
+ *   shapes     : host, n x 3 dimensions {I, J, K}
+ *   ranks      : host, n ranks R (1..32)
+ *   Y          : host array of n device pointers, row-major [I][J][K] floats
+ *   masks      : host array of n device pointers (N bytes each, nonzero =
+ *                observed), or NULL (every entry observed)
+ *   factors    : host array of n*restarts*3 device pointers: for problem p and
+ *                restart k, entries (p*restarts + k)*3 + {0,1,2} are A [I][R],
+ *                B [J][R], C [K][R], updated in place
+ *   restarts   : 1..16
+ *   alpha, beta, iters : as nef_fit
+ *   opt        : options (NULL = defaults); precision must be NEF_BF16
+ *   losses     : host, n*restarts doubles receiving the final sum of D over
+ *                observed entries per (problem, restart), or NULL
+ * Work buffers (a zero-padded copy of every Y, partials, operand copies) are
+ * allocated for the duration of the call.  Synchronises opt->stream.
+ * Errors: NEF_EINVAL, NEF_EUNSUPPORTED (precision or (alpha, beta)), NEF_ENOMEM
+ * or NEF_ECUDA (reported as NEF_ECUDA), NEF_ETIMEOUT (a bounded wait gave up).
+ */
+nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_t* ranks, const float* const* Y,
+                           const uint8_t* const* masks, float* const* factors, int restarts,
+                           double alpha, double beta, int iters, const nef_options* opt,
+                           double* losses);
+
+/*
  * nef_cp3_update_static -- update factor l of the 3-way CP model
  * "ir,jr,kr->ijk" in place (one inner step of the sweep, FP32, no mask)
  * without allocating any device memory.  The paper has no counterpart: this

@@ -26,6 +26,25 @@ extern "C" {
 int nef_tc_probe(int bond_pad, const uint16_t* P, const uint16_t* Q, const uint16_t* W, float* D1,
                  float* D2, int* err, void* stream);
 
+/*
+ * nef_tc_trace -- wait-cycle counters of the tensor-core fused pass, summed over
+ * every CTA of every launch on `plan` since the last reset (plans created with
+ * nef_options.profile only).  out (host) receives 32 values: out[0] = summed
+ * CTA lifetimes in SM cycles; out[k], k = 1..12 = cycles spent in bounded waits
+ * at site k: 1 producer waits for a free Y stage, 3 MMA waits for the P tile,
+ * 4 MMA waits for a Q tile, 5 MMA waits for a free yhat buffer, 6 MMA waits for
+ * a W tile, 8 operand warps wait for a free Q stage, 9 epilogue waits for yhat,
+ * 10 epilogue waits for Y, 11 epilogue waits for a free W buffer, 12 epilogue
+ * waits for the final S, 13 operand warps wait for staged source rows; busy
+ * phases: 16 operand look-ahead, 17 operand build, 18 operand fence and
+ * arrival, 20 epilogue TMEM load, 21 epilogue Y read, 22 epilogue weights,
+ * 23 epilogue W store, 24 epilogue fence and arrival (waits and phases of the
+ * operand and epilogue warps are counted once per warp).  reset != 0 clears the counters afterwards.  Returns 0, 1 for
+ * a plan without counters, 5 for a CUDA error.  Synchronises the plan's stream.
+ */
+typedef struct nef_plan_s* nef_plan_handle;
+int nef_tc_trace(nef_plan_handle plan, unsigned long long* out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@ from ._nef import (  # noqa: F401
     NefError,
     Plan,
     cp3_update_static,
+    fit_batched,
     load,
     split_model,
 )

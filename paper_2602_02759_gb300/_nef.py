@@ -21,9 +21,9 @@ PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 # every symbol include/nef.h declares
 EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_update",
            "nef_loss", "nef_plan_info", "nef_plan_launches", "nef_plan_profile", "nef_check",
-           "nef_cp3_update_static", "nef_last_error"]
+           "nef_fit_batched", "nef_cp3_update_static", "nef_last_error"]
 # every symbol include/nef_debug.h declares
-DEBUG_EXPORTS = ["nef_tc_probe"]
+DEBUG_EXPORTS = ["nef_tc_probe", "nef_tc_trace"]
 
 
 class Options(ctypes.Structure):
@@ -73,9 +73,15 @@ def load(path: str = LIB_PATH):
     lib.nef_check.argtypes = [vp]
     lib.nef_check.restype = ctypes.c_int
     lib.nef_last_error.restype = ctypes.c_char_p
+    lib.nef_fit_batched.argtypes = [ctypes.c_int, i64p, i64p, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, ctypes.POINTER(Options), dp]
+    lib.nef_fit_batched.restype = ctypes.c_int
     lib.nef_cp3_update_static.argtypes = [vp, i64p, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
     lib.nef_cp3_update_static.restype = ctypes.c_int
+    lib.nef_tc_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
+    lib.nef_tc_trace.restype = ctypes.c_int
     lib.nef_tc_probe.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.nef_tc_probe.restype = ctypes.c_int
     _lib = lib
@@ -97,6 +103,36 @@ def split_model(model_str: str):
         if ch not in rhs and ch not in latent:
             latent.append(ch)
     return list(rhs), latent, lhs.split(",")
+
+
+def fit_batched(Ys, masks, factors, alpha, beta, iters, eps=1e-10, stream=None, losses=True):
+    """nef_fit_batched: fit many CP models 'ir,jr,kr->ijk', each with several restarts.
+
+    Ys: list of n CUDA float32 [I, J, K] tensors; masks: None or a list of n uint8
+    tensors; factors: list over problems of lists over restarts of [A, B, C]
+    (CUDA float32, updated in place).  Returns an n x restarts list of losses."""
+    import torch
+    n = len(Ys)
+    restarts = len(factors[0])
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    shapes = (ctypes.c_int64 * (3 * n))(*[int(d) for y in Ys for d in y.shape])
+    ranks = (ctypes.c_int64 * n)(*[int(factors[p][0][0].shape[1]) for p in range(n)])
+    ys = (ctypes.c_void_p * n)(*[y.data_ptr() for y in Ys])
+    ms = None if masks is None else (ctypes.c_void_p * n)(*[m.data_ptr() for m in masks])
+    fs = (ctypes.c_void_p * (3 * n * restarts))(
+        *[f.data_ptr() for p in range(n) for k in range(restarts) for f in factors[p][k]])
+    opt = Options()
+    load().nef_default_options(ctypes.byref(opt))
+    opt.precision = NEF_BF16
+    opt.eps = float(eps)
+    opt.stream = ctypes.c_void_p(stream.cuda_stream)
+    out = (ctypes.c_double * (n * restarts))() if losses else None
+    check(load().nef_fit_batched(n, shapes, ranks, ys, ms, fs, restarts, float(alpha), float(beta), int(iters),
+                                 ctypes.byref(opt), out))
+    if not losses:
+        return None
+    return [[out[p * restarts + k] for k in range(restarts)] for p in range(n)]
 
 
 def cp3_update_static(Y, factors, l, alpha, beta, eps=1e-10, stream=None):
@@ -220,6 +256,14 @@ class Plan:
         cnt = (ctypes.c_int * 2)()
         check(load().nef_plan_profile(self._h, ms, cnt, int(bool(reset))))
         return {"tcgen05": (ms[0], cnt[0]), "simt": (ms[1], cnt[1])}
+
+    def tc_trace(self, reset: bool = True):
+        """Wait-cycle counters of the tensor-core pass (see include/nef_debug.h)."""
+        out = (ctypes.c_ulonglong * 32)()
+        rc = load().nef_tc_trace(self._h, out, int(bool(reset)))
+        if rc:
+            raise NefError(rc, "tensor-core trace unavailable (plan needs profile=True)")
+        return list(out)
 
     def info(self) -> str:
         n = load().nef_plan_info(self._h, None, 0)

@@ -236,6 +236,104 @@ __global__ void k_generic_weights(GenericRecon g, const T* __restrict__ y, const
     }
 }
 
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+    uint32_t u = __float_as_uint(x);
+    uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);  // round to nearest even (finite inputs)
+    return (uint16_t)(r >> 16);
+}
+
+template <typename T>
+__device__ __forceinline__ void decode_letters(int64_t e, int nlet, const int64_t* dim, int64_t* idx) {
+    for (int q = nlet - 1; q >= 0; --q) {
+        idx[q] = e % dim[q];
+        e /= dim[q];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void write_mirrors(const MirrorDesc& m, const int64_t* idx, int nlet, T v) {
+    for (int k = 0; k < m.n; ++k) {
+        int64_t off = 0;
+        for (int q = 0; q < nlet; ++q) off += idx[q] * m.st[k][q];
+        static_cast<T*>(m.p32[k])[off] = v;
+        if (m.p16[k]) m.p16[k][off] = bf16_bits((float)v);
+    }
+}
+
+template <typename T>
+__global__ void k_finish(FinishDesc d, UpdateSpec u) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    int64_t idx[kMaxFacLet];
+    decode_letters<T>(e, d.nlet, d.dim, idx);
+    int64_t soff = 0, boff = 0;
+    for (int q = 0; q < d.nlet; ++q) {
+        soff += idx[q] * d.s_st[q];
+        boff += idx[q] * d.b_st[q];
+    }
+    const T* pn = static_cast<const T*>(d.part_num);
+    T num = T(0);
+    for (int s = 0; s < d.n_split; ++s) num += pn[(int64_t)s * d.s_size + soff];
+    T den;
+    if (d.part_den) {
+        const T* pd = static_cast<const T*>(d.part_den);
+        den = T(0);
+        for (int s = 0; s < d.n_split; ++s) den += pd[(int64_t)s * d.s_size + soff];
+    } else {
+        den = T(1);
+        for (int s = 0; s < d.n_cs; ++s) den *= static_cast<const T*>(d.cs[s])[boff];
+    }
+    T* th = static_cast<T*>(d.theta);
+    const T v = mu_update(th[e], num, den, u);
+    th[e] = v;
+    write_mirrors<T>(d.mir, idx, d.nlet, v);
+}
+
+struct LetterDims {
+    int64_t d[kMaxFacLet];
+};
+
+template <typename T>
+__global__ void k_update_mirror(T* __restrict__ theta, const T* __restrict__ num, const T* __restrict__ den,
+                                int64_t n, UpdateSpec u, int nlet, LetterDims dim, MirrorDesc m) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const T v = mu_update(theta[e], num[e], den[e], u);
+    theta[e] = v;
+    int64_t idx[kMaxFacLet];
+    decode_letters<T>(e, nlet, dim.d, idx);
+    write_mirrors<T>(m, idx, nlet, v);
+}
+
+template <typename T>
+__global__ void k_mirror_init(const T* __restrict__ theta, int64_t n, int nlet, LetterDims dim, MirrorDesc m) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int64_t idx[kMaxFacLet];
+    decode_letters<T>(e, nlet, dim.d, idx);
+    write_mirrors<T>(m, idx, nlet, theta[e]);
+}
+
+// Column sums of canonical operands: block (job, column).
+template <typename T>
+__global__ void k_colsums(ColsumDesc d) {
+    const ColsumJob& j = d.job[blockIdx.x];
+    const int64_t b = blockIdx.y;
+    if (b >= j.ld) return;
+    const T* src = static_cast<const T*>(j.src);
+    T acc = T(0);
+    for (int64_t r = threadIdx.x; r < j.n_rows; r += blockDim.x) acc += src[r * j.ld + b];
+    __shared__ T sh[kThreads / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T t = T(0);
+        for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+        static_cast<T*>(j.out)[b] = t;
+    }
+}
+
 inline unsigned blocks_for(int64_t n, int threads = kThreads) {
     return (unsigned)((n + threads - 1) / threads);
 }
@@ -263,6 +361,38 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
     dim3 grid(blocks_for(d.n_out_el), (unsigned)n_split);
     k_einsum_part<T><<<grid, kThreads, 0, st>>>(d, chunk, partial);
     k_einsum_final<T><<<blocks_for(d.n_out_el), kThreads, 0, st>>>(d, (int)n_split, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t st) {
+    k_finish<T><<<blocks_for(d.n), kThreads, 0, st>>>(d, u);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
+                                 int nlet, const int64_t* dim, const MirrorDesc& m, cudaStream_t st) {
+    LetterDims ld{};
+    for (int q = 0; q < nlet; ++q) ld.d[q] = dim[q];
+    k_update_mirror<T><<<blocks_for(n), kThreads, 0, st>>>(theta, num, den, n, u, nlet, ld, m);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mirror_init(const T* theta, int64_t n, int nlet, const int64_t* dim,
+                               const MirrorDesc& m, cudaStream_t st) {
+    if (m.n == 0) return cudaSuccess;
+    LetterDims ld{};
+    for (int q = 0; q < nlet; ++q) ld.d[q] = dim[q];
+    k_mirror_init<T><<<blocks_for(n), kThreads, 0, st>>>(theta, n, nlet, ld, m);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_colsums(const ColsumDesc& d, int64_t max_ld, cudaStream_t st) {
+    if (d.n == 0) return cudaSuccess;
+    k_colsums<T><<<dim3((unsigned)d.n, (unsigned)max_ld), kThreads, 0, st>>>(d);
     return cudaGetLastError();
 }
 
@@ -330,7 +460,17 @@ cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint
                                                    const uint32_t*, const WeightSpec&, T*, T*, \
                                                    const LossSpec*, double*, int, cudaStream_t);
 
+#define NEF_INST2(T)                                                                          \
+    template cudaError_t launch_finish<T>(const FinishDesc&, const UpdateSpec&, cudaStream_t);    \
+    template cudaError_t launch_update_mirror<T>(T*, const T*, const T*, int64_t, const UpdateSpec&, \
+                                                 int, const int64_t*, const MirrorDesc&, cudaStream_t); \
+    template cudaError_t launch_mirror_init<T>(const T*, int64_t, int, const int64_t*,             \
+                                               const MirrorDesc&, cudaStream_t);                   \
+    template cudaError_t launch_colsums<T>(const ColsumDesc&, int64_t, cudaStream_t);
+
 NEF_INST(float)
 NEF_INST(double)
+NEF_INST2(float)
+NEF_INST2(double)
 
 }  // namespace nef

@@ -4,15 +4,22 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "k_view_tc.cuh"
 #include "nef_internal.h"
 
 namespace nef {
 namespace tc {
-cudaError_t launch_bp16(const CUtensorMap&, const Params&, int, int, int, cudaStream_t);
-cudaError_t launch_bp32(const CUtensorMap&, const Params&, int, int, int, cudaStream_t);
-cudaError_t launch_bp64(const CUtensorMap&, const Params&, int, int, int, cudaStream_t);
+cudaError_t launch_bp16(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp32(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp64(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_batched_bp16(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
+cudaError_t launch_batched_bp32(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 }  // namespace tc
 
 namespace {
@@ -40,6 +47,34 @@ int weight_kind(const WeightSpec& w) {
     return tc::WK_GEN;
 }
 
+// Operand mode 1 applies when every 64-column tile starts at a multiple of 64 and,
+// within a tile, one column-side source has consecutive rows (single index term,
+// divisor 1, modulus a multiple of 64) and the other, if any, a single row
+// (divisor a multiple of 64).  Returns the sources' indices or false.
+bool regular_q(const ViewDesc& v, int* q_var, int* q_const) {
+    const int TN = tc::TN;
+    if (v.Q.nsrc < 1 || v.Q.nsrc > 2) return false;
+    if (v.c_in != 1 && v.c_in % TN != 0) return false;
+    int var = -1, cst = -1;
+    for (int s = 0; s < v.Q.nsrc; ++s) {
+        const SrcDesc& d = v.Q.src[s];
+        if (d.nterm != 1 || d.mul[0] != 1) return false;
+        if (d.div[0] == 1 && d.mod[0] % TN == 0) {
+            if (var >= 0) return false;
+            var = s;
+        } else if (d.div[0] % TN == 0) {
+            if (cst >= 0) return false;
+            cst = s;
+        } else {
+            return false;
+        }
+    }
+    if (var < 0) return false;
+    *q_var = var;
+    *q_const = cst;
+    return true;
+}
+
 }  // namespace
 
 bool tc_view_supported(const ViewDesc& v, int) {
@@ -58,13 +93,14 @@ bool tc_view_supported(const ViewDesc& v, int) {
     return true;
 }
 
-cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w,
-                           int need_den, int n_split, float* s_num, float* s_den, int* err_flag,
-                           cudaStream_t st, TcLaunchInfo* info) {
-    if (!tc_view_supported(v, need_den)) return cudaErrorNotSupported;
+namespace {
+
+// Kernel parameters and tensor maps of one view pass.
+cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w, int n_split,
+                        float* s_num, float* s_den, int* err_flag, unsigned long long* trace, CUtensorMap* map,
+                        CUtensorMap* vmap, CUtensorMap* cmap, tc::Params* p, int* n_rb_out) {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    CUtensorMap map;
     const bool trans = (v.c_in == 1);
     CUresult r;
     if (trans) {
@@ -72,7 +108,7 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         cuuint64_t strides[1] = {(cuuint64_t)v.rows * 4};
         cuuint32_t box[2] = {(cuuint32_t)tc::TM, (cuuint32_t)tc::TN};
         cuuint32_t es[2] = {1, 1};
-        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(y), dims, strides, box, es,
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(y), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
@@ -80,33 +116,103 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         cuuint64_t strides[2] = {(cuuint64_t)v.c_in * 4, (cuuint64_t)v.c_in * v.rows * 4};
         cuuint32_t box[3] = {32, (cuuint32_t)tc::TM, 1};
         cuuint32_t es[3] = {1, 1, 1};
-        r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(y), dims, strides, box, es,
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(y), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    tc::Params p{};
-    p.mbits = mbits;
-    p.v = v;
-    p.w = w;
-    p.trans = trans ? 1 : 0;
-    p.n_cib = trans ? 1 : (v.c_in + tc::TN - 1) / tc::TN;
-    p.n_tiles = trans ? (v.c_out + tc::TN - 1) / tc::TN : v.c_out * p.n_cib;
-    p.tiles_per_split = (p.n_tiles + n_split - 1) / n_split;
-    p.s_num = s_num;
-    p.s_den = s_den;
-    p.err = err_flag;
-    const int64_t n_rb = (v.rows + tc::TM - 1) / tc::TM;
-    const int grid = (int)(n_rb * n_split);
+    *p = tc::Params{};
+    *vmap = *map;  // unused unless the Q operand is TMA-staged
+    *cmap = *map;
+    int q_var = -1, q_const = -1;
+    if (getenv("NEF_TC_GATHER") == nullptr && regular_q(v, &q_var, &q_const)) {
+        const SrcDesc& d = v.Q.src[q_var];
+        cuuint64_t vd[2] = {(cuuint64_t)d.ld, (cuuint64_t)d.mod[0]};
+        cuuint64_t vs[1] = {(cuuint64_t)d.ld * 2};
+        cuuint32_t vb[2] = {(cuuint32_t)v.bond_pad, (cuuint32_t)tc::TN};
+        cuuint32_t ves[2] = {1, 1};
+        const CUtensorMapSwizzle sw = v.bond_pad == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                      : (v.bond_pad == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+        r = enc(vmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(d.ptr), vd, vs, vb, ves,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        if (q_const >= 0) {
+            const SrcDesc& c = v.Q.src[q_const];
+            cuuint64_t cd[2] = {(cuuint64_t)c.ld, (cuuint64_t)c.mod[0]};
+            cuuint64_t cstr[1] = {(cuuint64_t)c.ld * 2};
+            cuuint32_t cb[2] = {(cuuint32_t)v.bond_pad, 1};
+            r = enc(cmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(c.ptr), cd, cstr, cb, ves,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        }
+        p->qmode = 1;
+        p->q_var = q_var;
+        p->q_const = q_const;
+    }
+    p->mbits = mbits;
+    p->v = v;
+    p->w = w;
+    p->trans = trans ? 1 : 0;
+    p->n_cib = trans ? 1 : (v.c_in + tc::TN - 1) / tc::TN;
+    p->n_tiles = trans ? (v.c_out + tc::TN - 1) / tc::TN : v.c_out * p->n_cib;
+    p->tiles_per_split = (p->n_tiles + n_split - 1) / n_split;
+    p->s_num = s_num;
+    p->s_den = s_den;
+    p->err = err_flag;
+    p->trace = trace;
+    *n_rb_out = (int)((v.rows + tc::TM - 1) / tc::TM);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w,
+                           int need_den, int n_split, float* s_num, float* s_den, int* err_flag,
+                           cudaStream_t st, TcLaunchInfo* info, unsigned long long* trace) {
+    if (!tc_view_supported(v, need_den)) return cudaErrorNotSupported;
+    CUtensorMap map, vmap, cmap;
+    tc::Params p;
+    int n_rb = 0;
+    cudaError_t e =
+        make_params(y, mbits, v, w, n_split, s_num, s_den, err_flag, trace, &map, &vmap, &cmap, &p, &n_rb);
+    if (e != cudaSuccess) return e;
+    const int grid = n_rb * n_split;
     if (info) {
         info->n_ctas = grid;
         info->smem_bytes = 0;
     }
     const int wk = weight_kind(w);
     switch (v.bond_pad) {
-        case 16: return tc::launch_bp16(map, p, need_den, wk, grid, st);
-        case 32: return tc::launch_bp32(map, p, need_den, wk, grid, st);
-        default: return tc::launch_bp64(map, p, need_den, wk, grid, st);
+        case 16: return tc::launch_bp16(map, vmap, cmap, p, need_den, wk, grid, st);
+        case 32: return tc::launch_bp32(map, vmap, cmap, p, need_den, wk, grid, st);
+        default: return tc::launch_bp64(map, vmap, cmap, p, need_den, wk, grid, st);
+    }
+}
+
+static_assert(sizeof(tc::Params) <= sizeof(TcUnit::prm), "TcUnit parameter area too small");
+
+bool tc_make_unit(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w, int n_split,
+                  float* s_num, float* s_den, int* err_flag, TcUnit* unit, int* n_rb) {
+    if (!tc_view_supported(v, 1)) return false;
+    tc::Params p;
+    if (make_params(y, mbits, v, w, n_split, s_num, s_den, err_flag, nullptr, &unit->ymap, &unit->vmap, &unit->cmap, &p,
+                    n_rb) != cudaSuccess)
+        return false;
+    memset(unit->prm, 0, sizeof(unit->prm));
+    memcpy(unit->prm, &p, sizeof(p));
+    return true;
+}
+
+cudaError_t launch_view_tc_batched(const TcUnit* units, const TcWork* work, int n_work, int bp, int need_den,
+                                   const WeightSpec& w, cudaStream_t st) {
+    if (n_work <= 0) return cudaSuccess;
+    const int wk = weight_kind(w);
+    switch (bp) {
+        case 16: return tc::launch_batched_bp16(units, work, n_work, need_den, wk, st);
+        case 32: return tc::launch_batched_bp32(units, work, n_work, need_den, wk, st);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -27,6 +27,7 @@
 
 #include <cstdint>
 
+#include "nef_batched.h"
 #include "nef_device.cuh"
 #include "nef_internal.h"
 
@@ -35,15 +36,14 @@ namespace tc {
 
 constexpr int TM = 128;        // rows per CTA (TMEM lanes)
 constexpr int TN = 64;         // columns per tile
-constexpr int NSY = 3;         // Y pipeline stages
-constexpr int NSQ = 3;         // Q pipeline stages
-constexpr int NW = 2;          // W buffers and yhat TMEM buffers
+constexpr int ND = 4;          // yhat TMEM buffers (MMA1 runs two tiles ahead)
+constexpr int NW = 2;          // W buffers
 constexpr int kThreads = 448;   // 14 warps
 constexpr int kEpiWarps = 8;
 constexpr int kOpWarps = 4;
 constexpr int kEpiWarp0 = 2 + kOpWarps;  // first epilogue warp
 constexpr int kYStageBytes = TM * TN * 4;   // 32 KB
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 enum WeightKind { WK_GEN = 0, WK_KL = 1, WK_B05 = 2, WK_HEL = 3 };
@@ -59,7 +59,14 @@ struct Params {
     float* s_num;
     float* s_den;
     int* err;
+    unsigned long long* trace;  // optional: [kTraceSites] summed wait cycles per wait site
+    // Q operand mode: 0 = gathered rows (any view); 1 = within every tile source
+    // q_var has consecutive rows (TMA-staged with the Y tile) and source q_const
+    // (or none, -1) a single row
+    int qmode, q_var, q_const;
 };
+
+constexpr int kTraceSites = 32;   // 0: CTA lifetime cycles, 1..13: wait sites, 16..: busy phases
 
 // ------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -92,13 +99,17 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait.  Returns false (and raises the CTA abort flag) on timeout or
-// when another role already aborted.
+// when another role already aborted.  With a trace array, the cycles spent
+// waiting are added to trace[code].
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int code) {
+                                          int* err, int code, unsigned long long* trace = nullptr) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try(bar, parity)) return true;
+        if (mbar_try(bar, parity)) {
+            if (trace) atomicAdd(&trace[code], (unsigned long long)(clock64() - t0));
+            return true;
+        }
         if ((it & 15) == 0) {
             if (*abort_flag) return false;
             if (clock64() - t0 > kWaitCycles) {
@@ -107,6 +118,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
                 return false;
             }
         }
+    }
+}
+
+// Busy-phase timer for the trace (lane 0 of a warp adds cycles since *t to site).
+__device__ __forceinline__ void phase_mark(unsigned long long* tr, int site, long long& t) {
+    if (tr) {
+        const long long now = clock64();
+        atomicAdd(&tr[site], (unsigned long long)(now - t));
+        t = now;
     }
 }
 
@@ -243,6 +263,15 @@ __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& 
 
 __device__ __forceinline__ int64_t src_row_tc(const SrcDesc& s, int64_t i) {
     int64_t r = 0;
+    if ((uint64_t)i < 0xffffffffull) {  // 32-bit division when the index fits (div, mod <= index range)
+        const uint32_t i32 = (uint32_t)i;
+        for (int t = 0; t < s.nterm; ++t) {
+            const uint32_t d = (uint32_t)min(s.div[t], (int64_t)0xffffffff);
+            const uint32_t m = (uint32_t)min(s.mod[t], (int64_t)0xffffffff);
+            r += (int64_t)((i32 / d) % m) * s.mul[t];
+        }
+        return r;
+    }
     for (int t = 0; t < s.nterm; ++t) r += ((i / s.div[t]) % s.mod[t]) * s.mul[t];
     return r;
 }
@@ -250,28 +279,44 @@ __device__ __forceinline__ int64_t src_row_tc(const SrcDesc& s, int64_t i) {
 // ---------------------------------------------------------- shared layout
 template <int BP, bool DEN>
 struct Layout {
+    static constexpr int NSY = 3;                            // Y (and V) pipeline stages
+    static constexpr int NSQ = DEN ? 3 : 4;                  // Q pipeline stages
     static constexpr int RB = BP * 2;                        // bytes per bond row (BF16)
     static constexpr int kY = 0;                             // NSY x 32 KB
-    static constexpr int kQ = kY + NSY * kYStageBytes;       // NSQ x TN x RB
+    static constexpr int kV = kY + NSY * kYStageBytes;       // NSY x TN x RB: TMA-staged source rows
+    static constexpr int kQ = kV + NSY * TN * RB;            // NSQ x TN x RB
     static constexpr int kQStage = TN * RB;
     static constexpr int kP = kQ + NSQ * kQStage;            // TM x RB
     static constexpr int kWa = kP + TM * RB;                 // NW x 16 KB
     static constexpr int kWStage = TM * TN * 2;
     static constexpr int kWb = kWa + NW * kWStage;
-    static constexpr int kBar = kWb + (DEN ? NW * kWStage : 0);
-    // barriers: yfull[NSY], yempty[NSY], qfull[NSQ], qempty[NSQ], dfull[NW], dempty[NW],
+    // NSY slots of kGSlot bytes: TMA-staged constant row (tensor-copy destinations are
+    // 128-byte aligned)
+    static constexpr int kGSlot = 128;
+    static constexpr int kG = kWb + (DEN ? NW * kWStage : 0);
+    static constexpr int kBar = kG + NSY * kGSlot;
+    static_assert(kY % 1024 == 0 && kV % 1024 == 0 && (TN * RB) % 256 == 0 && kG % 128 == 0 &&
+                      kGSlot >= RB,
+                  "TMA destinations must stay aligned");
+    // barriers: yfull[NSY], yempty[NSY], qfull[NSQ], qempty[NSQ], dfull[ND], dempty[ND],
     //           wfull[NW], wempty[NW], pfull, sfull, drain
-    static constexpr int kNumBars = 2 * NSY + 2 * NSQ + 4 * NW + 3;
+    static constexpr int kNumBars = 2 * NSY + 2 * NSQ + 2 * ND + 2 * NW + 3;
     static constexpr int kMisc = kBar + kNumBars * 8;         // tmem slot + abort flag
-    static constexpr int kTotal = kMisc + 16;
+    static constexpr int kTrace = kMisc + 16;                 // kTraceSites counters
+    static constexpr int kTotal = kTrace + kTraceSites * 8;
     static constexpr int kAlloc = kTotal + 1024;              // slack for 1024-B alignment
 };
 
+// The fused pass of one CTA: rows [rb*TM, rb*TM + TM) of the view and the
+// column tiles of split sp.
 template <int BP, bool DEN, int WK>
-__global__ void __launch_bounds__(kThreads, 1)
-k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
+__device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUtensorMap* vmap,
+                                             const CUtensorMap* cmap, const Params& prm, const int64_t rb,
+                                             const int64_t sp) {
     using LY = Layout<BP, DEN>;
     constexpr int RB = LY::RB;
+    constexpr int NSY = LY::NSY;
+    constexpr int NSQ = LY::NSQ;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t base = (raw_addr + 1023u) & ~1023u;
@@ -280,9 +325,6 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const ViewDesc& v = prm.v;
-    const int64_t n_rb = (v.rows + TM - 1) / TM;
-    const int64_t rb = blockIdx.x % n_rb;
-    const int64_t sp = blockIdx.x / n_rb;
     const int64_t r0 = rb * TM;
     const int64_t t_lo = sp * prm.tiles_per_split;
     const int64_t t_hi = min(t_lo + prm.tiles_per_split, prm.n_tiles);
@@ -294,21 +336,29 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
     auto qfull = [&](int s) { return bar0 + 8u * (2 * NSY + s); };
     auto qempty = [&](int s) { return bar0 + 8u * (2 * NSY + NSQ + s); };
     auto dfull = [&](int b) { return bar0 + 8u * (2 * NSY + 2 * NSQ + b); };
-    auto dempty = [&](int b) { return bar0 + 8u * (2 * NSY + 2 * NSQ + NW + b); };
-    auto wfull = [&](int b) { return bar0 + 8u * (2 * NSY + 2 * NSQ + 2 * NW + b); };
-    auto wempty = [&](int b) { return bar0 + 8u * (2 * NSY + 2 * NSQ + 3 * NW + b); };
-    const uint32_t pfull = bar0 + 8u * (2 * NSY + 2 * NSQ + 4 * NW);
+    auto dempty = [&](int b) { return bar0 + 8u * (2 * NSY + 2 * NSQ + ND + b); };
+    auto wfull = [&](int b) { return bar0 + 8u * (2 * NSY + 2 * NSQ + 2 * ND + b); };
+    auto wempty = [&](int b) { return bar0 + 8u * (2 * NSY + 2 * NSQ + 2 * ND + NW + b); };
+    const uint32_t pfull = bar0 + 8u * (2 * NSY + 2 * NSQ + 2 * ND + 2 * NW);
     const uint32_t sfull = pfull + 8u;
     const uint32_t drain = pfull + 16u;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + LY::kMisc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + LY::kMisc + 4);
+    unsigned long long* tr = prm.trace ? reinterpret_cast<unsigned long long*>(sm + LY::kTrace) : nullptr;
+    const long long t_start = clock64();
+    if (tr && tid < kTraceSites) tr[tid] = 0ull;
 
     if (tid == 0) {
-        for (int s = 0; s < NSY; ++s) { mbar_init(yfull(s), 1); mbar_init(yempty(s), kEpiWarps); }
+        for (int s = 0; s < NSY; ++s) {
+            mbar_init(yfull(s), 1);
+            mbar_init(yempty(s), kEpiWarps + (prm.qmode ? kOpWarps : 0));
+        }
         for (int s = 0; s < NSQ; ++s) { mbar_init(qfull(s), kOpWarps); mbar_init(qempty(s), 1); }
-        for (int b = 0; b < NW; ++b) {
+        for (int b = 0; b < ND; ++b) {
             mbar_init(dfull(b), 1);
             mbar_init(dempty(b), kEpiWarps);
+        }
+        for (int b = 0; b < NW; ++b) {
             mbar_init(wfull(b), kEpiWarps);
             mbar_init(wempty(b), 1);
         }
@@ -328,8 +378,8 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t t_snum = tmem + 2 * TN;
-    const uint32_t t_sden = tmem + 2 * TN + BP;
+    const uint32_t t_snum = tmem + ND * TN;
+    const uint32_t t_sden = tmem + ND * TN + BP;
 
     auto tile_info = [&](int64_t t, int64_t& col0, int& nvalid, int& x0, int& z0) {
         if (prm.trans) {
@@ -339,8 +389,10 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             x0 = (int)co0;
             z0 = 0;
         } else {
-            const int64_t co = t / prm.n_cib;
-            const int64_t ci0 = (t % prm.n_cib) * TN;
+            const int64_t co = ((uint64_t)t < 0xffffffffull && (uint64_t)prm.n_cib < 0xffffffffull)
+                                   ? (int64_t)((uint32_t)t / (uint32_t)prm.n_cib)
+                                   : t / prm.n_cib;
+            const int64_t ci0 = (t - co * prm.n_cib) * TN;
             col0 = co * v.c_in + ci0;
             nvalid = (int)min((int64_t)TN, v.c_in - ci0);
             x0 = (int)ci0;
@@ -354,17 +406,26 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             int issued = 0;
             for (int i = 0; i < T; ++i) {
                 const int s = i % NSY;
-                if (!mbar_wait(yempty(s), ((i / NSY) & 1) ^ 1, abort_flag, prm.err, 1)) break;
+                if (!mbar_wait(yempty(s), ((i / NSY) & 1) ^ 1, abort_flag, prm.err, 1, tr)) break;
                 int64_t col0;
                 int nvalid, x0, z0;
                 tile_info(t_lo + i, col0, nvalid, x0, z0);
                 const uint32_t dst = base + LY::kY + s * kYStageBytes;
-                mbar_expect_tx(yfull(s), kYStageBytes);
+                const bool crow_tma = prm.qmode && prm.q_const >= 0;
+                mbar_expect_tx(yfull(s), kYStageBytes + (prm.qmode ? TN * RB : 0) + (crow_tma ? RB : 0));
+                if (prm.qmode) {
+                    const int vrow = (int)src_row_tc(v.Q.src[prm.q_var], col0);
+                    tma_load_2d(base + LY::kV + s * (TN * RB), vmap, 0, vrow, yfull(s));
+                    if (crow_tma) {
+                        const int crow = (int)src_row_tc(v.Q.src[prm.q_const], col0);
+                        tma_load_2d(base + LY::kG + s * LY::kGSlot, cmap, 0, crow, yfull(s));
+                    }
+                }
                 if (prm.trans) {
-                    tma_load_2d(dst, &ymap, (int)r0, x0, yfull(s));
+                    tma_load_2d(dst, ymap, (int)r0, x0, yfull(s));
                 } else {
-                    tma_load_3d(dst, &ymap, x0, (int)r0, z0, yfull(s));
-                    tma_load_3d(dst + kYStageBytes / 2, &ymap, x0 + 32, (int)r0, z0, yfull(s));
+                    tma_load_3d(dst, ymap, x0, (int)r0, z0, yfull(s));
+                    tma_load_3d(dst + kYStageBytes / 2, ymap, x0 + 32, (int)r0, z0, yfull(s));
                 }
                 issued = i + 1;
             }
@@ -379,44 +440,47 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
         if (lane == 0) {
             constexpr uint32_t idesc1 = make_idesc(TM, TN, 0, 0);
             constexpr uint32_t idesc2 = make_idesc(TM, BP, 0, 1);
-            bool ok = mbar_wait(pfull, 0, abort_flag, prm.err, 3);
+            bool ok = mbar_wait(pfull, 0, abort_flag, prm.err, 3, tr);
             const uint32_t p_addr = base + LY::kP;
-            for (int i = 0; ok && i <= T; ++i) {
-                if (i < T) {
-                    const int sq = i % NSQ, b = i & 1;
-                    if (!mbar_wait(qfull(sq), (i / NSQ) & 1, abort_flag, prm.err, 4)) break;
-                    if (!mbar_wait(dempty(b), ((i >> 1) & 1) ^ 1, abort_flag, prm.err, 5)) break;
-                    tc_fence_after();
-                    const uint32_t q_addr = base + LY::kQ + sq * LY::kQStage;
+            // MMA1 of tile i: yhat into TMEM buffer i % ND
+            auto mma1 = [&](int i) -> bool {
+                const int sq = i % NSQ, b = i % ND;
+                if (!mbar_wait(qfull(sq), (i / NSQ) & 1, abort_flag, prm.err, 4, tr)) return false;
+                if (!mbar_wait(dempty(b), ((i / ND) & 1) ^ 1, abort_flag, prm.err, 5, tr)) return false;
+                tc_fence_after();
+                const uint32_t q_addr = base + LY::kQ + sq * LY::kQStage;
 #pragma unroll
-                    for (int k = 0; k < BP / 16; ++k) {
-                        const uint64_t ad = make_sdesc(p_addr + k * 32, 16, 8 * RB, swz_code(RB));
-                        const uint64_t bd = make_sdesc(q_addr + k * 32, 16, 8 * RB, swz_code(RB));
-                        tc_mma(tmem + b * TN, ad, bd, idesc1, k > 0 ? 1u : 0u);
-                    }
-                    tc_commit(dfull(b));
+                for (int k = 0; k < BP / 16; ++k) {
+                    const uint64_t ad = make_sdesc(p_addr + k * 32, 16, 8 * RB, swz_code(RB));
+                    const uint64_t bd = make_sdesc(q_addr + k * 32, 16, 8 * RB, swz_code(RB));
+                    tc_mma(tmem + b * TN, ad, bd, idesc1, k > 0 ? 1u : 0u);
                 }
-                if (i >= 1) {
-                    const int u = i - 1, bu = u & 1, squ = u % NSQ;
-                    if (!mbar_wait(wfull(bu), (u >> 1) & 1, abort_flag, prm.err, 6)) break;
-                    tc_fence_after();
-                    const uint32_t wa_addr = base + LY::kWa + bu * LY::kWStage;
-                    const uint32_t wb_addr = base + LY::kWb + bu * LY::kWStage;
-                    const uint32_t q_addr = base + LY::kQ + squ * LY::kQStage;
+                tc_commit(dfull(b));
+                return true;
+            };
+            if (ok && T > 0) ok = mma1(0);
+            if (ok && T > 1) ok = mma1(1);
+            for (int i = 0; ok && i < T; ++i) {
+                if (i + 2 < T && !mma1(i + 2)) break;
+                const int bw = i & 1, sq = i % NSQ;
+                if (!mbar_wait(wfull(bw), (i >> 1) & 1, abort_flag, prm.err, 6, tr)) break;
+                tc_fence_after();
+                const uint32_t wa_addr = base + LY::kWa + bw * LY::kWStage;
+                const uint32_t wb_addr = base + LY::kWb + bw * LY::kWStage;
+                const uint32_t q_addr = base + LY::kQ + sq * LY::kQStage;
 #pragma unroll
-                    for (int k = 0; k < TN / 16; ++k) {
-                        const uint64_t bd = make_sdesc(q_addr + k * 16 * RB, TN * RB, 8 * RB, swz_code(RB));
-                        const uint64_t ad = make_sdesc(wa_addr + k * 32, 16, 1024, swz_code(128));
-                        const uint32_t acc = (u > 0 || k > 0) ? 1u : 0u;
-                        tc_mma(t_snum, ad, bd, idesc2, acc);
-                        if (DEN) {
-                            const uint64_t ad2 = make_sdesc(wb_addr + k * 32, 16, 1024, swz_code(128));
-                            tc_mma(t_sden, ad2, bd, idesc2, acc);
-                        }
+                for (int k = 0; k < TN / 16; ++k) {
+                    const uint64_t bd = make_sdesc(q_addr + k * 16 * RB, TN * RB, 8 * RB, swz_code(RB));
+                    const uint64_t ad = make_sdesc(wa_addr + k * 32, 16, 1024, swz_code(128));
+                    const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
+                    tc_mma(t_snum, ad, bd, idesc2, acc);
+                    if (DEN) {
+                        const uint64_t ad2 = make_sdesc(wb_addr + k * 32, 16, 1024, swz_code(128));
+                        tc_mma(t_sden, ad2, bd, idesc2, acc);
                     }
-                    tc_commit(wempty(bu));
-                    tc_commit(qempty(squ));
                 }
+                tc_commit(wempty(bw));
+                tc_commit(qempty(sq));
             }
             tc_commit(sfull);
             // drain: wait until every MMA issued by this thread has completed
@@ -451,6 +515,63 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             __syncwarp();
             if (lane == 0) mbar_arrive(pfull);
         }
+        if (prm.qmode) {
+            // rows of source q_var and the single row of source q_const (if any) arrive
+            // with the Y tile (TMA); Q = their elementwise product
+            const bool has_c = prm.q_const >= 0;
+            long long tp = clock64();
+            const bool trl = tr && lane == 0;
+#pragma unroll 1
+            for (int i = 0; i < T; ++i) {
+                int64_t col0;
+                int nvalid, x0, z0;
+                tile_info(t_lo + i, col0, nvalid, x0, z0);
+                const bool ok = cq < nvalid;
+                const int s = i % NSY, sq = i % NSQ;
+                if (!__all_sync(0xffffffffu, mbar_wait(yfull(s), (i / NSY) & 1, abort_flag, prm.err, 13,
+                                                       lane == 0 ? tr : nullptr)))
+                    break;
+                if (!__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8,
+                                                       lane == 0 ? tr : nullptr)))
+                    break;
+                if (trl) tp = clock64();
+                const uint8_t* vsrc = sm + LY::kV + s * (TN * RB);
+                const uint8_t* gsrc = sm + LY::kG + s * LY::kGSlot;
+                uint8_t* qdst = sm + LY::kQ + sq * LY::kQStage;
+#pragma unroll
+                for (int j = 0; j < NH; ++j) {
+                    const int jj = hq * NH + j;
+                    const uint32_t off = swz<RB>(cq * RB + jj * 16);
+                    uint4 outv = make_uint4(0, 0, 0, 0);
+                    if (ok) {
+                        const uint4 raw = *reinterpret_cast<const uint4*>(vsrc + off);
+                        if (has_c) {
+                            const uint4 gv = *reinterpret_cast<const uint4*>(gsrc + jj * 16);
+                            float acc[8], f[8];
+                            unpack_bf16x8(raw, acc);
+                            unpack_bf16x8(gv, f);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) acc[e] *= f[e];
+                            outv.x = pack_bf16(acc[0], acc[1]);
+                            outv.y = pack_bf16(acc[2], acc[3]);
+                            outv.z = pack_bf16(acc[4], acc[5]);
+                            outv.w = pack_bf16(acc[6], acc[7]);
+                        } else {
+                            outv = raw;
+                        }
+                    }
+                    *reinterpret_cast<uint4*>(qdst + off) = outv;
+                }
+                if (trl) phase_mark(tr, 17, tp);
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(yempty(s));
+                    mbar_arrive(qfull(sq));
+                }
+                if (trl) phase_mark(tr, 18, tp);
+            }
+        } else {
         const int nsrc = v.Q.nsrc;
         const uint16_t* s0 = static_cast<const uint16_t*>(v.Q.src[0].ptr);
         const uint16_t* s1 = static_cast<const uint16_t*>(v.Q.src[nsrc > 1 ? 1 : 0].ptr);
@@ -487,7 +608,9 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             const bool cok = nok;
             if (i + 1 < T) issue(i + 1);
             const int sq = i % NSQ;
-            if (!mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8,
+                                                   lane == 0 ? tr : nullptr)))
+                break;
             uint8_t* qdst = sm + LY::kQ + sq * LY::kQStage;
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
@@ -518,6 +641,7 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             __syncwarp();
             if (lane == 0) mbar_arrive(qfull(sq));
         }
+        }
     } else {
         // ------------------------------------------------------ epilogue
         const int e = ((warp & 3) << 5) + lane;      // tile row == TMEM lane
@@ -527,21 +651,26 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
         const bool row_ok = row < v.rows;
         const WeightSpec w = prm.w;
         auto wwait = [&](uint32_t bar, uint32_t par, int code) {
-            const bool ok = mbar_wait(bar, par, abort_flag, prm.err, code);
+            const bool ok = mbar_wait(bar, par, abort_flag, prm.err, code, lane == 0 ? tr : nullptr);
             return __all_sync(0xffffffffu, ok);
         };
+        const bool trl = tr && lane == 0;
+        long long tp = clock64();
 #pragma unroll 1
         for (int i = 0; i < T; ++i) {
-            const int b = i & 1, s = i % NSY;
-            if (!wwait(dfull(b), (i >> 1) & 1, 9)) break;
+            const int bd = i % ND, b = i & 1, s = i % NSY;
+            if (!wwait(dfull(bd), (i / ND) & 1, 9)) break;
+            if (trl) tp = clock64();
             tc_fence_after();
             uint32_t yh[32];
-            tmem_ld32(tmem + lane_off + b * TN + 32 * h, yh);
+            tmem_ld32(tmem + lane_off + bd * TN + 32 * h, yh);
             tmem_wait_ld();
+            if (trl) phase_mark(tr, 20, tp);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(dempty(b));
+            if (lane == 0) mbar_arrive(dempty(bd));
             if (!wwait(yfull(s), (i / NSY) & 1, 10)) break;
+            if (trl) tp = clock64();
             int64_t col0;
             int nvalid, x0, z0;
             tile_info(t_lo + i, col0, nvalid, x0, z0);
@@ -564,6 +693,7 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(yempty(s));
+            if (trl) phase_mark(tr, 21, tp);
             // observed columns of this row within the half: bit c of `obs`
             const int nv = min(32, max(0, nvalid - 32 * h));
             uint32_t obs = row_ok ? (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u)) : 0u;
@@ -593,7 +723,9 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
                 wa2[c >> 1] = pack_bf16(o0 ? a0 : 0.f, o1 ? a1 : 0.f);
                 if (DEN) wb2[c >> 1] = pack_bf16(o0 ? b0 : 0.f, o1 ? b1 : 0.f);
             }
+            if (trl) phase_mark(tr, 22, tp);
             if (!wwait(wempty(b), ((i >> 1) & 1) ^ 1, 11)) break;
+            if (trl) tp = clock64();
             uint8_t* wa_dst = sm + LY::kWa + b * LY::kWStage;
             uint8_t* wb_dst = sm + LY::kWb + b * LY::kWStage;
 #pragma unroll
@@ -605,12 +737,14 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
                     *reinterpret_cast<uint4*>(wb_dst + off) =
                         make_uint4(wb2[4 * j], wb2[4 * j + 1], wb2[4 * j + 2], wb2[4 * j + 3]);
             }
+            if (trl) phase_mark(tr, 23, tp);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(wfull(b));
+            if (trl) phase_mark(tr, 24, tp);
         }
         // ---- S readout: the first four epilogue warps copy S_num, the other four S_den
-        bool have = (T > 0) && mbar_wait(sfull, 0, abort_flag, prm.err, 12);
+        bool have = (T > 0) && mbar_wait(sfull, 0, abort_flag, prm.err, 12, lane == 0 ? tr : nullptr);
         have = __all_sync(0xffffffffu, have);
         tc_fence_after();
         if (h == 0 || DEN) {
@@ -637,11 +771,37 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, Params prm) {
         tc_fence_before();
     }
     __syncthreads();
+    if (tr && tid < kTraceSites) {
+        const unsigned long long v = (tid == 0) ? (unsigned long long)(clock64() - t_start) : tr[tid];
+        atomicAdd(&prm.trace[tid], v);
+    }
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");
     }
+}
+
+template <int BP, bool DEN, int WK>
+__global__ void __launch_bounds__(kThreads, 1)
+k_view_tc(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap vmap,
+          const __grid_constant__ CUtensorMap cmap, const __grid_constant__ Params prm) {
+    const int64_t n_rb = (prm.v.rows + TM - 1) / TM;
+    view_tc_body<BP, DEN, WK>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb, blockIdx.x / n_rb);
+}
+
+// Batched form: CTA b runs work[b] = (unit, row block, split); the unit's tensor
+// maps stay in global memory and its parameters are staged in shared memory.
+template <int BP, bool DEN, int WK>
+__global__ void __launch_bounds__(kThreads, 1)
+k_view_tc_batched(const TcUnit* __restrict__ units, const TcWork* __restrict__ work) {
+    __shared__ __align__(16) unsigned char prm_sh[(sizeof(Params) + 15) / 16 * 16];
+    const TcWork wk = work[blockIdx.x];
+    const TcUnit* U = units + wk.unit;
+    for (int i = threadIdx.x; i < (int)(sizeof(prm_sh) / 16); i += blockDim.x)
+        reinterpret_cast<uint4*>(prm_sh)[i] = reinterpret_cast<const uint4*>(U->prm)[i];
+    __syncthreads();
+    view_tc_body<BP, DEN, WK>(&U->ymap, &U->vmap, &U->cmap, *reinterpret_cast<const Params*>(prm_sh), wk.rb, wk.sp);
 }
 
 }  // namespace tc

@@ -6,30 +6,54 @@ namespace nef {
 namespace tc {
 
 template <int BP, bool DEN, int WK>
-cudaError_t launch_one(const CUtensorMap& map, const Params& p, int grid, cudaStream_t st) {
+cudaError_t launch_one(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int grid,
+                       cudaStream_t st) {
     auto kern = k_view_tc<BP, DEN, WK>;
     const int sm = Layout<BP, DEN>::kAlloc;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, sm, st>>>(map, p);
+    kern<<<grid, kThreads, sm, st>>>(map, vmap, cmap, p);
     return cudaGetLastError();
 }
 
 template <int BP>
-cudaError_t launch_bp(const CUtensorMap& map, const Params& p, int den, int wk, int grid, cudaStream_t st) {
+cudaError_t launch_bp(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int den,
+                      int wk, int grid, cudaStream_t st) {
     if (den) {
         switch (wk) {
-            case WK_KL: return launch_one<BP, true, WK_KL>(map, p, grid, st);
-            case WK_B05: return launch_one<BP, true, WK_B05>(map, p, grid, st);
-            case WK_HEL: return launch_one<BP, true, WK_HEL>(map, p, grid, st);
-            default: return launch_one<BP, true, WK_GEN>(map, p, grid, st);
+            case WK_KL: return launch_one<BP, true, WK_KL>(map, vmap, cmap, p, grid, st);
+            case WK_B05: return launch_one<BP, true, WK_B05>(map, vmap, cmap, p, grid, st);
+            case WK_HEL: return launch_one<BP, true, WK_HEL>(map, vmap, cmap, p, grid, st);
+            default: return launch_one<BP, true, WK_GEN>(map, vmap, cmap, p, grid, st);
         }
     }
     switch (wk) {
-        case WK_KL: return launch_one<BP, false, WK_KL>(map, p, grid, st);
-        case WK_HEL: return launch_one<BP, false, WK_HEL>(map, p, grid, st);
-        default: return launch_one<BP, false, WK_GEN>(map, p, grid, st);
+        case WK_KL: return launch_one<BP, false, WK_KL>(map, vmap, cmap, p, grid, st);
+        case WK_HEL: return launch_one<BP, false, WK_HEL>(map, vmap, cmap, p, grid, st);
+        default: return launch_one<BP, false, WK_GEN>(map, vmap, cmap, p, grid, st);
     }
+}
+
+template <int BP, bool DEN, int WK>
+cudaError_t launch_batched_one(const TcUnit* units, const TcWork* work, int n_work, cudaStream_t st) {
+    auto kern = k_view_tc_batched<BP, DEN, WK>;
+    const int sm = Layout<BP, DEN>::kAlloc;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<n_work, kThreads, sm, st>>>(units, work);
+    return cudaGetLastError();
+}
+
+template <int BP>
+cudaError_t launch_batched_bp(const TcUnit* units, const TcWork* work, int n_work, int den, int wk,
+                              cudaStream_t st) {
+    if (den) {
+        switch (wk) {
+            case WK_KL: return launch_batched_one<BP, true, WK_KL>(units, work, n_work, st);
+            default: return launch_batched_one<BP, true, WK_GEN>(units, work, n_work, st);
+        }
+    }
+    return launch_batched_one<BP, false, WK_GEN>(units, work, n_work, st);
 }
 
 }  // namespace tc
@@ -38,9 +62,19 @@ cudaError_t launch_bp(const CUtensorMap& map, const Params& p, int den, int wk, 
 #define NEF_TC_INSTANCE(BP)                                                                  \
     namespace nef {                                                                          \
     namespace tc {                                                                           \
-    cudaError_t launch_bp##BP(const CUtensorMap& map, const Params& p, int den, int wk,      \
-                              int grid, cudaStream_t st) {                                   \
-        return launch_bp<BP>(map, p, den, wk, grid, st);                                     \
+    cudaError_t launch_bp##BP(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, \
+                              const Params& p, int den, int wk, int grid, cudaStream_t st) { \
+        return launch_bp<BP>(map, vmap, cmap, p, den, wk, grid, st);                         \
+    }                                                                                        \
+    }                                                                                        \
+    }
+
+#define NEF_TC_BATCHED_INSTANCE(BP)                                                          \
+    namespace nef {                                                                          \
+    namespace tc {                                                                           \
+    cudaError_t launch_batched_bp##BP(const TcUnit* units, const TcWork* work, int n_work,   \
+                                      int den, int wk, cudaStream_t st) {                    \
+        return launch_batched_bp<BP>(units, work, n_work, den, wk, st);                      \
     }                                                                                        \
     }                                                                                        \
     }

@@ -95,6 +95,63 @@ struct EinDesc {
     int accumulate;                        // 1: out += result, 0: out = result
 };
 
+// ----------------------------------------------------- finishing a pass
+constexpr int kMaxMirror = 8;
+constexpr int kMaxFacLet = 8;
+
+// Canonical operand copies of one factor that its update writes directly
+// (element e of the factor, decoded over the factor's letters in term order,
+// goes to offset sum_q idx[q] * st[k][q] of copy k).
+struct MirrorDesc {
+    int n;
+    void* p32[kMaxMirror];          // copy in the plan's element type
+    uint16_t* p16[kMaxMirror];      // BF16 copy of the same layout, or null
+    int64_t st[kMaxMirror][kMaxFacLet];
+};
+
+// Split reduction + denominator + update (Eq. 3.4) + copies, for passes whose
+// epilogue is a relabelling of S[rows][bond_pad] onto the factor's layout.
+struct FinishDesc {
+    int nlet;
+    int64_t dim[kMaxFacLet];        // the factor's letter sizes, term order
+    int64_t s_st[kMaxFacLet];       // offset into S per letter
+    int64_t b_st[kMaxFacLet];       // offset into the bond vector per letter (closed-form den)
+    const void* part_num;           // [n_split][s_size]
+    const void* part_den;           // [n_split][s_size], or null: closed-form den
+    int n_split;
+    int64_t s_size;
+    int n_cs;                       // closed-form den = product of these column sums
+    const void* cs[kMaxSrc];
+    void* theta;
+    int64_t n;
+    MirrorDesc mir;
+};
+
+struct ColsumJob {
+    const void* src;                // canonical [n_rows x ld] operand
+    int64_t n_rows, ld;
+    void* out;                      // [ld] column sums
+};
+constexpr int kMaxColsumJobs = 16;
+struct ColsumDesc {
+    int n;
+    ColsumJob job[kMaxColsumJobs];
+};
+
+template <typename T>
+cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
+                                 int nlet, const int64_t* dim, const MirrorDesc& m, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_mirror_init(const T* theta, int64_t n, int nlet, const int64_t* dim,
+                               const MirrorDesc& m, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_colsums(const ColsumDesc& d, int64_t max_ld, cudaStream_t st);
+
 // Message returned by nef_last_error() on this thread.
 void set_last_error(const char* msg);
 
@@ -157,7 +214,8 @@ cudaError_t launch_convert_bf16(const float* src, int64_t n, uint16_t* dst, cuda
 
 cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v,
                            const WeightSpec& w, int need_den, int n_split, float* s_num,
-                           float* s_den, int* err_flag, cudaStream_t st, TcLaunchInfo* info);
+                           float* s_den, int* err_flag, cudaStream_t st, TcLaunchInfo* info,
+                           unsigned long long* trace = nullptr);
 
 bool tc_view_supported(const ViewDesc& v, int need_den);
 

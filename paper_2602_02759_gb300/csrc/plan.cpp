@@ -164,13 +164,17 @@ struct EinRecipe {
 };
 
 enum BufId { B_NUM = 0, B_DEN, B_SNUM, B_SDEN, B_SPART_N, B_SPART_D, B_DENVEC, B_COLSUM0,
-             B_WA = 20, B_WB, B_SRC0 = 32 };
+             B_WA = 20, B_WB, B_SRC0 = 32, B_CS0 = 4096 };
 
 struct SourcePlan {
     EinRecipe build;       // writes the canonical [n x ld] matrix into buffer src_buf
     int buf;               // buffer id (>= B_SRC0)
     int64_t n_rows;        // rows of the canonical matrix
     SrcDesc desc;          // index terms (ptr bound at run time)
+    int copy_of = -1;      // factor whose relabelled copy this is (kept current by its update)
+    std::vector<int> deps;             // factors the build reads
+    std::vector<int64_t> built_at;     // their versions when last built (empty = stale)
+    int cs_buf = -1;       // column sums of this operand (closed-form denominators), or -1
 };
 
 struct PassPlan {
@@ -191,6 +195,7 @@ struct PassPlan {
     int n_split = 1;
     int64_t cost = 0;
     std::string desc;
+    bool finish_identity = false;     // epilogue is a relabelling of S: fused finish kernel
     // generic
     EinRecipe gen_num, gen_den;
 };
@@ -218,12 +223,18 @@ struct nef_plan_s {
     double* loss_out = nullptr;
     int* flag = nullptr;
     int* tc_err = nullptr;
+    unsigned long long* tc_trace = nullptr;  // wait-cycle counters of the tensor-core pass (profiling)
     std::vector<uint16_t*> src_bf16;  // per buffer id >= B_SRC0 (BF16 plans)
     std::string info;
     // profiling: event pairs around fused-pass launches, per kernel family
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     size_t ev_next = 0;
+    // canonical operand copies kept current by each factor's update
+    std::vector<std::vector<std::pair<int, int>>> mirrors_of;   // factor -> (pass, source: -1 = P)
+    std::vector<int64_t> fac_version;
+    int64_t version_counter = 0;
+    int64_t max_ld = 16;
 };
 
 namespace nef {
@@ -715,13 +726,6 @@ nef_status run_ein(nef_plan_t p, const EinRecipe& r, void* const* factors, cudaS
         if (s_ != NEF_OK) return s_;   \
     } while (0)
 
-template <typename T>
-nef_status prepare_sources(nef_plan_t p, PassPlan& pp, void* const* factors, cudaStream_t st) {
-    NEF_TRY(run_ein<T>(p, pp.P.build, factors, st));
-    for (auto& q : pp.Q) NEF_TRY(run_ein<T>(p, q.build, factors, st));
-    return NEF_OK;
-}
-
 ViewDesc bind_view(nef_plan_t p, const PassPlan& pp, bool bf16) {
     ViewDesc v = pp.view;
     v.P.nsrc = 1;
@@ -733,6 +737,100 @@ ViewDesc bind_view(nef_plan_t p, const PassPlan& pp, bool bf16) {
         v.Q.src[k].ptr = bf16 ? (const void*)p->src_bf16[pp.Q[k].buf] : buf_ptr(p, pp.Q[k].buf);
     }
     return v;
+}
+
+SourcePlan& source_ref(PassPlan& pp, int k) { return k < 0 ? pp.P : pp.Q[k]; }
+
+// The canonical copies of factor f that its update writes (FP32/FP64 and BF16).
+MirrorDesc mirror_desc(nef_plan_t p, int f) {
+    MirrorDesc m{};
+    const Model& md = p->md;
+    for (auto& ps : p->mirrors_of[f]) {
+        SourcePlan& sp = source_ref(p->pass[ps.first], ps.second);
+        const int k = m.n++;
+        m.p32[k] = buf_ptr(p, sp.buf);
+        m.p16[k] = (p->prec == NEF_BF16) ? p->src_bf16[sp.buf] : nullptr;
+        for (size_t q = 0; q < md.term[f].size(); ++q) {
+            const int x = md.term[f][q];
+            const auto it = std::find(sp.build.out_let.begin(), sp.build.out_let.end(), x);
+            m.st[k][q] = sp.build.out_st[it - sp.build.out_let.begin()];
+        }
+    }
+    return m;
+}
+
+// Column-sum jobs for the closed-form denominators that read copies of factor f
+// (f < 0: every factor).
+ColsumDesc colsum_jobs(nef_plan_t p, int f) {
+    ColsumDesc d{};
+    for (int g = 0; g < p->md.L; ++g) {
+        if (f >= 0 && g != f) continue;
+        for (auto& ps : p->mirrors_of[g]) {
+            SourcePlan& sp = source_ref(p->pass[ps.first], ps.second);
+            if (sp.cs_buf < 0 || d.n >= kMaxColsumJobs) continue;
+            ColsumJob& j = d.job[d.n++];
+            j.src = buf_ptr(p, sp.buf);
+            j.n_rows = sp.n_rows;
+            j.ld = sp.desc.ld;
+            j.out = buf_ptr(p, sp.cs_buf);
+        }
+    }
+    return d;
+}
+
+bool source_stale(nef_plan_t p, const SourcePlan& sp) {
+    if (sp.copy_of >= 0) return false;
+    if (sp.built_at.size() != sp.deps.size()) return true;
+    for (size_t k = 0; k < sp.deps.size(); ++k)
+        if (sp.built_at[k] != p->fac_version[sp.deps[k]]) return true;
+    return false;
+}
+
+// Start of every call: the caller may have changed the factors, so rebuild every
+// kept copy from them and mark the contracted operands stale.
+template <typename T>
+nef_status init_sources(nef_plan_t p, void* const* factors, cudaStream_t st) {
+    const Model& md = p->md;
+    for (int f = 0; f < md.L; ++f) {
+        p->fac_version[f] = ++p->version_counter;
+        if (p->mirrors_of[f].empty()) continue;
+        MirrorDesc m = mirror_desc(p, f);
+        std::vector<int64_t> dims;
+        for (int x : md.term[f]) dims.push_back(md.dim[x]);
+        NEF_CUDA(launch_mirror_init<T>(static_cast<const T*>(factors[f]), md.fac_size(f), (int)dims.size(),
+                                       dims.data(), m, st));
+    }
+    ColsumDesc cs = colsum_jobs(p, -1);
+    NEF_CUDA(launch_colsums<T>(cs, p->max_ld, st));
+    return NEF_OK;
+}
+
+// Rebuild the contracted operands of a pass whose factors changed since their last build.
+template <typename T>
+nef_status refresh_sources(nef_plan_t p, PassPlan& pp, void* const* factors, cudaStream_t st, bool bf16) {
+    for (int k = -1; k < (int)pp.Q.size(); ++k) {
+        SourcePlan& sp = source_ref(pp, k);
+        if (!source_stale(p, sp)) continue;
+        NEF_TRY(run_ein<T>(p, sp.build, factors, st));
+        if constexpr (sizeof(T) == 4) {
+            if (bf16)
+                NEF_CUDA(launch_convert_bf16(static_cast<const float*>(buf_ptr(p, sp.buf)),
+                                             sp.n_rows * pp.view.bond_pad, p->src_bf16[sp.buf], st));
+        }
+        sp.built_at.clear();
+        for (int g : sp.deps) sp.built_at.push_back(p->fac_version[g]);
+    }
+    return NEF_OK;
+}
+
+// After factor l changed: its copies were written by the update; refresh the
+// column sums that read them and bump its version.
+template <typename T>
+nef_status after_update(nef_plan_t p, int l, cudaStream_t st) {
+    ColsumDesc cs = colsum_jobs(p, l);
+    NEF_CUDA(launch_colsums<T>(cs, p->max_ld, st));
+    p->fac_version[l] = ++p->version_counter;
+    return NEF_OK;
 }
 
 // Event pair for one profiled launch (pool grows on demand, reused after reset).
@@ -755,6 +853,9 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
     const int64_t nl = md.fac_size(pp.l);
     T* num = static_cast<T*>(buf_ptr(p, B_NUM));
     T* den = static_cast<T*>(buf_ptr(p, B_DEN));
+    std::vector<int64_t> ldims;
+    for (int x : md.term[pp.l]) ldims.push_back(md.dim[x]);
+    const MirrorDesc mir = mirror_desc(p, pp.l);
     if (pp.generic) {
         GenericRecon g{};
         g.n_obs = md.M;
@@ -772,50 +873,62 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
                                            static_cast<T*>(buf_ptr(p, B_WB)), nullptr, nullptr, 0, st));
         NEF_TRY(run_ein<T>(p, pp.gen_num, factors, st));
         NEF_TRY(run_ein<T>(p, pp.gen_den, factors, st));
-        NEF_CUDA(launch_update<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, st));
-        return NEF_OK;
+        NEF_CUDA(launch_update_mirror<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, (int)ldims.size(),
+                                         ldims.data(), mir, st));
+        return after_update<T>(p, pp.l, st);
     }
     const bool b_is_one = (w.log_case || w.b_code == POW_ONE);
     const bool closed = pp.den_closed && b_is_one && mbits == nullptr;
     const int need_den = closed ? 0 : 1;
-    NEF_TRY(prepare_sources<T>(p, pp, factors, st));
+    bool use_tc = false;
+    if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den);
+    NEF_TRY(refresh_sources<T>(p, pp, factors, st, use_tc));
     const int64_t sz = pp.view.rows * pp.view.bond_pad;
     T* spn = static_cast<T*>(buf_ptr(p, B_SPART_N));
     T* spd = static_cast<T*>(buf_ptr(p, B_SPART_D));
-    bool used_tc = false;
-    if constexpr (sizeof(T) == 4) {
-        if (p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den)) {
-            NEF_CUDA(launch_convert_bf16(static_cast<const float*>(buf_ptr(p, pp.P.buf)),
-                                         pp.P.n_rows * pp.view.bond_pad, p->src_bf16[pp.P.buf], st));
-            for (auto& q : pp.Q)
-                NEF_CUDA(launch_convert_bf16(static_cast<const float*>(buf_ptr(p, q.buf)),
-                                             q.n_rows * pp.view.bond_pad, p->src_bf16[q.buf], st));
+    const int n_split = pp.n_split;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->opt.profile) NEF_TRY(prof_begin(p, st, &e0, &e1));
+    if (use_tc) {
+        if constexpr (sizeof(T) == 4) {
             ViewDesc v = bind_view(p, pp, true);
             TcLaunchInfo info{};
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (p->opt.profile) NEF_TRY(prof_begin(p, st, &e0, &e1));
-            NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den,
-                                    pp.n_split, reinterpret_cast<float*>(spn),
-                                    reinterpret_cast<float*>(spd), p->tc_err, st, &info));
-            if (p->opt.profile) {
-                NEF_CUDA(cudaEventRecord(e1, st));
-                p->ev_used.push_back({0, {e0, e1}});
-            }
-            used_tc = true;
+            NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den, n_split,
+                                    reinterpret_cast<float*>(spn), reinterpret_cast<float*>(spd),
+                                    p->tc_err, st, &info, p->tc_trace));
         }
-    }
-    int n_split = pp.n_split;
-    if (!used_tc) {
+    } else {
         ViewDesc v = bind_view(p, pp, false);
         int n_ctas = 0;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (p->opt.profile) NEF_TRY(prof_begin(p, st, &e0, &e1));
         NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, need_den, n_split, spn, need_den ? spd : nullptr,
                                      nullptr, nullptr, st, &n_ctas));
-        if (p->opt.profile) {
-            NEF_CUDA(cudaEventRecord(e1, st));
-            p->ev_used.push_back({1, {e0, e1}});
+    }
+    if (p->opt.profile) {
+        NEF_CUDA(cudaEventRecord(e1, st));
+        p->ev_used.push_back({use_tc ? 0 : 1, {e0, e1}});
+    }
+    if (pp.finish_identity) {
+        // split reduction, denominator, update and the factor's copies in one kernel
+        FinishDesc d{};
+        d.nlet = (int)ldims.size();
+        for (int q = 0; q < d.nlet; ++q) {
+            const int x = md.term[pp.l][q];
+            d.dim[q] = ldims[q];
+            d.s_st[q] = pp.epi_num.ops[0].st[x];
+            d.b_st[q] = closed ? pp.epi_den_closed.ops[0].st[x] : 0;
         }
+        d.part_num = spn;
+        d.part_den = closed ? nullptr : spd;
+        d.n_split = n_split;
+        d.s_size = sz;
+        d.n_cs = closed ? (int)pp.Q.size() : 0;
+        if (closed)
+            for (size_t k = 0; k < pp.Q.size(); ++k) d.cs[k] = buf_ptr(p, pp.Q[k].cs_buf);
+        d.theta = factors[pp.l];
+        d.n = nl;
+        d.mir = mir;
+        NEF_CUDA(launch_finish<T>(d, u, st));
+        return after_update<T>(p, pp.l, st);
     }
     NEF_CUDA(launch_reduce_splits<T>(spn, n_split, sz, static_cast<T*>(buf_ptr(p, B_SNUM)), st));
     if (need_den)
@@ -828,8 +941,9 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
         NEF_TRY(run_ein<T>(p, pp.den_prod, factors, st));
         NEF_TRY(run_ein<T>(p, pp.epi_den_closed, factors, st));
     }
-    NEF_CUDA(launch_update<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, st));
-    return NEF_OK;
+    NEF_CUDA(launch_update_mirror<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, (int)ldims.size(),
+                                     ldims.data(), mir, st));
+    return after_update<T>(p, pp.l, st);
 }
 
 nef_status check_ab(double al, double be) {
@@ -871,6 +985,7 @@ nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
     const WeightSpec w = weight_spec(al, be);
     const UpdateSpec u = update_spec(al, be, p->opt.eps);
     const T* y = static_cast<const T*>(Y);
+    if (iters > 0) NEF_TRY(init_sources<T>(p, factors, st));
     for (int it = 0; it < iters; ++it) {
         for (int l = 0; l < p->md.L; ++l) {
             if (only_l >= 0 && l != only_l) continue;
@@ -896,7 +1011,8 @@ nef_status loss_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* con
         if (!p->pass[l].generic) { vl = l; break; }
     if (vl >= 0) {
         PassPlan& pp = p->pass[vl];
-        NEF_TRY(prepare_sources<T>(p, pp, factors, st));
+        NEF_TRY(init_sources<T>(p, factors, st));
+        NEF_TRY(refresh_sources<T>(p, pp, factors, st, false));
         ViewDesc v = bind_view(p, pp, false);
         const int64_t tm = sizeof(T) == 8 ? 32 : 64;
         const int64_t n_rb = (v.rows + tm - 1) / tm;
@@ -953,6 +1069,7 @@ void destroy(nef_plan_t p) {
     if (p->loss_out) cudaFree(p->loss_out);
     if (p->flag) cudaFree(p->flag);
     if (p->tc_err) cudaFree(p->tc_err);
+    if (p->tc_trace) cudaFree(p->tc_trace);
     for (auto e : p->ev_pool) cudaEventDestroy(e);
     delete p;
 }
@@ -1027,6 +1144,44 @@ nef_status build_plan(nef_plan_t p) {
         p->pass.push_back(best);
     }
     p->info = info;
+    // ---- operand bookkeeping: relabelled copies of one factor are kept current by
+    // that factor's update; contracted operands are rebuilt when a factor they read changed
+    p->mirrors_of.assign(md.L, {});
+    p->fac_version.assign(md.L, 0);
+    int next_cs = B_CS0;
+    for (int pi = 0; pi < (int)p->pass.size(); ++pi) {
+        PassPlan& pp = p->pass[pi];
+        if (pp.generic) continue;
+        for (int k = -1; k < (int)pp.Q.size(); ++k) {
+            SourcePlan& sp = source_ref(pp, k);
+            const EinRecipe& r = sp.build;
+            sp.deps.clear();
+            for (auto& o : r.ops)
+                if (o.kind == 0) sp.deps.push_back(o.index);
+            sp.copy_of = -1;
+            if (r.ops.size() == 1 && r.ops[0].kind == 0 && r.free_let.empty()) {
+                const int f = r.ops[0].index;
+                bool perm = r.out_let.size() == md.term[f].size();
+                for (int x : r.out_let) perm = perm && md.fac_has(f, x);
+                if (perm && p->mirrors_of[f].size() < (size_t)kMaxMirror) {
+                    sp.copy_of = f;
+                    p->mirrors_of[f].push_back({pi, k});
+                }
+            }
+            if (k >= 0 && pp.den_closed && sp.copy_of >= 0) sp.cs_buf = next_cs++;
+        }
+        // a closed-form denominator needs the column sums of every column-side operand
+        if (pp.den_closed)
+            for (auto& q : pp.Q)
+                if (q.cs_buf < 0) pp.den_closed = false;
+        const bool id_num = pp.epi_num.ops.size() == 1 && pp.epi_num.free_let.empty() &&
+                            pp.epi_num.out_let.size() <= (size_t)kMaxFacLet;
+        const bool id_den = pp.epi_den.ops.size() == 1 && pp.epi_den.free_let.empty();
+        const bool id_closed = !pp.den_closed ||
+                               (pp.epi_den_closed.ops.size() == 1 && pp.epi_den_closed.free_let.empty());
+        pp.finish_identity = id_num && id_den && id_closed && md.term[pp.l].size() <= (size_t)kMaxFacLet;
+        p->max_ld = std::max<int64_t>(p->max_ld, pp.view.bond_pad);
+    }
     // ---- workspace
     size_t es = p->esz;
     int64_t max_fac = 1, max_s = 16, max_part = 16;
@@ -1050,6 +1205,11 @@ nef_status build_plan(nef_plan_t p) {
     if (any_generic) {
         NEF_TRY(alloc(p, B_WA, md.N * es));
         NEF_TRY(alloc(p, B_WB, md.N * es));
+    }
+    for (auto& pp : p->pass) {
+        if (pp.generic) continue;
+        for (auto& q : pp.Q)
+            if (q.cs_buf >= 0) NEF_TRY(alloc(p, q.cs_buf, (size_t)pp.view.bond_pad * es));
     }
     p->src_bf16.assign(next_buf + 1, nullptr);
     for (auto& pp : p->pass) {
@@ -1087,6 +1247,10 @@ nef_status build_plan(nef_plan_t p) {
     NEF_CUDA(cudaMalloc(&p->flag, sizeof(int)));
     NEF_CUDA(cudaMalloc(&p->tc_err, sizeof(int)));
     NEF_CUDA(cudaMemset(p->tc_err, 0, sizeof(int)));
+    if (p->opt.profile) {
+        NEF_CUDA(cudaMalloc(&p->tc_trace, 32 * sizeof(unsigned long long)));
+        NEF_CUDA(cudaMemset(p->tc_trace, 0, 32 * sizeof(unsigned long long)));
+    }
     return NEF_OK;
 }
 
@@ -1182,20 +1346,34 @@ int nef_plan_info(nef_plan_t plan, char* buf, int cap) {
 
 int nef_plan_launches(nef_plan_t plan, int has_mask) {
     if (!plan) return 0;
+    // one sweep inside a nef_fit call (the per-call start-up is not counted)
     int total = 0;
     for (auto& pp : plan->pass) {
         if (pp.generic) {
-            total += 1 + 2 + 2 + 1;
+            total += 1 + 2 + 2 + 1 + 1;
             continue;
         }
-        int n = 2 * (1 + (int)pp.Q.size());            // source einsums
-        if (plan->prec == NEF_BF16) n += 1 + (int)pp.Q.size();  // BF16 conversions
-        n += 1;                                         // view kernel
-        bool closed = pp.den_closed && !has_mask;      // (b == 1 is decided per call)
-        n += closed ? 1 : 2;                            // split reductions
-        n += 2;                                         // epilogue num
-        n += closed ? 2 * ((int)pp.colsum.size() + 2) : 2;
-        n += 1;                                         // update
+        int n = 0;
+        for (int k = -1; k < (int)pp.Q.size(); ++k) {
+            const SourcePlan& sp = k < 0 ? pp.P : pp.Q[k];
+            if (sp.copy_of < 0) n += 2 + (plan->prec == NEF_BF16 ? 1 : 0);  // rebuild (+ BF16 copy)
+        }
+        n += 1;  // fused pass
+        const bool closed = pp.den_closed && !has_mask;
+        if (pp.finish_identity) {
+            n += 1;
+        } else {
+            n += closed ? 1 : 2;                                // split reductions
+            n += 2;                                             // epilogue num
+            n += closed ? 2 * ((int)pp.colsum.size() + 2) : 2;  // den
+            n += 1;                                             // update
+        }
+        bool any_cs = false;
+        for (auto& ps : plan->mirrors_of[pp.l]) {
+            const SourcePlan& sp = ps.second < 0 ? plan->pass[ps.first].P : plan->pass[ps.first].Q[ps.second];
+            any_cs = any_cs || sp.cs_buf >= 0;
+        }
+        n += any_cs ? 1 : 0;                                    // column sums
         total += n;
     }
     return total;
@@ -1220,6 +1398,19 @@ nef_status nef_plan_profile(nef_plan_t plan, double* ms, int* count, int reset) 
         plan->ev_next = 0;
     }
     return NEF_OK;
+}
+
+int nef_tc_trace(nef_plan_t plan, unsigned long long* out, int reset) {
+    if (!plan || !out || !plan->tc_trace) return 1;
+    cudaStream_t st = static_cast<cudaStream_t>(plan->opt.stream);
+    if (cudaMemcpyAsync(out, plan->tc_trace, 32 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return 5;
+    if (reset) {
+        if (cudaMemsetAsync(plan->tc_trace, 0, 32 * sizeof(unsigned long long), st) != cudaSuccess) return 5;
+    }
+    return 0;
 }
 
 nef_status nef_check(nef_plan_t plan) {

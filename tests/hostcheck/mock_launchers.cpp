@@ -5,6 +5,7 @@
 // library that the product never loads.  The element math (weights, divergence,
 // update) is the product's own nef_device.cuh compiled for the host.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #define __device__
@@ -188,9 +189,88 @@ cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint
     return cudaSuccess;
 }
 
+static uint16_t bf16_bits_host(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+template <typename T>
+static void write_mirrors_host(const MirrorDesc& m, const int64_t* idx, int nlet, T v) {
+    for (int k = 0; k < m.n; ++k) {
+        int64_t off = 0;
+        for (int q = 0; q < nlet; ++q) off += idx[q] * m.st[k][q];
+        static_cast<T*>(m.p32[k])[off] = v;
+        if (m.p16[k]) m.p16[k][off] = bf16_bits_host((float)v);
+    }
+}
+
+static void decode(int64_t e, int nlet, const int64_t* dim, int64_t* idx) {
+    for (int q = nlet - 1; q >= 0; --q) { idx[q] = e % dim[q]; e /= dim[q]; }
+}
+
+template <typename T>
+cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t) {
+    for (int64_t e = 0; e < d.n; ++e) {
+        int64_t idx[kMaxFacLet];
+        decode(e, d.nlet, d.dim, idx);
+        int64_t soff = 0, boff = 0;
+        for (int q = 0; q < d.nlet; ++q) { soff += idx[q] * d.s_st[q]; boff += idx[q] * d.b_st[q]; }
+        T num = 0, den;
+        for (int s = 0; s < d.n_split; ++s) num += static_cast<const T*>(d.part_num)[s * d.s_size + soff];
+        if (d.part_den) {
+            den = 0;
+            for (int s = 0; s < d.n_split; ++s) den += static_cast<const T*>(d.part_den)[s * d.s_size + soff];
+        } else {
+            den = 1;
+            for (int s = 0; s < d.n_cs; ++s) den *= static_cast<const T*>(d.cs[s])[boff];
+        }
+        T* th = static_cast<T*>(d.theta);
+        th[e] = mu_update(th[e], num, den, u);
+        write_mirrors_host<T>(d.mir, idx, d.nlet, th[e]);
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
+                                 int nlet, const int64_t* dim, const MirrorDesc& m, cudaStream_t) {
+    for (int64_t e = 0; e < n; ++e) {
+        theta[e] = mu_update(theta[e], num[e], den[e], u);
+        int64_t idx[kMaxFacLet];
+        decode(e, nlet, dim, idx);
+        write_mirrors_host<T>(m, idx, nlet, theta[e]);
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_mirror_init(const T* theta, int64_t n, int nlet, const int64_t* dim,
+                               const MirrorDesc& m, cudaStream_t) {
+    for (int64_t e = 0; e < n; ++e) {
+        int64_t idx[kMaxFacLet];
+        decode(e, nlet, dim, idx);
+        write_mirrors_host<T>(m, idx, nlet, theta[e]);
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_colsums(const ColsumDesc& d, int64_t, cudaStream_t) {
+    for (int k = 0; k < d.n; ++k) {
+        const ColsumJob& j = d.job[k];
+        for (int64_t b = 0; b < j.ld; ++b) {
+            T acc = 0;
+            for (int64_t r = 0; r < j.n_rows; ++r) acc += static_cast<const T*>(j.src)[r * j.ld + b];
+            static_cast<T*>(j.out)[b] = acc;
+        }
+    }
+    return cudaSuccess;
+}
+
 bool tc_view_supported(const ViewDesc&, int) { return false; }
 cudaError_t launch_view_tc(const float*, const uint32_t*, const ViewDesc&, const WeightSpec&, int,
-                           int, float*, float*, int*, cudaStream_t, TcLaunchInfo*) {
+                           int, float*, float*, int*, cudaStream_t, TcLaunchInfo*, unsigned long long*) {
     return cudaErrorNotSupported;
 }
 
@@ -207,7 +287,16 @@ cudaError_t launch_view_tc(const float*, const uint32_t*, const ViewDesc&, const
     template cudaError_t launch_generic_weights<T>(const GenericRecon&, const T*,                 \
                                                    const uint32_t*, const WeightSpec&, T*, T*,     \
                                                    const LossSpec*, double*, int, cudaStream_t);
+#define INST2(T)                                                                                 \
+    template cudaError_t launch_finish<T>(const FinishDesc&, const UpdateSpec&, cudaStream_t);       \
+    template cudaError_t launch_update_mirror<T>(T*, const T*, const T*, int64_t, const UpdateSpec&,  \
+                                                 int, const int64_t*, const MirrorDesc&, cudaStream_t); \
+    template cudaError_t launch_mirror_init<T>(const T*, int64_t, int, const int64_t*,                \
+                                               const MirrorDesc&, cudaStream_t);                      \
+    template cudaError_t launch_colsums<T>(const ColsumDesc&, int64_t, cudaStream_t);
 INST(float)
 INST(double)
+INST2(float)
+INST2(double)
 
 }  // namespace nef
