@@ -65,8 +65,9 @@ typedef struct {
     double eps;         /* floor of Eq. 3.1 (paper: "a very small eps > 0"); default 1e-10  */
     int check_data;     /* nonzero: nef_fit/nef_update first check Y >= 0 and finite        */
     int force_generic;  /* nonzero: use the unfused path (yhat, a, b materialised)          */
-    int profile;        /* nonzero: time every fused-pass launch with CUDA events on the    */
-                        /* plan's stream (read back with nef_plan_profile)                  */
+    int profile;        /* 1: time every fused-pass launch with CUDA events on the plan's   */
+                        /* stream (nef_plan_profile); 2: also count wait and phase cycles   */
+                        /* inside the tensor-core pass (nef_tc_trace; slows it down)        */
     void* stream;       /* cudaStream_t used by every call on the plan                      */
 } nef_options;
 

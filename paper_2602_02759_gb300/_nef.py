@@ -157,7 +157,7 @@ class Plan:
     """
 
     def __init__(self, model_str: str, dims: dict, precision: str = "fp32", eps: float = 1e-10,
-                 check_data: bool = False, force_generic: bool = False, profile: bool = False,
+                 check_data: bool = False, force_generic: bool = False, profile: int = 0,
                  stream=None):
         lib = load()
         obs, lat, terms = split_model(model_str)
@@ -173,7 +173,7 @@ class Plan:
         opt.eps = float(eps)
         opt.check_data = int(bool(check_data))
         opt.force_generic = int(bool(force_generic))
-        opt.profile = int(bool(profile))
+        opt.profile = int(profile)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream()
@@ -262,7 +262,7 @@ class Plan:
         out = (ctypes.c_ulonglong * 32)()
         rc = load().nef_tc_trace(self._h, out, int(bool(reset)))
         if rc:
-            raise NefError(rc, "tensor-core trace unavailable (plan needs profile=True)")
+            raise NefError(rc, "tensor-core trace unavailable (plan needs profile=2)")
         return list(out)
 
     def info(self) -> str:

@@ -37,7 +37,6 @@ namespace tc {
 constexpr int TM = 128;        // rows per CTA (TMEM lanes)
 constexpr int TN = 64;         // columns per tile
 constexpr int ND = 4;          // yhat TMEM buffers (MMA1 runs two tiles ahead)
-constexpr int NW = 2;          // W buffers
 constexpr int kThreads = 448;   // 14 warps
 constexpr int kEpiWarps = 8;
 constexpr int kOpWarps = 4;
@@ -98,13 +97,29 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
     return ok;
 }
 
+// Non-blocking probe of a phase.
+__device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok;
+}
+
 // Bounded wait.  Returns false (and raises the CTA abort flag) on timeout or
 // when another role already aborted.  With a trace array, the cycles spent
 // waiting are added to trace[code].
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           int* err, int code, unsigned long long* trace = nullptr) {
-    if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
+    if (mbar_try(bar, parity)) {
+        if (trace) atomicAdd(&trace[code], (unsigned long long)(clock64() - t0));
+        return true;
+    }
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) {
             if (trace) atomicAdd(&trace[code], (unsigned long long)(clock64() - t0));
@@ -279,8 +294,11 @@ __device__ __forceinline__ int64_t src_row_tc(const SrcDesc& s, int64_t i) {
 // ---------------------------------------------------------- shared layout
 template <int BP, bool DEN>
 struct Layout {
-    static constexpr int NSY = 3;                            // Y (and V) pipeline stages
-    static constexpr int NSQ = DEN ? 3 : 4;                  // Q pipeline stages
+    // Ring depths by shared-memory budget: as many Y stages (bytes in flight
+    // towards HBM latency) as fit next to the operand and weight buffers.
+    static constexpr int NSY = (BP == 64) ? (DEN ? 3 : 4) : (BP == 32 ? (DEN ? 3 : 4) : 4);  // Y (and V) stages
+    static constexpr int NSQ = (BP == 64 && !DEN) ? 2 : (DEN ? 3 : 4);                       // Q stages
+    static constexpr int NW = (DEN || BP == 64) ? 2 : 3;                                     // W buffers
     static constexpr int RB = BP * 2;                        // bytes per bond row (BF16)
     static constexpr int kY = 0;                             // NSY x 32 KB
     static constexpr int kV = kY + NSY * kYStageBytes;       // NSY x TN x RB: TMA-staged source rows
@@ -317,6 +335,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     constexpr int RB = LY::RB;
     constexpr int NSY = LY::NSY;
     constexpr int NSQ = LY::NSQ;
+    constexpr int NW = LY::NW;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t base = (raw_addr + 1023u) & ~1023u;
@@ -458,12 +477,9 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 tc_commit(dfull(b));
                 return true;
             };
-            if (ok && T > 0) ok = mma1(0);
-            if (ok && T > 1) ok = mma1(1);
-            for (int i = 0; ok && i < T; ++i) {
-                if (i + 2 < T && !mma1(i + 2)) break;
-                const int bw = i & 1, sq = i % NSQ;
-                if (!mbar_wait(wfull(bw), (i >> 1) & 1, abort_flag, prm.err, 6, tr)) break;
+            // issue MMA1 and MMA2 in whichever order their inputs become ready
+            auto mma2 = [&](int i) {
+                const int bw = i % NW, sq = i % NSQ;
                 tc_fence_after();
                 const uint32_t wa_addr = base + LY::kWa + bw * LY::kWStage;
                 const uint32_t wb_addr = base + LY::kWb + bw * LY::kWStage;
@@ -481,6 +497,31 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 }
                 tc_commit(wempty(bw));
                 tc_commit(qempty(sq));
+            };
+            int i1 = 0, i2 = 0;
+            long long last = clock64();
+            while (ok && i2 < T) {
+                bool prog = false;
+                if (i1 < T && mbar_test(qfull(i1 % NSQ), (i1 / NSQ) & 1) &&
+                    mbar_test(dempty(i1 % ND), ((i1 / ND) & 1) ^ 1)) {
+                    ok = mma1(i1);  // inputs ready: the waits inside return at once
+                    ++i1;
+                    prog = true;
+                }
+                if (ok && i2 < i1 && mbar_test(wfull(i2 % NW), (i2 / NW) & 1)) {
+                    mma2(i2);
+                    ++i2;
+                    prog = true;
+                }
+                if (prog) {
+                    last = clock64();
+                } else if (*abort_flag) {
+                    ok = false;
+                } else if (clock64() - last > kWaitCycles) {
+                    *abort_flag = 1;
+                    atomicCAS(prm.err, 0, 6);
+                    ok = false;
+                }
             }
             tc_commit(sfull);
             // drain: wait until every MMA issued by this thread has completed
@@ -658,7 +699,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         long long tp = clock64();
 #pragma unroll 1
         for (int i = 0; i < T; ++i) {
-            const int bd = i % ND, b = i & 1, s = i % NSY;
+            const int bd = i % ND, b = i % NW, s = i % NSY;
             if (!wwait(dfull(bd), (i / ND) & 1, 9)) break;
             if (trl) tp = clock64();
             tc_fence_after();
@@ -724,7 +765,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 if (DEN) wb2[c >> 1] = pack_bf16(o0 ? b0 : 0.f, o1 ? b1 : 0.f);
             }
             if (trl) phase_mark(tr, 22, tp);
-            if (!wwait(wempty(b), ((i >> 1) & 1) ^ 1, 11)) break;
+            if (!wwait(wempty(b), ((i / NW) & 1) ^ 1, 11)) break;
             if (trl) tp = clock64();
             uint8_t* wa_dst = sm + LY::kWa + b * LY::kWStage;
             uint8_t* wb_dst = sm + LY::kWb + b * LY::kWStage;

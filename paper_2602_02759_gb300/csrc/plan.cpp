@@ -1247,7 +1247,7 @@ nef_status build_plan(nef_plan_t p) {
     NEF_CUDA(cudaMalloc(&p->flag, sizeof(int)));
     NEF_CUDA(cudaMalloc(&p->tc_err, sizeof(int)));
     NEF_CUDA(cudaMemset(p->tc_err, 0, sizeof(int)));
-    if (p->opt.profile) {
+    if (p->opt.profile >= 2) {
         NEF_CUDA(cudaMalloc(&p->tc_trace, 32 * sizeof(unsigned long long)));
         NEF_CUDA(cudaMemset(p->tc_trace, 0, 32 * sizeof(unsigned long long)));
     }
