@@ -17,14 +17,16 @@ extern "C" {
  * Eq. 3.6-3.8 contraction):
  *   D1[128 x 64]  = P[128 x bp] . Q[64 x bp]^T
  *   D2[128 x bp]  = W[128 x 64] . Q[64 x bp]
+ * with the A operands P and W in shared memory (a_in_tmem = 0) or in tensor
+ * memory (a_in_tmem != 0).
  * All pointers are device pointers to row-major arrays; BF16 values are raw
  * 16-bit patterns.  bond_pad is 16, 32 or 64.  err (device int) receives a
  * nonzero code if the bounded completion wait gave up.  Enqueued on `stream`
  * (a cudaStream_t).  Returns 0 on a successful launch, 1 for a bad bond_pad,
  * 5 for a CUDA error.
  */
-int nef_tc_probe(int bond_pad, const uint16_t* P, const uint16_t* Q, const uint16_t* W, float* D1,
-                 float* D2, int* err, void* stream);
+int nef_tc_probe(int bond_pad, int a_in_tmem, const uint16_t* P, const uint16_t* Q, const uint16_t* W,
+                 float* D1, float* D2, int* err, void* stream);
 
 /*
  * nef_tc_trace -- wait-cycle counters of the tensor-core fused pass, summed over

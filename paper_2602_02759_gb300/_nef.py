@@ -82,7 +82,7 @@ def load(path: str = LIB_PATH):
     lib.nef_cp3_update_static.restype = ctypes.c_int
     lib.nef_tc_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
     lib.nef_tc_trace.restype = ctypes.c_int
-    lib.nef_tc_probe.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+    lib.nef_tc_probe.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.nef_tc_probe.restype = ctypes.c_int
     _lib = lib
     return lib

@@ -2,16 +2,18 @@
 //
 // One CTA owns a block of 128 rows of the view Y[row, col] and a range of
 // 64-column tiles.  Per tile:
-//   TMA      : Y tile (128 x 64 FP32) -> shared memory (3-stage ring)
-//   Q warps  : Q tile (64 cols x BP bond, BF16) = Hadamard product of gathered
-//              source rows (Eq. 2.1 restricted to the column side)
-//   MMA1     : yhat[128 x 64] = P[128 x BP] . Q^T       -> TMEM (double-buffered)
+//   TMA      : Y tile (128 x 64 FP32) -> shared memory (multi-stage ring)
+//   Q warps  : Q tile (64 cols x BP bond, BF16, shared memory) = Hadamard
+//              product of the source rows (Eq. 2.1 restricted to the column side)
+//   MMA1     : yhat[128 x 64] = P[128 x BP] . Q^T       -> TMEM (P in TMEM)
 //   epilogue : W_a = M*a(y, yhat), W_b = M*b(y, yhat)  (App. B) in FP32 registers,
-//              rounded to BF16 into shared memory (K-major, 128B swizzle)
+//              rounded to BF16 and stored into TMEM (one tile row per lane)
 //   MMA2     : S_a[128 x BP] += W_a[128 x 64] . Q[64 x BP]  -> TMEM (Eq. 3.6-3.8)
 //              (and S_b with W_b when the denominator needs the contraction)
-// yhat and the weights never leave the chip.  At the end the epilogue warps
-// copy S from TMEM to the per-split partial buffers.
+// yhat and the weights never leave the chip, and both A operands (P, W) are
+// read by the tensor cores from TMEM, so shared-memory bandwidth is spent on
+// the Y stream, the staged source rows and Q only.  At the end the epilogue
+// warps copy S from TMEM to the per-split partial buffers.
 //
 // Warp roles (448 threads): warp 0 TMA producer + TMEM allocator, warp 1 MMA
 // issuer, warps 2-5 Q/P operand builders (two threads per tile column, each
@@ -36,7 +38,6 @@ namespace tc {
 
 constexpr int TM = 128;        // rows per CTA (TMEM lanes)
 constexpr int TN = 64;         // columns per tile
-constexpr int ND = 4;          // yhat TMEM buffers (MMA1 runs two tiles ahead)
 constexpr int kThreads = 448;   // 14 warps
 constexpr int kEpiWarps = 8;
 constexpr int kOpWarps = 4;
@@ -181,6 +182,19 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_
         : "memory");
 }
 
+// Same product with the A operand read from tensor memory: rows of A in TMEM
+// lanes 0..127, K packed along columns (two BF16 values per 32-bit column, the
+// lower K index in the low half), starting at column address a_tmem.
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -207,6 +221,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+
+// Store 8/16/32 consecutive 32-bit columns of this thread's TMEM lane.
+template <int N>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t* r) {
+    if constexpr (N == 8) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                     "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                     : "memory");
+    } else if constexpr (N == 16) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16};" ::"r"(taddr),
+            "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+            "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+            : "memory");
+    } else {
+        static_assert(N == 32, "8, 16 or 32 columns");
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+            "%32};" ::"r"(taddr),
+            "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+            "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+            "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+            "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_ld() {
@@ -294,24 +340,24 @@ __device__ __forceinline__ int64_t src_row_tc(const SrcDesc& s, int64_t i) {
 // ---------------------------------------------------------- shared layout
 template <int BP, bool DEN>
 struct Layout {
-    // Ring depths by shared-memory budget: as many Y stages (bytes in flight
-    // towards HBM latency) as fit next to the operand and weight buffers.
-    static constexpr int NSY = (BP == 64) ? (DEN ? 3 : 4) : (BP == 32 ? (DEN ? 3 : 4) : 4);  // Y (and V) stages
-    static constexpr int NSQ = (BP == 64 && !DEN) ? 2 : (DEN ? 3 : 4);                       // Q stages
-    static constexpr int NW = (DEN || BP == 64) ? 2 : 3;                                     // W buffers
+    // Shared memory holds only what the async proxy brings in (Y, staged source
+    // rows) and the Q operand; the A operands of both products (P, W) live in
+    // tensor memory, so the shared-memory bandwidth of a tile goes to the Y
+    // stream.  Ring depths: as many Y stages (bytes in flight towards HBM
+    // latency) as fit next to the Q stages.
+    static constexpr int NSY = (BP == 64) ? 5 : (BP == 32 ? 5 : 6);  // Y (and V) stages
+    static constexpr int NSQ = (BP == 64) ? 3 : 4;                    // Q stages
+    static constexpr int NW = DEN ? 2 : 3;                            // W buffers (TMEM)
+    static constexpr int ND = (DEN && BP == 64) ? 3 : 4;              // yhat buffers (TMEM)
     static constexpr int RB = BP * 2;                        // bytes per bond row (BF16)
     static constexpr int kY = 0;                             // NSY x 32 KB
     static constexpr int kV = kY + NSY * kYStageBytes;       // NSY x TN x RB: TMA-staged source rows
     static constexpr int kQ = kV + NSY * TN * RB;            // NSQ x TN x RB
     static constexpr int kQStage = TN * RB;
-    static constexpr int kP = kQ + NSQ * kQStage;            // TM x RB
-    static constexpr int kWa = kP + TM * RB;                 // NW x 16 KB
-    static constexpr int kWStage = TM * TN * 2;
-    static constexpr int kWb = kWa + NW * kWStage;
     // NSY slots of kGSlot bytes: TMA-staged constant row (tensor-copy destinations are
     // 128-byte aligned)
     static constexpr int kGSlot = 128;
-    static constexpr int kG = kWb + (DEN ? NW * kWStage : 0);
+    static constexpr int kG = kQ + NSQ * kQStage;
     static constexpr int kBar = kG + NSY * kGSlot;
     static_assert(kY % 1024 == 0 && kV % 1024 == 0 && (TN * RB) % 256 == 0 && kG % 128 == 0 &&
                       kGSlot >= RB,
@@ -323,6 +369,14 @@ struct Layout {
     static constexpr int kTrace = kMisc + 16;                 // kTraceSites counters
     static constexpr int kTotal = kTrace + kTraceSites * 8;
     static constexpr int kAlloc = kTotal + 1024;              // slack for 1024-B alignment
+    static_assert(kAlloc <= 232448, "shared memory per CTA");
+    // tensor-memory columns (128 lanes x 32 bit): yhat buffers, S_num, S_den, P
+    // (BF16 pairs), W_a and W_b buffers (64 BF16 = 32 columns each)
+    static constexpr uint32_t cS = ND * TN;
+    static constexpr uint32_t cP = ((cS + (DEN ? 2 : 1) * BP + 31) / 32) * 32;
+    static constexpr uint32_t cWa = cP + ((BP / 2 + 31) / 32) * 32;
+    static constexpr uint32_t cWb = cWa + NW * 32;
+    static_assert(cWb + (DEN ? NW * 32 : 0) <= kTmemCols, "tensor-memory columns");
 };
 
 // The fused pass of one CTA: rows [rb*TM, rb*TM + TM) of the view and the
@@ -336,6 +390,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     constexpr int NSY = LY::NSY;
     constexpr int NSQ = LY::NSQ;
     constexpr int NW = LY::NW;
+    constexpr int ND = LY::ND;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t base = (raw_addr + 1023u) & ~1023u;
@@ -397,8 +452,11 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t t_snum = tmem + ND * TN;
-    const uint32_t t_sden = tmem + ND * TN + BP;
+    const uint32_t t_snum = tmem + LY::cS;
+    const uint32_t t_sden = tmem + LY::cS + BP;
+    const uint32_t t_p = tmem + LY::cP;
+    const uint32_t t_wa = tmem + LY::cWa;
+    const uint32_t t_wb = tmem + LY::cWb;
 
     auto tile_info = [&](int64_t t, int64_t& col0, int& nvalid, int& x0, int& z0) {
         if (prm.trans) {
@@ -460,7 +518,6 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             constexpr uint32_t idesc1 = make_idesc(TM, TN, 0, 0);
             constexpr uint32_t idesc2 = make_idesc(TM, BP, 0, 1);
             bool ok = mbar_wait(pfull, 0, abort_flag, prm.err, 3, tr);
-            const uint32_t p_addr = base + LY::kP;
             // MMA1 of tile i: yhat into TMEM buffer i % ND
             auto mma1 = [&](int i) -> bool {
                 const int sq = i % NSQ, b = i % ND;
@@ -470,9 +527,8 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 const uint32_t q_addr = base + LY::kQ + sq * LY::kQStage;
 #pragma unroll
                 for (int k = 0; k < BP / 16; ++k) {
-                    const uint64_t ad = make_sdesc(p_addr + k * 32, 16, 8 * RB, swz_code(RB));
                     const uint64_t bd = make_sdesc(q_addr + k * 32, 16, 8 * RB, swz_code(RB));
-                    tc_mma(tmem + b * TN, ad, bd, idesc1, k > 0 ? 1u : 0u);
+                    tc_mma_ts(tmem + b * TN, t_p + k * 8, bd, idesc1, k > 0 ? 1u : 0u);
                 }
                 tc_commit(dfull(b));
                 return true;
@@ -481,19 +537,13 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             auto mma2 = [&](int i) {
                 const int bw = i % NW, sq = i % NSQ;
                 tc_fence_after();
-                const uint32_t wa_addr = base + LY::kWa + bw * LY::kWStage;
-                const uint32_t wb_addr = base + LY::kWb + bw * LY::kWStage;
                 const uint32_t q_addr = base + LY::kQ + sq * LY::kQStage;
 #pragma unroll
                 for (int k = 0; k < TN / 16; ++k) {
                     const uint64_t bd = make_sdesc(q_addr + k * 16 * RB, TN * RB, 8 * RB, swz_code(RB));
-                    const uint64_t ad = make_sdesc(wa_addr + k * 32, 16, 1024, swz_code(128));
                     const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-                    tc_mma(t_snum, ad, bd, idesc2, acc);
-                    if (DEN) {
-                        const uint64_t ad2 = make_sdesc(wb_addr + k * 32, 16, 1024, swz_code(128));
-                        tc_mma(t_sden, ad2, bd, idesc2, acc);
-                    }
+                    tc_mma_ts(t_snum, t_wa + bw * 32 + k * 8, bd, idesc2, acc);
+                    if (DEN) tc_mma_ts(t_sden, t_wb + bw * 32 + k * 8, bd, idesc2, acc);
                 }
                 tc_commit(wempty(bw));
                 tc_commit(qempty(sq));
@@ -540,19 +590,26 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         constexpr int NH = NCH / 2;             // chunks per thread
         const int cq = q & 63, hq = q >> 6;
         {
+            // P row of TMEM lane (warp % 4) * 32 + lane (the lanes this warp may access)
             const SrcDesc& ps = v.P.src[0];
             const uint16_t* pbase = static_cast<const uint16_t*>(ps.ptr);
-            const int64_t prow = r0 + q;
+            const int pl = ((warp & 3) << 5) + lane;
+            const int64_t prow = r0 + pl;
             const bool ok = prow < v.rows;
             const int64_t pr = ok ? src_row_tc(ps, prow) : 0;
-            uint4 pv[NCH];
+            uint32_t pv[BP / 2];
 #pragma unroll
-            for (int j = 0; j < NCH; ++j)
-                pv[j] = ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int j = 0; j < NCH; ++j)
-                *reinterpret_cast<uint4*>(sm + LY::kP + swz<RB>(q * RB + j * 16)) = pv[j];
-            fence_proxy_async();
+            for (int j = 0; j < NCH; ++j) {
+                const uint4 x =
+                    ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8) : make_uint4(0, 0, 0, 0);
+                pv[4 * j] = x.x;
+                pv[4 * j + 1] = x.y;
+                pv[4 * j + 2] = x.z;
+                pv[4 * j + 3] = x.w;
+            }
+            tmem_st<(BP / 2 < 8 ? 8 : BP / 2)>(t_p + ((uint32_t)((warp & 3) * 32) << 16), pv);
+            tmem_wait_st();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(pfull);
         }
@@ -767,19 +824,13 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             if (trl) phase_mark(tr, 22, tp);
             if (!wwait(wempty(b), ((i / NW) & 1) ^ 1, 11)) break;
             if (trl) tp = clock64();
-            uint8_t* wa_dst = sm + LY::kWa + b * LY::kWStage;
-            uint8_t* wb_dst = sm + LY::kWb + b * LY::kWStage;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t off = e * 128 + (((4 * h + j) ^ (e & 7)) << 4);
-                *reinterpret_cast<uint4*>(wa_dst + off) =
-                    make_uint4(wa2[4 * j], wa2[4 * j + 1], wa2[4 * j + 2], wa2[4 * j + 3]);
-                if (DEN)
-                    *reinterpret_cast<uint4*>(wb_dst + off) =
-                        make_uint4(wb2[4 * j], wb2[4 * j + 1], wb2[4 * j + 2], wb2[4 * j + 3]);
-            }
+            tc_fence_after();
+            // W row halves into TMEM: this warp's lanes, columns 16*h.. of buffer b
+            tmem_st<16>(t_wa + lane_off + b * 32 + 16 * h, wa2);
+            if (DEN) tmem_st<16>(t_wb + lane_off + b * 32 + 16 * h, wb2);
             if (trl) phase_mark(tr, 23, tp);
-            fence_proxy_async();
+            tmem_wait_st();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(wfull(b));
             if (trl) phase_mark(tr, 24, tp);

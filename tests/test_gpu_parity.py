@@ -41,8 +41,9 @@ def bf16_round(x):
 
 # ------------------------------------------------------------- layout probe
 
+@pytest.mark.parametrize("a_in_tmem", [0, 1])
 @pytest.mark.parametrize("bp", [16, 32, 64])
-def test_tc_probe_layouts(bp):
+def test_tc_probe_layouts(bp, a_in_tmem):
     nef = _nef()
     rng = np.random.default_rng(bp)
     P = rng.uniform(0, 1, (128, bp)).astype(np.float32)
@@ -53,7 +54,7 @@ def test_tc_probe_layouts(bp):
     D2 = torch.zeros(128, bp, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     lib = nef.load()
-    rc = lib.nef_tc_probe(bp, tP.data_ptr(), tQ.data_ptr(), tW.data_ptr(), D1.data_ptr(), D2.data_ptr(),
+    rc = lib.nef_tc_probe(bp, a_in_tmem, tP.data_ptr(), tQ.data_ptr(), tW.data_ptr(), D1.data_ptr(), D2.data_ptr(),
                           err.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert rc == 0 and int(err.item()) == 0
