@@ -38,7 +38,8 @@ int nef_tc_probe(int bond_pad, int a_in_tmem, const uint16_t* P, const uint16_t*
  * 4 MMA waits for a Q tile, 5 MMA waits for a free yhat buffer, 6 MMA waits for
  * a W tile, 8 operand warps wait for a free Q stage, 9 epilogue waits for yhat,
  * 10 epilogue waits for Y, 11 epilogue waits for a free W buffer, 12 epilogue
- * waits for the final S, 13 operand warps wait for staged source rows; busy
+ * waits for the final S, 13 operand warps wait for staged source rows, 14
+ * producer waits for a free row stage; busy
  * phases: 16 operand look-ahead, 17 operand build, 18 operand fence and
  * arrival, 20 epilogue TMEM load, 21 epilogue Y read, 22 epilogue weights,
  * 23 epilogue W store, 24 epilogue fence and arrival (waits and phases of the

@@ -99,7 +99,7 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Non-blocking probe of a phase.
-__device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity) {
+[[maybe_unused]] __device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -116,11 +116,12 @@ __device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity) {
 // waiting are added to trace[code].
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           int* err, int code, unsigned long long* trace = nullptr) {
-    const long long t0 = clock64();
+    long long t0 = trace ? clock64() : 0;
     if (mbar_try(bar, parity)) {
         if (trace) atomicAdd(&trace[code], (unsigned long long)(clock64() - t0));
         return true;
     }
+    if (!trace) t0 = clock64();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) {
             if (trace) atomicAdd(&trace[code], (unsigned long long)(clock64() - t0));
@@ -345,26 +346,27 @@ struct Layout {
     // tensor memory, so the shared-memory bandwidth of a tile goes to the Y
     // stream.  Ring depths: as many Y stages (bytes in flight towards HBM
     // latency) as fit next to the Q stages.
-    static constexpr int NSY = (BP == 64) ? 5 : (BP == 32 ? 5 : 6);  // Y (and V) stages
-    static constexpr int NSQ = (BP == 64) ? 3 : 4;                    // Q stages
+    static constexpr int NSY = (BP == 64) ? 4 : (BP == 32 ? 5 : 6);  // Y stages
+    static constexpr int NSV = (BP == 64) ? 6 : 8;                    // staged source-row stages
+    static constexpr int NSQ = (BP == 64) ? 5 : 6;                    // Q stages
     static constexpr int NW = DEN ? 2 : 3;                            // W buffers (TMEM)
     static constexpr int ND = (DEN && BP == 64) ? 3 : 4;              // yhat buffers (TMEM)
     static constexpr int RB = BP * 2;                        // bytes per bond row (BF16)
     static constexpr int kY = 0;                             // NSY x 32 KB
-    static constexpr int kV = kY + NSY * kYStageBytes;       // NSY x TN x RB: TMA-staged source rows
-    static constexpr int kQ = kV + NSY * TN * RB;            // NSQ x TN x RB
+    static constexpr int kV = kY + NSY * kYStageBytes;       // NSV x TN x RB: TMA-staged source rows
+    static constexpr int kQ = kV + NSV * TN * RB;            // NSQ x TN x RB
     static constexpr int kQStage = TN * RB;
-    // NSY slots of kGSlot bytes: TMA-staged constant row (tensor-copy destinations are
+    // NSV slots of kGSlot bytes: TMA-staged constant row (tensor-copy destinations are
     // 128-byte aligned)
     static constexpr int kGSlot = 128;
     static constexpr int kG = kQ + NSQ * kQStage;
-    static constexpr int kBar = kG + NSY * kGSlot;
+    static constexpr int kBar = kG + NSV * kGSlot;
     static_assert(kY % 1024 == 0 && kV % 1024 == 0 && (TN * RB) % 256 == 0 && kG % 128 == 0 &&
                       kGSlot >= RB,
                   "TMA destinations must stay aligned");
     // barriers: yfull[NSY], yempty[NSY], qfull[NSQ], qempty[NSQ], dfull[ND], dempty[ND],
-    //           wfull[NW], wempty[NW], pfull, sfull, drain
-    static constexpr int kNumBars = 2 * NSY + 2 * NSQ + 2 * ND + 2 * NW + 3;
+    //           wfull[NW], wempty[NW], pfull, sfull, drain, vfull[NSV], vempty[NSV]
+    static constexpr int kNumBars = 2 * NSY + 2 * NSQ + 2 * ND + 2 * NW + 3 + 2 * NSV;
     static constexpr int kMisc = kBar + kNumBars * 8;         // tmem slot + abort flag
     static constexpr int kTrace = kMisc + 16;                 // kTraceSites counters
     static constexpr int kTotal = kTrace + kTraceSites * 8;
@@ -416,6 +418,8 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     const uint32_t pfull = bar0 + 8u * (2 * NSY + 2 * NSQ + 2 * ND + 2 * NW);
     const uint32_t sfull = pfull + 8u;
     const uint32_t drain = pfull + 16u;
+    auto vfull = [&](int s) { return drain + 8u * (1 + s); };
+    auto vempty = [&](int s) { return drain + 8u * (1 + LY::NSV + s); };
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + LY::kMisc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + LY::kMisc + 4);
     unsigned long long* tr = prm.trace ? reinterpret_cast<unsigned long long*>(sm + LY::kTrace) : nullptr;
@@ -425,15 +429,21 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     if (tid == 0) {
         for (int s = 0; s < NSY; ++s) {
             mbar_init(yfull(s), 1);
-            mbar_init(yempty(s), kEpiWarps + (prm.qmode ? kOpWarps : 0));
+            mbar_init(yempty(s), kEpiWarps / 2);
+        }
+        for (int s = 0; s < LY::NSV; ++s) {
+            mbar_init(vfull(s), 1);
+            mbar_init(vempty(s), kOpWarps);
         }
         for (int s = 0; s < NSQ; ++s) { mbar_init(qfull(s), kOpWarps); mbar_init(qempty(s), 1); }
+        // yhat, Y and W buffers of a tile are released by the four warps of the
+        // epilogue group that processes it
         for (int b = 0; b < ND; ++b) {
             mbar_init(dfull(b), 1);
-            mbar_init(dempty(b), kEpiWarps);
+            mbar_init(dempty(b), kEpiWarps / 2);
         }
         for (int b = 0; b < NW; ++b) {
-            mbar_init(wfull(b), kEpiWarps);
+            mbar_init(wfull(b), kEpiWarps / 2);
             mbar_init(wempty(b), 1);
         }
         mbar_init(pfull, kOpWarps);
@@ -458,46 +468,102 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     const uint32_t t_wa = tmem + LY::cWa;
     const uint32_t t_wb = tmem + LY::cWb;
 
-    auto tile_info = [&](int64_t t, int64_t& col0, int& nvalid, int& x0, int& z0) {
+    // Column-tile cursor: tile t is tile `ci` of c_out slice `co` (non-transposed
+    // view) or tile t of the transposed view (co stays 0).  Every role starts one
+    // at t_lo and advances it tile by tile, so no role divides per tile.
+    struct Cursor {
+        int64_t co, ci;
+    };
+    auto cursor_at = [&](int64_t t) {
+        Cursor c;
         if (prm.trans) {
-            const int64_t co0 = t * TN;
-            col0 = co0;
-            nvalid = (int)min((int64_t)TN, v.c_out - co0);
-            x0 = (int)co0;
+            c.co = 0;
+            c.ci = t;
+        } else {
+            c.co = t / prm.n_cib;
+            c.ci = t - c.co * prm.n_cib;
+        }
+        return c;
+    };
+    auto advance = [&](Cursor& c) {
+        if (++c.ci == prm.n_cib && !prm.trans) {
+            c.ci = 0;
+            ++c.co;
+        }
+    };
+    auto tile_info = [&](const Cursor& c, int64_t& col0, int& nvalid, int& x0, int& z0) {
+        const int64_t ci0 = c.ci * TN;
+        x0 = (int)ci0;
+        if (prm.trans) {
+            col0 = ci0;
+            nvalid = (int)min((int64_t)TN, v.c_out - ci0);
             z0 = 0;
         } else {
-            const int64_t co = ((uint64_t)t < 0xffffffffull && (uint64_t)prm.n_cib < 0xffffffffull)
-                                   ? (int64_t)((uint32_t)t / (uint32_t)prm.n_cib)
-                                   : t / prm.n_cib;
-            const int64_t ci0 = (t - co * prm.n_cib) * TN;
-            col0 = co * v.c_in + ci0;
+            col0 = c.co * v.c_in + ci0;
             nvalid = (int)min((int64_t)TN, v.c_in - ci0);
-            x0 = (int)ci0;
-            z0 = (int)co;
+            z0 = (int)c.co;
         }
     };
 
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
         if (lane == 0) {
+            // Staged source rows (qmode 1) run NSV - 1 tiles ahead of the Y stream.
+            // In qmode 1, c_in is 1 or a multiple of TN, so tile t starts at column
+            // t*TN: the staged row (col mod m, m a multiple of TN) advances by TN per
+            // tile and the constant row ((col / d) mod m, d a multiple of TN) by one
+            // every d / TN tiles, so both are kept as counters.
+            constexpr int NSV = LY::NSV;
+            const bool has_c = prm.q_const >= 0;
+            int64_t vrow = 0, vmod = 1, crow = 0, cmod = 1, cc = 0, per = 1;
+            if (prm.qmode) {
+                const SrcDesc& dv = v.Q.src[prm.q_var];
+                vmod = dv.mod[0];
+                vrow = (t_lo * TN) % vmod;
+                if (has_c) {
+                    const SrcDesc& dc = v.Q.src[prm.q_const];
+                    per = dc.div[0] / TN;
+                    cmod = dc.mod[0];
+                    const int64_t g = t_lo / per;
+                    cc = t_lo - g * per;
+                    crow = g % cmod;
+                }
+            }
+            int iv = 0;
+            bool vok = true;
+            auto issue_v = [&]() {
+                const int sv = iv % NSV;
+                // slot of tile iv - NSV: free once every operand warp has built that Q
+                if (!mbar_wait(vempty(sv), ((iv / NSV) & 1) ^ 1, abort_flag, prm.err, 14, tr)) {
+                    vok = false;
+                    return;
+                }
+                mbar_expect_tx(vfull(sv), TN * RB + (has_c ? RB : 0));
+                tma_load_2d(base + LY::kV + sv * (TN * RB), vmap, 0, (int)vrow, vfull(sv));
+                if (has_c) tma_load_2d(base + LY::kG + sv * LY::kGSlot, cmap, 0, (int)crow, vfull(sv));
+                vrow += TN;
+                if (vrow == vmod) vrow = 0;
+                if (++cc == per) {
+                    cc = 0;
+                    if (++crow == cmod) crow = 0;
+                }
+                ++iv;
+            };
+            if (prm.qmode)
+                while (vok && iv < T && iv < NSV - 1) issue_v();
             int issued = 0;
+            Cursor cur = cursor_at(t_lo);
             for (int i = 0; i < T; ++i) {
+                if (prm.qmode && vok && iv < T) issue_v();  // rows of tile i + NSV - 1
+                if (!vok) break;
                 const int s = i % NSY;
                 if (!mbar_wait(yempty(s), ((i / NSY) & 1) ^ 1, abort_flag, prm.err, 1, tr)) break;
                 int64_t col0;
                 int nvalid, x0, z0;
-                tile_info(t_lo + i, col0, nvalid, x0, z0);
+                tile_info(cur, col0, nvalid, x0, z0);
+                advance(cur);
                 const uint32_t dst = base + LY::kY + s * kYStageBytes;
-                const bool crow_tma = prm.qmode && prm.q_const >= 0;
-                mbar_expect_tx(yfull(s), kYStageBytes + (prm.qmode ? TN * RB : 0) + (crow_tma ? RB : 0));
-                if (prm.qmode) {
-                    const int vrow = (int)src_row_tc(v.Q.src[prm.q_var], col0);
-                    tma_load_2d(base + LY::kV + s * (TN * RB), vmap, 0, vrow, yfull(s));
-                    if (crow_tma) {
-                        const int crow = (int)src_row_tc(v.Q.src[prm.q_const], col0);
-                        tma_load_2d(base + LY::kG + s * LY::kGSlot, cmap, 0, crow, yfull(s));
-                    }
-                }
+                mbar_expect_tx(yfull(s), kYStageBytes);
                 if (prm.trans) {
                     tma_load_2d(dst, ymap, (int)r0, x0, yfull(s));
                 } else {
@@ -510,6 +576,10 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             for (int i = max(0, issued - NSY); i < issued; ++i) {
                 volatile int dummy_abort = 0;
                 mbar_wait(yfull(i % NSY), (i / NSY) & 1, &dummy_abort, prm.err, 2);
+            }
+            for (int k = max(0, iv - NSV); k < iv; ++k) {
+                volatile int dummy_abort = 0;
+                mbar_wait(vfull(k % NSV), (k / NSV) & 1, &dummy_abort, prm.err, 2);
             }
         }
     } else if (warp == 1) {
@@ -533,7 +603,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 tc_commit(dfull(b));
                 return true;
             };
-            // issue MMA1 and MMA2 in whichever order their inputs become ready
+            // MMA2 of tile i: S += W(i) . Q(i); frees the W buffer and the Q stage
             auto mma2 = [&](int i) {
                 const int bw = i % NW, sq = i % NSQ;
                 tc_fence_after();
@@ -548,30 +618,16 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 tc_commit(wempty(bw));
                 tc_commit(qempty(sq));
             };
-            int i1 = 0, i2 = 0;
-            long long last = clock64();
-            while (ok && i2 < T) {
-                bool prog = false;
-                if (i1 < T && mbar_test(qfull(i1 % NSQ), (i1 / NSQ) & 1) &&
-                    mbar_test(dempty(i1 % ND), ((i1 / ND) & 1) ^ 1)) {
-                    ok = mma1(i1);  // inputs ready: the waits inside return at once
-                    ++i1;
-                    prog = true;
-                }
-                if (ok && i2 < i1 && mbar_test(wfull(i2 % NW), (i2 / NW) & 1)) {
-                    mma2(i2);
-                    ++i2;
-                    prog = true;
-                }
-                if (prog) {
-                    last = clock64();
-                } else if (*abort_flag) {
-                    ok = false;
-                } else if (clock64() - last > kWaitCycles) {
-                    *abort_flag = 1;
-                    atomicCAS(prm.err, 0, 6);
-                    ok = false;
-                }
+            // MMA1 runs LA tiles ahead of MMA2.  LA < NSQ keeps the Q stage of tile
+            // i + LA free once MMA2(i - 1) is issued, LA < ND the yhat buffer once the
+            // epilogue has finished tile i - 1, so the blocking waits cannot deadlock.
+            constexpr int LA = 2;
+            static_assert(LA < NSQ && LA < ND, "MMA1 look-ahead");
+            for (int j = 0; ok && j < LA && j < T; ++j) ok = mma1(j);
+            for (int i = 0; ok && i < T; ++i) {
+                if (i + LA < T && !mma1(i + LA)) break;
+                if (!mbar_wait(wfull(i % NW), (i / NW) & 1, abort_flag, prm.err, 6, tr)) break;
+                mma2(i);
             }
             tc_commit(sfull);
             // drain: wait until every MMA issued by this thread has completed
@@ -614,19 +670,24 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             if (lane == 0) mbar_arrive(pfull);
         }
         if (prm.qmode) {
-            // rows of source q_var and the single row of source q_const (if any) arrive
-            // with the Y tile (TMA); Q = their elementwise product
+            // The rows of source q_var and the single row of source q_const (if any) of
+            // each tile are staged by TMA in their own ring, NSV - 1 tiles ahead of the
+            // tile's Y (they are small and mostly L2-resident), so Q and yhat can be
+            // ready before the Y tile arrives.  Q = the elementwise product of the rows.
+            constexpr int NSV = LY::NSV;
             const bool has_c = prm.q_const >= 0;
             long long tp = clock64();
             const bool trl = tr && lane == 0;
+            Cursor cur = cursor_at(t_lo);
 #pragma unroll 1
             for (int i = 0; i < T; ++i) {
                 int64_t col0;
                 int nvalid, x0, z0;
-                tile_info(t_lo + i, col0, nvalid, x0, z0);
+                tile_info(cur, col0, nvalid, x0, z0);
+                advance(cur);
                 const bool ok = cq < nvalid;
-                const int s = i % NSY, sq = i % NSQ;
-                if (!__all_sync(0xffffffffu, mbar_wait(yfull(s), (i / NSY) & 1, abort_flag, prm.err, 13,
+                const int s = i % NSV, sq = i % NSQ;
+                if (!__all_sync(0xffffffffu, mbar_wait(vfull(s), (i / NSV) & 1, abort_flag, prm.err, 13,
                                                        lane == 0 ? tr : nullptr)))
                     break;
                 if (!__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8,
@@ -664,11 +725,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(yempty(s));
+                    mbar_arrive(vempty(s));
                     mbar_arrive(qfull(sq));
                 }
                 if (trl) phase_mark(tr, 18, tp);
             }
+
         } else {
         const int nsrc = v.Q.nsrc;
         const uint16_t* s0 = static_cast<const uint16_t*>(v.Q.src[0].ptr);
@@ -677,10 +739,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         uint4 nx0[NH], nx1[NH];
         int64_t nrow[kMaxSrc];
         bool nok = false;
-        auto issue = [&](int i) {  // gathered rows of tile i into nx0/nx1
+        Cursor gcur = cursor_at(t_lo);
+        auto issue = [&]() {  // gathered rows of the next tile into nx0/nx1
             int64_t col0;
             int nvalid, x0, z0;
-            tile_info(t_lo + i, col0, nvalid, x0, z0);
+            tile_info(gcur, col0, nvalid, x0, z0);
+            advance(gcur);
             nok = cq < nvalid;
             const int64_t col = col0 + cq;
 #pragma unroll
@@ -694,7 +758,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                                            : make_uint4(0, 0, 0, 0);
             }
         };
-        if (T > 0) issue(0);
+        if (T > 0) issue();
 #pragma unroll 1
         for (int i = 0; i < T; ++i) {
             uint4 c0[NH], c1[NH];
@@ -704,7 +768,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
 #pragma unroll
             for (int s2 = 0; s2 < kMaxSrc; ++s2) crow[s2] = nrow[s2];
             const bool cok = nok;
-            if (i + 1 < T) issue(i + 1);
+            if (i + 1 < T) issue();
             const int sq = i % NSQ;
             if (!__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8,
                                                    lane == 0 ? tr : nullptr)))
@@ -742,8 +806,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         }
     } else {
         // ------------------------------------------------------ epilogue
+        // Two groups of four warps take alternate tiles (group h: tiles h, h + 2,
+        // ...), so one group's weight arithmetic overlaps the other's waits and
+        // loads.  Warp w of a group owns TMEM lanes 32*(w%4).. (one tile row per
+        // thread) and all 64 columns of its tiles, in two halves of 32.
         const int e = ((warp & 3) << 5) + lane;      // tile row == TMEM lane
-        const int h = (warp - kEpiWarp0) >> 2;        // column half of the tile
+        const int h = (warp - kEpiWarp0) >> 2;        // group
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         const int64_t row = r0 + e;
         const bool row_ok = row < v.rows;
@@ -754,81 +822,96 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         };
         const bool trl = tr && lane == 0;
         long long tp = clock64();
+        Cursor cur = cursor_at(t_lo);
+        if (h == 1) advance(cur);
 #pragma unroll 1
-        for (int i = 0; i < T; ++i) {
+        for (int i = h; i < T; i += 2) {
             const int bd = i % ND, b = i % NW, s = i % NSY;
-            if (!wwait(dfull(bd), (i / ND) & 1, 9)) break;
-            if (trl) tp = clock64();
-            tc_fence_after();
-            uint32_t yh[32];
-            tmem_ld32(tmem + lane_off + bd * TN + 32 * h, yh);
-            tmem_wait_ld();
-            if (trl) phase_mark(tr, 20, tp);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(dempty(bd));
-            if (!wwait(yfull(s), (i / NSY) & 1, 10)) break;
-            if (trl) tp = clock64();
             int64_t col0;
             int nvalid, x0, z0;
-            tile_info(t_lo + i, col0, nvalid, x0, z0);
-            const uint8_t* ys = sm + LY::kY + s * kYStageBytes;
-            float yv[32];
-            if (prm.trans) {
-#pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    yv[c] = *reinterpret_cast<const float*>(ys + (32 * h + c) * (TM * 4) + e * 4);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float4 f = *reinterpret_cast<const float4*>(ys + h * (kYStageBytes / 2) + e * 128 +
-                                                                      ((j ^ (e & 7)) << 4));
-                    yv[4 * j + 0] = f.x;
-                    yv[4 * j + 1] = f.y;
-                    yv[4 * j + 2] = f.z;
-                    yv[4 * j + 3] = f.w;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(yempty(s));
-            if (trl) phase_mark(tr, 21, tp);
-            // observed columns of this row within the half: bit c of `obs`
-            const int nv = min(32, max(0, nvalid - 32 * h));
-            uint32_t obs = row_ok ? (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u)) : 0u;
-            if (prm.mbits && obs) {
-                const int64_t cbase = col0 + 32 * h;
-                if (prm.trans) {
-                    uint32_t m = 0;
-                    for (int c = 0; c < nv; ++c)
-                        m |= (uint32_t)mask_bit(prm.mbits, (cbase + c) * v.rows + row) << c;
-                    obs &= m;
-                } else {
-                    const int64_t idx0 = (cbase / v.c_in) * v.rows * v.c_in + row * v.c_in + (cbase % v.c_in);
-                    const int64_t w0 = idx0 >> 5;
-                    const int sh = (int)(idx0 & 31);
-                    uint64_t m = prm.mbits[w0];
-                    if (sh) m |= (uint64_t)prm.mbits[w0 + 1] << 32;
-                    obs &= (uint32_t)(m >> sh);
-                }
-            }
-            uint32_t wa2[16], wb2[16];
-#pragma unroll
-            for (int c = 0; c < 32; c += 2) {
-                float a0, b0, a1, b1;
-                tc_weights<WK>(yv[c], __uint_as_float(yh[c]), w, a0, b0);
-                tc_weights<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), w, a1, b1);
-                const bool o0 = (obs >> c) & 1u, o1 = (obs >> (c + 1)) & 1u;
-                wa2[c >> 1] = pack_bf16(o0 ? a0 : 0.f, o1 ? a1 : 0.f);
-                if (DEN) wb2[c >> 1] = pack_bf16(o0 ? b0 : 0.f, o1 ? b1 : 0.f);
-            }
-            if (trl) phase_mark(tr, 22, tp);
+            tile_info(cur, col0, nvalid, x0, z0);
+            advance(cur);
+            advance(cur);
+            if (!wwait(dfull(bd), (i / ND) & 1, 9)) break;
+            if (!wwait(yfull(s), (i / NSY) & 1, 10)) break;
             if (!wwait(wempty(b), ((i / NW) & 1) ^ 1, 11)) break;
             if (trl) tp = clock64();
             tc_fence_after();
-            // W row halves into TMEM: this warp's lanes, columns 16*h.. of buffer b
-            tmem_st<16>(t_wa + lane_off + b * 32 + 16 * h, wa2);
-            if (DEN) tmem_st<16>(t_wb + lane_off + b * 32 + 16 * h, wb2);
-            if (trl) phase_mark(tr, 23, tp);
+            const uint8_t* ys = sm + LY::kY + s * kYStageBytes;
+#pragma unroll 1
+            for (int hh = 0; hh < 2; ++hh) {
+                uint32_t yh[32];
+                tmem_ld32(tmem + lane_off + bd * TN + 32 * hh, yh);
+                float yv[32];
+                if (prm.trans) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        yv[c] = *reinterpret_cast<const float*>(ys + (32 * hh + c) * (TM * 4) + e * 4);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 f = *reinterpret_cast<const float4*>(ys + hh * (kYStageBytes / 2) + e * 128 +
+                                                                          ((j ^ (e & 7)) << 4));
+                        yv[4 * j + 0] = f.x;
+                        yv[4 * j + 1] = f.y;
+                        yv[4 * j + 2] = f.z;
+                        yv[4 * j + 3] = f.w;
+                    }
+                }
+                tmem_wait_ld();
+                if (hh == 1) {
+                    // both halves of yhat and Y are in registers: release the buffers
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(dempty(bd));
+                        mbar_arrive(yempty(s));
+                    }
+                }
+                // observed columns of this row within the half: bit c of `obs`
+                const int nv = min(32, max(0, nvalid - 32 * hh));
+                uint32_t obs = row_ok ? (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u)) : 0u;
+                if (prm.mbits && obs) {
+                    const int64_t cbase = col0 + 32 * hh;
+                    if (prm.trans) {
+                        uint32_t m = 0;
+                        for (int c = 0; c < nv; ++c)
+                            m |= (uint32_t)mask_bit(prm.mbits, (cbase + c) * v.rows + row) << c;
+                        obs &= m;
+                    } else {
+                        const int64_t idx0 = (cbase / v.c_in) * v.rows * v.c_in + row * v.c_in + (cbase % v.c_in);
+                        const int64_t w0 = idx0 >> 5;
+                        const int sh = (int)(idx0 & 31);
+                        uint64_t m = prm.mbits[w0];
+                        if (sh) m |= (uint64_t)prm.mbits[w0 + 1] << 32;
+                        obs &= (uint32_t)(m >> sh);
+                    }
+                }
+                uint32_t wa2[16], wb2[16];
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    float a0, b0, a1, b1;
+                    tc_weights<WK>(yv[c], __uint_as_float(yh[c]), w, a0, b0);
+                    tc_weights<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), w, a1, b1);
+                    wa2[c >> 1] = pack_bf16(a0, a1);
+                    if (DEN) wb2[c >> 1] = pack_bf16(b0, b1);
+                }
+                if (obs != 0xffffffffu) {
+                    // unobserved, padding or out-of-range entries: clear their BF16 halves
+                    // (this also drops the Inf/NaN weights of entries with yhat == 0)
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const uint32_t m = (((obs >> (2 * q)) & 1u) ? 0x0000ffffu : 0u) |
+                                           (((obs >> (2 * q + 1)) & 1u) ? 0xffff0000u : 0u);
+                        wa2[q] &= m;
+                        if (DEN) wb2[q] &= m;
+                    }
+                }
+                // W row half into TMEM: this warp's lanes, columns 16*hh.. of buffer b
+                tmem_st<16>(t_wa + lane_off + b * 32 + 16 * hh, wa2);
+                if (DEN) tmem_st<16>(t_wb + lane_off + b * 32 + 16 * hh, wb2);
+            }
+            if (trl) phase_mark(tr, 22, tp);
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
