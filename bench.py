@@ -42,8 +42,8 @@ CPU_BASELINE_ROWS = 64  # rows of factor A updated by the cpu_baseline leg
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=512, help="cube side (512 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -80,10 +80,14 @@ def kernel_hash():
 def load_traffic():
     """DRAM bytes per launch of the fused pass from the committed ncu summary,
     or None when the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "fused_pass_traffic.json")
+    path = os.path.join(ROOT, "profiles", "fused_pass_traffic.txt")
     try:
+        d = {}
         with open(path) as fh:
-            d = json.load(fh)
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    d[k.strip()] = v.strip()
         if d.get("kernel_hash") == kernel_hash():
             return float(d["bytes_per_launch_full"])
     except Exception:
@@ -101,35 +105,51 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (receive time, line)
+        self.window = None
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
+        """Start sampling every 20 ms and wait (up to wait_s) for the first sample."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < wait_s and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t_begin: float, t_end: float):
+        """Host wall-clock bounds of the timed region."""
+        self.window = (t_begin, t_end)
 
     def stop(self):
         if not self.proc:
             return None
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
+        lines = self.lines
+        if self.window:
+            inside = [x for x in lines if self.window[0] <= x[0] <= self.window[1] + 0.025]
+            if not inside:  # region shorter than the sampling interval: the first sample after it began
+                inside = [x for x in lines if x[0] >= self.window[0]][:1]
+            lines = inside
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -236,25 +256,26 @@ def run_ours(args):
     def fresh():
         return [f.clone() for f in init]
 
+    sampler = ClockSampler(local)
+    sampler.start()
     plan = nef.Plan(p.model_str, dims, precision="bf16", profile=True, stream=stream)
     fs = fresh()
     for _ in range(args.warmup):
         plan.fit(Y, None, fs, p.alpha, p.beta, 1)
     plan.check()
     plan.profile(reset=True)
-
-    sampler = ClockSampler(local)
-    sampler.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    t_begin = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
         plan.fit(Y, None, fs, p.alpha, p.beta, 1)
     ev1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(t_begin, time.time())
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()

@@ -33,6 +33,10 @@
 #include "nef_device.cuh"
 #include "nef_internal.h"
 
+#ifndef NEF_TC_SUSPEND_NS
+#define NEF_TC_SUSPEND_NS 20000u
+#endif
+
 namespace nef {
 namespace tc {
 
@@ -86,14 +90,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                  : "memory");
 }
 
+// Potentially blocking test of a phase: the thread may sleep until the phase
+// completes or kSuspendNs nanoseconds pass, so waiting warps spend no issue slots.
+constexpr uint32_t kSuspendNs = NEF_TC_SUSPEND_NS;
 __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok;
 }
@@ -294,6 +301,12 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N, int a_mn_major, 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t mul_bf16x2(uint32_t a, uint32_t b) {
+    const __nv_bfloat162 r =
+        __hmul2(*reinterpret_cast<const __nv_bfloat162*>(&a), *reinterpret_cast<const __nv_bfloat162*>(&b));
+    return *reinterpret_cast<const uint32_t*>(&r);
 }
 
 __device__ __forceinline__ void unpack_bf16x8(const uint4& q, float (&f)[8]) {
@@ -588,18 +601,21 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             constexpr uint32_t idesc1 = make_idesc(TM, TN, 0, 0);
             constexpr uint32_t idesc2 = make_idesc(TM, BP, 0, 1);
             bool ok = mbar_wait(pfull, 0, abort_flag, prm.err, 3, tr);
+            // Q descriptors of stage 0 (the 14-bit start-address field of a stage or
+            // K-step offset is added to it; shared addresses stay below 256 KB)
+            const uint64_t qdesc1 = make_sdesc(base + LY::kQ, 16, 8 * RB, swz_code(RB));
+            const uint64_t qdesc2 = make_sdesc(base + LY::kQ, TN * RB, 8 * RB, swz_code(RB));
             // MMA1 of tile i: yhat into TMEM buffer i % ND
             auto mma1 = [&](int i) -> bool {
                 const int sq = i % NSQ, b = i % ND;
                 if (!mbar_wait(qfull(sq), (i / NSQ) & 1, abort_flag, prm.err, 4, tr)) return false;
                 if (!mbar_wait(dempty(b), ((i / ND) & 1) ^ 1, abort_flag, prm.err, 5, tr)) return false;
                 tc_fence_after();
-                const uint32_t q_addr = base + LY::kQ + sq * LY::kQStage;
+                // descriptor of K-step k: start address field advanced by k * 32 B
+                const uint64_t bd0 = qdesc1 + (uint64_t)((sq * LY::kQStage) >> 4);
 #pragma unroll
-                for (int k = 0; k < BP / 16; ++k) {
-                    const uint64_t bd = make_sdesc(q_addr + k * 32, 16, 8 * RB, swz_code(RB));
-                    tc_mma_ts(tmem + b * TN, t_p + k * 8, bd, idesc1, k > 0 ? 1u : 0u);
-                }
+                for (int k = 0; k < BP / 16; ++k)
+                    tc_mma_ts(tmem + b * TN, t_p + k * 8, bd0 + (uint64_t)(k * 2), idesc1, k > 0 ? 1u : 0u);
                 tc_commit(dfull(b));
                 return true;
             };
@@ -607,10 +623,10 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             auto mma2 = [&](int i) {
                 const int bw = i % NW, sq = i % NSQ;
                 tc_fence_after();
-                const uint32_t q_addr = base + LY::kQ + sq * LY::kQStage;
+                const uint64_t bd0 = qdesc2 + (uint64_t)((sq * LY::kQStage) >> 4);
 #pragma unroll
                 for (int k = 0; k < TN / 16; ++k) {
-                    const uint64_t bd = make_sdesc(q_addr + k * 16 * RB, TN * RB, 8 * RB, swz_code(RB));
+                    const uint64_t bd = bd0 + (uint64_t)((k * 16 * RB) >> 4);
                     const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
                     tc_mma_ts(t_snum, t_wa + bw * 32 + k * 8, bd, idesc2, acc);
                     if (DEN) tc_mma_ts(t_sden, t_wb + bw * 32 + k * 8, bd, idesc2, acc);
@@ -705,16 +721,14 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                     if (ok) {
                         const uint4 raw = *reinterpret_cast<const uint4*>(vsrc + off);
                         if (has_c) {
+                            // packed BF16 products: the exact product of two BF16 values
+                            // fits in FP32, so this rounds exactly like an FP32 product
+                            // converted to BF16
                             const uint4 gv = *reinterpret_cast<const uint4*>(gsrc + jj * 16);
-                            float acc[8], f[8];
-                            unpack_bf16x8(raw, acc);
-                            unpack_bf16x8(gv, f);
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) acc[e] *= f[e];
-                            outv.x = pack_bf16(acc[0], acc[1]);
-                            outv.y = pack_bf16(acc[2], acc[3]);
-                            outv.z = pack_bf16(acc[4], acc[5]);
-                            outv.w = pack_bf16(acc[6], acc[7]);
+                            outv.x = mul_bf16x2(raw.x, gv.x);
+                            outv.y = mul_bf16x2(raw.y, gv.y);
+                            outv.z = mul_bf16x2(raw.z, gv.z);
+                            outv.w = mul_bf16x2(raw.w, gv.w);
                         } else {
                             outv = raw;
                         }
