@@ -15,13 +15,14 @@
 // the Y stream, the staged source rows and Q only.  At the end the epilogue
 // warps copy S from TMEM to the per-split partial buffers.
 //
-// Warp roles (448 threads): warp 0 TMA producer + TMEM allocator, warp 1 MMA
-// issuer, warps 2-5 Q/P operand builders (two threads per tile column, each
-// building half of the bond chunks), warps 6-13 epilogue.  Epilogue warp w
-// reads TMEM lanes 32*(w%4).. (one tile row per thread) and owns columns
-// 32*((w-6)/4)..+31 of each tile, so every SM sub-partition runs two epilogue
-// warps that hide each other's latency.  Every mbarrier wait is bounded: on timeout the CTA raises an
-// error flag, drains its own in-flight copies and MMAs, frees TMEM and exits.
+// Warp roles (512 threads, 128 registers each): warp 0 TMA producer (Y tiles
+// and the staged source rows) + TMEM allocator, warp 1 MMA issuer, warps 2-3
+// Q operand builders (one thread per tile column), warps 4-15 epilogue in three
+// groups of four that take turns on the tiles.  Epilogue warp w reads TMEM
+// lanes 32*(w%4).. (one tile row per thread), so every SM sub-partition runs
+// one warp of each group.  Every mbarrier wait is bounded: on timeout the CTA
+// raises an error flag, drains its own in-flight copies and MMAs, frees TMEM
+// and exits.
 #pragma once
 
 #include <cuda.h>
@@ -42,9 +43,11 @@ namespace tc {
 
 constexpr int TM = 128;        // rows per CTA (TMEM lanes)
 constexpr int TN = 64;         // columns per tile
-constexpr int kThreads = 448;   // 14 warps
-constexpr int kEpiWarps = 8;
-constexpr int kOpWarps = 4;
+constexpr int kThreads = 512;   // 16 warps: 128 registers per thread
+constexpr int kOpWarps = 2;
+constexpr int kGroupWarps = 4;  // one epilogue group: one warp per TMEM lane quarter
+constexpr int kEpiGroups = 3;
+constexpr int kEpiWarps = kEpiGroups * kGroupWarps;
 constexpr int kEpiWarp0 = 2 + kOpWarps;  // first epilogue warp
 constexpr int kYStageBytes = TM * TN * 4;   // 32 KB
 constexpr uint32_t kTmemCols = 512;
@@ -208,6 +211,55 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
+// Elected-issue forms: the whole warp executes them with warp-uniform operands
+// and elect.sync lets one lane issue.  Issuing from warp-uniform code keeps the
+// operands in uniform registers; issuing from a one-lane branch costs several
+// times more per instruction.  The same lane is elected every time, so commits
+// track the MMAs that lane issued.
+__device__ __forceinline__ void tc_mma_ts_e(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit_e(uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx_e(uint32_t bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}" ::"r"(bar), "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d_e(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                              uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n\t}" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_e(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n\t}" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -362,7 +414,7 @@ struct Layout {
     static constexpr int NSY = (BP == 64) ? 4 : (BP == 32 ? 5 : 6);  // Y stages
     static constexpr int NSV = (BP == 64) ? 6 : 8;                    // staged source-row stages
     static constexpr int NSQ = (BP == 64) ? 5 : 6;                    // Q stages
-    static constexpr int NW = DEN ? 2 : 3;                            // W buffers (TMEM)
+    static constexpr int NW = DEN ? (BP == 16 ? 3 : 2) : 4;           // W buffers (TMEM)
     static constexpr int ND = (DEN && BP == 64) ? 3 : 4;              // yhat buffers (TMEM)
     static constexpr int RB = BP * 2;                        // bytes per bond row (BF16)
     static constexpr int kY = 0;                             // NSY x 32 KB
@@ -442,7 +494,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     if (tid == 0) {
         for (int s = 0; s < NSY; ++s) {
             mbar_init(yfull(s), 1);
-            mbar_init(yempty(s), kEpiWarps / 2);
+            mbar_init(yempty(s), kGroupWarps);
         }
         for (int s = 0; s < LY::NSV; ++s) {
             mbar_init(vfull(s), 1);
@@ -450,16 +502,16 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         }
         for (int s = 0; s < NSQ; ++s) { mbar_init(qfull(s), kOpWarps); mbar_init(qempty(s), 1); }
         // yhat, Y and W buffers of a tile are released by the four warps of the
-        // epilogue group that processes it
+        // epilogue group that processes it; P is written by epilogue group 0
         for (int b = 0; b < ND; ++b) {
             mbar_init(dfull(b), 1);
-            mbar_init(dempty(b), kEpiWarps / 2);
+            mbar_init(dempty(b), kGroupWarps);
         }
         for (int b = 0; b < NW; ++b) {
-            mbar_init(wfull(b), kEpiWarps / 2);
+            mbar_init(wfull(b), kGroupWarps);
             mbar_init(wempty(b), 1);
         }
-        mbar_init(pfull, kOpWarps);
+        mbar_init(pfull, kGroupWarps);
         mbar_init(sfull, 1);
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -518,9 +570,14 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         }
     };
 
+    // waits of the warp-uniform producer and MMA loops (every lane polls)
+    auto uwait = [&](uint32_t bar, uint32_t par, int code) {
+        return __all_sync(0xffffffffu, mbar_wait(bar, par, abort_flag, prm.err, code, lane == 0 ? tr : nullptr));
+    };
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
-        if (lane == 0) {
+        // The whole warp runs the loop; one elected lane issues the copies.
+        {
             // Staged source rows (qmode 1) run NSV - 1 tiles ahead of the Y stream.
             // In qmode 1, c_in is 1 or a multiple of TN, so tile t starts at column
             // t*TN: the staged row (col mod m, m a multiple of TN) advances by TN per
@@ -547,13 +604,13 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             auto issue_v = [&]() {
                 const int sv = iv % NSV;
                 // slot of tile iv - NSV: free once every operand warp has built that Q
-                if (!mbar_wait(vempty(sv), ((iv / NSV) & 1) ^ 1, abort_flag, prm.err, 14, tr)) {
+                if (!uwait(vempty(sv), ((iv / NSV) & 1) ^ 1, 14)) {
                     vok = false;
                     return;
                 }
-                mbar_expect_tx(vfull(sv), TN * RB + (has_c ? RB : 0));
-                tma_load_2d(base + LY::kV + sv * (TN * RB), vmap, 0, (int)vrow, vfull(sv));
-                if (has_c) tma_load_2d(base + LY::kG + sv * LY::kGSlot, cmap, 0, (int)crow, vfull(sv));
+                mbar_expect_tx_e(vfull(sv), TN * RB + (has_c ? RB : 0));
+                tma_load_2d_e(base + LY::kV + sv * (TN * RB), vmap, 0, (int)vrow, vfull(sv));
+                if (has_c) tma_load_2d_e(base + LY::kG + sv * LY::kGSlot, cmap, 0, (int)crow, vfull(sv));
                 vrow += TN;
                 if (vrow == vmod) vrow = 0;
                 if (++cc == per) {
@@ -570,18 +627,18 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 if (prm.qmode && vok && iv < T) issue_v();  // rows of tile i + NSV - 1
                 if (!vok) break;
                 const int s = i % NSY;
-                if (!mbar_wait(yempty(s), ((i / NSY) & 1) ^ 1, abort_flag, prm.err, 1, tr)) break;
+                if (!uwait(yempty(s), ((i / NSY) & 1) ^ 1, 1)) break;
                 int64_t col0;
                 int nvalid, x0, z0;
                 tile_info(cur, col0, nvalid, x0, z0);
                 advance(cur);
                 const uint32_t dst = base + LY::kY + s * kYStageBytes;
-                mbar_expect_tx(yfull(s), kYStageBytes);
+                mbar_expect_tx_e(yfull(s), kYStageBytes);
                 if (prm.trans) {
-                    tma_load_2d(dst, ymap, (int)r0, x0, yfull(s));
+                    tma_load_2d_e(dst, ymap, (int)r0, x0, yfull(s));
                 } else {
-                    tma_load_3d(dst, ymap, x0, (int)r0, z0, yfull(s));
-                    tma_load_3d(dst + kYStageBytes / 2, ymap, x0 + 32, (int)r0, z0, yfull(s));
+                    tma_load_3d_e(dst, ymap, x0, (int)r0, z0, yfull(s));
+                    tma_load_3d_e(dst + kYStageBytes / 2, ymap, x0 + 32, (int)r0, z0, yfull(s));
                 }
                 issued = i + 1;
             }
@@ -597,10 +654,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        // The whole warp runs the loop; one elected lane (the same one every time)
+        // issues the MMAs and the commits that track them.
+        {
             constexpr uint32_t idesc1 = make_idesc(TM, TN, 0, 0);
             constexpr uint32_t idesc2 = make_idesc(TM, BP, 0, 1);
-            bool ok = mbar_wait(pfull, 0, abort_flag, prm.err, 3, tr);
+            bool ok = uwait(pfull, 0, 3);
             // Q descriptors of stage 0 (the 14-bit start-address field of a stage or
             // K-step offset is added to it; shared addresses stay below 256 KB)
             const uint64_t qdesc1 = make_sdesc(base + LY::kQ, 16, 8 * RB, swz_code(RB));
@@ -608,15 +667,15 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             // MMA1 of tile i: yhat into TMEM buffer i % ND
             auto mma1 = [&](int i) -> bool {
                 const int sq = i % NSQ, b = i % ND;
-                if (!mbar_wait(qfull(sq), (i / NSQ) & 1, abort_flag, prm.err, 4, tr)) return false;
-                if (!mbar_wait(dempty(b), ((i / ND) & 1) ^ 1, abort_flag, prm.err, 5, tr)) return false;
+                if (!uwait(qfull(sq), (i / NSQ) & 1, 4)) return false;
+                if (!uwait(dempty(b), ((i / ND) & 1) ^ 1, 5)) return false;
                 tc_fence_after();
                 // descriptor of K-step k: start address field advanced by k * 32 B
                 const uint64_t bd0 = qdesc1 + (uint64_t)((sq * LY::kQStage) >> 4);
 #pragma unroll
                 for (int k = 0; k < BP / 16; ++k)
-                    tc_mma_ts(tmem + b * TN, t_p + k * 8, bd0 + (uint64_t)(k * 2), idesc1, k > 0 ? 1u : 0u);
-                tc_commit(dfull(b));
+                    tc_mma_ts_e(tmem + b * TN, t_p + k * 8, bd0 + (uint64_t)(k * 2), idesc1, k > 0 ? 1u : 0u);
+                tc_commit_e(dfull(b));
                 return true;
             };
             // MMA2 of tile i: S += W(i) . Q(i); frees the W buffer and the Q stage
@@ -628,63 +687,39 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 for (int k = 0; k < TN / 16; ++k) {
                     const uint64_t bd = bd0 + (uint64_t)((k * 16 * RB) >> 4);
                     const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-                    tc_mma_ts(t_snum, t_wa + bw * 32 + k * 8, bd, idesc2, acc);
-                    if (DEN) tc_mma_ts(t_sden, t_wb + bw * 32 + k * 8, bd, idesc2, acc);
+                    tc_mma_ts_e(t_snum, t_wa + bw * 32 + k * 8, bd, idesc2, acc);
+                    if (DEN) tc_mma_ts_e(t_sden, t_wb + bw * 32 + k * 8, bd, idesc2, acc);
                 }
-                tc_commit(wempty(bw));
-                tc_commit(qempty(sq));
+                tc_commit_e(wempty(bw));
+                tc_commit_e(qempty(sq));
             };
             // MMA1 runs LA tiles ahead of MMA2.  LA < NSQ keeps the Q stage of tile
             // i + LA free once MMA2(i - 1) is issued, LA < ND the yhat buffer once the
             // epilogue has finished tile i - 1, so the blocking waits cannot deadlock.
-            constexpr int LA = 2;
+            // With LA >= kEpiGroups, the group that finishes tile i - kEpiGroups finds
+            // yhat of its next tile i already issued.
+            constexpr int LA = ND - 1;
             static_assert(LA < NSQ && LA < ND, "MMA1 look-ahead");
             for (int j = 0; ok && j < LA && j < T; ++j) ok = mma1(j);
             for (int i = 0; ok && i < T; ++i) {
                 if (i + LA < T && !mma1(i + LA)) break;
-                if (!mbar_wait(wfull(i % NW), (i / NW) & 1, abort_flag, prm.err, 6, tr)) break;
+                if (!uwait(wfull(i % NW), (i / NW) & 1, 6)) break;
                 mma2(i);
             }
-            tc_commit(sfull);
-            // drain: wait until every MMA issued by this thread has completed
-            tc_commit(drain);
+            tc_commit_e(sfull);
+            // drain: wait until every MMA issued by the elected lane has completed
+            tc_commit_e(drain);
             volatile int dummy_abort = 0;
             mbar_wait(drain, 0, &dummy_abort, prm.err, 7);
         }
     } else if (warp < kEpiWarp0) {
-        // ------------------------------------------------------ P / Q operand builders
-        // Thread q builds bond chunks [hq*NH, hq*NH + NH) of column cq of every Q
-        // tile.  The gathered rows of the next tile are loaded while the current one
-        // is built, so the L2 latency of the gathers overlaps the build and the wait
-        // for a free stage.
-        const int q = tid - 64;                 // 0..127
+        // ------------------------------------------------------ Q operand builders
+        // Thread q builds column cq of every Q tile (all bond chunks; in the
+        // gathered mode in two halves of NH chunks).
+        const int q = tid - 64;                 // 0 .. kOpWarps*32 - 1
         constexpr int NCH = BP / 8;             // 16-byte chunks per bond row
-        constexpr int NH = NCH / 2;             // chunks per thread
-        const int cq = q & 63, hq = q >> 6;
-        {
-            // P row of TMEM lane (warp % 4) * 32 + lane (the lanes this warp may access)
-            const SrcDesc& ps = v.P.src[0];
-            const uint16_t* pbase = static_cast<const uint16_t*>(ps.ptr);
-            const int pl = ((warp & 3) << 5) + lane;
-            const int64_t prow = r0 + pl;
-            const bool ok = prow < v.rows;
-            const int64_t pr = ok ? src_row_tc(ps, prow) : 0;
-            uint32_t pv[BP / 2];
-#pragma unroll
-            for (int j = 0; j < NCH; ++j) {
-                const uint4 x =
-                    ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8) : make_uint4(0, 0, 0, 0);
-                pv[4 * j] = x.x;
-                pv[4 * j + 1] = x.y;
-                pv[4 * j + 2] = x.z;
-                pv[4 * j + 3] = x.w;
-            }
-            tmem_st<(BP / 2 < 8 ? 8 : BP / 2)>(t_p + ((uint32_t)((warp & 3) * 32) << 16), pv);
-            tmem_wait_st();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(pfull);
-        }
+        static_assert(kOpWarps * 32 == TN, "one operand thread per tile column");
+        const int cq = q;
         if (prm.qmode) {
             // The rows of source q_var and the single row of source q_const (if any) of
             // each tile are staged by TMA in their own ring, NSV - 1 tiles ahead of the
@@ -694,14 +729,11 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             const bool has_c = prm.q_const >= 0;
             long long tp = clock64();
             const bool trl = tr && lane == 0;
-            Cursor cur = cursor_at(t_lo);
+            // Every qmode-1 tile is full (c_in is a multiple of TN, or c_in == 1 and
+            // c_out is a multiple of the staged source's extent), so the build has no
+            // column predicate.
 #pragma unroll 1
             for (int i = 0; i < T; ++i) {
-                int64_t col0;
-                int nvalid, x0, z0;
-                tile_info(cur, col0, nvalid, x0, z0);
-                advance(cur);
-                const bool ok = cq < nvalid;
                 const int s = i % NSV, sq = i % NSQ;
                 if (!__all_sync(0xffffffffu, mbar_wait(vfull(s), (i / NSV) & 1, abort_flag, prm.err, 13,
                                                        lane == 0 ? tr : nullptr)))
@@ -713,28 +745,26 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 const uint8_t* vsrc = sm + LY::kV + s * (TN * RB);
                 const uint8_t* gsrc = sm + LY::kG + s * LY::kGSlot;
                 uint8_t* qdst = sm + LY::kQ + sq * LY::kQStage;
+                uint4 vv[NCH];
 #pragma unroll
-                for (int j = 0; j < NH; ++j) {
-                    const int jj = hq * NH + j;
-                    const uint32_t off = swz<RB>(cq * RB + jj * 16);
-                    uint4 outv = make_uint4(0, 0, 0, 0);
-                    if (ok) {
-                        const uint4 raw = *reinterpret_cast<const uint4*>(vsrc + off);
-                        if (has_c) {
-                            // packed BF16 products: the exact product of two BF16 values
-                            // fits in FP32, so this rounds exactly like an FP32 product
-                            // converted to BF16
-                            const uint4 gv = *reinterpret_cast<const uint4*>(gsrc + jj * 16);
-                            outv.x = mul_bf16x2(raw.x, gv.x);
-                            outv.y = mul_bf16x2(raw.y, gv.y);
-                            outv.z = mul_bf16x2(raw.z, gv.z);
-                            outv.w = mul_bf16x2(raw.w, gv.w);
-                        } else {
-                            outv = raw;
-                        }
+                for (int jj = 0; jj < NCH; ++jj)
+                    vv[jj] = *reinterpret_cast<const uint4*>(vsrc + swz<RB>(cq * RB + jj * 16));
+                if (has_c) {
+                    // packed BF16 products: the exact product of two BF16 values fits
+                    // in FP32, so this rounds exactly like an FP32 product converted
+                    // to BF16
+#pragma unroll
+                    for (int jj = 0; jj < NCH; ++jj) {
+                        const uint4 gv = *reinterpret_cast<const uint4*>(gsrc + jj * 16);
+                        vv[jj].x = mul_bf16x2(vv[jj].x, gv.x);
+                        vv[jj].y = mul_bf16x2(vv[jj].y, gv.y);
+                        vv[jj].z = mul_bf16x2(vv[jj].z, gv.z);
+                        vv[jj].w = mul_bf16x2(vv[jj].w, gv.w);
                     }
-                    *reinterpret_cast<uint4*>(qdst + off) = outv;
                 }
+#pragma unroll
+                for (int jj = 0; jj < NCH; ++jj)
+                    *reinterpret_cast<uint4*>(qdst + swz<RB>(cq * RB + jj * 16)) = vv[jj];
                 if (trl) phase_mark(tr, 17, tp);
                 fence_proxy_async();
                 __syncwarp();
@@ -746,6 +776,11 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             }
 
         } else {
+        // Gathered rows, in steps of half a column: step 2i + h builds chunks
+        // [h*NH, h*NH + NH) of tile i.  The rows of the next step are loaded while
+        // the current one is built, so the L2 latency of the gathers overlaps the
+        // build and the wait for a free stage.
+        constexpr int NH = NCH / 2;
         const int nsrc = v.Q.nsrc;
         const uint16_t* s0 = static_cast<const uint16_t*>(v.Q.src[0].ptr);
         const uint16_t* s1 = static_cast<const uint16_t*>(v.Q.src[nsrc > 1 ? 1 : 0].ptr);
@@ -754,11 +789,11 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         int64_t nrow[kMaxSrc];
         bool nok = false;
         Cursor gcur = cursor_at(t_lo);
-        auto issue = [&]() {  // gathered rows of the next tile into nx0/nx1
+        auto issue = [&](int hs) {  // rows of half hs of the tile at gcur into nx0/nx1
             int64_t col0;
             int nvalid, x0, z0;
             tile_info(gcur, col0, nvalid, x0, z0);
-            advance(gcur);
+            if (hs == 1) advance(gcur);
             nok = cq < nvalid;
             const int64_t col = col0 + cq;
 #pragma unroll
@@ -766,15 +801,16 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 nrow[s2] = (nok && s2 < nsrc) ? src_row_tc(v.Q.src[s2], col) : 0;
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
-                const int jj = hq * NH + j;
+                const int jj = hs * NH + j;
                 nx0[j] = nok ? *reinterpret_cast<const uint4*>(s0 + nrow[0] * ld0 + jj * 8) : make_uint4(0, 0, 0, 0);
                 nx1[j] = (nok && nsrc > 1) ? *reinterpret_cast<const uint4*>(s1 + nrow[1] * ld1 + jj * 8)
                                            : make_uint4(0, 0, 0, 0);
             }
         };
-        if (T > 0) issue();
+        if (T > 0) issue(0);
 #pragma unroll 1
-        for (int i = 0; i < T; ++i) {
+        for (int st = 0; st < 2 * T; ++st) {
+            const int i = st >> 1, hh = st & 1;
             uint4 c0[NH], c1[NH];
             int64_t crow[kMaxSrc];
 #pragma unroll
@@ -782,15 +818,15 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
 #pragma unroll
             for (int s2 = 0; s2 < kMaxSrc; ++s2) crow[s2] = nrow[s2];
             const bool cok = nok;
-            if (i + 1 < T) issue();
+            if (st + 1 < 2 * T) issue((st + 1) & 1);
             const int sq = i % NSQ;
-            if (!__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8,
-                                                   lane == 0 ? tr : nullptr)))
+            if (hh == 0 && !__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag,
+                                                              prm.err, 8, lane == 0 ? tr : nullptr)))
                 break;
             uint8_t* qdst = sm + LY::kQ + sq * LY::kQStage;
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
-                const int jj = hq * NH + j;
+                const int jj = hh * NH + j;
                 float acc[8], f[8];
                 unpack_bf16x8(c0[j], acc);
                 if (nsrc > 1) {
@@ -813,17 +849,20 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 outv.w = pack_bf16(acc[6], acc[7]);
                 *reinterpret_cast<uint4*>(qdst + swz<RB>(cq * RB + jj * 16)) = outv;
             }
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(qfull(sq));
+            if (hh == 1) {
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(qfull(sq));
+            }
         }
         }
     } else {
         // ------------------------------------------------------ epilogue
-        // Two groups of four warps take alternate tiles (group h: tiles h, h + 2,
-        // ...), so one group's weight arithmetic overlaps the other's waits and
-        // loads.  Warp w of a group owns TMEM lanes 32*(w%4).. (one tile row per
-        // thread) and all 64 columns of its tiles, in two halves of 32.
+        // kEpiGroups groups of four warps take turns on the tiles (group h: tiles
+        // h, h + kEpiGroups, ...), so one group's weight arithmetic overlaps the
+        // others' waits and loads.  Warp w of a group owns TMEM lanes 32*(w%4)..
+        // (one tile row per thread) and all 64 columns of its tiles, in two halves
+        // of 32.  Group 0 also writes P into TMEM before its first tile.
         const int e = ((warp & 3) << 5) + lane;      // tile row == TMEM lane
         const int h = (warp - kEpiWarp0) >> 2;        // group
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
@@ -836,16 +875,37 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         };
         const bool trl = tr && lane == 0;
         long long tp = clock64();
+        if (h == 0) {
+            // P row of TMEM lane e (this warp's lane quarter)
+            const SrcDesc& ps = v.P.src[0];
+            const uint16_t* pbase = static_cast<const uint16_t*>(ps.ptr);
+            constexpr int NCH = BP / 8;
+            const int64_t pr = row_ok ? src_row_tc(ps, row) : 0;
+            uint32_t pv[BP / 2];
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+                const uint4 x =
+                    row_ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8) : make_uint4(0, 0, 0, 0);
+                pv[4 * j] = x.x;
+                pv[4 * j + 1] = x.y;
+                pv[4 * j + 2] = x.z;
+                pv[4 * j + 3] = x.w;
+            }
+            tmem_st<(BP / 2 < 8 ? 8 : BP / 2)>(t_p + lane_off, pv);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(pfull);
+        }
         Cursor cur = cursor_at(t_lo);
-        if (h == 1) advance(cur);
+        for (int k = 0; k < h; ++k) advance(cur);
 #pragma unroll 1
-        for (int i = h; i < T; i += 2) {
+        for (int i = h; i < T; i += kEpiGroups) {
             const int bd = i % ND, b = i % NW, s = i % NSY;
             int64_t col0;
             int nvalid, x0, z0;
             tile_info(cur, col0, nvalid, x0, z0);
-            advance(cur);
-            advance(cur);
+            for (int k = 0; k < kEpiGroups; ++k) advance(cur);
             if (!wwait(dfull(bd), (i / ND) & 1, 9)) break;
             if (!wwait(yfull(s), (i / NSY) & 1, 10)) break;
             if (!wwait(wempty(b), ((i / NW) & 1) ^ 1, 11)) break;
@@ -932,11 +992,11 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             if (lane == 0) mbar_arrive(wfull(b));
             if (trl) phase_mark(tr, 24, tp);
         }
-        // ---- S readout: the first four epilogue warps copy S_num, the other four S_den
+        // ---- S readout: group 0 copies S_num, group 1 S_den
         bool have = (T > 0) && mbar_wait(sfull, 0, abort_flag, prm.err, 12, lane == 0 ? tr : nullptr);
         have = __all_sync(0xffffffffu, have);
         tc_fence_after();
-        if (h == 0 || DEN) {
+        if (h == 0 || (DEN && h == 1)) {
             const uint32_t tsrc = (h == 0) ? t_snum : t_sden;
             float* dst = ((h == 0) ? prm.s_num : prm.s_den) + (sp * v.rows + row) * BP;
 #pragma unroll 1
