@@ -258,12 +258,12 @@ def run_ours(args):
 
     sampler = ClockSampler(local)
     sampler.start()
-    plan = nef.Plan(p.model_str, dims, precision="bf16", profile=True, stream=stream)
+    # timed region: one nef_fit call of K sweeps (sweeps 3.. replay a captured
+    # CUDA graph of one sweep); warm-up: W sweeps the same way
+    plan = nef.Plan(p.model_str, dims, precision="bf16", stream=stream)
     fs = fresh()
-    for _ in range(args.warmup):
-        plan.fit(Y, None, fs, p.alpha, p.beta, 1)
+    plan.fit(Y, None, fs, p.alpha, p.beta, args.warmup)
     plan.check()
-    plan.profile(reset=True)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -271,8 +271,7 @@ def run_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     t_begin = time.time()
     ev0.record(stream)
-    for _ in range(args.steps):
-        plan.fit(Y, None, fs, p.alpha, p.beta, 1)
+    plan.fit(Y, None, fs, p.alpha, p.beta, args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     sampler.mark(t_begin, time.time())
@@ -281,12 +280,30 @@ def run_ours(args):
     clocks = sampler.stop()
     plan.check()
     ms = ev0.elapsed_time(ev1)
-    prof = plan.profile(reset=True)
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     value = world * args.steps / (ms / 1e3)
+
+    # kernel durations: the same sweeps launched eagerly with a CUDA event pair
+    # around every fused-pass launch (on the plan's stream)
+    n_prof = min(args.steps, 100)
+    pplan = nef.Plan(p.model_str, dims, precision="bf16", profile=True, stream=stream)
+    gp = fresh()
+    pplan.fit(Y, None, gp, p.alpha, p.beta, 2)
+    pplan.profile(reset=True)
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    pplan.fit(Y, None, gp, p.alpha, p.beta, n_prof)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    pplan.check()
+    ms_prof = e2.elapsed_time(e3)
+    prof = pplan.profile(reset=True)
+    del pplan, gp
 
     # roofline of the dominant kernel: the tensor-core fused pass
     hbm, bf16, src = load_peaks()
@@ -301,23 +318,23 @@ def run_ours(args):
                 "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
                 "kernel": "k_view_tc (tcgen05 fused pass)", "avg_launch_us": avg_s * 1e6,
                 "algorithmic_bytes_per_launch": alg_bytes,
-                "share_of_step": tc_ms / ms}
+                "share_of_step": tc_ms / ms_prof,
+                "timing": f"CUDA events around each fused-pass launch in {n_prof} eagerly launched sweeps "
+                          f"right after the timed region"}
     launches_per_sweep = plan.launches(False)
     loss_bf16 = plan.loss(Y, None, fs, p.alpha, p.beta)[0]
 
     variants = {}
     if rank == 0 and not args.no_variants:
         # plain FP32 CUDA-core sweep from the same start, same number of sweeps
-        plan32 = nef.Plan(p.model_str, dims, precision="fp32", profile=True, stream=stream)
+        plan32 = nef.Plan(p.model_str, dims, precision="fp32", stream=stream)
         g = fresh()
-        for _ in range(args.warmup):
-            plan32.fit(Y, None, g, p.alpha, p.beta, 1)
+        plan32.fit(Y, None, g, p.alpha, p.beta, args.warmup)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            plan32.fit(Y, None, g, p.alpha, p.beta, 1)
+        plan32.fit(Y, None, g, p.alpha, p.beta, args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
         plan32.check()
@@ -331,6 +348,22 @@ def run_ours(args):
                                   "sweeps": args.warmup + args.steps,
                                   "note": "the FP32 sweep matches the FP64 oracle to 1e-5 (parity tests)"}
         del plan32
+        # the same BF16 sweeps with the per-sweep loss trace (loss summed inside the first pass)
+        n_lt = min(args.steps, 200)
+        g = fresh()
+        tr = torch.full((n_lt + 1,), float("nan"), dtype=torch.float64, device="cuda")
+        plan.fit(Y, None, g, p.alpha, p.beta, 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plan.fit(Y, None, g, p.alpha, p.beta, n_lt, loss_trace=tr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms_lt = e0.elapsed_time(e1)
+        last = float(tr[-1].item())
+        ref_last = plan.loss(Y, None, g, p.alpha, p.beta)[0]
+        variants["bf16_loss_trace"] = {"value": n_lt / (ms_lt / 1e3), "unit": UNIT, "sweeps": n_lt,
+                                       "final_trace_vs_nef_loss_rel": abs(last - ref_last) / ref_last}
 
     e2e = None
     if not args.no_e2e:

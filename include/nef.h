@@ -69,10 +69,18 @@ typedef struct {
                         /* stream (nef_plan_profile); 2: also count wait and phase cycles   */
                         /* inside the tensor-core pass (nef_tc_trace; slows it down)        */
     void* stream;       /* cudaStream_t used by every call on the plan                      */
+    double tol;         /* > 0: nef_fit stops after the first sweep k >= 2 whose preceding  */
+                        /* relative loss decrease (L[k-2] - L[k-1]) / L[k-2] is below tol   */
+                        /* (the training-loss stopping rule of App. B); 0 = exactly iters   */
+    double* loss_trace; /* device, iters + 1 doubles, or NULL: loss_trace[k] = Eq. 3.1's    */
+                        /* objective (sum over observed entries of D) after k sweeps;       */
+                        /* entries past an early stop are left untouched                    */
+    int eager;          /* nonzero: launch every kernel of every sweep directly; zero: from */
+                        /* the third sweep on, replay a captured CUDA graph of one sweep    */
 } nef_options;
 
 /* Fill *opt with the defaults: NEF_FP32, eps = 1e-10, no data check, fused, no
- * profiling, stream NULL. */
+ * profiling, stream NULL, tol 0, no loss trace, graph replay. */
 void nef_default_options(nef_options* opt);
 
 /*
@@ -103,12 +111,31 @@ void nef_plan_destroy(nef_plan_t plan);
  *   factors : host array of L device pointers, updated in place
  *   alpha, beta : the (alpha,beta)-divergence parameters of App. B
  *   iters   : number of sweeps (0 is a no-op)
+ * The loss of the current factors is summed inside the first pass of every
+ * sweep (its Yhat is already on chip) when opt.loss_trace or opt.tol asks for
+ * it; one extra loss pass follows the last sweep.  With tol > 0 the stream is
+ * synchronised once per sweep to read the loss; nef_plan_sweeps reports how
+ * many sweeps ran.
  * Errors: NEF_EUNSUPPORTED for alpha == 0 with beta != 1; NEF_EINVAL for a
  * null pointer or iters < 0; NEF_EDATA if check_data found a bad Y entry
  * (factors untouched); NEF_ECUDA for a failed launch.
  */
 nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask,
                    void* const* factors, double alpha, double beta, int iters);
+
+/*
+ * nef_fit_ex -- nef_fit with a per-call stopping tolerance and loss trace
+ * (instead of the plan's opt.tol / opt.loss_trace).
+ *   tol        : as nef_options.tol (0 = exactly iters sweeps)
+ *   loss_trace : device, iters + 1 doubles, or NULL (as nef_options.loss_trace)
+ *   sweeps     : host, receives the number of sweeps run, or NULL
+ * Errors as nef_fit; NEF_EINVAL for tol < 0.
+ */
+nef_status nef_fit_ex(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
+                      double alpha, double beta, int iters, double tol, double* loss_trace, int* sweeps);
+
+/* Number of sweeps the last nef_fit on `plan` ran (iters unless tol stopped it). */
+int nef_plan_sweeps(nef_plan_t plan);
 
 /*
  * nef_update -- one inner step of Algorithm 1: update factor l only, with the

@@ -19,9 +19,9 @@ STATUS = {0: "NEF_OK", 1: "NEF_EINVAL", 2: "NEF_EPARSE", 3: "NEF_EUNSUPPORTED", 
 PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 
 # every symbol include/nef.h declares
-EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_update",
-           "nef_loss", "nef_plan_info", "nef_plan_launches", "nef_plan_profile", "nef_check",
-           "nef_fit_batched", "nef_cp3_update_static", "nef_last_error"]
+EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex",
+           "nef_plan_sweeps", "nef_update", "nef_loss", "nef_plan_info", "nef_plan_launches",
+           "nef_plan_profile", "nef_check", "nef_fit_batched", "nef_cp3_update_static", "nef_last_error"]
 # every symbol include/nef_debug.h declares
 DEBUG_EXPORTS = ["nef_tc_probe", "nef_tc_trace"]
 
@@ -29,7 +29,8 @@ DEBUG_EXPORTS = ["nef_tc_probe", "nef_tc_trace"]
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double),
                 ("check_data", ctypes.c_int), ("force_generic", ctypes.c_int),
-                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("eager", ctypes.c_int)]
 
 
 class NefError(RuntimeError):
@@ -58,6 +59,11 @@ def load(path: str = LIB_PATH):
     lib.nef_fit.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
                             ctypes.c_int]
     lib.nef_fit.restype = ctypes.c_int
+    lib.nef_fit_ex.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.nef_fit_ex.restype = ctypes.c_int
+    lib.nef_plan_sweeps.argtypes = [vp]
+    lib.nef_plan_sweeps.restype = ctypes.c_int
     lib.nef_update.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(vp), ctypes.c_double,
                                ctypes.c_double]
     lib.nef_update.restype = ctypes.c_int
@@ -158,7 +164,7 @@ class Plan:
 
     def __init__(self, model_str: str, dims: dict, precision: str = "fp32", eps: float = 1e-10,
                  check_data: bool = False, force_generic: bool = False, profile: int = 0,
-                 stream=None):
+                 stream=None, eager: bool = False):
         lib = load()
         obs, lat, terms = split_model(model_str)
         self.model_str = model_str
@@ -174,6 +180,7 @@ class Plan:
         opt.check_data = int(bool(check_data))
         opt.force_generic = int(bool(force_generic))
         opt.profile = int(profile)
+        opt.eager = int(bool(eager))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream()
@@ -228,10 +235,20 @@ class Plan:
                 raise ValueError(f"factor {t} must be a contiguous CUDA {want} tensor of shape {shp}")
 
     # -------------------------------------------------------------- ABI
-    def fit(self, Y, mask, factors, alpha, beta, iters):
+    def fit(self, Y, mask, factors, alpha, beta, iters, tol: float = 0.0, loss_trace=None):
+        """Run `iters` sweeps (nef_fit_ex).  ``loss_trace``: a float64 CUDA tensor of
+        at least iters + 1 entries that receives the loss after each sweep;
+        ``tol`` > 0 stops early.  Returns the number of sweeps run."""
         self._check_args(Y, mask, factors)
-        check(load().nef_fit(self._h, self._ptr(Y), self._ptr(mask), self._facs(factors),
-                             float(alpha), float(beta), int(iters)))
+        if loss_trace is not None:
+            import torch
+            if loss_trace.dtype != torch.float64 or not loss_trace.is_cuda or loss_trace.numel() < int(iters) + 1:
+                raise ValueError("loss_trace must be a float64 CUDA tensor with iters + 1 entries")
+        done = ctypes.c_int(0)
+        check(load().nef_fit_ex(self._h, self._ptr(Y), self._ptr(mask), self._facs(factors),
+                                float(alpha), float(beta), int(iters), float(tol),
+                                self._ptr(loss_trace), ctypes.byref(done)))
+        return int(done.value)
 
     def update(self, l, Y, mask, factors, alpha, beta):
         self._check_args(Y, mask, factors)

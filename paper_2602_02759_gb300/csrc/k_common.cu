@@ -161,6 +161,36 @@ __global__ void k_sum_f64(const double* __restrict__ part, int n, double* out) {
     }
 }
 
+// out[0..1] = sums of part[0..n) and part[n..2n) (loss, observed count); the
+// loss is also written to trace[*count] (if trace) and *count is incremented.
+__global__ void k_loss_append(const double* __restrict__ part, int n, double* trace, int* count, double* out) {
+    __shared__ double sh[2][32];
+    double a = 0.0, c = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        a += part[k];
+        c += part[n + k];
+    }
+    a = warp_sum(a);
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = a;
+        sh[1][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const bool ok = threadIdx.x < (blockDim.x >> 5);
+        double va = ok ? sh[0][threadIdx.x] : 0.0, vc = ok ? sh[1][threadIdx.x] : 0.0;
+        va = warp_sum(va);
+        vc = warp_sum(vc);
+        if (threadIdx.x == 0) {
+            out[0] = va;
+            out[1] = vc;
+            if (trace) trace[*count] = va;
+            *count += 1;
+        }
+    }
+}
+
 __global__ void k_convert_bf16(const float* __restrict__ src, int64_t n, uint16_t* __restrict__ dst) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
@@ -430,6 +460,12 @@ cudaError_t launch_fill(T* p, int64_t n, T v, cudaStream_t st) {
 
 cudaError_t launch_sum_f64(const double* part, int n, double* out, cudaStream_t st) {
     k_sum_f64<<<1, 1024, 0, st>>>(part, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_append(const double* part, int n, double* trace, int* count, double* out,
+                               cudaStream_t st) {
+    k_loss_append<<<1, 1024, 0, st>>>(part, n, trace, count, out);
     return cudaGetLastError();
 }
 

@@ -244,7 +244,13 @@ cudaError_t dispatch_flags(const T* y, const uint32_t* mbits, const ViewDesc& v,
         return run<T, TM, TN, BP, false, false, true>(y, mbits, v, w, L, n_split, s_num, s_den,
                                                       loss_part, st, n_ctas);
     }
-    if (loss) return cudaErrorInvalidValue;
+    if (loss) {  // update pass that also sums the loss of the current factors
+        if (need_den)
+            return run<T, TM, TN, BP, true, true, true>(y, mbits, v, w, L, n_split, s_num, s_den,
+                                                        loss_part, st, n_ctas);
+        return run<T, TM, TN, BP, false, true, true>(y, mbits, v, w, L, n_split, s_num, s_den,
+                                                     loss_part, st, n_ctas);
+    }
     if (need_den)
         return run<T, TM, TN, BP, true, true, false>(y, mbits, v, w, L, n_split, s_num, s_den,
                                                      loss_part, st, n_ctas);

@@ -162,6 +162,8 @@ cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v
     p->s_den = s_den;
     p->err = err_flag;
     p->trace = trace;
+    p->loss_part = nullptr;
+    p->L = LossSpec{};
     *n_rb_out = (int)((v.rows + tc::TM - 1) / tc::TM);
     return cudaSuccess;
 }
@@ -170,7 +172,8 @@ cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v
 
 cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w,
                            int need_den, int n_split, float* s_num, float* s_den, int* err_flag,
-                           cudaStream_t st, TcLaunchInfo* info, unsigned long long* trace) {
+                           cudaStream_t st, TcLaunchInfo* info, unsigned long long* trace, const LossSpec* loss,
+                           double* loss_part) {
     if (!tc_view_supported(v, need_den)) return cudaErrorNotSupported;
     CUtensorMap map, vmap, cmap;
     tc::Params p;
@@ -178,6 +181,10 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
     cudaError_t e =
         make_params(y, mbits, v, w, n_split, s_num, s_den, err_flag, trace, &map, &vmap, &cmap, &p, &n_rb);
     if (e != cudaSuccess) return e;
+    if (loss) {
+        p.loss_part = loss_part;
+        p.L = *loss;
+    }
     const int grid = n_rb * n_split;
     if (info) {
         info->n_ctas = grid;

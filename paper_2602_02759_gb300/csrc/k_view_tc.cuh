@@ -71,6 +71,11 @@ struct Params {
     // q_var has consecutive rows (TMA-staged with the Y tile) and source q_const
     // (or none, -1) a single row
     int qmode, q_var, q_const;
+    // optional loss of the current factors (Eq. 3.1 with App. B's D): per-CTA
+    // sums over observed entries at loss_part[cta], their count at
+    // loss_part[n_ctas + cta]; NULL = not computed
+    double* loss_part;
+    LossSpec L;
 };
 
 constexpr int kTraceSites = 32;   // 0: CTA lifetime cycles, 1..13: wait sites, 16..: busy phases
@@ -371,6 +376,13 @@ __device__ __forceinline__ void unpack_bf16x8(const uint4& q, float (&f)[8]) {
     }
 }
 
+// One loss term D(y, yhat) in FP32 (App. B); KL in closed form.
+template <int WK>
+__device__ __forceinline__ float tc_loss(float y, float yh, const LossSpec& L) {
+    if (WK == WK_KL) return (y > 0.f ? y * __logf(__fdividef(y, yh)) : 0.f) - y + yh;
+    return divergence<float>(y, yh, L);
+}
+
 template <int WK>
 __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& w, float& wa, float& wb) {
     if (WK == WK_KL) {
@@ -434,7 +446,8 @@ struct Layout {
     static constexpr int kNumBars = 2 * NSY + 2 * NSQ + 2 * ND + 2 * NW + 3 + 2 * NSV;
     static constexpr int kMisc = kBar + kNumBars * 8;         // tmem slot + abort flag
     static constexpr int kTrace = kMisc + 16;                 // kTraceSites counters
-    static constexpr int kTotal = kTrace + kTraceSites * 8;
+    static constexpr int kLoss = kTrace + kTraceSites * 8;    // per epilogue warp: loss sum, count
+    static constexpr int kTotal = kLoss + kEpiWarps * 16;
     static constexpr int kAlloc = kTotal + 1024;              // slack for 1024-B alignment
     static_assert(kAlloc <= 232448, "shared memory per CTA");
     // tensor-memory columns (128 lanes x 32 bit): yhat buffers, S_num, S_den, P
@@ -899,6 +912,8 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         }
         Cursor cur = cursor_at(t_lo);
         for (int k = 0; k < h; ++k) advance(cur);
+        const bool do_loss = prm.loss_part != nullptr;
+        double lsum = 0.0, lcnt = 0.0;
 #pragma unroll 1
         for (int i = h; i < T; i += kEpiGroups) {
             const int bd = i % ND, b = i % NW, s = i % NSY;
@@ -962,6 +977,15 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                     }
                 }
                 uint32_t wa2[16], wb2[16];
+                if (do_loss) {
+                    // loss terms of the observed entries: FP32 within the half, FP64 across
+                    float t = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        if ((obs >> c) & 1u) t += tc_loss<WK>(yv[c], __uint_as_float(yh[c]), prm.L);
+                    lsum += (double)t;
+                    lcnt += (double)__popc(obs);
+                }
 #pragma unroll
                 for (int c = 0; c < 32; c += 2) {
                     float a0, b0, a1, b1;
@@ -991,6 +1015,27 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             __syncwarp();
             if (lane == 0) mbar_arrive(wfull(b));
             if (trl) phase_mark(tr, 24, tp);
+        }
+        if (do_loss) {
+            // per-CTA loss partial: warp sums, then the epilogue warps (named barrier 1)
+            lsum = warp_sum(lsum);
+            lcnt = warp_sum(lcnt);
+            double* lred = reinterpret_cast<double*>(sm + LY::kLoss);
+            const int ew = warp - kEpiWarp0;
+            if (lane == 0) {
+                lred[2 * ew] = lsum;
+                lred[2 * ew + 1] = lcnt;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+            if (ew == 0 && lane == 0) {
+                double ts = 0.0, tcn = 0.0;
+                for (int k = 0; k < kEpiWarps; ++k) {
+                    ts += lred[2 * k];
+                    tcn += lred[2 * k + 1];
+                }
+                prm.loss_part[blockIdx.x] = ts;
+                prm.loss_part[gridDim.x + blockIdx.x] = tcn;
+            }
         }
         // ---- S readout: group 0 copies S_num, group 1 S_den
         bool have = (T > 0) && mbar_wait(sfull, 0, abort_flag, prm.err, 12, lane == 0 ? tr : nullptr);

@@ -212,10 +212,16 @@ struct TcLaunchInfo {
 
 cudaError_t launch_convert_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st);
 
+// Sum per-CTA loss partials (part[0..n): loss, part[n..2n): count) into out[0..1];
+// also append the loss to trace[*count] when trace is set, and increment *count.
+cudaError_t launch_loss_append(const double* part, int n, double* trace, int* count, double* out,
+                               cudaStream_t st);
+
 cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v,
                            const WeightSpec& w, int need_den, int n_split, float* s_num,
                            float* s_den, int* err_flag, cudaStream_t st, TcLaunchInfo* info,
-                           unsigned long long* trace = nullptr);
+                           unsigned long long* trace = nullptr, const LossSpec* loss = nullptr,
+                           double* loss_part = nullptr);
 
 bool tc_view_supported(const ViewDesc& v, int need_den);
 

@@ -235,6 +235,14 @@ struct nef_plan_s {
     std::vector<int64_t> fac_version;
     int64_t version_counter = 0;
     int64_t max_ld = 16;
+    // per-sweep loss and graph replay of sweeps
+    int* loss_count = nullptr;        // device: entries appended to the loss trace
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t sweep_graph = nullptr;
+    std::vector<const void*> graph_key;  // arguments the captured sweep was recorded with
+    double graph_ab[2] = {0.0, 0.0};
+    int last_sweeps = 0;
 };
 
 namespace nef {
@@ -848,7 +856,8 @@ nef_status prof_begin(nef_plan_t p, cudaStream_t st, cudaEvent_t* a, cudaEvent_t
 
 template <typename T>
 nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbits,
-                    void* const* factors, const WeightSpec& w, const UpdateSpec& u, cudaStream_t st) {
+                    void* const* factors, const WeightSpec& w, const UpdateSpec& u, cudaStream_t st,
+                    const LossSpec* loss = nullptr, int* n_part = nullptr) {
     const Model& md = p->md;
     const int64_t nl = md.fac_size(pp.l);
     T* num = static_cast<T*>(buf_ptr(p, B_NUM));
@@ -869,8 +878,11 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
         g.n = md.N;
         g.n_lat_el = 1;
         for (int x = md.M; x < g.n_let; ++x) g.n_lat_el *= md.dim[x];
+        const int np = loss ? (int)std::min<int64_t>((md.N + 255) / 256, p->loss_part_cap / 2) : 0;
+        if (n_part) *n_part = np;
         NEF_CUDA(launch_generic_weights<T>(g, y, mbits, w, static_cast<T*>(buf_ptr(p, B_WA)),
-                                           static_cast<T*>(buf_ptr(p, B_WB)), nullptr, nullptr, 0, st));
+                                           static_cast<T*>(buf_ptr(p, B_WB)), loss, loss ? p->loss_part : nullptr,
+                                           np, st));
         NEF_TRY(run_ein<T>(p, pp.gen_num, factors, st));
         NEF_TRY(run_ein<T>(p, pp.gen_den, factors, st));
         NEF_CUDA(launch_update_mirror<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, (int)ldims.size(),
@@ -895,13 +907,15 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
             TcLaunchInfo info{};
             NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den, n_split,
                                     reinterpret_cast<float*>(spn), reinterpret_cast<float*>(spd),
-                                    p->tc_err, st, &info, p->tc_trace));
+                                    p->tc_err, st, &info, p->tc_trace, loss, loss ? p->loss_part : nullptr));
+            if (n_part) *n_part = info.n_ctas;
         }
     } else {
         ViewDesc v = bind_view(p, pp, false);
         int n_ctas = 0;
         NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, need_den, n_split, spn, need_den ? spd : nullptr,
-                                     nullptr, nullptr, st, &n_ctas));
+                                     loss, loss ? p->loss_part : nullptr, st, &n_ctas));
+        if (n_part) *n_part = n_ctas;
     }
     if (p->opt.profile) {
         NEF_CUDA(cudaEventRecord(e1, st));
@@ -976,22 +990,182 @@ nef_status prologue(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
     return NEF_OK;
 }
 
+// One sweep of Algorithm 1 (or the single update only_l).  With `loss`, the
+// first pass also sums the loss of the factors it starts from, and the sum is
+// appended to the loss trace.
+template <typename T>
+nef_status sweep_once(nef_plan_t p, const T* y, const uint32_t* mbits, void* const* factors, const WeightSpec& w,
+                      const UpdateSpec& u, const LossSpec* loss, double* trace, int only_l, cudaStream_t st) {
+    bool first = true;
+    for (int l = 0; l < p->md.L; ++l) {
+        if (only_l >= 0 && l != only_l) continue;
+        const LossSpec* lp = first ? loss : nullptr;
+        first = false;
+        int n_part = 0;
+        NEF_TRY(run_pass<T>(p, p->pass[l], y, mbits, factors, w, u, st, lp, &n_part));
+        if (lp) NEF_CUDA(launch_loss_append(p->loss_part, n_part, trace, p->loss_count, p->loss_out, st));
+    }
+    return NEF_OK;
+}
+
+// Loss of the current factors without an update: the fused kernel of the first
+// viewable pass with its partial products discarded (or the unfused weights).
+template <typename T>
+nef_status loss_pass(nef_plan_t p, const T* y, const uint32_t* mbits, void* const* factors, const WeightSpec& w,
+                     const LossSpec& L, cudaStream_t st, int* n_part);
+
+nef_status ensure_capture_stream(nef_plan_t p) {
+    if (p->cap_stream) return NEF_OK;
+    NEF_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    NEF_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    NEF_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    return NEF_OK;
+}
+
 template <typename T>
 nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* const* factors,
-                    double al, double be, int iters, int only_l) {
+                    double al, double be, int iters, int only_l, double tol = 0.0, double* trace = nullptr) {
     cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
     const uint32_t* mbits = nullptr;
+    p->last_sweeps = 0;
     NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
     const WeightSpec w = weight_spec(al, be);
     const UpdateSpec u = update_spec(al, be, p->opt.eps);
+    const LossSpec L = loss_spec(al, be);
+    const bool want_loss = only_l < 0 && (trace != nullptr || tol > 0.0);
+    const LossSpec* lp = want_loss ? &L : nullptr;
     const T* y = static_cast<const T*>(Y);
-    if (iters > 0) NEF_TRY(init_sources<T>(p, factors, st));
-    for (int it = 0; it < iters; ++it) {
-        for (int l = 0; l < p->md.L; ++l) {
-            if (only_l >= 0 && l != only_l) continue;
-            NEF_TRY(run_pass<T>(p, p->pass[l], y, mbits, factors, w, u, st));
+    if (iters <= 0) return NEF_OK;
+    NEF_TRY(init_sources<T>(p, factors, st));
+    if (want_loss) NEF_CUDA(cudaMemsetAsync(p->loss_count, 0, sizeof(int), st));
+    std::vector<double> hist;  // losses read back for the tol rule
+    auto converged = [&]() -> nef_status {
+        double h[2];
+        NEF_CUDA(cudaMemcpyAsync(h, p->loss_out, sizeof(h), cudaMemcpyDeviceToHost, st));
+        NEF_CUDA(cudaStreamSynchronize(st));
+        hist.push_back(h[0]);
+        return NEF_OK;
+    };
+    auto stop_now = [&]() {
+        const size_t k = hist.size();
+        return tol > 0.0 && k >= 2 && hist[k - 2] != 0.0 && (hist[k - 2] - hist[k - 1]) / hist[k - 2] < tol;
+    };
+    // sweep 1 runs directly (it also settles which contracted operands each pass rebuilds)
+    NEF_TRY(sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, only_l, st));
+    int done = 1;
+    if (tol > 0.0) NEF_TRY(converged());
+    const bool graph = !p->opt.eager && !p->opt.profile && only_l < 0 && iters >= 3;
+    if (done < iters && !stop_now()) {
+        if (graph) {
+            // sweeps 2.. replay one captured sweep on the plan's capture stream
+            NEF_TRY(ensure_capture_stream(p));
+            std::vector<const void*> key = {Y, mbits, trace, reinterpret_cast<const void*>((intptr_t)want_loss)};
+            for (int f = 0; f < p->md.L; ++f) key.push_back(factors[f]);
+            if (!p->sweep_graph || key != p->graph_key || p->graph_ab[0] != al || p->graph_ab[1] != be) {
+                if (p->sweep_graph) {
+                    cudaGraphExecDestroy(p->sweep_graph);
+                    p->sweep_graph = nullptr;
+                }
+                NEF_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+                const nef_status rs = sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, -1, p->cap_stream);
+                cudaGraph_t g = nullptr;
+                const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &g);
+                if (rs != NEF_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return rs;
+                }
+                NEF_CUDA(ec);
+                const cudaError_t ei = cudaGraphInstantiate(&p->sweep_graph, g, 0);
+                cudaGraphDestroy(g);
+                NEF_CUDA(ei);
+                p->graph_key = key;
+                p->graph_ab[0] = al;
+                p->graph_ab[1] = be;
+            }
+            NEF_CUDA(cudaEventRecord(p->ev_fork, st));
+            NEF_CUDA(cudaStreamWaitEvent(p->cap_stream, p->ev_fork, 0));
+            while (done < iters) {
+                NEF_CUDA(cudaGraphLaunch(p->sweep_graph, p->cap_stream));
+                ++done;
+                if (tol > 0.0) {
+                    double h[2];
+                    NEF_CUDA(cudaMemcpyAsync(h, p->loss_out, sizeof(h), cudaMemcpyDeviceToHost, p->cap_stream));
+                    NEF_CUDA(cudaStreamSynchronize(p->cap_stream));
+                    hist.push_back(h[0]);
+                    if (stop_now()) break;
+                }
+            }
+            NEF_CUDA(cudaEventRecord(p->ev_join, p->cap_stream));
+            NEF_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
+            // the replays changed every factor behind the host bookkeeping: mark the
+            // contracted operands stale
+            for (int f = 0; f < p->md.L; ++f) p->fac_version[f] = ++p->version_counter;
+        } else {
+            while (done < iters) {
+                NEF_TRY(sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, only_l, st));
+                ++done;
+                if (tol > 0.0) {
+                    NEF_TRY(converged());
+                    if (stop_now()) break;
+                }
+            }
         }
     }
+    p->last_sweeps = done;
+    if (want_loss) {
+        // the loss after the last sweep
+        int n_part = 0;
+        NEF_TRY(loss_pass<T>(p, y, mbits, factors, w, L, st, &n_part));
+        NEF_CUDA(launch_loss_append(p->loss_part, n_part, trace, p->loss_count, p->loss_out, st));
+    }
+    return NEF_OK;
+}
+
+template <typename T>
+nef_status loss_pass(nef_plan_t p, const T* y, const uint32_t* mbits, void* const* factors, const WeightSpec& w,
+                     const LossSpec& L, cudaStream_t st, int* n_part) {
+    int vl = -1;
+    for (int l = 0; l < p->md.L; ++l)
+        if (!p->pass[l].generic) { vl = l; break; }
+    if (vl < 0) {
+        GenericRecon g{};
+        const Model& md = p->md;
+        g.n_obs = md.M;
+        g.n_let = (int)md.letter.size();
+        g.n_fac = md.L;
+        for (int x = 0; x < g.n_let; ++x) g.dim[x] = md.dim[x];
+        for (int f = 0; f < md.L; ++f) {
+            for (int x = 0; x < g.n_let; ++x) g.fst[f][x] = md.fac_stride(f, x);
+            g.fac[f] = factors[f];
+        }
+        g.n = md.N;
+        g.n_lat_el = 1;
+        for (int x = md.M; x < g.n_let; ++x) g.n_lat_el *= md.dim[x];
+        *n_part = (int)std::min<int64_t>((md.N + 255) / 256, p->loss_part_cap / 2);
+        NEF_CUDA(launch_generic_weights<T>(g, y, mbits, w, nullptr, nullptr, &L, p->loss_part, *n_part, st));
+        return NEF_OK;
+    }
+    PassPlan& pp = p->pass[vl];
+    bool use_tc = false;
+    if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), 1);
+    NEF_TRY(refresh_sources<T>(p, pp, factors, st, use_tc));
+    if (use_tc) {
+        if constexpr (sizeof(T) == 4) {
+            ViewDesc v = bind_view(p, pp, true);
+            TcLaunchInfo info{};
+            NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, 1, pp.n_split,
+                                    static_cast<float*>(buf_ptr(p, B_SPART_N)),
+                                    static_cast<float*>(buf_ptr(p, B_SPART_D)), p->tc_err, st, &info, nullptr, &L,
+                                    p->loss_part));
+            *n_part = info.n_ctas;
+        }
+        return NEF_OK;
+    }
+    ViewDesc v = bind_view(p, pp, false);
+    const int64_t tm = sizeof(T) == 8 ? 32 : 64;
+    const int64_t n_rb = (v.rows + tm - 1) / tm;
+    int ns = (int)std::max<int64_t>(1, std::min<int64_t>(pp.n_split, p->loss_part_cap / 2 / n_rb));
+    NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, 0, ns, nullptr, nullptr, &L, p->loss_part, st, n_part));
     return NEF_OK;
 }
 
@@ -1070,6 +1244,11 @@ void destroy(nef_plan_t p) {
     if (p->flag) cudaFree(p->flag);
     if (p->tc_err) cudaFree(p->tc_err);
     if (p->tc_trace) cudaFree(p->tc_trace);
+    if (p->loss_count) cudaFree(p->loss_count);
+    if (p->sweep_graph) cudaGraphExecDestroy(p->sweep_graph);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto e : p->ev_pool) cudaEventDestroy(e);
     delete p;
 }
@@ -1234,16 +1413,17 @@ nef_status build_plan(nef_plan_t p) {
     NEF_CUDA(cudaMalloc(&p->ein_partial, p->ein_partial_cap * es));
     NEF_CUDA(cudaMalloc(&p->mask_bits, ((md.N + 31) / 32 + 1) * sizeof(uint32_t)));
     // loss partials: two doubles per CTA of the loss pass (view of the first viewable factor)
+    // (and the update passes that also sum the loss: one CTA per row block and split)
     int64_t loss_ctas = 152 * 64;
     for (auto& pp : p->pass) {
         if (pp.generic) continue;
-        const int64_t tm = p->prec == NEF_FP64 ? 32 : 64;
-        loss_ctas = std::max<int64_t>(loss_ctas, ((pp.view.rows + tm - 1) / tm) * 2);
-        break;
+        loss_ctas = std::max<int64_t>(loss_ctas, ((pp.view.rows + 31) / 32) * std::max<int64_t>(2, pp.n_split));
     }
     p->loss_part_cap = (int)(2 * loss_ctas);
     NEF_CUDA(cudaMalloc(&p->loss_part, p->loss_part_cap * sizeof(double)));
     NEF_CUDA(cudaMalloc(&p->loss_out, 2 * sizeof(double)));
+    NEF_CUDA(cudaMalloc(&p->loss_count, sizeof(int)));
+    NEF_CUDA(cudaMemset(p->loss_count, 0, sizeof(int)));
     NEF_CUDA(cudaMalloc(&p->flag, sizeof(int)));
     NEF_CUDA(cudaMalloc(&p->tc_err, sizeof(int)));
     NEF_CUDA(cudaMemset(p->tc_err, 0, sizeof(int)));
@@ -1267,6 +1447,9 @@ void nef_default_options(nef_options* opt) {
     opt->force_generic = 0;
     opt->profile = 0;
     opt->stream = nullptr;
+    opt->tol = 0.0;
+    opt->loss_trace = nullptr;
+    opt->eager = 0;
 }
 
 nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, const int64_t* ranks,
@@ -1303,15 +1486,31 @@ nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, con
 
 void nef_plan_destroy(nef_plan_t plan) { destroy(plan); }
 
-nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
-                   double alpha, double beta, int iters) {
+nef_status nef_fit_ex(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors, double alpha,
+                      double beta, int iters, double tol, double* loss_trace, int* sweeps) {
     g_err.clear();
+    if (sweeps) *sweeps = 0;
     if (!plan) return fail(NEF_EINVAL, "plan is NULL");
     if (iters < 0) return fail(NEF_EINVAL, "iters must be >= 0");
+    if (!(tol >= 0.0)) return fail(NEF_EINVAL, "tol must be >= 0");
     NEF_TRY(check_ab(alpha, beta));
-    if (plan->prec == NEF_FP64) return fit_impl<double>(plan, Y, mask, factors, alpha, beta, iters, -1);
-    return fit_impl<float>(plan, Y, mask, factors, alpha, beta, iters, -1);
+    const nef_status r = plan->prec == NEF_FP64
+                             ? fit_impl<double>(plan, Y, mask, factors, alpha, beta, iters, -1, tol, loss_trace)
+                             : fit_impl<float>(plan, Y, mask, factors, alpha, beta, iters, -1, tol, loss_trace);
+    if (sweeps) *sweeps = plan->last_sweeps;
+    return r;
 }
+
+nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
+                   double alpha, double beta, int iters) {
+    if (!plan) {
+        g_err = "plan is NULL";
+        return NEF_EINVAL;
+    }
+    return nef_fit_ex(plan, Y, mask, factors, alpha, beta, iters, plan->opt.tol, plan->opt.loss_trace, nullptr);
+}
+
+int nef_plan_sweeps(nef_plan_t plan) { return plan ? plan->last_sweeps : 0; }
 
 nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask, void* const* factors,
                       double alpha, double beta) {

@@ -20,6 +20,7 @@ namespace nef {
 
 template <typename T>
 cudaError_t launch_einsum(const EinDesc& d, T*, int64_t, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     const int nl = d.n_out + d.n_free;
     std::vector<int64_t> idx(nl);
     for (int64_t o = 0; o < d.n_out_el; ++o) {
@@ -48,9 +49,11 @@ cudaError_t launch_einsum(const EinDesc& d, T*, int64_t, cudaStream_t) {
         out[dst] = d.accumulate ? out[dst] + acc : acc;
     }
     return cudaSuccess;
+    });
 }
 
 cudaError_t launch_pack_mask(const uint8_t* m, int64_t n, uint32_t* bits, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     for (int64_t w = 0; w < (n + 31) / 32; ++w) {
         uint32_t v = 0;
         for (int b = 0; b < 32; ++b)
@@ -58,13 +61,16 @@ cudaError_t launch_pack_mask(const uint8_t* m, int64_t n, uint32_t* bits, cudaSt
         bits[w] = v;
     }
     return cudaSuccess;
+    });
 }
 
 template <typename T>
 cudaError_t launch_check_data(const T* y, int64_t n, int* flag, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     for (int64_t e = 0; e < n; ++e)
         if (!(y[e] >= 0) || std::isinf((double)y[e])) *flag = 1;
     return cudaSuccess;
+    });
 }
 
 template <typename T>
@@ -82,7 +88,12 @@ static T side_value(const SideDesc& sd, int64_t i, int b) {
 template <typename T>
 cudaError_t launch_view_simt(const T* y, const uint32_t* mbits, const ViewDesc& v,
                              const WeightSpec& w, int need_den, int n_split, T* s_num, T* s_den,
-                             const LossSpec* loss, double* loss_part, cudaStream_t, int* n_ctas) {
+                             const LossSpec* loss_in, double* loss_part, cudaStream_t, int* n_ctas) {
+    if (n_ctas) *n_ctas = 1;
+    const bool has_loss = loss_in != nullptr;
+    const LossSpec lval = loss_in ? *loss_in : LossSpec{};
+    return host_submit([=]() -> cudaError_t {
+    const LossSpec* loss = has_loss ? &lval : nullptr;
     const int64_t ncols = v.c_out * v.c_in;
     const int BP = v.bond_pad;
     if (s_num) {
@@ -114,38 +125,46 @@ cudaError_t launch_view_simt(const T* y, const uint32_t* mbits, const ViewDesc& 
         }
     }
     if (loss) { loss_part[0] = ls; loss_part[1] = lc; }
-    if (n_ctas) *n_ctas = 1;
     return cudaSuccess;
+    });
 }
 
 template <typename T>
 cudaError_t launch_reduce_splits(const T* part, int n_split, int64_t n, T* out, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     for (int64_t e = 0; e < n; ++e) {
         T acc = 0;
         for (int s = 0; s < n_split; ++s) acc += part[s * n + e];
         out[e] = acc;
     }
     return cudaSuccess;
+    });
 }
 
 template <typename T>
 cudaError_t launch_update(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
                           cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     for (int64_t e = 0; e < n; ++e) theta[e] = mu_update(theta[e], num[e], den[e], u);
     return cudaSuccess;
+    });
 }
 
 template <typename T>
 cudaError_t launch_fill(T* p, int64_t n, T v, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     for (int64_t e = 0; e < n; ++e) p[e] = v;
     return cudaSuccess;
+    });
 }
 
 cudaError_t launch_sum_f64(const double* part, int n, double* out, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     double s = 0;
     for (int k = 0; k < n; ++k) s += part[k];
     *out = s;
     return cudaSuccess;
+    });
 }
 
 cudaError_t launch_convert_bf16(const float*, int64_t, uint16_t*, cudaStream_t) {
@@ -154,8 +173,12 @@ cudaError_t launch_convert_bf16(const float*, int64_t, uint16_t*, cudaStream_t) 
 
 template <typename T>
 cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint32_t* mbits,
-                                   const WeightSpec& w, T* wa, T* wb, const LossSpec* loss,
+                                   const WeightSpec& w, T* wa, T* wb, const LossSpec* loss_in,
                                    double* loss_part, int n_part, cudaStream_t) {
+    const bool has_loss = loss_in != nullptr;
+    const LossSpec lval = loss_in ? *loss_in : LossSpec{};
+    return host_submit([=]() -> cudaError_t {
+    const LossSpec* loss = has_loss ? &lval : nullptr;
     double ls = 0, lc = 0;
     std::vector<int64_t> idx(g.n_let);
     for (int64_t e = 0; e < g.n; ++e) {
@@ -187,6 +210,7 @@ cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint
         loss_part[n_part] = lc;
     }
     return cudaSuccess;
+    });
 }
 
 static uint16_t bf16_bits_host(float x) {
@@ -211,6 +235,7 @@ static void decode(int64_t e, int nlet, const int64_t* dim, int64_t* idx) {
 
 template <typename T>
 cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     for (int64_t e = 0; e < d.n; ++e) {
         int64_t idx[kMaxFacLet];
         decode(e, d.nlet, d.dim, idx);
@@ -230,11 +255,15 @@ cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t
         write_mirrors_host<T>(d.mir, idx, d.nlet, th[e]);
     }
     return cudaSuccess;
+    });
 }
 
 template <typename T>
 cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
-                                 int nlet, const int64_t* dim, const MirrorDesc& m, cudaStream_t) {
+                                 int nlet, const int64_t* dim_in, const MirrorDesc& m, cudaStream_t) {
+    const std::vector<int64_t> dv(dim_in, dim_in + nlet);
+    return host_submit([=]() -> cudaError_t {
+    const int64_t* dim = dv.data();
     for (int64_t e = 0; e < n; ++e) {
         theta[e] = mu_update(theta[e], num[e], den[e], u);
         int64_t idx[kMaxFacLet];
@@ -242,21 +271,27 @@ cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n
         write_mirrors_host<T>(m, idx, nlet, theta[e]);
     }
     return cudaSuccess;
+    });
 }
 
 template <typename T>
-cudaError_t launch_mirror_init(const T* theta, int64_t n, int nlet, const int64_t* dim,
+cudaError_t launch_mirror_init(const T* theta, int64_t n, int nlet, const int64_t* dim_in,
                                const MirrorDesc& m, cudaStream_t) {
+    const std::vector<int64_t> dv(dim_in, dim_in + nlet);
+    return host_submit([=]() -> cudaError_t {
+    const int64_t* dim = dv.data();
     for (int64_t e = 0; e < n; ++e) {
         int64_t idx[kMaxFacLet];
         decode(e, nlet, dim, idx);
         write_mirrors_host<T>(m, idx, nlet, theta[e]);
     }
     return cudaSuccess;
+    });
 }
 
 template <typename T>
 cudaError_t launch_colsums(const ColsumDesc& d, int64_t, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
     for (int k = 0; k < d.n; ++k) {
         const ColsumJob& j = d.job[k];
         for (int64_t b = 0; b < j.ld; ++b) {
@@ -266,12 +301,29 @@ cudaError_t launch_colsums(const ColsumDesc& d, int64_t, cudaStream_t) {
         }
     }
     return cudaSuccess;
+    });
 }
 
 bool tc_view_supported(const ViewDesc&, int) { return false; }
 cudaError_t launch_view_tc(const float*, const uint32_t*, const ViewDesc&, const WeightSpec&, int,
-                           int, float*, float*, int*, cudaStream_t, TcLaunchInfo*, unsigned long long*) {
+                           int, float*, float*, int*, cudaStream_t, TcLaunchInfo*, unsigned long long*,
+                           const LossSpec*, double*) {
     return cudaErrorNotSupported;
+}
+
+cudaError_t launch_loss_append(const double* part, int n, double* trace, int* count, double* out, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
+        double a = 0, c = 0;
+        for (int k = 0; k < n; ++k) {
+            a += part[k];
+            c += part[n + k];
+        }
+        out[0] = a;
+        out[1] = c;
+        if (trace) trace[*count] = a;
+        *count += 1;
+        return cudaSuccess;
+    });
 }
 
 #define INST(T)                                                                                  \

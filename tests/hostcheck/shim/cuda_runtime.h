@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <vector>
 
 typedef int cudaError_t;
 typedef void* cudaStream_t;
@@ -24,14 +26,60 @@ inline cudaError_t cudaMalloc(T** p, size_t n) {
 }
 inline cudaError_t cudaFree(void* p) { std::free(p); return cudaSuccess; }
 inline cudaError_t cudaMemset(void* p, int v, size_t n) { std::memset(p, v, n); return cudaSuccess; }
-inline cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t = nullptr) {
-    std::memset(p, v, n);
+// Stream capture: while a capture is open, launches and async copies are
+// recorded instead of run; a graph launch replays them in order.
+struct HostGraph {
+    std::vector<std::function<void()>> ops;
+};
+typedef HostGraph* cudaGraph_t;
+typedef HostGraph* cudaGraphExec_t;
+inline HostGraph*& host_capture() {
+    static HostGraph* g = nullptr;
+    return g;
+}
+template <class F>
+inline cudaError_t host_submit(F f) {
+    if (host_capture()) {
+        host_capture()->ops.push_back([f]() { (void)f(); });
+        return cudaSuccess;
+    }
+    return f();
+}
+enum cudaStreamCaptureMode { cudaStreamCaptureModeGlobal = 0, cudaStreamCaptureModeThreadLocal = 1,
+                             cudaStreamCaptureModeRelaxed = 2 };
+enum { cudaStreamNonBlocking = 1, cudaEventDisableTiming = 2 };
+inline cudaError_t cudaStreamBeginCapture(cudaStream_t, cudaStreamCaptureMode) {
+    host_capture() = new HostGraph;
     return cudaSuccess;
+}
+inline cudaError_t cudaStreamEndCapture(cudaStream_t, cudaGraph_t* g) {
+    *g = host_capture();
+    host_capture() = nullptr;
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphInstantiate(cudaGraphExec_t* e, cudaGraph_t g, unsigned long long) {
+    *e = new HostGraph(*g);
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphLaunch(cudaGraphExec_t e, cudaStream_t) {
+    for (auto& f : e->ops) f();
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphDestroy(cudaGraph_t g) { delete g; return cudaSuccess; }
+inline cudaError_t cudaGraphExecDestroy(cudaGraphExec_t e) { delete e; return cudaSuccess; }
+inline cudaError_t cudaStreamCreateWithFlags(cudaStream_t* s, unsigned) {
+    static int dummy;
+    *s = &dummy;
+    return cudaSuccess;
+}
+inline cudaError_t cudaStreamDestroy(cudaStream_t) { return cudaSuccess; }
+
+inline cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t = nullptr) {
+    return host_submit([=]() { std::memset(p, v, n); return cudaSuccess; });
 }
 inline cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t n, cudaMemcpyKind,
                                    cudaStream_t = nullptr) {
-    std::memcpy(d, s, n);
-    return cudaSuccess;
+    return host_submit([=]() { std::memcpy(d, s, n); return cudaSuccess; });
 }
 inline cudaError_t cudaMemcpy(void* d, const void* s, size_t n, cudaMemcpyKind) {
     std::memcpy(d, s, n);
@@ -42,6 +90,8 @@ typedef struct CUevent_st* cudaEvent_t;
 inline cudaError_t cudaEventCreate(cudaEvent_t* e) { *e = nullptr; return cudaSuccess; }
 inline cudaError_t cudaEventDestroy(cudaEvent_t) { return cudaSuccess; }
 inline cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t = nullptr) { return cudaSuccess; }
+inline cudaError_t cudaEventCreateWithFlags(cudaEvent_t* e, unsigned) { *e = nullptr; return cudaSuccess; }
+inline cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned) { return cudaSuccess; }
 inline cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t, cudaEvent_t) { *ms = 0.f; return cudaSuccess; }
 inline cudaError_t cudaGetLastError() { return cudaSuccess; }
 inline const char* cudaGetErrorString(cudaError_t) { return "host test double error"; }

@@ -25,7 +25,8 @@ NEF_FP32, NEF_BF16, NEF_FP64 = 0, 1, 2
 class Opt(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double),
                 ("check_data", ctypes.c_int), ("force_generic", ctypes.c_int),
-                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("eager", ctypes.c_int)]
 
 
 @pytest.fixture(scope="module")
@@ -45,6 +46,8 @@ def lib():
     lib.nef_plan_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_int]
     lib.nef_last_error.restype = ctypes.c_char_p
     lib.nef_default_options.argtypes = [ctypes.POINTER(Opt)]
+    lib.nef_fit_ex.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int)]
     return lib
 
 
@@ -57,7 +60,7 @@ def split(model_str):
     return list(rhs), lat, lhs.split(",")
 
 
-def make_plan(lib, model_str, dims, prec, force_generic=False, eps=1e-10):
+def make_plan(lib, model_str, dims, prec, force_generic=False, eps=1e-10, eager=False):
     obs, lat, _ = split(model_str)
     shapes = (ctypes.c_int64 * max(1, len(obs)))(*[dims[c] for c in obs])
     ranks = (ctypes.c_int64 * max(1, len(lat)))(*[dims[c] for c in lat])
@@ -66,6 +69,7 @@ def make_plan(lib, model_str, dims, prec, force_generic=False, eps=1e-10):
     o.precision = prec
     o.eps = eps
     o.force_generic = int(force_generic)
+    o.eager = int(eager)
     h = ctypes.c_void_p()
     rc = lib.nef_plan(model_str.encode(), shapes, len(obs), ranks, len(lat), ctypes.byref(o),
                       ctypes.byref(h))
@@ -219,3 +223,79 @@ def test_argument_errors(lib):
     ranks = (ctypes.c_int64 * 1)(2)
     hh = ctypes.c_void_p()
     assert lib.nef_plan(b"ir,jr->ij", shapes, 2, ranks, 1, None, ctypes.byref(hh)) == 1
+
+
+# ----------------------------------------------- loss trace, tol, graph replay
+
+@pytest.mark.parametrize("model_str,dims", [MODELS[0], MODELS[2], MODELS[4], MODELS[8]])
+@pytest.mark.parametrize("masked", [False, True])
+def test_loss_trace_and_graph_replay(lib, model_str, dims, masked):
+    """Sweeps 2.. replayed from a captured sweep equal the eagerly launched ones
+    exactly, and loss_trace[k] is the oracle's loss after k sweeps (Eq. 3.1)."""
+    a, b = 1.0, 0.0
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(7)
+    fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)) for l in range(m.n_factors)]
+    y = rng.uniform(0.2, 3.0, size=m.y_shape)
+    mask = (rng.random(m.y_shape) > 0.3).astype(np.uint8) if masked else None
+    iters = 5
+    _, ref_trace = m.fit(y, mask, [f.copy() for f in fs], a, b, iters, trace=True)
+    outs = []
+    for eager in (True, False):
+        rc, h = make_plan(lib, model_str, dims, NEF_FP64, eager=eager)
+        assert rc == 0, lib.nef_last_error()
+        try:
+            work = [f.copy() for f in fs]
+            tr = np.full(iters + 1, np.nan)
+            done = ctypes.c_int(0)
+            for rep in range(2):  # the second call reuses the captured graph
+                work = [f.copy() for f in fs]
+                tr[:] = np.nan
+                rc = lib.nef_fit_ex(h, y.ctypes.data, None if mask is None else mask.ctypes.data,
+                                    facs_arr(work), a, b, iters, 0.0, tr.ctypes.data, ctypes.byref(done))
+                assert rc == 0, lib.nef_last_error()
+                assert done.value == iters
+            outs.append(([w.copy() for w in work], tr.copy()))
+        finally:
+            lib.nef_plan_destroy(h)
+    (w_e, tr_e), (w_g, tr_g) = outs
+    for l in range(m.n_factors):
+        assert np.array_equal(w_e[l], w_g[l]), l
+    np.testing.assert_array_equal(tr_e, tr_g)
+    np.testing.assert_allclose(tr_e, np.asarray(ref_trace[: iters + 1]), rtol=1e-10)
+
+
+@pytest.mark.parametrize("tol", [0.5, 1e-2, 1e-9])
+def test_tol_stops_after_small_decrease(lib, tol):
+    """App. B's stopping rule: stop after the first sweep k >= 2 whose preceding
+    relative decrease (L[k-2] - L[k-1]) / L[k-2] is below tol."""
+    model_str, dims = MODELS[0]
+    a, b = 1.0, 0.0
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(3)
+    fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)) for l in range(m.n_factors)]
+    y = rng.uniform(0.2, 3.0, size=m.y_shape)
+    iters = 12
+    _, ref = m.fit(y, None, [f.copy() for f in fs], a, b, iters, trace=True)
+    expect = iters
+    for k in range(2, iters + 1):
+        if (ref[k - 2] - ref[k - 1]) / ref[k - 2] < tol:
+            expect = k
+            break
+    rc, h = make_plan(lib, model_str, dims, NEF_FP64)
+    assert rc == 0
+    try:
+        work = [f.copy() for f in fs]
+        tr = np.full(iters + 1, np.nan)
+        done = ctypes.c_int(0)
+        rc = lib.nef_fit_ex(h, y.ctypes.data, None, facs_arr(work), a, b, iters, tol, tr.ctypes.data,
+                            ctypes.byref(done))
+        assert rc == 0, lib.nef_last_error()
+        assert done.value == expect
+        np.testing.assert_allclose(tr[: expect + 1], np.asarray(ref[: expect + 1]), rtol=1e-10)
+        assert np.all(np.isnan(tr[expect + 1:]))
+        _, ref_f = None, m.fit(y, None, [f.copy() for f in fs], a, b, expect)
+        for l in range(m.n_factors):
+            assert np.linalg.norm(work[l] - ref_f[l]) / np.linalg.norm(ref_f[l]) < 1e-10
+    finally:
+        lib.nef_plan_destroy(h)
