@@ -18,6 +18,12 @@ cudaError_t launch_bp32(const CUtensorMap&, const CUtensorMap&, const CUtensorMa
                         cudaStream_t);
 cudaError_t launch_bp64(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
                         cudaStream_t);
+cudaError_t launch_bp16_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp32_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp64_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
 cudaError_t launch_batched_bp16(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 cudaError_t launch_batched_bp32(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 }  // namespace tc
@@ -191,6 +197,13 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         info->smem_bytes = 0;
     }
     const int wk = weight_kind(w);
+    if (p.loss_part) {
+        switch (v.bond_pad) {
+            case 16: return tc::launch_bp16_loss(map, vmap, cmap, p, need_den, wk, grid, st);
+            case 32: return tc::launch_bp32_loss(map, vmap, cmap, p, need_den, wk, grid, st);
+            default: return tc::launch_bp64_loss(map, vmap, cmap, p, need_den, wk, grid, st);
+        }
+    }
     switch (v.bond_pad) {
         case 16: return tc::launch_bp16(map, vmap, cmap, p, need_den, wk, grid, st);
         case 32: return tc::launch_bp32(map, vmap, cmap, p, need_den, wk, grid, st);

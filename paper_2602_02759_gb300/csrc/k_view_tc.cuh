@@ -376,10 +376,11 @@ __device__ __forceinline__ void unpack_bf16x8(const uint4& q, float (&f)[8]) {
     }
 }
 
-// One loss term D(y, yhat) in FP32 (App. B); KL in closed form.
+// One loss term D(y, yhat) in FP32 (App. B).  For KL the weight a = y / yhat
+// is already at hand: D = y log(a) - y + yhat.
 template <int WK>
-__device__ __forceinline__ float tc_loss(float y, float yh, const LossSpec& L) {
-    if (WK == WK_KL) return (y > 0.f ? y * __logf(__fdividef(y, yh)) : 0.f) - y + yh;
+__device__ __forceinline__ float tc_loss(float y, float yh, float a, const LossSpec& L) {
+    if (WK == WK_KL) return (y > 0.f ? y * __logf(a) : 0.f) - y + yh;
     return divergence<float>(y, yh, L);
 }
 
@@ -461,7 +462,7 @@ struct Layout {
 
 // The fused pass of one CTA: rows [rb*TM, rb*TM + TM) of the view and the
 // column tiles of split sp.
-template <int BP, bool DEN, int WK>
+template <int BP, bool DEN, int WK, bool LOSS>
 __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUtensorMap* vmap,
                                              const CUtensorMap* cmap, const Params& prm, const int64_t rb,
                                              const int64_t sp) {
@@ -912,7 +913,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         }
         Cursor cur = cursor_at(t_lo);
         for (int k = 0; k < h; ++k) advance(cur);
-        const bool do_loss = prm.loss_part != nullptr;
+        constexpr bool do_loss = LOSS;
         double lsum = 0.0, lcnt = 0.0;
 #pragma unroll 1
         for (int i = h; i < T; i += kEpiGroups) {
@@ -977,15 +978,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                     }
                 }
                 uint32_t wa2[16], wb2[16];
-                if (do_loss) {
-                    // loss terms of the observed entries: FP32 within the half, FP64 across
-                    float t = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 32; ++c)
-                        if ((obs >> c) & 1u) t += tc_loss<WK>(yv[c], __uint_as_float(yh[c]), prm.L);
-                    lsum += (double)t;
-                    lcnt += (double)__popc(obs);
-                }
+                float t = 0.f;  // loss terms of the observed entries (FP32 within the half)
 #pragma unroll
                 for (int c = 0; c < 32; c += 2) {
                     float a0, b0, a1, b1;
@@ -993,6 +986,16 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                     tc_weights<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), w, a1, b1);
                     wa2[c >> 1] = pack_bf16(a0, a1);
                     if (DEN) wb2[c >> 1] = pack_bf16(b0, b1);
+                    if (do_loss) {
+                        const float d0 = tc_loss<WK>(yv[c], __uint_as_float(yh[c]), a0, prm.L);
+                        const float d1 = tc_loss<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), a1, prm.L);
+                        t += ((obs >> c) & 1u) ? d0 : 0.f;
+                        t += ((obs >> (c + 1)) & 1u) ? d1 : 0.f;
+                    }
+                }
+                if (do_loss) {
+                    lsum += (double)t;
+                    lcnt += (double)__popc(obs);
                 }
                 if (obs != 0xffffffffu) {
                     // unobserved, padding or out-of-range entries: clear their BF16 halves
@@ -1076,12 +1079,14 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     }
 }
 
-template <int BP, bool DEN, int WK>
+// LOSS: also sum the loss terms into prm.loss_part (a separate instance, so the
+// plain pass carries none of that code).
+template <int BP, bool DEN, int WK, bool LOSS>
 __global__ void __launch_bounds__(kThreads, 1)
 k_view_tc(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap vmap,
           const __grid_constant__ CUtensorMap cmap, const __grid_constant__ Params prm) {
     const int64_t n_rb = (prm.v.rows + TM - 1) / TM;
-    view_tc_body<BP, DEN, WK>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb, blockIdx.x / n_rb);
+    view_tc_body<BP, DEN, WK, LOSS>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb, blockIdx.x / n_rb);
 }
 
 // Batched form: CTA b runs work[b] = (unit, row block, split); the unit's tensor
@@ -1095,7 +1100,8 @@ k_view_tc_batched(const TcUnit* __restrict__ units, const TcWork* __restrict__ w
     for (int i = threadIdx.x; i < (int)(sizeof(prm_sh) / 16); i += blockDim.x)
         reinterpret_cast<uint4*>(prm_sh)[i] = reinterpret_cast<const uint4*>(U->prm)[i];
     __syncthreads();
-    view_tc_body<BP, DEN, WK>(&U->ymap, &U->vmap, &U->cmap, *reinterpret_cast<const Params*>(prm_sh), wk.rb, wk.sp);
+    view_tc_body<BP, DEN, WK, false>(&U->ymap, &U->vmap, &U->cmap, *reinterpret_cast<const Params*>(prm_sh), wk.rb,
+                                     wk.sp);
 }
 
 }  // namespace tc

@@ -5,10 +5,10 @@
 namespace nef {
 namespace tc {
 
-template <int BP, bool DEN, int WK>
+template <int BP, bool DEN, int WK, bool LOSS>
 cudaError_t launch_one(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int grid,
                        cudaStream_t st) {
-    auto kern = k_view_tc<BP, DEN, WK>;
+    auto kern = k_view_tc<BP, DEN, WK, LOSS>;
     const int sm = Layout<BP, DEN>::kAlloc;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
@@ -16,21 +16,21 @@ cudaError_t launch_one(const CUtensorMap& map, const CUtensorMap& vmap, const CU
     return cudaGetLastError();
 }
 
-template <int BP>
+template <int BP, bool LOSS>
 cudaError_t launch_bp(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int den,
                       int wk, int grid, cudaStream_t st) {
     if (den) {
         switch (wk) {
-            case WK_KL: return launch_one<BP, true, WK_KL>(map, vmap, cmap, p, grid, st);
-            case WK_B05: return launch_one<BP, true, WK_B05>(map, vmap, cmap, p, grid, st);
-            case WK_HEL: return launch_one<BP, true, WK_HEL>(map, vmap, cmap, p, grid, st);
-            default: return launch_one<BP, true, WK_GEN>(map, vmap, cmap, p, grid, st);
+            case WK_KL: return launch_one<BP, true, WK_KL, LOSS>(map, vmap, cmap, p, grid, st);
+            case WK_B05: return launch_one<BP, true, WK_B05, LOSS>(map, vmap, cmap, p, grid, st);
+            case WK_HEL: return launch_one<BP, true, WK_HEL, LOSS>(map, vmap, cmap, p, grid, st);
+            default: return launch_one<BP, true, WK_GEN, LOSS>(map, vmap, cmap, p, grid, st);
         }
     }
     switch (wk) {
-        case WK_KL: return launch_one<BP, false, WK_KL>(map, vmap, cmap, p, grid, st);
-        case WK_HEL: return launch_one<BP, false, WK_HEL>(map, vmap, cmap, p, grid, st);
-        default: return launch_one<BP, false, WK_GEN>(map, vmap, cmap, p, grid, st);
+        case WK_KL: return launch_one<BP, false, WK_KL, LOSS>(map, vmap, cmap, p, grid, st);
+        case WK_HEL: return launch_one<BP, false, WK_HEL, LOSS>(map, vmap, cmap, p, grid, st);
+        default: return launch_one<BP, false, WK_GEN, LOSS>(map, vmap, cmap, p, grid, st);
     }
 }
 
@@ -59,15 +59,19 @@ cudaError_t launch_batched_bp(const TcUnit* units, const TcWork* work, int n_wor
 }  // namespace tc
 }  // namespace nef
 
-#define NEF_TC_INSTANCE(BP)                                                                  \
+// SUFFIX: empty for the plain pass, _loss for the loss-summing one (LOSS true)
+#define NEF_TC_INSTANCE_X(BP, SUFFIX, LOSS)                                                   \
     namespace nef {                                                                          \
     namespace tc {                                                                           \
-    cudaError_t launch_bp##BP(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, \
-                              const Params& p, int den, int wk, int grid, cudaStream_t st) { \
-        return launch_bp<BP>(map, vmap, cmap, p, den, wk, grid, st);                         \
+    cudaError_t launch_bp##BP##SUFFIX(const CUtensorMap& map, const CUtensorMap& vmap,        \
+                                      const CUtensorMap& cmap, const Params& p, int den, int wk, \
+                                      int grid, cudaStream_t st) {                           \
+        return launch_bp<BP, LOSS>(map, vmap, cmap, p, den, wk, grid, st);                   \
     }                                                                                        \
     }                                                                                        \
     }
+#define NEF_TC_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, , false)
+#define NEF_TC_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _loss, true)
 
 #define NEF_TC_BATCHED_INSTANCE(BP)                                                          \
     namespace nef {                                                                          \

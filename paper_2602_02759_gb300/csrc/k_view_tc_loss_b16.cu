@@ -1,0 +1,4 @@
+// k_view_tc_loss_b16.cu -- loss-summing tcgen05 fused pass for bond_pad 16.
+#include "k_view_tc_inst.cuh"
+
+NEF_TC_LOSS_INSTANCE(16)
