@@ -192,6 +192,76 @@ def sweep_fraction(rows, n):
     return rows / (3.0 * n)
 
 
+def foldin_variant(nef, torch, stream, train_sweeps=100, steps=200, lr=1e-3):
+    """The fold-in workload (CP 2048x128x128 rank 32, KL): MU fit of the 1536
+    training slices, encoder training on (slice, component count mass) pairs,
+    then the 512 held-out slices folded in from the encoder's loadings and from
+    the plain initialisation, with k MU passes on mode 0 (B, C fixed)."""
+    import numpy as np
+    import synth
+    p = synth.config5()
+    n, J, K = p.y.shape
+    R = p.dims["r"]
+    n_tr = 1536
+    n_te = n - n_tr
+    d = J * K
+    y = torch.from_numpy(p.y).cuda()
+    ytr, yte = y[:n_tr].contiguous(), y[n_tr:].contiguous()
+    A0, B0, C0 = (torch.from_numpy(f).cuda() for f in p.inits[0])
+    fs = [A0[:n_tr].contiguous(), B0.clone(), C0.clone()]
+    fit = nef.Plan(p.model_str, dict(i=n_tr, j=J, k=K, r=R), precision="bf16", stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fit.fit(ytr, None, fs, 1.0, 0.0, train_sweeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_fit = e0.elapsed_time(e1) / 1e3
+    A_tr, B, C = fs
+    mass = (B.sum(0) * C.sum(0))[None, :]
+    targets = (A_tr * mass).contiguous()
+    xs = ytr.reshape(n_tr, d).contiguous()
+    enc = nef.FoldIn(d, 512, R, n_tr, torch.from_numpy(nef.pack_params(synth.mlp_params((d, 512, 512, R), 3))).cuda(),
+                     stream=stream)
+    l0 = enc.train_step(xs, targets, lr)
+    e0.record(stream)
+    for _ in range(steps - 2):
+        enc.train_step(xs, targets, lr, want_loss=False)
+    e1.record(stream)
+    l_end = enc.train_step(xs, targets, lr)
+    t_train = e0.elapsed_time(e1) / 1e3 / (steps - 2)
+    flops = 2.0 * 3.0 * n_tr * (d * 512 + 512 * 512 + 512 * R)  # forward + two backward products
+    ref = nef.Plan(p.model_str, dict(i=n_te, j=J, k=K, r=R), precision="fp32", stream=stream)
+    e0.record(stream)
+    A_enc = (enc.predict(yte.reshape(n_te, d).contiguous()) / mass).contiguous()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pred = e0.elapsed_time(e1) / 1e3
+
+    def gaps(A, ks):
+        fs2 = [A.clone(), B, C]
+        out, done = {}, 0
+        for k in ks:
+            for _ in range(k - done):
+                ref.update(0, yte, None, fs2, 1.0, 0.0)
+            done = k
+            out[k] = ref.loss(yte, None, fs2, 1.0, 0.0)[0]
+        return out
+
+    ks = [0, 1, 2, 5, 10, 20]
+    full = gaps(A0[n_tr:].contiguous(), [500])[500]
+    g_enc = gaps(A_enc, ks)
+    g_pl = gaps(A0[n_tr:].contiguous(), ks)
+    return {"workload": p.note + ", KL; encoder 16384->512->512->32, targets = loading x column-sum mass",
+            "mu_fit_train": {"sweeps": train_sweeps, "seconds": t_fit},
+            "encoder_train": {"adam_steps": steps, "batch": n_tr, "loss_first": l0, "loss_last": l_end,
+                              "ms_per_step": t_train * 1e3, "tflops": flops / t_train / 1e12},
+            "predict_ms": t_pred * 1e3,
+            "heldout_gap_vs_full_mu_foldin": {"k_passes": ks,
+                                              "encoder": [g_enc[k] / full - 1 for k in ks],
+                                              "plain_init": [g_pl[k] / full - 1 for k in ks],
+                                              "full_foldin_passes": 500}}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -364,6 +434,9 @@ def run_ours(args):
         ref_last = plan.loss(Y, None, g, p.alpha, p.beta)[0]
         variants["bf16_loss_trace"] = {"value": n_lt / (ms_lt / 1e3), "unit": UNIT, "sweeps": n_lt,
                                        "final_trace_vs_nef_loss_rel": abs(last - ref_last) / ref_last}
+
+    if rank == 0 and not args.no_variants:
+        variants["foldin"] = foldin_variant(nef, torch, stream)
 
     e2e = None
     if not args.no_e2e:

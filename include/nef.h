@@ -250,6 +250,64 @@ nef_status nef_cp3_update_static(const float* Y, const int64_t* shape, int rank,
 /* Message for the last failed call on this thread ("" if none). */
 const char* nef_last_error(void);
 
+/* ------------------------------------------------------------- fold-in encoder
+ * A learned initialiser for folding a new slice into a fitted 3-way CP model
+ * 'ir,jr,kr->ijk' (the paper has no learned part: its fold-in of a new slice is
+ * Algorithm 1's update of that slice's loading with the other factors fixed,
+ * which nef_update(l = 0) performs and which refines this encoder's output).
+ * The encoder is the MLP
+ *     out = softplus(relu(relu(log1p(x) W1 + b1) W2 + b2) W3 + b3)
+ * from one slice x = Y[i, :, :] (d_in = J*K values) to its loading row A[i, :]
+ * (d_out = R values), trained on (slice, loading) pairs by Adam on
+ *     L = mean over the batch and outputs of (log1p(out) - log1p(target))^2.
+ * Products run on the tensor cores in BF16 with FP32 accumulation; parameters,
+ * gradients and Adam moments are FP32.  Parameters are packed (device FP32) as
+ * W1 [d_in x d_h], b1 [d_h], W2 [d_h x d_h], b2 [d_h], W3 [d_h x d_out], b3
+ * [d_out], weights row-major [fan_in x fan_out].  All calls are ordered on the
+ * encoder's stream; calls that return a loss synchronise it.
+ */
+typedef struct nef_foldin_s* nef_foldin_t;
+
+/* Number of FP32 values of the packed parameters. */
+int64_t nef_foldin_num_params(int d_in, int d_h, int d_out);
+
+/*
+ * nef_foldin_create -- an encoder d_in -> d_h -> d_h -> d_out for batches of at
+ * most max_batch slices, starting from `params` (device, packed, copied).
+ * Widths must be positive multiples of 8.  stream: cudaStream_t or NULL.
+ * Errors: NEF_EINVAL, NEF_ENOMEM, NEF_ECUDA.  On error *out is NULL.
+ */
+nef_status nef_foldin_create(int d_in, int d_h, int d_out, int max_batch, const float* params, void* stream,
+                             nef_foldin_t* out);
+void nef_foldin_destroy(nef_foldin_t enc);
+
+/*
+ * nef_foldin_grad -- gradient of L at the current parameters for one batch.
+ *   slices  : device [n x d_in] FP32 (raw nonnegative values; log1p is applied inside)
+ *   targets : device [n x d_out] FP32 loadings
+ *   grads   : device, packed like the parameters, receives dL/dparams
+ *   loss    : host, receives L (synchronises), or NULL
+ * Errors: NEF_EINVAL (n outside [1, max_batch], NULL pointer), NEF_ECUDA,
+ * NEF_ETIMEOUT (a bounded wait inside a product gave up).
+ */
+nef_status nef_foldin_grad(nef_foldin_t enc, const float* slices, const float* targets, int n, float* grads,
+                           double* loss);
+
+/*
+ * nef_foldin_train_step -- forward, backward and one Adam step (Kingma & Ba,
+ * bias-corrected with the encoder's step count) on one batch; loss (host, or
+ * NULL) receives L before the step.  Errors as nef_foldin_grad, plus NEF_EINVAL
+ * for lr <= 0, beta outside [0, 1) or eps <= 0.
+ */
+nef_status nef_foldin_train_step(nef_foldin_t enc, const float* slices, const float* targets, int n, double lr,
+                                 double beta1, double beta2, double eps, double* loss);
+
+/* nef_foldin_predict -- out (device [n x d_out]) = the encoder's loadings for n slices. */
+nef_status nef_foldin_predict(nef_foldin_t enc, const float* slices, int n, float* out);
+
+/* nef_foldin_params -- copy the current packed parameters to out (device). */
+nef_status nef_foldin_params(nef_foldin_t enc, float* out);
+
 #ifdef __cplusplus
 }
 #endif

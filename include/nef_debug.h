@@ -46,6 +46,17 @@ int nef_tc_probe(int bond_pad, int a_in_tmem, const uint16_t* P, const uint16_t*
  * operand and epilogue warps are counted once per warp).  reset != 0 clears the counters afterwards.  Returns 0, 1 for
  * a plan without counters, 5 for a CUDA error.  Synchronises the plan's stream.
  */
+/*
+ * nef_tc_gemm -- the tensor-core GEMM of the fold-in encoder on its own:
+ * C[M x N] = A[M x K] . B[N x K]^T.  A, B: device row-major BF16 (raw 16-bit
+ * patterns) with row pitches lda, ldb (elements, multiples of 8) and 16-byte
+ * aligned bases; C: device row-major FP32, pitch ldc.  err (device int)
+ * receives a nonzero code if a bounded wait gave up.  Enqueued on `stream`.
+ * Returns 0 on a successful launch, 5 for a CUDA error (including bad pitches).
+ */
+int nef_tc_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
+                int K, int* err, void* stream);
+
 typedef struct nef_plan_s* nef_plan_handle;
 int nef_tc_trace(nef_plan_handle plan, unsigned long long* out, int reset);
 

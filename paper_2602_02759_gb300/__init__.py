@@ -13,6 +13,7 @@ from ._nef import (  # noqa: F401
     DEBUG_EXPORTS,
     EXPORTS,
     LIB_PATH,
+    FoldIn,
     NEF_BF16,
     NEF_FP32,
     NEF_FP64,
@@ -21,5 +22,6 @@ from ._nef import (  # noqa: F401
     cp3_update_static,
     fit_batched,
     load,
+    pack_params,
     split_model,
 )

@@ -21,9 +21,11 @@ PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 # every symbol include/nef.h declares
 EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex",
            "nef_plan_sweeps", "nef_update", "nef_loss", "nef_plan_info", "nef_plan_launches",
-           "nef_plan_profile", "nef_check", "nef_fit_batched", "nef_cp3_update_static", "nef_last_error"]
+           "nef_plan_profile", "nef_check", "nef_fit_batched", "nef_cp3_update_static", "nef_last_error",
+           "nef_foldin_num_params", "nef_foldin_create", "nef_foldin_destroy", "nef_foldin_grad",
+           "nef_foldin_train_step", "nef_foldin_predict", "nef_foldin_params"]
 # every symbol include/nef_debug.h declares
-DEBUG_EXPORTS = ["nef_tc_probe", "nef_tc_trace"]
+DEBUG_EXPORTS = ["nef_tc_probe", "nef_tc_trace", "nef_tc_gemm"]
 
 
 class Options(ctypes.Structure):
@@ -86,10 +88,27 @@ def load(path: str = LIB_PATH):
     lib.nef_cp3_update_static.argtypes = [vp, i64p, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
     lib.nef_cp3_update_static.restype = ctypes.c_int
+    ci, dbl = ctypes.c_int, ctypes.c_double
+    lib.nef_foldin_num_params.argtypes = [ci, ci, ci]
+    lib.nef_foldin_num_params.restype = ctypes.c_int64
+    lib.nef_foldin_create.argtypes = [ci, ci, ci, ci, vp, vp, ctypes.POINTER(vp)]
+    lib.nef_foldin_create.restype = ci
+    lib.nef_foldin_destroy.argtypes = [vp]
+    lib.nef_foldin_grad.argtypes = [vp, vp, vp, ci, vp, dp]
+    lib.nef_foldin_grad.restype = ci
+    lib.nef_foldin_train_step.argtypes = [vp, vp, vp, ci, dbl, dbl, dbl, dbl, dp]
+    lib.nef_foldin_train_step.restype = ci
+    lib.nef_foldin_predict.argtypes = [vp, vp, ci, vp]
+    lib.nef_foldin_predict.restype = ci
+    lib.nef_foldin_params.argtypes = [vp, vp]
+    lib.nef_foldin_params.restype = ci
     lib.nef_tc_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
     lib.nef_tc_trace.restype = ctypes.c_int
     lib.nef_tc_probe.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.nef_tc_probe.restype = ctypes.c_int
+    lib.nef_tc_gemm.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, vp, vp]
+    lib.nef_tc_gemm.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -290,3 +309,90 @@ class Plan:
 
     def launches(self, has_mask: bool) -> int:
         return int(load().nef_plan_launches(self._h, int(bool(has_mask))))
+
+
+class FoldIn:
+    """The fold-in encoder (nef_foldin_*): an MLP from a slice Y[i, :, :] to its
+    loading row, trained and run by the library's kernels.  ``params`` is a
+    float32 CUDA tensor holding W1, b1, W2, b2, W3, b3 packed (weights
+    [fan_in x fan_out]); slices and targets are float32 CUDA tensors
+    [n, d_in] and [n, d_out]."""
+
+    def __init__(self, d_in: int, d_h: int, d_out: int, max_batch: int, params, stream=None):
+        import torch
+        lib = load()
+        self.d_in, self.d_h, self.d_out, self.max_batch = int(d_in), int(d_h), int(d_out), int(max_batch)
+        self.n_params = int(lib.nef_foldin_num_params(self.d_in, self.d_h, self.d_out))
+        if params.dtype != torch.float32 or not params.is_cuda or params.numel() != self.n_params:
+            raise ValueError(f"params must be a float32 CUDA tensor of {self.n_params} values")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        check(lib.nef_foldin_create(self.d_in, self.d_h, self.d_out, self.max_batch,
+                                    ctypes.c_void_p(params.contiguous().data_ptr()),
+                                    ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    @staticmethod
+    def num_params(d_in: int, d_h: int, d_out: int) -> int:
+        return int(load().nef_foldin_num_params(int(d_in), int(d_h), int(d_out)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nef_foldin_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, x, cols):
+        import torch
+        if x.dtype != torch.float32 or not x.is_cuda or x.dim() != 2 or x.shape[1] != cols or not x.is_contiguous():
+            raise ValueError(f"expected a contiguous float32 CUDA tensor [n, {cols}]")
+
+    def grad(self, slices, targets):
+        """(packed gradient tensor, loss) at the current parameters."""
+        import torch
+        self._check(slices, self.d_in)
+        self._check(targets, self.d_out)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=slices.device)
+        loss = ctypes.c_double(0.0)
+        check(load().nef_foldin_grad(self._h, ctypes.c_void_p(slices.data_ptr()),
+                                     ctypes.c_void_p(targets.data_ptr()), int(slices.shape[0]),
+                                     ctypes.c_void_p(g.data_ptr()), ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train_step(self, slices, targets, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=True):
+        self._check(slices, self.d_in)
+        self._check(targets, self.d_out)
+        loss = ctypes.c_double(0.0)
+        check(load().nef_foldin_train_step(self._h, ctypes.c_void_p(slices.data_ptr()),
+                                           ctypes.c_void_p(targets.data_ptr()), int(slices.shape[0]),
+                                           float(lr), float(beta1), float(beta2), float(eps),
+                                           ctypes.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def predict(self, slices):
+        import torch
+        self._check(slices, self.d_in)
+        out = torch.empty(slices.shape[0], self.d_out, dtype=torch.float32, device=slices.device)
+        check(load().nef_foldin_predict(self._h, ctypes.c_void_p(slices.data_ptr()), int(slices.shape[0]),
+                                        ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def params(self):
+        import torch
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        check(load().nef_foldin_params(self._h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+
+def pack_params(arrays):
+    """Concatenate W1, b1, W2, b2, W3, b3 (numpy arrays) into one float32 vector."""
+    import numpy as np
+    return np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in arrays])

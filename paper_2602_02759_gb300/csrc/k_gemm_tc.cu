@@ -1,0 +1,199 @@
+// k_gemm_tc.cu -- BF16 tensor-core GEMM C = A . B^T (FP32 out) on tcgen05, for
+// the fold-in encoder's forward and backward products.
+//
+// A is [M x K] and B is [N x K], both row-major BF16 (K contiguous, "K-major");
+// C is [M x N] row-major FP32 (ldc).  One CTA computes a 128 x 128 tile of C:
+//   warp 0 (one elected lane): TMA loads of 128 x 64 tiles of A and B into a
+//          4-stage ring (128B swizzle), out-of-range rows/columns read as zero;
+//   warp 1 (one elected lane): tcgen05.mma kind::f16, M = 128, N = 128, K = 16
+//          steps, accumulator in TMEM (128 columns);
+//   all four warps: epilogue, TMEM lane = tile row, FP32 stores (guarded).
+// The operand layouts and descriptors are those of the fused pass's first
+// product (yhat = P . Q^T).  Every mbarrier wait is bounded; a timeout sets the
+// error flag and the CTA drains its copies and MMAs before freeing TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "../../include/nef_debug.h"
+#include "k_view_tc.cuh"
+#include "nef_internal.h"
+
+namespace nef {
+namespace gemm {
+
+using namespace tc;
+
+// tcgen05.mma with both operands from shared-memory descriptors, issued by one
+// elected lane of a warp-uniform loop.
+__device__ __forceinline__ void tc_mma_ss_e(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+constexpr int BM = 128, BN = 128, BK = 64, NST = 4;
+constexpr int kThreadsG = 128;
+constexpr int kTileBytes = BM * BK * 2;  // 16 KB (A and B tiles alike)
+constexpr int kStage = 2 * kTileBytes;
+constexpr int kBar = NST * kStage;            // full[NST], empty[NST], done
+constexpr int kMisc = kBar + (2 * NST + 1) * 8;
+constexpr int kSmem = kMisc + 16 + 1024;      // + alignment slack
+
+__global__ void __launch_bounds__(kThreadsG, 1)
+k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, float* __restrict__ C,
+          int M, int N, int K, int ldc, int accumulate, int* err) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* sm = smem_raw + (base - raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = (K + BK - 1) / BK;
+    const uint32_t bar0 = base + kBar;
+    auto full = [&](int s) { return bar0 + 8u * s; };
+    auto empty = [&](int s) { return bar0 + 8u * (NST + s); };
+    const uint32_t done = bar0 + 8u * (2 * NST);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kMisc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kMisc + 4);
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(128u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    auto uwait = [&](uint32_t bar, uint32_t par, int code) {
+        return __all_sync(0xffffffffu, mbar_wait(bar, par, abort_flag, err, code));
+    };
+    if (warp == 0) {
+        // ---- TMA producer (warp-uniform loop, elected issue)
+        int issued = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % NST;
+            if (!uwait(empty(s), ((kb / NST) & 1) ^ 1, 1)) break;
+            mbar_expect_tx_e(full(s), kStage);
+            tma_load_2d_e(base + s * kStage, &amap, kb * BK, m0, full(s));
+            tma_load_2d_e(base + s * kStage + kTileBytes, &bmap, kb * BK, n0, full(s));
+            issued = kb + 1;
+        }
+        for (int kb = max(0, issued - NST); kb < issued; ++kb) {
+            volatile int dummy = 0;
+            mbar_wait(full(kb % NST), (kb / NST) & 1, &dummy, err, 2);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer (warp-uniform loop, elected issue)
+        constexpr uint32_t idesc = make_idesc(BM, BN, 0, 0);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % NST;
+            if (!uwait(full(s), (kb / NST) & 1, 3)) break;
+            tc_fence_after();
+            const uint64_t ad = make_sdesc(base + s * kStage, 16, 8 * 128, swz_code(128));
+            const uint64_t bd = make_sdesc(base + s * kStage + kTileBytes, 16, 8 * 128, swz_code(128));
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+                tc_mma_ss_e(tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit_e(empty(s));
+        }
+        tc_commit_e(done);
+    }
+    // ---- epilogue: every warp reads its 32 TMEM lanes (rows) of the 128 columns
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag, err, 4));
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + lane_off + c0, r);
+        tmem_wait_ld();
+        if (ok && row < M) {
+            float* dst = C + (int64_t)row * ldc + n0 + c0;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                if (n0 + c0 + k < N) {
+                    const float v = (nk > 0) ? __uint_as_float(r[k]) : 0.f;
+                    dst[k] = accumulate ? dst[k] + v : v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+    }
+}
+
+}  // namespace gemm
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 gemm_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a row-major BF16 [rows x K] matrix (row pitch ld elements), box 64 x 128.
+bool encode_kmajor(CUtensorMap* map, const uint16_t* p, int64_t rows, int64_t K, int64_t ld) {
+    auto enc = gemm_encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)gemm::BK, (cuuint32_t)gemm::BM};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(p), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
+                           int M, int N, int K, int accumulate, int* err, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    // TMA: 16-byte aligned base and row pitch
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) || (lda * 2) % 16 ||
+        (ldb * 2) % 16 || K < 0)
+        return cudaErrorInvalidValue;
+    CUtensorMap am, bm;
+    if (!encode_kmajor(&am, A, M, K, lda) || !encode_kmajor(&bm, B, N, K, ldb)) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaFuncSetAttribute(gemm::k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm::kSmem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((M + gemm::BM - 1) / gemm::BM), (unsigned)((N + gemm::BN - 1) / gemm::BN));
+    gemm::k_gemm_nt<<<grid, gemm::kThreadsG, gemm::kSmem, st>>>(am, bm, C, M, N, K, (int)ldc, accumulate, err);
+    return cudaGetLastError();
+}
+
+}  // namespace nef
+
+extern "C" int nef_tc_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int M,
+                           int N, int K, int* err, void* stream) {
+    const cudaError_t e =
+        nef::launch_gemm_nt(A, lda, B, ldb, C, ldc, M, N, K, 0, err, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? 0 : 5;
+}

@@ -212,6 +212,28 @@ struct TcLaunchInfo {
 
 cudaError_t launch_convert_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st);
 
+// Tensor-core GEMM C[M x N] (=, or += with accumulate) A[M x K] . B[N x K]^T; A and B
+// row-major BF16 (pitches lda, ldb elements, multiples of 8; 16-byte aligned bases),
+// C row-major FP32 (pitch ldc).  err: device flag set when a bounded wait gives up.
+cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
+                           int M, int N, int K, int accumulate, int* err, cudaStream_t st);
+
+// Fold-in encoder kernels (k_foldin.cu).
+cudaError_t launch_fi_features(const float* slices, int n, int d, uint16_t* x, uint16_t* xt, int ldt, cudaStream_t st);
+cudaError_t launch_fi_bias_act(float* z, const float* b, int n, int h, int act, uint16_t* hb, uint16_t* ht, int ldt,
+                               float* out, cudaStream_t st);
+cudaError_t launch_fi_out_grad(const float* out, const float* t, const float* z, int64_t n_el, float inv_count,
+                               float* g, double* part, int n_part, cudaStream_t st);
+cudaError_t launch_fi_relu_grad(float* g, const float* z, int n, int h, uint16_t* gb, uint16_t* gt, int ldt,
+                                cudaStream_t st);
+cudaError_t launch_fi_convert(const float* src, int n, int d, uint16_t* dst, uint16_t* dst_t, int ldt,
+                              cudaStream_t st);
+cudaError_t launch_fi_colsum(const float* g, int n, int h, float* out, cudaStream_t st);
+cudaError_t launch_fi_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                           float eps, float bc1, float bc2, cudaStream_t st);
+cudaError_t launch_fi_weight_copy(const float* w, int rows, int cols, uint16_t* dst, uint16_t* dst_t,
+                                  cudaStream_t st);
+
 // Sum per-CTA loss partials (part[0..n): loss, part[n..2n): count) into out[0..1];
 // also append the loss to trace[*count] when trace is set, and increment *count.
 cudaError_t launch_loss_append(const double* part, int n, double* trace, int* count, double* out,

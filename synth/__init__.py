@@ -132,3 +132,27 @@ def random_factors(model_str, dims, seed, lo=0.5, hi=1.5):
     terms, _ = parse_terms(model_str)
     rng = np.random.default_rng(seed)
     return [rng.uniform(lo, hi, size=tuple(dims[c] for c in t)) for t in terms]
+
+
+def config5(seed=0, n=2048, jk=(128, 128), rank=32, n_train=1536) -> Problem:
+    """Fold-in workload: CP 'ir,jr,kr->ijk' n x J x K rank 32, Gamma(0.3,1) truth,
+    Poisson data, no mask, KL.  Slices 0..n_train-1 train the model and the
+    encoder; the rest are held out."""
+    j, k = jk
+    p = make_problem("ir,jr,kr->ijk", {"i": n, "j": j, "k": k, "r": rank}, seed,
+                     gamma=(0.3, 1.0), missing=0.0, alpha=1.0, beta=0.0)
+    p.note = f"fold-in cp {n}x{j}x{k} R{rank}, {n_train} train slices"
+    return p
+
+
+def mlp_params(sizes, seed=0):
+    """Initial encoder parameters: He-uniform weights U(-sqrt(6/fan_in), +),
+    zero biases, for layer widths sizes = (d_in, h, h, d_out); returned as the
+    list W1, b1, W2, b2, W3, b3 (float64, weights [fan_in x fan_out])."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        lim = np.sqrt(6.0 / a)
+        params.append(rng.uniform(-lim, lim, size=(a, b)))
+        params.append(np.zeros(b))
+    return params

@@ -1,0 +1,155 @@
+"""GPU: the fold-in encoder (nef_foldin_*) and its tensor-core GEMM.
+
+Tolerances: the GEMM is compared with the FP64 product of the same BF16
+values (FP32 accumulation: 1e-5 relative).  The encoder computes its products
+in BF16 (inputs, weights, activations and backward signals rounded to BF16,
+FP32 accumulation), so its loss is compared with the FP64 oracle run on the
+same parameters within 2e-3 relative, and each parameter's gradient within
+3e-2 relative (Frobenius).  One Adam step moves every parameter by at most lr
+(Adam's first step); the GPU and oracle steps agree elementwise within 2 lr and
+on average within 0.05 lr.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _nef():
+    import paper_2602_02759_gb300 as nef
+    return nef
+
+
+def bf16(x):
+    return torch.as_tensor(np.asarray(x, np.float32)).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 72, 96), (64, 32, 32), (1536, 512, 1024), (96, 512, 1536)])
+def test_tc_gemm(M, N, K):
+    nef = _nef()
+    rng = np.random.default_rng(M * 7 + N + K)
+    A = rng.uniform(-1, 1, (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (N, K)).astype(np.float32)
+    tA = torch.as_tensor(A).cuda().to(torch.bfloat16).contiguous()
+    tB = torch.as_tensor(B).cuda().to(torch.bfloat16).contiguous()
+    C = torch.full((M, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = nef.load().nef_tc_gemm(tA.data_ptr(), K, tB.data_ptr(), K, C.data_ptr(), N, M, N, K, err.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert rc == 0 and int(err.item()) == 0
+    ref = bf16(A) @ bf16(B).T
+    got = C.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+def _setup(d=256, h=64, o=16, n=48, seed=0):
+    rng = np.random.default_rng(seed)
+    params = synth.mlp_params((d, h, h, o), seed=seed)
+    params = [p + rng.uniform(-0.05, 0.05, p.shape) for p in params]   # nonzero biases
+    slices = rng.poisson(rng.gamma(0.5, 2.0, (n, d))).astype(np.float32)
+    targets = rng.gamma(0.5, 1.0, (n, o)).astype(np.float32)
+    return params, slices, targets
+
+
+def test_foldin_grad_matches_oracle():
+    nef = _nef()
+    d, h, o, n = 256, 64, 16, 48
+    params, slices, targets = _setup(d, h, o, n)
+    flat = torch.as_tensor(nef.pack_params(params)).cuda()
+    enc = nef.FoldIn(d, h, o, n, flat)
+    g, loss = enc.grad(torch.as_tensor(slices).cuda(), torch.as_tensor(targets).cuda())
+    torch.cuda.synchronize()
+    # oracle at the parameters the GPU computes with (BF16 inputs and weights)
+    p_bf = [bf16(p) if p.ndim == 2 else p for p in params]
+    out, cache = mlp.forward(p_bf, bf16(np.log1p(slices.astype(np.float64))))
+    ref_loss = mlp.loss(out, targets.astype(np.float64))
+    ref_g = mlp.backward(p_bf, cache, targets.astype(np.float64))
+    assert loss == pytest.approx(ref_loss, rel=2e-3)
+    got = g.cpu().numpy().astype(np.float64)
+    off = 0
+    for k, rg in enumerate(ref_g):
+        gk = got[off:off + rg.size].reshape(rg.shape)
+        off += rg.size
+        rel = np.linalg.norm(gk - rg) / max(np.linalg.norm(rg), 1e-30)
+        assert rel < 3e-2, (k, rel)
+    assert off == got.size
+
+
+def test_foldin_adam_step_matches_oracle():
+    nef = _nef()
+    d, h, o, n = 256, 64, 16, 48
+    params, slices, targets = _setup(d, h, o, n, seed=1)
+    flat = torch.as_tensor(nef.pack_params(params)).cuda()
+    enc = nef.FoldIn(d, h, o, n, flat)
+    lr = 1e-3
+    enc.train_step(torch.as_tensor(slices).cuda(), torch.as_tensor(targets).cuda(), lr)
+    got = enc.params().cpu().numpy().astype(np.float64)
+    p_ref = [p.astype(np.float64).copy() for p in params]
+    p_bf = [bf16(p) if p.ndim == 2 else p for p in params]
+    out, cache = mlp.forward(p_bf, bf16(np.log1p(slices.astype(np.float64))))
+    grads = mlp.backward(p_bf, cache, targets.astype(np.float64))
+    mlp.adam_step(p_ref, grads, mlp.adam_state(p_ref), lr, 1)
+    ref = np.concatenate([p.reshape(-1) for p in p_ref])
+    start = np.concatenate([np.asarray(p, np.float32).reshape(-1) for p in params]).astype(np.float64)
+    assert np.max(np.abs(got - start)) <= lr * 1.001 + 1e-7
+    diff = np.abs(got - ref)
+    assert diff.max() <= 2 * lr * 1.001 + 1e-7
+    assert diff.mean() < 0.05 * lr
+
+
+def test_foldin_gain_over_plain_foldin():
+    """The trained encoder's loadings, refined by k MU passes on mode 0 with B, C
+    fixed, reach a lower held-out loss than the plain MU fold-in from the usual
+    initialisation after the same k passes (k = 0, 1, 2).  The encoder is trained
+    on each component's expected count in the slice, A[i, r] * sum_j B[j, r] *
+    sum_k C[k, r] (the scale of the data, where log1p separates small loadings),
+    and its output is divided by the same factor."""
+    nef = _nef()
+    n_tr, n_te, J, K, R = 256, 128, 16, 16, 8
+    p = synth.make_problem("ir,jr,kr->ijk", {"i": n_tr + n_te, "j": J, "k": K, "r": R}, seed=5,
+                           gamma=(0.3, 1.0), missing=0.0, alpha=1.0, beta=0.0)
+    y = torch.as_tensor(p.y).cuda()
+    ytr, yte = y[:n_tr].contiguous(), y[n_tr:].contiguous()
+    # 1. MU fit on the training slices: B, C and the training loadings
+    A0, B0, C0 = (torch.as_tensor(f).cuda() for f in p.inits[0])
+    fs = [A0[:n_tr].contiguous(), B0.clone(), C0.clone()]
+    fit = nef.Plan("ir,jr,kr->ijk", dict(i=n_tr, j=J, k=K, r=R), precision="fp32")
+    fit.fit(ytr, None, fs, 1.0, 0.0, 300)
+    A_tr, B, C = fs
+    # 2. train the encoder on (slice, loading) pairs
+    d = J * K
+    params = synth.mlp_params((d, 64, 64, R), seed=3)
+    enc = nef.FoldIn(d, 64, R, n_tr, torch.as_tensor(nef.pack_params(params)).cuda())
+    xs = ytr.reshape(n_tr, d).contiguous()
+    mass = (B.sum(0) * C.sum(0))[None, :]
+    targets = (A_tr * mass).contiguous()
+    first = last = None
+    for step in range(400):
+        l = enc.train_step(xs, targets, 2e-3, want_loss=(step % 50 == 0 or step == 399))
+        if l is not None:
+            first = l if first is None else first
+            last = l
+    assert last < 0.5 * first
+    # 3. fold in the held-out slices: encoder + k passes vs plain init + k passes
+    ref = nef.Plan("ir,jr,kr->ijk", dict(i=n_te, j=J, k=K, r=R), precision="fp32")
+    A_enc = (enc.predict(yte.reshape(n_te, d).contiguous()) / mass).contiguous()
+    A_plain = A0[n_tr:].contiguous()
+
+    def held_out_loss(A, k):
+        fs2 = [A.clone(), B, C]
+        for _ in range(k):
+            ref.update(0, yte, None, fs2, 1.0, 0.0)
+        return ref.loss(yte, None, fs2, 1.0, 0.0)[0]
+
+    full = held_out_loss(A_plain, 200)
+    for k in (0, 1, 2):
+        le, lp = held_out_loss(A_enc, k), held_out_loss(A_plain, k)
+        # the gap to the converged fold-in shrinks by at least 2x
+        assert (le - full) < 0.5 * (lp - full), (k, le, lp, full)
+    assert held_out_loss(A_enc, 20) == pytest.approx(full, rel=1e-2)
