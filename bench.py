@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--workload", default="cp_kl",
+                    choices=["cp_kl", "cp_beta05", "custom4", "small", "batched"],
+                    help="cp_kl: the benchmark line (default); the others print one measurement "
+                         "line each for the other workloads")
+    ap.add_argument("--batched-problems", type=int, default=48)
     return ap.parse_args()
 
 
@@ -483,10 +488,117 @@ def run_ours(args):
     return 0
 
 
+def time_fit(nef, torch, p, precision, sweeps, warmup, stream, eager=False):
+    """Seconds per sweep of one nef_fit call of `sweeps` sweeps (after `warmup`
+    sweeps), and the final loss, from p.inits[0]."""
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    Y = torch.from_numpy(p.y).cuda().to(dt)
+    M = None if p.mask is None else torch.from_numpy(p.mask).cuda()
+    fs = [torch.from_numpy(f).cuda().to(dt) for f in p.inits[0]]
+    plan = nef.Plan(p.model_str, p.dims, precision=precision, stream=stream, eager=eager)
+    plan.fit(Y, M, fs, p.alpha, p.beta, warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.fit(Y, M, fs, p.alpha, p.beta, sweeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    sec = e0.elapsed_time(e1) / 1e3 / sweeps
+    loss = plan.loss(Y, M, fs, p.alpha, p.beta)[0]
+    # per-family kernel time in two profiled sweeps
+    pp = nef.Plan(p.model_str, p.dims, precision=precision, stream=stream, profile=1)
+    gs = [f.clone() for f in fs]
+    pp.fit(Y, M, gs, p.alpha, p.beta, 2)
+    prof = pp.profile(reset=True)
+    info = plan.info()
+    del plan, pp, Y, M
+    return sec, loss, prof, info
+
+
+def run_workload(args):
+    """Measurement lines for the workloads other than the benchmark line."""
+    import numpy as np
+    import torch
+    import paper_2602_02759_gb300 as nef
+    import synth
+    hbm, _, src = load_peaks()
+    stream = torch.cuda.current_stream()
+    sweeps = max(3, args.steps)
+    if args.workload in ("cp_beta05", "custom4", "small"):
+        p = {"cp_beta05": lambda: synth.config2(beta=-0.5, n=args.n),
+             "custom4": synth.config3, "small": synth.config1}[args.workload]()
+        n_el = p.y.size
+        n_fac = len(p.factor_shapes())
+        bytes_sweep = n_fac * (4.0 * n_el + (n_el / 8.0 if p.mask is not None else 0.0))
+        out = {"workload": p.note, "alpha_beta": [p.alpha, p.beta], "entries": int(n_el),
+               "algorithmic_bytes_per_sweep": bytes_sweep, "sweeps": sweeps}
+        precs = ["bf16", "fp32"] + (["fp64"] if args.workload == "small" else [])
+        for prec in precs:
+            sec, loss, prof, info = time_fit(nef, torch, p, prec, sweeps, args.warmup, stream)
+            out[prec] = {"sweeps_per_s": 1.0 / sec, "ms_per_sweep": sec * 1e3,
+                         "hbm_frac": bytes_sweep / sec / 1e9 / hbm, "loss": loss,
+                         "fused_pass_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1]},
+                         "fused_pass_launches_per_2_sweeps": {k: v[1] for k, v in prof.items()}}
+        out["bf16_vs_fp32_loss_rel"] = abs(out["bf16"]["loss"] - out["fp32"]["loss"]) / out["fp32"]["loss"]
+        out["bf16_vs_fp32_speedup"] = out["bf16"]["sweeps_per_s"] / out["fp32"]["sweeps_per_s"]
+        out["peak_source"] = f"hbm_gbs {hbm} of {src}"
+        print(json.dumps(out), flush=True)
+        return 0
+    # batched: a bounded subset of the batched workload, every problem with 8 restarts
+    specs = synth.batched_specs()[: args.batched_problems]
+    restarts = 8
+    probs = [synth.batched_problem(shape, r, seed=1000 + q, restarts=restarts) for q, (shape, r) in enumerate(specs)]
+    Ys = [torch.from_numpy(q.y).cuda() for q in probs]
+    Ms = [torch.from_numpy(q.mask).cuda() for q in probs]
+
+    def fresh():
+        return [[[torch.from_numpy(f).cuda() for f in q.inits[k]] for k in range(restarts)] for q in probs]
+
+    n_sum = sum(q.y.size for q in probs)
+    bytes_sweep = 3 * n_sum * (4.0 + 1.0 / 8.0)
+    fits = len(probs) * restarts
+    facs = fresh()
+    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, args.warmup, losses=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, sweeps)
+    t_b = time.perf_counter() - t0
+    # one plain FP32 plan per (problem, restart), the same sweeps
+    facs2 = fresh()
+    t1 = time.perf_counter()
+    loss_fp32 = []
+    for qi, q in enumerate(probs):
+        plan = nef.Plan(q.model_str, q.dims, precision="fp32", stream=stream)
+        for k in range(restarts):
+            plan.fit(Ys[qi], Ms[qi], facs2[qi][k], 1.0, 0.0, args.warmup + sweeps)
+        torch.cuda.synchronize()
+        loss_fp32.append([plan.loss(Ys[qi], Ms[qi], facs2[qi][k], 1.0, 0.0)[0] for k in range(restarts)])
+        del plan
+    t_s = time.perf_counter() - t1
+    sweeps_fp32 = fits * (args.warmup + sweeps)
+    rel = [abs(losses[a][b] - loss_fp32[a][b]) / loss_fp32[a][b] for a in range(len(probs)) for b in range(restarts)]
+    out = {"workload": f"batched CP: first {len(probs)} of the 512 problems (dims U{{20..300}}^3, ranks U{{4..32}}, "
+                       f"10% missing), {restarts} restarts each, KL",
+           "entries": int(n_sum), "fits": fits, "sweeps": sweeps,
+           "batched_bf16": {"fit_sweeps_per_s": fits * sweeps / t_b, "seconds": t_b,
+                            "hbm_frac": bytes_sweep * sweeps / t_b / 1e9 / hbm,
+                            "note": "wall clock of one nef_fit_batched call (one graph-captured sweep loop)"},
+           "per_fit_fp32": {"fit_sweeps_per_s": sweeps_fp32 / t_s, "seconds": t_s,
+                            "note": "one NEF_FP32 plan per problem, restarts fitted one after another"},
+           "speedup": (fits * sweeps / t_b) / (sweeps_fp32 / t_s),
+           "loss_rel_batched_vs_fp32": {"max": max(rel), "median": float(np.median(rel))},
+           "peak_source": f"hbm_gbs {hbm} of {src}"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "cp_kl":
+        return run_workload(args)
     return run_ours(args)
 
 
