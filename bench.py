@@ -337,6 +337,7 @@ def run_ours(args):
     # CUDA graph of one sweep); warm-up: W sweeps the same way
     plan = nef.Plan(p.model_str, dims, precision="bf16", stream=stream)
     fs = fresh()
+    splits = plan.autotune(Y, None, fs, p.alpha, p.beta)   # plan setup: column splits per pass
     plan.fit(Y, None, fs, p.alpha, p.beta, args.warmup)
     plan.check()
     if world > 1:
@@ -366,6 +367,7 @@ def run_ours(args):
     n_prof = min(args.steps, 100)
     pplan = nef.Plan(p.model_str, dims, precision="bf16", profile=True, stream=stream)
     gp = fresh()
+    pplan.autotune(Y, None, gp, p.alpha, p.beta)
     pplan.fit(Y, None, gp, p.alpha, p.beta, 2)
     pplan.profile(reset=True)
     torch.cuda.synchronize()
@@ -477,7 +479,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "bf16 (tcgen05)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2_flush": "inputs larger than L2 (Y = 537 MB)"},
+                       "l2_flush": "inputs larger than L2 (Y = 537 MB)",
+                       "column_splits": splits},
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e,
             "gpu_launches": launches_per_sweep * args.steps,
             "clocks": clocks, "loss": loss_bf16, "variants": variants,

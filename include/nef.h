@@ -138,6 +138,20 @@ nef_status nef_fit_ex(nef_plan_t plan, const void* Y, const uint8_t* mask, void*
 int nef_plan_sweeps(nef_plan_t plan);
 
 /*
+ * nef_plan_autotune -- choose the column-split count (CTAs per row block) of
+ * every fused pass by timing the pass kernel alone (CUDA events, median of 3)
+ * for candidates of one to four waves of CTAs over the device's SMs, on the
+ * given data (arguments as nef_fit; the factors are read, not changed).  With
+ * cache_path, choices are looked up first in that text file (one "key<TAB>split"
+ * line per pass view, precision, loss, mask and SM count) and the file is
+ * rewritten with every choice.  splits (host, L ints, or NULL) receives the
+ * chosen splits (-1 for passes without a fused kernel).  Synchronises the
+ * plan's stream.  Errors as nef_fit, plus NEF_EINVAL for an unwritable cache.
+ */
+nef_status nef_plan_autotune(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
+                             double alpha, double beta, const char* cache_path, int* splits);
+
+/*
  * nef_update -- one inner step of Algorithm 1: update factor l only, with the
  * other factors held fixed.  Arguments as nef_fit; l in [0, L).
  */

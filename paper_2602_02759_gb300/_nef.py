@@ -20,7 +20,7 @@ PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 
 # every symbol include/nef.h declares
 EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex",
-           "nef_plan_sweeps", "nef_update", "nef_loss", "nef_plan_info", "nef_plan_launches",
+           "nef_plan_sweeps", "nef_plan_autotune", "nef_update", "nef_loss", "nef_plan_info", "nef_plan_launches",
            "nef_plan_profile", "nef_check", "nef_fit_batched", "nef_cp3_update_static", "nef_last_error",
            "nef_foldin_num_params", "nef_foldin_create", "nef_foldin_destroy", "nef_foldin_grad",
            "nef_foldin_train_step", "nef_foldin_predict", "nef_foldin_params"]
@@ -64,6 +64,9 @@ def load(path: str = LIB_PATH):
     lib.nef_fit_ex.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
                                ctypes.c_int, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int)]
     lib.nef_fit_ex.restype = ctypes.c_int
+    lib.nef_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+    lib.nef_plan_autotune.restype = ctypes.c_int
     lib.nef_plan_sweeps.argtypes = [vp]
     lib.nef_plan_sweeps.restype = ctypes.c_int
     lib.nef_update.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(vp), ctypes.c_double,
@@ -268,6 +271,17 @@ class Plan:
                                 float(alpha), float(beta), int(iters), float(tol),
                                 self._ptr(loss_trace), ctypes.byref(done)))
         return int(done.value)
+
+    def autotune(self, Y, mask, factors, alpha, beta, cache=None):
+        """Time candidate column splits of every fused pass (nef_plan_autotune);
+        returns the chosen split per factor (-1: no fused kernel)."""
+        self._check_args(Y, mask, factors)
+        n = len(factors)
+        out = (ctypes.c_int * n)()
+        check(load().nef_plan_autotune(self._h, self._ptr(Y), self._ptr(mask), self._facs(factors),
+                                       float(alpha), float(beta), None if cache is None else str(cache).encode(),
+                                       out))
+        return [int(v) for v in out]
 
     def update(self, l, Y, mask, factors, alpha, beta):
         self._check_args(Y, mask, factors)

@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/nef.h"
@@ -235,6 +236,7 @@ struct nef_plan_s {
     std::vector<int64_t> fac_version;
     int64_t version_counter = 0;
     int64_t max_ld = 16;
+    int64_t n_sm = 152;               // SMs of the plan's device (grid sizing)
     // per-sweep loss and graph replay of sweeps
     int* loss_count = nullptr;        // device: entries appended to the loss trace
     cudaStream_t cap_stream = nullptr;
@@ -637,7 +639,9 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, PassPlan& o
     const int tn = (p.prec == NEF_FP64) ? 32 : (p.prec == NEF_BF16 ? 128 : 64);
     const int64_t n_rb = (rows + tm - 1) / tm;
     const int64_t tiles = (ncols + tn - 1) / tn;
-    const int64_t target = (p.prec == NEF_BF16) ? 148 : 152 * 4;
+    // one wave: one tensor-core CTA per SM (its shared memory fills the SM), four
+    // CUDA-core CTAs per SM
+    const int64_t target = (p.prec == NEF_BF16) ? p.n_sm : p.n_sm * 4;
     int64_t ns = std::max<int64_t>(1, target / std::max<int64_t>(1, n_rb));
     ns = std::min<int64_t>(ns, tiles);
     ns = std::max<int64_t>(ns, 1);
@@ -1216,6 +1220,174 @@ nef_status loss_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* con
     return NEF_OK;
 }
 
+nef_status alloc(nef_plan_t p, int id, size_t bytes);
+
+// Key of one pass's tuned split in the cache file: the pass's view (rows, columns,
+// bond), precision, weight kind, denominator mode, mask and the SM count.
+std::string tune_key(nef_plan_t p, const PassPlan& pp, const WeightSpec& w, int need_den, bool masked) {
+    char k[512];
+    snprintf(k, sizeof(k), "view rows=%lld c_out=%lld c_in=%lld bond_pad=%lld nq=%d prec=%d ab=%.17g,%.17g den=%d mask=%d "
+             "sm=%lld",
+             (long long)pp.view.rows, (long long)pp.view.c_out, (long long)pp.view.c_in, (long long)pp.view.bond_pad,
+             (int)pp.Q.size(), p->prec, w.alpha, w.beta, need_den, masked ? 1 : 0, (long long)p->n_sm);
+    return k;
+}
+
+// Grow the split-partial and loss-partial buffers to what the current splits need.
+nef_status ensure_split_buffers(nef_plan_t p) {
+    int64_t need = 16, loss_ctas = 0;
+    for (auto& pp : p->pass) {
+        if (pp.generic) continue;
+        need = std::max(need, (int64_t)pp.n_split * pp.view.rows * pp.view.bond_pad);
+        loss_ctas = std::max<int64_t>(loss_ctas, ((pp.view.rows + 31) / 32) * std::max<int64_t>(2, pp.n_split));
+    }
+    const size_t bytes = (size_t)need * p->esz;
+    for (int id : {(int)B_SPART_N, (int)B_SPART_D}) {
+        if (p->buf[id].bytes >= bytes) continue;
+        cudaFree(p->buf[id].ptr);
+        p->buf[id].ptr = nullptr;
+        NEF_TRY(alloc(p, id, bytes));
+    }
+    if (2 * loss_ctas > p->loss_part_cap) {
+        cudaFree(p->loss_part);
+        p->loss_part = nullptr;
+        p->loss_part_cap = (int)(2 * loss_ctas);
+        NEF_CUDA(cudaMalloc(&p->loss_part, p->loss_part_cap * sizeof(double)));
+    }
+    return NEF_OK;
+}
+
+template <typename T>
+nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* const* factors, double al,
+                         double be, const char* cache_path, int* splits) {
+    cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
+    const uint32_t* mbits = nullptr;
+    NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
+    const WeightSpec w = weight_spec(al, be);
+    const T* y = static_cast<const T*>(Y);
+    std::map<std::string, int> cache;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[1024];
+            while (fgets(line, sizeof(line), f)) {
+                char* tab = strrchr(line, '\t');
+                if (!tab) continue;
+                *tab = 0;
+                cache[line] = atoi(tab + 1);
+            }
+            fclose(f);
+        }
+    }
+    NEF_TRY(init_sources<T>(p, factors, st));
+    cudaEvent_t e0, e1;
+    NEF_CUDA(cudaEventCreate(&e0));
+    NEF_CUDA(cudaEventCreate(&e1));
+    nef_status rs = NEF_OK;
+    for (int l = 0; l < p->md.L && rs == NEF_OK; ++l) {
+        PassPlan& pp = p->pass[l];
+        if (splits) splits[l] = -1;
+        if (pp.generic) continue;
+        const bool b_is_one = (w.log_case || w.b_code == POW_ONE);
+        const bool closed = pp.den_closed && b_is_one && mbits == nullptr;
+        const int need_den = closed ? 0 : 1;
+        bool use_tc = false;
+        if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den);
+        const int64_t tm = use_tc ? 128 : (sizeof(T) == 8 ? 32 : 64);
+        const int64_t tn = sizeof(T) == 8 ? 32 : 64;
+        const int64_t n_rb = (pp.view.rows + tm - 1) / tm;
+        const int64_t tiles = std::max<int64_t>(1, (pp.view.c_out * pp.view.c_in + tn - 1) / tn);
+        const std::string key = tune_key(p, pp, w, need_den, mbits != nullptr);
+        auto hit = cache.find(key);
+        if (hit != cache.end()) {
+            pp.n_split = (int)std::max<int64_t>(1, std::min<int64_t>(hit->second, tiles));
+            if (splits) splits[l] = pp.n_split;
+            continue;
+        }
+        // candidates: 1..4 waves of CTAs over the SMs, and the current choice
+        const int64_t per_sm = use_tc ? 1 : 4;
+        std::vector<int> cand = {pp.n_split};
+        for (int k = 1; k <= 4; ++k) {
+            const int64_t c = std::max<int64_t>(1, std::min<int64_t>(tiles, k * p->n_sm * per_sm / n_rb));
+            if (std::find(cand.begin(), cand.end(), (int)c) == cand.end()) cand.push_back((int)c);
+        }
+        const int keep = pp.n_split;
+        pp.n_split = *std::max_element(cand.begin(), cand.end());
+        if ((rs = ensure_split_buffers(p)) != NEF_OK) break;
+        pp.n_split = keep;
+        if ((rs = refresh_sources<T>(p, pp, factors, st, use_tc)) != NEF_OK) break;
+        T* spn = static_cast<T*>(buf_ptr(p, B_SPART_N));
+        T* spd = static_cast<T*>(buf_ptr(p, B_SPART_D));
+        double best_ms = 1e300;
+        int best = keep;
+        for (int c : cand) {
+            auto launch = [&]() -> cudaError_t {
+                if (use_tc) {
+                    if constexpr (sizeof(T) == 4) {
+                        TcLaunchInfo info{};
+                        return launch_view_tc(reinterpret_cast<const float*>(y), mbits, bind_view(p, pp, true), w,
+                                              need_den, c, reinterpret_cast<float*>(spn), reinterpret_cast<float*>(spd),
+                                              p->tc_err, st, &info);
+                    }
+                    return cudaErrorNotSupported;
+                }
+                int n_ctas = 0;
+                return launch_view_simt<T>(y, mbits, bind_view(p, pp, false), w, need_den, c, spn,
+                                           need_den ? spd : nullptr, nullptr, nullptr, st, &n_ctas);
+            };
+            std::vector<float> ms;
+            cudaError_t ce = launch();  // warm-up
+            for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {
+                cudaEventRecord(e0, st);
+                ce = launch();
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms.push_back(t);
+            }
+            if (ce != cudaSuccess) {
+                rs = fail(NEF_ECUDA, "autotune launch failed: %s", cudaGetErrorString(ce));
+                break;
+            }
+            std::sort(ms.begin(), ms.end());
+            if (ms[1] < best_ms) {
+                best_ms = ms[1];
+                best = c;
+            }
+        }
+        pp.n_split = best;
+        cache[key] = best;
+        if (splits) splits[l] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    NEF_TRY(rs);
+    NEF_TRY(ensure_split_buffers(p));
+    // the plan description carries the splits
+    std::string info;
+    for (auto& pp : p->pass) {
+        const size_t at = pp.desc.find("splits=");
+        if (at != std::string::npos) {
+            const size_t end = pp.desc.find(' ', at);
+            pp.desc = pp.desc.substr(0, at) + "splits=" + std::to_string(pp.n_split) +
+                      (end == std::string::npos ? std::string() : pp.desc.substr(end));
+        }
+        info += pp.desc + "\n";
+    }
+    p->info = info;
+    if (p->sweep_graph) {  // recorded with the old splits
+        cudaGraphExecDestroy(p->sweep_graph);
+        p->sweep_graph = nullptr;
+    }
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "w");
+        if (!f) return fail(NEF_EINVAL, "cannot write the autotune cache %s", cache_path);
+        for (auto& kv : cache) fprintf(f, "%s\t%d\n", kv.first.c_str(), kv.second);
+        fclose(f);
+    }
+    return NEF_OK;
+}
+
 nef_status alloc(nef_plan_t p, int id, size_t bytes) {
     if ((int)p->buf.size() <= id) p->buf.resize(id + 1);
     if (bytes == 0) bytes = 16;
@@ -1470,6 +1642,13 @@ nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, con
     }
     p->prec = p->opt.precision;
     p->esz = p->prec == NEF_FP64 ? 8 : 4;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            p->n_sm = nsm;
+        cudaGetLastError();
+    }
     nef_status s = parse_model(model_str, shapes, n_obs, ranks, n_lat, p->md);
     if (s != NEF_OK) {
         delete p;
@@ -1511,6 +1690,16 @@ nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask, void* co
 }
 
 int nef_plan_sweeps(nef_plan_t plan) { return plan ? plan->last_sweeps : 0; }
+
+nef_status nef_plan_autotune(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
+                             double alpha, double beta, const char* cache_path, int* splits) {
+    g_err.clear();
+    if (!plan) return fail(NEF_EINVAL, "plan is NULL");
+    NEF_TRY(check_ab(alpha, beta));
+    if (plan->prec == NEF_FP64)
+        return autotune_impl<double>(plan, Y, mask, factors, alpha, beta, cache_path, splits);
+    return autotune_impl<float>(plan, Y, mask, factors, alpha, beta, cache_path, splits);
+}
 
 nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask, void* const* factors,
                       double alpha, double beta) {

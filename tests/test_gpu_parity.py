@@ -225,3 +225,32 @@ def test_config2_sampled_update(prec, beta):
         expect = np.maximum(1e-10, init[l].reshape(-1)[elems] * (num / den) ** eta)
         np.testing.assert_allclose(got.reshape(-1)[elems], expect, rtol=tol)
         assert np.all(np.isfinite(got)) and np.all(got >= 1e-10)
+
+
+# ------------------------------------------------------------------ autotune
+
+def test_autotune_bf16_then_fit(tmp_path):
+    """nef_plan_autotune picks a split per pass on the GPU, a second plan reads the
+    same choices from the cache, and the tuned plan's fit still matches the FP64
+    oracle's loss within 1e-3."""
+    nef = _nef()
+    model_str, dims = "ir,jr,kr->ijk", dict(i=256, j=160, k=288, r=32)
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(21)
+    truth = [rng.gamma(0.5, 1.0, m.factor_shape(l)) for l in range(3)]
+    y = rng.poisson(np.einsum(model_str, *truth)).astype(np.float32)
+    init = [rng.uniform(0.5, 1.5, m.factor_shape(l)) for l in range(3)]
+    Y = dev(y)
+    cache = tmp_path / "splits.txt"
+    plan = nef.Plan(model_str, dims, precision="bf16")
+    splits = plan.autotune(Y, None, [dev(f) for f in init], 1.0, 0.0, cache=cache)
+    assert all(s >= 1 for s in splits), splits
+    plan2 = nef.Plan(model_str, dims, precision="bf16")
+    assert plan2.autotune(Y, None, [dev(f) for f in init], 1.0, 0.0, cache=cache) == splits
+    iters = 10
+    _, trace = m.fit(y, None, init, 1.0, 0.0, iters, trace=True)
+    fs = [dev(f) for f in init]
+    plan.fit(Y, None, fs, 1.0, 0.0, iters)
+    plan.check()
+    lo, _ = plan.loss(Y, None, fs, 1.0, 0.0)
+    assert lo == pytest.approx(trace[-1], rel=1e-3)

@@ -299,3 +299,47 @@ def test_tol_stops_after_small_decrease(lib, tol):
             assert np.linalg.norm(work[l] - ref_f[l]) / np.linalg.norm(ref_f[l]) < 1e-10
     finally:
         lib.nef_plan_destroy(h)
+
+
+# ------------------------------------------------------------------ autotune
+
+def test_autotune_cache_roundtrip(lib, tmp_path):
+    """nef_plan_autotune writes one line per fused pass to its cache, reads it
+    back on the next plan, and a fit with the cached (different) splits still
+    matches the oracle."""
+    vp = ctypes.c_void_p
+    lib.nef_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+    model_str, dims = "ir,jr,kr->ijk", dict(i=40, j=36, k=300, r=3)
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(9)
+    fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)) for l in range(m.n_factors)]
+    y = rng.uniform(0.2, 3.0, size=m.y_shape)
+    cache = tmp_path / "splits.txt"
+    rc, h = make_plan(lib, model_str, dims, NEF_FP64)
+    assert rc == 0
+    out = (ctypes.c_int * 3)()
+    try:
+        rc = lib.nef_plan_autotune(h, y.ctypes.data, None, facs_arr(fs), 1.0, 0.0, str(cache).encode(), out)
+        assert rc == 0, lib.nef_last_error()
+    finally:
+        lib.nef_plan_destroy(h)
+    first = list(out)
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == sum(1 for s in first if s > 0) and all("\t" in ln for ln in lines)
+    # rewrite every cached split to 2 and tune a fresh plan from the cache
+    cache.write_text("".join(ln.rsplit("\t", 1)[0] + "\t2\n" for ln in lines))
+    rc, h = make_plan(lib, model_str, dims, NEF_FP64)
+    try:
+        rc = lib.nef_plan_autotune(h, y.ctypes.data, None, facs_arr(fs), 1.0, 0.0, str(cache).encode(), out)
+        assert rc == 0, lib.nef_last_error()
+        assert [s for s in out if s > 0] == [2] * len(lines)
+        assert "splits=2" in info(lib, h)
+        work = [f.copy() for f in fs]
+        rc = lib.nef_fit(h, y.ctypes.data, None, facs_arr(work), 1.0, 0.0, 3)
+        assert rc == 0, lib.nef_last_error()
+        ref = m.fit(y, None, [f.copy() for f in fs], 1.0, 0.0, 3)
+        for l in range(3):
+            assert np.linalg.norm(work[l] - ref[l]) / np.linalg.norm(ref[l]) < 1e-10
+    finally:
+        lib.nef_plan_destroy(h)
