@@ -64,6 +64,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """The maximum of x over all ranks of the default process group (x itself
+    when world == 1): every rank's timed region is bracketed by barriers, and the
+    job's time is the slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, ms):
+    """Units per second of the whole job: every rank ran `steps` steps of its own
+    replica and `ms` is the slowest rank's time."""
+    return world * steps / (ms / 1e3)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -355,12 +374,8 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     plan.check()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, device="cuda")
+    value = whole_job_rate(world, args.steps, ms)
 
     # kernel durations: the same sweeps launched eagerly with a CUDA event pair
     # around every fused-pass launch (on the plan's stream)
@@ -466,8 +481,8 @@ def run_ours(args):
             for a, b in zip(Fo, fd):
                 a.copy_(b, non_blocking=True)
             torch.cuda.current_stream().synchronize()
-        el = time.perf_counter() - t0
-        e2e = {"value": world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        el = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
+        e2e = {"value": whole_job_rate(world, args.steps, el * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
         del Yd, Yh
 
