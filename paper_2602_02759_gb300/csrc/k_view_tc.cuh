@@ -961,7 +961,23 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 // observed columns of this row within the half: bit c of `obs`
                 const int nv = min(32, max(0, nvalid - 32 * hh));
                 uint32_t obs = row_ok ? (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u)) : 0u;
-                if (prm.mbits && obs) {
+                if (prm.mbits && prm.trans && (v.rows & 31) == 0) {
+                    // rows are the contiguous dimension and a warp's 32 rows are one mask
+                    // word per column: lane c loads the word of column c, and a ballot per
+                    // bit hands row b its 32 column bits (warp-uniform: nv and, with rows
+                    // a multiple of 32, row_ok are the same for every lane)
+                    const int64_t cbase = col0 + 32 * hh;
+                    const int64_t wstride = v.rows >> 5;
+                    const int64_t wbase = (cbase * v.rows + r0 + 32 * (warp & 3)) >> 5;
+                    const uint32_t myw = (lane < nv && row_ok) ? prm.mbits[wbase + (int64_t)lane * wstride] : 0u;
+                    uint32_t m = 0;
+#pragma unroll
+                    for (int b = 0; b < 32; ++b) {
+                        const uint32_t r = __ballot_sync(0xffffffffu, (myw >> b) & 1u);
+                        if (lane == b) m = r;
+                    }
+                    obs &= m;
+                } else if (prm.mbits && obs) {
                     const int64_t cbase = col0 + 32 * hh;
                     if (prm.trans) {
                         uint32_t m = 0;
