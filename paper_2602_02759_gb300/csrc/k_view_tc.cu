@@ -181,6 +181,7 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
                            cudaStream_t st, TcLaunchInfo* info, unsigned long long* trace, const LossSpec* loss,
                            double* loss_part) {
     if (!tc_view_supported(v, need_den)) return cudaErrorNotSupported;
+    if (mbits && !need_den) return cudaErrorInvalidValue;  // mask code lives in the DEN instances only
     CUtensorMap map, vmap, cmap;
     tc::Params p;
     int n_rb = 0;

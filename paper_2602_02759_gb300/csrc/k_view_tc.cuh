@@ -37,6 +37,22 @@
 #ifndef NEF_TC_SUSPEND_NS
 #define NEF_TC_SUSPEND_NS 20000u
 #endif
+// ring depths (compile-time; the layout's static_asserts check shared memory and TMEM)
+#ifndef NEF_TC_NSY64
+#define NEF_TC_NSY64 4
+#endif
+#ifndef NEF_TC_NSV64
+#define NEF_TC_NSV64 6
+#endif
+#ifndef NEF_TC_NSQ64
+#define NEF_TC_NSQ64 5
+#endif
+#ifndef NEF_TC_NW
+#define NEF_TC_NW 4
+#endif
+#ifndef NEF_TC_ND
+#define NEF_TC_ND 4
+#endif
 
 namespace nef {
 namespace tc {
@@ -424,11 +440,11 @@ struct Layout {
     // tensor memory, so the shared-memory bandwidth of a tile goes to the Y
     // stream.  Ring depths: as many Y stages (bytes in flight towards HBM
     // latency) as fit next to the Q stages.
-    static constexpr int NSY = (BP == 64) ? 4 : (BP == 32 ? 5 : 6);  // Y stages
-    static constexpr int NSV = (BP == 64) ? 6 : 8;                    // staged source-row stages
-    static constexpr int NSQ = (BP == 64) ? 5 : 6;                    // Q stages
-    static constexpr int NW = DEN ? (BP == 16 ? 3 : 2) : 4;           // W buffers (TMEM)
-    static constexpr int ND = (DEN && BP == 64) ? 3 : 4;              // yhat buffers (TMEM)
+    static constexpr int NSY = (BP == 64) ? NEF_TC_NSY64 : (BP == 32 ? 5 : 6);  // Y stages
+    static constexpr int NSV = (BP == 64) ? NEF_TC_NSV64 : 8;                    // staged source-row stages
+    static constexpr int NSQ = (BP == 64) ? NEF_TC_NSQ64 : 6;                    // Q stages
+    static constexpr int NW = DEN ? (BP == 16 ? 3 : 2) : NEF_TC_NW;              // W buffers (TMEM)
+    static constexpr int ND = DEN ? (BP == 64 ? 3 : 4) : NEF_TC_ND;             // yhat buffers (TMEM)
     static constexpr int RB = BP * 2;                        // bytes per bond row (BF16)
     static constexpr int kY = 0;                             // NSY x 32 KB
     static constexpr int kV = kY + NSY * kYStageBytes;       // NSV x TN x RB: TMA-staged source rows
@@ -961,6 +977,9 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 // observed columns of this row within the half: bit c of `obs`
                 const int nv = min(32, max(0, nvalid - 32 * hh));
                 uint32_t obs = row_ok ? (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u)) : 0u;
+                // masked views always carry the denominator contraction (a mask rules out
+                // the closed form), so only DEN instances compile the mask code
+                if constexpr (DEN) {
                 if (prm.mbits && prm.trans && (v.rows & 31) == 0) {
                     // rows are the contiguous dimension and a warp's 32 rows are one mask
                     // word per column: lane c loads the word of column c, and a ballot per
@@ -992,6 +1011,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                         if (sh) m |= (uint64_t)prm.mbits[w0 + 1] << 32;
                         obs &= (uint32_t)(m >> sh);
                     }
+                }
                 }
                 uint32_t wa2[16], wb2[16];
                 float t = 0.f;  // loss terms of the observed entries (FP32 within the half)
