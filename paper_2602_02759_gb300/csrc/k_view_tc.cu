@@ -24,6 +24,18 @@ cudaError_t launch_bp32_loss(const CUtensorMap&, const CUtensorMap&, const CUten
                         cudaStream_t);
 cudaError_t launch_bp64_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
                         cudaStream_t);
+cudaError_t launch_bp16_g(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp32_g(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp64_g(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp16_g_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp32_g_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp64_g_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
 cudaError_t launch_batched_bp16(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 cudaError_t launch_batched_bp32(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 }  // namespace tc
@@ -198,18 +210,15 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         info->smem_bytes = 0;
     }
     const int wk = weight_kind(w);
-    if (p.loss_part) {
-        switch (v.bond_pad) {
-            case 16: return tc::launch_bp16_loss(map, vmap, cmap, p, need_den, wk, grid, st);
-            case 32: return tc::launch_bp32_loss(map, vmap, cmap, p, need_den, wk, grid, st);
-            default: return tc::launch_bp64_loss(map, vmap, cmap, p, need_den, wk, grid, st);
-        }
-    }
-    switch (v.bond_pad) {
-        case 16: return tc::launch_bp16(map, vmap, cmap, p, need_den, wk, grid, st);
-        case 32: return tc::launch_bp32(map, vmap, cmap, p, need_den, wk, grid, st);
-        default: return tc::launch_bp64(map, vmap, cmap, p, need_den, wk, grid, st);
-    }
+    using LaunchFn = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const tc::Params&,
+                                     int, int, int, cudaStream_t);
+    // [loss][staged rows][bond 16/32/64]
+    static const LaunchFn table[2][2][3] = {
+        {{tc::launch_bp16_g, tc::launch_bp32_g, tc::launch_bp64_g}, {tc::launch_bp16, tc::launch_bp32, tc::launch_bp64}},
+        {{tc::launch_bp16_g_loss, tc::launch_bp32_g_loss, tc::launch_bp64_g_loss},
+         {tc::launch_bp16_loss, tc::launch_bp32_loss, tc::launch_bp64_loss}}};
+    const int bi = v.bond_pad == 16 ? 0 : (v.bond_pad == 32 ? 1 : 2);
+    return table[p.loss_part ? 1 : 0][p.qmode ? 1 : 0][bi](map, vmap, cmap, p, need_den, wk, grid, st);
 }
 
 static_assert(sizeof(tc::Params) <= sizeof(TcUnit::prm), "TcUnit parameter area too small");

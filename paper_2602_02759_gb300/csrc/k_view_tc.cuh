@@ -34,6 +34,9 @@
 #include "nef_device.cuh"
 #include "nef_internal.h"
 
+#ifndef NEF_TC_TRACE
+#define NEF_TC_TRACE 0  // 1: per-site wait and phase cycle counters (nef_tc_trace; slows the pass)
+#endif
 #ifndef NEF_TC_SUSPEND_NS
 #define NEF_TC_SUSPEND_NS 20000u
 #endif
@@ -478,7 +481,9 @@ struct Layout {
 
 // The fused pass of one CTA: rows [rb*TM, rb*TM + TM) of the view and the
 // column tiles of split sp.
-template <int BP, bool DEN, int WK, bool LOSS>
+// QM: the Q-operand path compiled in: 0 gathered rows, 1 TMA-staged rows
+// (prm.qmode must match), 2 both, chosen by prm.qmode at run time (batched launches)
+template <int BP, bool DEN, int WK, bool LOSS, int QM>
 __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUtensorMap* vmap,
                                              const CUtensorMap* cmap, const Params& prm, const int64_t rb,
                                              const int64_t sp) {
@@ -517,7 +522,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     auto vempty = [&](int s) { return drain + 8u * (1 + LY::NSV + s); };
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + LY::kMisc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + LY::kMisc + 4);
+#if NEF_TC_TRACE
     unsigned long long* tr = prm.trace ? reinterpret_cast<unsigned long long*>(sm + LY::kTrace) : nullptr;
+#else
+    constexpr unsigned long long* tr = nullptr;  // wait counters compiled out (build with NEF_TC_TRACE=1)
+#endif
+    const bool qmode = (QM == 2) ? (prm.qmode != 0) : (QM == 1);
     const long long t_start = clock64();
     if (tr && tid < kTraceSites) tr[tid] = 0ull;
 
@@ -616,7 +626,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             constexpr int NSV = LY::NSV;
             const bool has_c = prm.q_const >= 0;
             int64_t vrow = 0, vmod = 1, crow = 0, cmod = 1, cc = 0, per = 1;
-            if (prm.qmode) {
+            if (qmode) {
                 const SrcDesc& dv = v.Q.src[prm.q_var];
                 vmod = dv.mod[0];
                 vrow = (t_lo * TN) % vmod;
@@ -649,12 +659,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 }
                 ++iv;
             };
-            if (prm.qmode)
+            if (qmode)
                 while (vok && iv < T && iv < NSV - 1) issue_v();
             int issued = 0;
             Cursor cur = cursor_at(t_lo);
             for (int i = 0; i < T; ++i) {
-                if (prm.qmode && vok && iv < T) issue_v();  // rows of tile i + NSV - 1
+                if (qmode && vok && iv < T) issue_v();  // rows of tile i + NSV - 1
                 if (!vok) break;
                 const int s = i % NSY;
                 if (!uwait(yempty(s), ((i / NSY) & 1) ^ 1, 1)) break;
@@ -750,7 +760,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         constexpr int NCH = BP / 8;             // 16-byte chunks per bond row
         static_assert(kOpWarps * 32 == TN, "one operand thread per tile column");
         const int cq = q;
-        if (prm.qmode) {
+        if (QM != 0 && qmode) {
             // The rows of source q_var and the single row of source q_const (if any) of
             // each tile are staged by TMA in their own ring, NSV - 1 tiles ahead of the
             // tile's Y (they are small and mostly L2-resident), so Q and yhat can be
@@ -805,7 +815,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 if (trl) phase_mark(tr, 18, tp);
             }
 
-        } else {
+        } else if constexpr (QM != 1) {
         // Gathered rows, in steps of half a column: step 2i + h builds chunks
         // [h*NH, h*NH + NH) of tile i.  The rows of the next step are loaded while
         // the current one is built, so the L2 latency of the gathers overlaps the
@@ -1117,12 +1127,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
 
 // LOSS: also sum the loss terms into prm.loss_part (a separate instance, so the
 // plain pass carries none of that code).
-template <int BP, bool DEN, int WK, bool LOSS>
+template <int BP, bool DEN, int WK, bool LOSS, int QM>
 __global__ void __launch_bounds__(kThreads, 1)
 k_view_tc(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap vmap,
           const __grid_constant__ CUtensorMap cmap, const __grid_constant__ Params prm) {
     const int64_t n_rb = (prm.v.rows + TM - 1) / TM;
-    view_tc_body<BP, DEN, WK, LOSS>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb, blockIdx.x / n_rb);
+    view_tc_body<BP, DEN, WK, LOSS, QM>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb, blockIdx.x / n_rb);
 }
 
 // Batched form: CTA b runs work[b] = (unit, row block, split); the unit's tensor
@@ -1136,8 +1146,8 @@ k_view_tc_batched(const TcUnit* __restrict__ units, const TcWork* __restrict__ w
     for (int i = threadIdx.x; i < (int)(sizeof(prm_sh) / 16); i += blockDim.x)
         reinterpret_cast<uint4*>(prm_sh)[i] = reinterpret_cast<const uint4*>(U->prm)[i];
     __syncthreads();
-    view_tc_body<BP, DEN, WK, false>(&U->ymap, &U->vmap, &U->cmap, *reinterpret_cast<const Params*>(prm_sh), wk.rb,
-                                     wk.sp);
+    view_tc_body<BP, DEN, WK, false, 2>(&U->ymap, &U->vmap, &U->cmap, *reinterpret_cast<const Params*>(prm_sh),
+                                        wk.rb, wk.sp);
 }
 
 }  // namespace tc

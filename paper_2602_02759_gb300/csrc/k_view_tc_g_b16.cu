@@ -1,0 +1,5 @@
+// k_view_tc_g_b16.cu -- tcgen05 fused pass with gathered Q rows, bond_pad 16.
+#include "k_view_tc_inst.cuh"
+
+NEF_TC_GATHER_INSTANCE(16)
+NEF_TC_GATHER_LOSS_INSTANCE(16)

@@ -5,10 +5,10 @@
 namespace nef {
 namespace tc {
 
-template <int BP, bool DEN, int WK, bool LOSS>
+template <int BP, bool DEN, int WK, bool LOSS, int QM>
 cudaError_t launch_one(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int grid,
                        cudaStream_t st) {
-    auto kern = k_view_tc<BP, DEN, WK, LOSS>;
+    auto kern = k_view_tc<BP, DEN, WK, LOSS, QM>;
     const int sm = Layout<BP, DEN>::kAlloc;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
@@ -16,21 +16,21 @@ cudaError_t launch_one(const CUtensorMap& map, const CUtensorMap& vmap, const CU
     return cudaGetLastError();
 }
 
-template <int BP, bool LOSS>
+template <int BP, bool LOSS, int QM>
 cudaError_t launch_bp(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int den,
                       int wk, int grid, cudaStream_t st) {
     if (den) {
         switch (wk) {
-            case WK_KL: return launch_one<BP, true, WK_KL, LOSS>(map, vmap, cmap, p, grid, st);
-            case WK_B05: return launch_one<BP, true, WK_B05, LOSS>(map, vmap, cmap, p, grid, st);
-            case WK_HEL: return launch_one<BP, true, WK_HEL, LOSS>(map, vmap, cmap, p, grid, st);
-            default: return launch_one<BP, true, WK_GEN, LOSS>(map, vmap, cmap, p, grid, st);
+            case WK_KL: return launch_one<BP, true, WK_KL, LOSS, QM>(map, vmap, cmap, p, grid, st);
+            case WK_B05: return launch_one<BP, true, WK_B05, LOSS, QM>(map, vmap, cmap, p, grid, st);
+            case WK_HEL: return launch_one<BP, true, WK_HEL, LOSS, QM>(map, vmap, cmap, p, grid, st);
+            default: return launch_one<BP, true, WK_GEN, LOSS, QM>(map, vmap, cmap, p, grid, st);
         }
     }
     switch (wk) {
-        case WK_KL: return launch_one<BP, false, WK_KL, LOSS>(map, vmap, cmap, p, grid, st);
-        case WK_HEL: return launch_one<BP, false, WK_HEL, LOSS>(map, vmap, cmap, p, grid, st);
-        default: return launch_one<BP, false, WK_GEN, LOSS>(map, vmap, cmap, p, grid, st);
+        case WK_KL: return launch_one<BP, false, WK_KL, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        case WK_HEL: return launch_one<BP, false, WK_HEL, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        default: return launch_one<BP, false, WK_GEN, LOSS, QM>(map, vmap, cmap, p, grid, st);
     }
 }
 
@@ -59,19 +59,22 @@ cudaError_t launch_batched_bp(const TcUnit* units, const TcWork* work, int n_wor
 }  // namespace tc
 }  // namespace nef
 
-// SUFFIX: empty for the plain pass, _loss for the loss-summing one (LOSS true)
-#define NEF_TC_INSTANCE_X(BP, SUFFIX, LOSS)                                                   \
+// SUFFIX names the instance set: plain or loss-summing (LOSS), with the Q operand
+// built from TMA-staged rows (QM 1) or gathered rows (QM 0, suffix _g)
+#define NEF_TC_INSTANCE_X(BP, SUFFIX, LOSS, QM)                                               \
     namespace nef {                                                                          \
     namespace tc {                                                                           \
     cudaError_t launch_bp##BP##SUFFIX(const CUtensorMap& map, const CUtensorMap& vmap,        \
                                       const CUtensorMap& cmap, const Params& p, int den, int wk, \
                                       int grid, cudaStream_t st) {                           \
-        return launch_bp<BP, LOSS>(map, vmap, cmap, p, den, wk, grid, st);                   \
+        return launch_bp<BP, LOSS, QM>(map, vmap, cmap, p, den, wk, grid, st);               \
     }                                                                                        \
     }                                                                                        \
     }
-#define NEF_TC_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, , false)
-#define NEF_TC_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _loss, true)
+#define NEF_TC_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, , false, 1)
+#define NEF_TC_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _loss, true, 1)
+#define NEF_TC_GATHER_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _g, false, 0)
+#define NEF_TC_GATHER_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _g_loss, true, 0)
 
 #define NEF_TC_BATCHED_INSTANCE(BP)                                                          \
     namespace nef {                                                                          \
