@@ -31,8 +31,9 @@ int nef_tc_probe(int bond_pad, int a_in_tmem, const uint16_t* P, const uint16_t*
 /*
  * nef_tc_trace -- wait-cycle counters of the tensor-core fused pass, summed over
  * every CTA of every launch on `plan` since the last reset (plans created with
- * nef_options.profile = 2 only; the counters add shared-memory atomics to every
- * tile, so timings taken with them are not representative).  out (host) receives 32 values: out[0] = summed
+ * nef_options.profile = 2, in a library built with -DNEF_TC_TRACE=1; other builds
+ * compile the counters out and leave them zero.  The counters add shared-memory
+ * atomics to every tile, so timings taken with them are not representative).  out (host) receives 32 values: out[0] = summed
  * CTA lifetimes in SM cycles; out[k], k = 1..12 = cycles spent in bounded waits
  * at site k: 1 producer waits for a free Y stage, 3 MMA waits for the P tile,
  * 4 MMA waits for a Q tile, 5 MMA waits for a free yhat buffer, 6 MMA waits for
