@@ -54,6 +54,9 @@ def parse():
                     help="cp_kl: the benchmark line (default); the others print one measurement "
                          "line each for the other workloads")
     ap.add_argument("--batched-problems", type=int, default=48)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the planner's default column splits (for profiler runs, where the "
+                         "autotuner's event timings include the profiler's own overhead)")
     return ap.parse_args()
 
 
@@ -356,7 +359,7 @@ def run_ours(args):
     # CUDA graph of one sweep); warm-up: W sweeps the same way
     plan = nef.Plan(p.model_str, dims, precision="bf16", stream=stream)
     fs = fresh()
-    splits = plan.autotune(Y, None, fs, p.alpha, p.beta)   # plan setup: column splits per pass
+    splits = None if args.no_autotune else plan.autotune(Y, None, fs, p.alpha, p.beta)  # plan setup
     plan.fit(Y, None, fs, p.alpha, p.beta, args.warmup)
     plan.check()
     if world > 1:
@@ -382,7 +385,8 @@ def run_ours(args):
     n_prof = min(args.steps, 100)
     pplan = nef.Plan(p.model_str, dims, precision="bf16", profile=True, stream=stream)
     gp = fresh()
-    pplan.autotune(Y, None, gp, p.alpha, p.beta)
+    if not args.no_autotune:
+        pplan.autotune(Y, None, gp, p.alpha, p.beta)
     pplan.fit(Y, None, gp, p.alpha, p.beta, 2)
     pplan.profile(reset=True)
     torch.cuda.synchronize()
