@@ -65,34 +65,6 @@ int weight_kind(const WeightSpec& w) {
     return tc::WK_GEN;
 }
 
-// Operand mode 1 applies when every 64-column tile starts at a multiple of 64 and,
-// within a tile, one column-side source has consecutive rows (single index term,
-// divisor 1, modulus a multiple of 64) and the other, if any, a single row
-// (divisor a multiple of 64).  Returns the sources' indices or false.
-bool regular_q(const ViewDesc& v, int* q_var, int* q_const) {
-    const int TN = tc::TN;
-    if (v.Q.nsrc < 1 || v.Q.nsrc > 2) return false;
-    if (v.c_in != 1 && v.c_in % TN != 0) return false;
-    int var = -1, cst = -1;
-    for (int s = 0; s < v.Q.nsrc; ++s) {
-        const SrcDesc& d = v.Q.src[s];
-        if (d.nterm != 1 || d.mul[0] != 1) return false;
-        if (d.div[0] == 1 && d.mod[0] % TN == 0) {
-            if (var >= 0) return false;
-            var = s;
-        } else if (d.div[0] % TN == 0) {
-            if (cst >= 0) return false;
-            cst = s;
-        } else {
-            return false;
-        }
-    }
-    if (var < 0) return false;
-    *q_var = var;
-    *q_const = cst;
-    return true;
-}
-
 }  // namespace
 
 bool tc_view_supported(const ViewDesc& v, int) {
@@ -143,7 +115,7 @@ cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v
     *vmap = *map;  // unused unless the Q operand is TMA-staged
     *cmap = *map;
     int q_var = -1, q_const = -1;
-    if (getenv("NEF_TC_GATHER") == nullptr && regular_q(v, &q_var, &q_const)) {
+    if (getenv("NEF_TC_GATHER") == nullptr && q_rows_staged(v, tc::TN, &q_var, &q_const)) {
         const SrcDesc& d = v.Q.src[q_var];
         cuuint64_t vd[2] = {(cuuint64_t)d.ld, (cuuint64_t)d.mod[0]};
         cuuint64_t vs[1] = {(cuuint64_t)d.ld * 2};
@@ -222,6 +194,7 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
 }
 
 static_assert(sizeof(tc::Params) <= sizeof(TcUnit::prm), "TcUnit parameter area too small");
+static_assert(tc::TN == kTcTileN, "planner and kernel disagree on the tile width");
 
 bool tc_make_unit(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w, int n_split,
                   float* s_num, float* s_den, int* err_flag, TcUnit* unit, int* n_rb) {

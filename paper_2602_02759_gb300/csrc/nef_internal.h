@@ -22,6 +22,7 @@ constexpr int kMaxLet = 26;
 constexpr int kMaxFac = 16;
 constexpr int kMaxSrc = 4;    // gathered sources per operand side
 constexpr int kMaxTerm = 3;   // index terms per source
+constexpr int kTcTileN = 64;  // columns per tile of the tensor-core pass
 constexpr int kMaxEinOps = 8; // operands of a small einsum
 constexpr int kMaxEinLet = 12;
 
@@ -246,5 +247,33 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
                            double* loss_part = nullptr);
 
 bool tc_view_supported(const ViewDesc& v, int need_den);
+
+// The tensor-core pass stages the Q operand's rows with TMA, instead of gathering
+// them per tile, when every tn-column tile starts at a multiple of tn and, within a
+// tile, one source has consecutive rows (one index term, divisor 1, modulus a
+// multiple of tn) and the other, if any, a single row (divisor a multiple of tn).
+// Returns the two sources' indices (q_const = -1 when there is one source).
+inline bool q_rows_staged(const ViewDesc& v, int tn, int* q_var, int* q_const) {
+    if (v.Q.nsrc < 1 || v.Q.nsrc > 2) return false;
+    if (v.c_in != 1 && v.c_in % tn != 0) return false;
+    int var = -1, cst = -1;
+    for (int s = 0; s < v.Q.nsrc; ++s) {
+        const SrcDesc& d = v.Q.src[s];
+        if (d.nterm != 1 || d.mul[0] != 1) return false;
+        if (d.div[0] == 1 && d.mod[0] % tn == 0) {
+            if (var >= 0) return false;
+            var = s;
+        } else if (d.div[0] % tn == 0) {
+            if (cst >= 0) return false;
+            cst = s;
+        } else {
+            return false;
+        }
+    }
+    if (var < 0) return false;
+    *q_var = var;
+    *q_const = cst;
+    return true;
+}
 
 }  // namespace nef

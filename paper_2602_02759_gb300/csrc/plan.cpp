@@ -370,7 +370,8 @@ std::vector<int> letters_used(const Model& md, const std::vector<int>& facs) {
     return used;
 }
 
-bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, PassPlan& out, int& next_buf) {
+bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, int qform, PassPlan& out,
+               int& next_buf) {
     const Model& md = p.md;
     std::vector<int> run, cols;
     for (int m = 0; m < md.M; ++m) (m >= s && m < e ? run : cols).push_back(m);
@@ -467,27 +468,87 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, PassPlan& o
         pp.P = sp;
         // a row letter without any row-side factor cannot happen: every observed letter is in a term
     }
-    // ---- Q: gathered sources when every column factor carries exactly the bond latents
-    bool gather = true;
-    std::vector<int> seen_obs;
-    for (int f : colf) {
-        std::vector<int> fl;
-        for (int x : md.term[f]) if (!md.is_obs(x)) fl.push_back(x);
-        std::vector<int> sb = bond, sf = fl;
-        std::sort(sb.begin(), sb.end());
-        std::sort(sf.begin(), sf.end());
-        if (sb != sf) gather = false;
-        int nobs = 0;
-        for (int x : md.term[f]) if (md.is_obs(x)) ++nobs;
-        if (nobs == 0 || nobs > kMaxTerm) gather = false;
-        for (int x : md.term[f])
-            if (md.is_obs(x)) {
-                if (std::find(seen_obs.begin(), seen_obs.end(), x) != seen_obs.end()) gather = false;
-                seen_obs.push_back(x);
-            }
+    // ---- Q: gathered sources, or one dense operand over every column letter.
+    // Each source is a group of column factors contracted over the latents private
+    // to the group, indexed by the group's observed letters (RHS order) and the
+    // bond; Q is the elementwise product of the sources, so every group must carry
+    // every bond letter and no two groups may share a letter outside the bond.
+    // qform 0 takes each column factor as its own group (it must carry exactly the
+    // bond latents) and falls back to the dense operand; qform 1 joins factors that
+    // share a letter outside the bond, and is tried only where qform 0 would not
+    // gather.
+    std::vector<std::vector<int>> groups;
+    auto is_bond = [&](int x) { return std::find(bond.begin(), bond.end(), x) != bond.end(); };
+    bool gather = (int)colf.size() <= kMaxSrc;
+    {
+        std::vector<int> seen_obs;
+        for (int f : colf) {
+            std::vector<int> sb = bond, sf;
+            for (int x : md.term[f]) if (!md.is_obs(x)) sf.push_back(x);
+            std::sort(sb.begin(), sb.end());
+            std::sort(sf.begin(), sf.end());
+            int nobs = 0;
+            for (int x : md.term[f])
+                if (md.is_obs(x)) {
+                    ++nobs;
+                    if (std::find(seen_obs.begin(), seen_obs.end(), x) != seen_obs.end()) gather = false;
+                    seen_obs.push_back(x);
+                }
+            if (sb != sf || nobs == 0) gather = false;
+        }
+        if ((int)seen_obs.size() != (int)cols.size()) gather = false;
     }
-    if ((int)colf.size() > kMaxSrc) gather = false;
-    if (gather && (int)seen_obs.size() != (int)cols.size()) gather = false;
+    if (qform == 0) {
+        if (gather)
+            for (int f : colf) groups.push_back({f});
+    } else {
+        if (gather) return false;  // qform 0 already gathers this view
+        std::vector<int> comp(colf.size());
+        for (size_t a = 0; a < colf.size(); ++a) comp[a] = (int)a;
+        auto root = [&](int a) {
+            while (comp[a] != a) a = comp[a];
+            return a;
+        };
+        for (size_t a = 0; a < colf.size(); ++a)
+            for (size_t b = a + 1; b < colf.size(); ++b)
+                for (int x : md.term[colf[a]])
+                    if (!is_bond(x) && md.fac_has(colf[b], x)) comp[root((int)b)] = root((int)a);
+        std::vector<int> rep;
+        for (size_t a = 0; a < colf.size(); ++a) {
+            const int r = root((int)a);
+            auto it = std::find(rep.begin(), rep.end(), r);
+            if (it == rep.end()) {
+                rep.push_back(r);
+                groups.push_back({colf[a]});
+            } else {
+                groups[it - rep.begin()].push_back(colf[a]);
+            }
+        }
+        // a group without observed letters is a vector over the bond: fold it into
+        // the first group that has some
+        int host = -1;
+        for (size_t g = 0; g < groups.size(); ++g)
+            for (int x : letters_used(md, groups[g]))
+                if (md.is_obs(x) && host < 0) host = (int)g;
+        if (host < 0) return false;
+        for (size_t g = 0; g < groups.size();) {
+            bool has_obs = false;
+            for (int x : letters_used(md, groups[g])) has_obs = has_obs || md.is_obs(x);
+            if (has_obs) {
+                ++g;
+                continue;
+            }
+            for (int f : groups[g]) groups[host].push_back(f);
+            groups.erase(groups.begin() + g);
+            if ((int)g < host) --host;
+        }
+        if ((int)groups.size() > kMaxSrc) return false;
+        for (auto& g : groups) {
+            const std::vector<int> used = letters_used(md, g);
+            for (int x : bond)
+                if (std::find(used.begin(), used.end(), x) == used.end()) return false;
+        }
+    }
     // column index digits: col = mixed radix over `cols` (RHS order)
     auto col_div = [&](int x) {
         int64_t d = 1;
@@ -498,36 +559,77 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, PassPlan& o
         }
         return d;
     };
+    // index terms of a source over its observed letters: one per letter, and
+    // neighbours in both the column order and the source's row order merge
+    struct Terms {
+        std::vector<int64_t> div, mod, mul;
+    };
+    auto index_terms = [&](const std::vector<int>& fobs, const std::vector<int64_t>& cst) {
+        Terms t;
+        for (int x : fobs) {
+            const int64_t d = col_div(x), m = md.dim[x], u = cst[x] / bond_pad;
+            if (!t.div.empty() && t.div.back() == d * m && t.mul.back() == u * m) {
+                t.div.back() = d;
+                t.mod.back() *= m;
+                t.mul.back() = u;
+            } else {
+                t.div.push_back(d);
+                t.mod.push_back(m);
+                t.mul.push_back(u);
+            }
+        }
+        return t;
+    };
+    auto group_obs = [&](const std::vector<int>& g) {
+        std::vector<int> fobs;
+        for (int x : letters_used(md, g))
+            if (md.is_obs(x)) fobs.push_back(x);  // ascending = RHS order
+        return fobs;
+    };
+    for (auto& g : groups) {
+        const std::vector<int> fobs = group_obs(g);
+        std::vector<int64_t> cst;
+        canon_strides(md, fobs, bond, bond_pad, cst);
+        const bool too_big = g.size() > 1 && prod_dims(md, fobs) * bond_pad > md.N / 4;
+        if (too_big || (int)index_terms(fobs, cst).div.size() > kMaxTerm) {
+            if (qform != 0) return false;
+            groups.clear();  // qform 0: dense operand instead
+            break;
+        }
+    }
     int64_t prep_elems = rows * bond_pad;
+    for (auto& g : groups) {
+        SourcePlan sp;
+        sp.buf = next_buf++;
+        const std::vector<int> fobs = group_obs(g);
+        sp.n_rows = prod_dims(md, fobs);
+        std::vector<int64_t> cst;
+        canon_strides(md, fobs, bond, bond_pad, cst);
+        EinRecipe& r = sp.build;
+        r.out_let = fobs;
+        for (int x : bond) r.out_let.push_back(x);
+        for (int x : r.out_let) r.out_st.push_back(cst[x]);
+        for (int x : letters_used(md, g))
+            if (std::find(r.out_let.begin(), r.out_let.end(), x) == r.out_let.end()) r.free_let.push_back(x);
+        for (int f : g) r.ops.push_back(factor_op(md, f));
+        r.out_kind = 1;
+        r.out_index = sp.buf;
+        finish_recipe(md, r);
+        sp.desc = SrcDesc{};
+        sp.desc.ld = bond_pad;
+        const Terms t = index_terms(fobs, cst);
+        sp.desc.nterm = (int)t.div.size();
+        for (size_t k = 0; k < t.div.size(); ++k) {
+            sp.desc.div[k] = t.div[k];
+            sp.desc.mod[k] = t.mod[k];
+            sp.desc.mul[k] = t.mul[k];
+        }
+        prep_elems += sp.n_rows * bond_pad;
+        pp.Q.push_back(sp);
+    }
+    gather = !groups.empty();
     if (gather) {
         pp.q_gathered = true;
-        for (int f : colf) {
-            SourcePlan sp;
-            sp.buf = next_buf++;
-            std::vector<int> fobs;
-            for (int x : md.term[f]) if (md.is_obs(x)) fobs.push_back(x);
-            sp.n_rows = prod_dims(md, fobs);
-            std::vector<int64_t> cst;
-            canon_strides(md, fobs, bond, bond_pad, cst);
-            EinRecipe& r = sp.build;
-            r.out_let = fobs;
-            for (int x : bond) r.out_let.push_back(x);
-            for (int x : r.out_let) r.out_st.push_back(cst[x]);
-            r.ops.push_back(factor_op(md, f));
-            r.out_kind = 1;
-            r.out_index = sp.buf;
-            finish_recipe(md, r);
-            sp.desc = SrcDesc{};
-            sp.desc.ld = bond_pad;
-            sp.desc.nterm = (int)fobs.size();
-            for (size_t t = 0; t < fobs.size(); ++t) {
-                sp.desc.div[t] = col_div(fobs[t]);
-                sp.desc.mod[t] = md.dim[fobs[t]];
-                sp.desc.mul[t] = cst[fobs[t]] / bond_pad;
-            }
-            prep_elems += sp.n_rows * bond_pad;
-            pp.Q.push_back(sp);
-        }
     } else {
         if (ncols * bond_pad > md.N / 4) return false;
         SourcePlan sp;
@@ -652,6 +754,15 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, PassPlan& o
     int64_t epi_cost = pp.epi_num.n_out_el * pp.epi_num.n_free_el;
     pp.cost = md.N * 4 + prep_elems * 8 + ns * rows * bond_pad * 8 + epi_cost / 4 +
               (gather ? 0 : ncols * bond_pad * 4 * 4);
+    if (p.prec == NEF_BF16) {
+        // the tensor-core pass gathers Q rows per tile where it cannot stage them
+        // with TMA, which is slower: weigh that as half a read of Y
+        ViewDesc vv = pp.view;
+        vv.Q.nsrc = (int)pp.Q.size();
+        for (size_t k = 0; k < pp.Q.size() && k < (size_t)kMaxSrc; ++k) vv.Q.src[k] = pp.Q[k].desc;
+        int q_var, q_const;
+        if (!q_rows_staged(vv, kTcTileN, &q_var, &q_const)) pp.cost += md.N * 2;
+    }
     char d[512];
     snprintf(d, sizeof(d),
              "factor %d '%s': view rows='%s' (%lld) cols=%lld [c_out=%lld c_in=%lld] bond='%s' "
@@ -1439,10 +1550,11 @@ nef_status build_plan(nef_plan_t p) {
                     for (int x : md.term[l])
                         if (md.is_obs(x) && !(x >= s && x < e)) ok_run = false;
                     if (!ok_run) continue;
-                  for (int assign = 0; assign < 64; ++assign) {
+                  for (int assign = 0; assign < 64; ++assign)
+                  for (int qform = 0; qform < 2; ++qform) {
                     PassPlan cand;
                     int nb = next_buf;
-                    if (!plan_view(*p, l, s, e, assign, cand, nb)) continue;
+                    if (!plan_view(*p, l, s, e, assign, qform, cand, nb)) continue;
                     bool fits = recipe_fits(cand.P.build) && recipe_fits(cand.epi_num) &&
                                 recipe_fits(cand.epi_den);
                     for (auto& q : cand.Q) fits = fits && recipe_fits(q.build);

@@ -227,6 +227,32 @@ def test_config2_sampled_update(prec, beta):
         assert np.all(np.isfinite(got)) and np.all(got >= 1e-10)
 
 
+def test_config3_sampled_update():
+    """Custom 4-way model 'ia,ja,ab,kb,lb->ijkl' at 256x256x64x32 (a = 16, b = 8),
+    (1/2, 1/2), 30 % missing, BF16, in the launch configuration the benchmark
+    times: one update each of factors ia, ja (256-row views whose Q operand is the
+    product of B or A with the contracted group sum_b C K L) and kb (a 2048-row
+    transposed view), checked on sampled elements against the oracle."""
+    nef = _nef()
+    p = synth.config3()
+    m = OracleModel(p.model_str, p.dims)
+    init = [f.astype(np.float64) for f in p.inits[0]]
+    plan = nef.Plan(p.model_str, p.dims, precision="bf16", profile=True)
+    Y, M = dev(p.y), dev(p.mask, torch.uint8)
+    rng = np.random.default_rng(12)
+    for l in (0, 1, 3):
+        fs = [dev(f) for f in init]
+        plan.update(l, Y, M, fs, p.alpha, p.beta)
+        plan.check()
+        assert plan.profile(reset=True)["tcgen05"][1] == 1, plan.info()
+        got = fs[l].cpu().numpy().reshape(-1)
+        elems = rng.choice(got.size, size=2, replace=False)
+        num, den = m.numden_sampled(l, elems, p.y, p.mask, init, p.alpha, p.beta)
+        expect = m.apply_update(init[l].reshape(-1)[elems], num, den, p.alpha, p.beta)
+        np.testing.assert_allclose(got[elems], expect, rtol=2e-3)
+        assert np.all(np.isfinite(got)) and np.all(got >= 1e-10)
+
+
 # ------------------------------------------------------------------ autotune
 
 def test_autotune_bf16_then_fit(tmp_path):
