@@ -395,6 +395,29 @@ __device__ __forceinline__ void unpack_bf16x8(const uint4& q, float (&f)[8]) {
     }
 }
 
+// sqrt.approx.f32 (one SFU operation): the weights are rounded to BF16 next, so
+// the correctly rounded square root buys nothing here.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 32 x 32 bit transpose across a warp: lane c holds column c (bit r = row r); on
+// return lane r holds row r (bit c = column c).  Five exchange steps swap the
+// off-diagonal blocks of halving size (16, 8, 4, 2, 1 bits).
+__device__ __forceinline__ uint32_t warp_transpose_bits(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const uint32_t m = masks[k];
+        const uint32_t p = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((p >> j) & m)) : ((x & m) | ((p & m) << j));
+    }
+    return x;
+}
+
 // One loss term D(y, yhat) in FP32 (App. B).  For KL the weight a = y / yhat
 // is already at hand: D = y log(a) - y + yhat.
 template <int WK>
@@ -413,7 +436,7 @@ __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& 
         wb = r;
         wa = y * r * r * r;
     } else if (WK == WK_HEL) {
-        wa = sqrtf(y) * rsqrtf(yh);
+        wa = sqrt_approx(y) * rsqrtf(yh);
         wb = 1.0f;
     } else {
         ab_weights(y, yh, w, wa, wb);
@@ -992,20 +1015,14 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 if constexpr (DEN) {
                 if (prm.mbits && prm.trans && (v.rows & 31) == 0) {
                     // rows are the contiguous dimension and a warp's 32 rows are one mask
-                    // word per column: lane c loads the word of column c, and a ballot per
-                    // bit hands row b its 32 column bits (warp-uniform: nv and, with rows
-                    // a multiple of 32, row_ok are the same for every lane)
+                    // word per column: lane c loads the word of column c, and a 32 x 32 bit
+                    // transpose hands row b its 32 column bits (warp-uniform: nv and, with
+                    // rows a multiple of 32, row_ok are the same for every lane)
                     const int64_t cbase = col0 + 32 * hh;
                     const int64_t wstride = v.rows >> 5;
                     const int64_t wbase = (cbase * v.rows + r0 + 32 * (warp & 3)) >> 5;
                     const uint32_t myw = (lane < nv && row_ok) ? prm.mbits[wbase + (int64_t)lane * wstride] : 0u;
-                    uint32_t m = 0;
-#pragma unroll
-                    for (int b = 0; b < 32; ++b) {
-                        const uint32_t r = __ballot_sync(0xffffffffu, (myw >> b) & 1u);
-                        if (lane == b) m = r;
-                    }
-                    obs &= m;
+                    obs &= warp_transpose_bits(myw, lane);
                 } else if (prm.mbits && obs) {
                     const int64_t cbase = col0 + 32 * hh;
                     if (prm.trans) {
@@ -1014,7 +1031,8 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                             m |= (uint32_t)mask_bit(prm.mbits, (cbase + c) * v.rows + row) << c;
                         obs &= m;
                     } else {
-                        const int64_t idx0 = (cbase / v.c_in) * v.rows * v.c_in + row * v.c_in + (cbase % v.c_in);
+                        // a tile lies inside one c_in block: its block is z0, its offset x0
+                        const int64_t idx0 = ((int64_t)z0 * v.rows + row) * v.c_in + x0 + 32 * hh;
                         const int64_t w0 = idx0 >> 5;
                         const int sh = (int)(idx0 & 31);
                         uint64_t m = prm.mbits[w0];
