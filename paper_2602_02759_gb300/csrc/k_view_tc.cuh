@@ -395,12 +395,31 @@ __device__ __forceinline__ void unpack_bf16x8(const uint4& q, float (&f)[8]) {
     }
 }
 
-// sqrt.approx.f32 (one SFU operation): the weights are rounded to BF16 next, so
-// the correctly rounded square root buys nothing here.
+// sqrt.approx / rsqrt.approx with subnormals flushed (one SFU operation each):
+// the weights are rounded to BF16 next, so neither the correctly rounded square
+// root nor subnormal inputs (yhat below 1.2e-38) buy anything here.
 __device__ __forceinline__ float sqrt_approx(float x) {
     float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Mask of BF16 pair q of a 32-entry half: low half kept if bit 2q of the
+// observed bits is set, high half if bit 2q+1 is.  sh[k] = obs << (7 - k)
+// carries bits k, k+8, k+16, k+24 in the sign bits of its four bytes, so one
+// byte permute with sign replication (prmt selector nibbles with the msb set)
+// builds the mask from sh[2q mod 8] and sh[2q+1 mod 8].
+__device__ __forceinline__ uint32_t pair_mask(const uint32_t (&sh)[8], int q) {
+    const uint32_t b = (uint32_t)(q >> 2);
+    const uint32_t sel = ((8u | b) * 0x11u) | (((8u | (4u + b)) * 0x11u) << 8);
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(sh[(2 * q) & 7]), "r"(sh[(2 * q + 1) & 7]), "r"(sel));
+    return d;
 }
 
 // 32 x 32 bit transpose across a warp: lane c holds column c (bit r = row r); on
@@ -432,11 +451,11 @@ __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& 
         wa = __fdividef(y, yh);
         wb = 1.0f;
     } else if (WK == WK_B05) {
-        const float r = rsqrtf(yh);
+        const float r = rsqrt_approx(yh);
         wb = r;
         wa = y * r * r * r;
     } else if (WK == WK_HEL) {
-        wa = sqrt_approx(y) * rsqrtf(yh);
+        wa = sqrt_approx(y) * rsqrt_approx(yh);
         wb = 1.0f;
     } else {
         ab_weights(y, yh, w, wa, wb);
@@ -1064,10 +1083,12 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 if (obs != 0xffffffffu) {
                     // unobserved, padding or out-of-range entries: clear their BF16 halves
                     // (this also drops the Inf/NaN weights of entries with yhat == 0)
+                    uint32_t sh[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) sh[k] = obs << (7 - k);
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const uint32_t m = (((obs >> (2 * q)) & 1u) ? 0x0000ffffu : 0u) |
-                                           (((obs >> (2 * q + 1)) & 1u) ? 0xffff0000u : 0u);
+                        const uint32_t m = pair_mask(sh, q);
                         wa2[q] &= m;
                         if (DEN) wb2[q] &= m;
                     }
