@@ -85,6 +85,62 @@ __global__ void k_einsum_direct(EinDesc d) {
     out[dst] = d.accumulate ? out[dst] + acc : acc;
 }
 
+// Contraction with G threads per output element: the threads of a group take the
+// free combinations f = sub, sub + G, ... (each decodes its own f) and the group
+// sums its partials in a fixed order (xor shuffles within a warp; for G = 256 the
+// warp sums are added in warp order).  Used where each output has few enough free
+// combinations that G threads cover them in a handful of steps.
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
+    constexpr int kGroups = kThreads / G;
+    const int sub = (int)(threadIdx.x % G);
+    const int64_t o = (int64_t)blockIdx.x * kGroups + threadIdx.x / G;
+    const bool ok = o < d.n_out_el;
+    T acc = T(0);
+    int64_t dst = 0;
+    if (ok) {
+        int64_t base[kMaxEinOps];
+        for (int k = 0; k < d.n_ops; ++k) base[k] = 0;
+        int64_t rem = o;
+        for (int q = d.n_out - 1; q >= 0; --q) {
+            const int64_t v = rem % d.dim[q];
+            rem /= d.dim[q];
+            dst += v * d.out_st[q];
+            for (int k = 0; k < d.n_ops; ++k) base[k] += v * d.ost[k][q];
+        }
+        for (int64_t f = sub; f < d.n_free_el; f += G) {
+            int64_t off[kMaxEinOps];
+            for (int k = 0; k < d.n_ops; ++k) off[k] = base[k];
+            uint32_t r = (uint32_t)f;  // n_free_el < 2^31 on this path
+            for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
+                const uint32_t dq = (uint32_t)d.dim[q];
+                const uint32_t v = r % dq;
+                r /= dq;
+                for (int k = 0; k < d.n_ops; ++k) off[k] += (int64_t)v * d.ost[k][q];
+            }
+            T p = T(1);
+            for (int k = 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
+            acc += p;
+        }
+    }
+    if constexpr (G <= 32) {
+#pragma unroll
+        for (int w = G / 2; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    } else {
+        static_assert(G == kThreads, "group size");
+        __shared__ T sh[kThreads / 32];
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        acc = T(0);
+        for (int k = 0; k < kThreads / 32; ++k) acc += sh[k];
+    }
+    if (ok && sub == 0) {
+        T* out = static_cast<T*>(d.out);
+        out[dst] = d.accumulate ? out[dst] + acc : acc;
+    }
+}
+
 template <typename T>
 __global__ void k_einsum_final(EinDesc d, int n_split, const T* partial) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,25 +346,43 @@ __device__ __forceinline__ void write_mirrors(const MirrorDesc& m, const int64_t
     }
 }
 
+// One block per 32 consecutive factor elements: the 8 warps sum the split
+// partials s = g, g + 8, ... (lane = element, so the reads are coalesced), and
+// warp 0 adds the 8 group sums in order and applies the update.
+constexpr int kFinEl = 32;
+
 template <typename T>
-__global__ void k_finish(FinishDesc d, UpdateSpec u) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= d.n) return;
+__global__ void __launch_bounds__(kThreads) k_finish(FinishDesc d, UpdateSpec u) {
+    constexpr int kGrp = kThreads / kFinEl;
+    __shared__ T sn[kGrp][kFinEl], sd[kGrp][kFinEl];
+    const int lane = (int)(threadIdx.x % kFinEl), g = (int)(threadIdx.x / kFinEl);
+    const int64_t e = (int64_t)blockIdx.x * kFinEl + lane;
+    const bool ok = e < d.n;
     int64_t idx[kMaxFacLet];
-    decode_letters<T>(e, d.nlet, d.dim, idx);
     int64_t soff = 0, boff = 0;
-    for (int q = 0; q < d.nlet; ++q) {
-        soff += idx[q] * d.s_st[q];
-        boff += idx[q] * d.b_st[q];
+    T num = T(0), den = T(0);
+    if (ok) {
+        decode_letters<T>(e, d.nlet, d.dim, idx);
+        for (int q = 0; q < d.nlet; ++q) {
+            soff += idx[q] * d.s_st[q];
+            boff += idx[q] * d.b_st[q];
+        }
+        const T* pn = static_cast<const T*>(d.part_num);
+        for (int s = g; s < d.n_split; s += kGrp) num += pn[(int64_t)s * d.s_size + soff];
+        if (d.part_den) {
+            const T* pd = static_cast<const T*>(d.part_den);
+            for (int s = g; s < d.n_split; s += kGrp) den += pd[(int64_t)s * d.s_size + soff];
+        }
     }
-    const T* pn = static_cast<const T*>(d.part_num);
-    T num = T(0);
-    for (int s = 0; s < d.n_split; ++s) num += pn[(int64_t)s * d.s_size + soff];
-    T den;
+    sn[g][lane] = num;
+    sd[g][lane] = den;
+    __syncthreads();
+    if (g != 0 || !ok) return;
+    num = T(0);
+    for (int k = 0; k < kGrp; ++k) num += sn[k][lane];
     if (d.part_den) {
-        const T* pd = static_cast<const T*>(d.part_den);
         den = T(0);
-        for (int s = 0; s < d.n_split; ++s) den += pd[(int64_t)s * d.s_size + soff];
+        for (int k = 0; k < kGrp; ++k) den += sd[k][lane];
     } else {
         den = T(1);
         for (int s = 0; s < d.n_cs; ++s) den *= static_cast<const T*>(d.cs[s])[boff];
@@ -373,6 +447,21 @@ inline unsigned blocks_for(int64_t n, int threads = kThreads) {
 template <typename T>
 cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cudaStream_t st) {
     if (d.n_out_el <= 0) return cudaSuccess;
+    // few free combinations per output: a group of G threads per output
+    if (d.n_free_el > 4 && d.n_free_el < ((int64_t)1 << 31)) {
+        const int g = d.n_free_el <= 64 ? 8 : (d.n_free_el <= 1024 ? 32 : kThreads);
+        const bool part_ok = partial_cap >= 2 * d.n_out_el;
+        if (d.n_free_el / g <= 64 || !part_ok) {
+            const int64_t per = kThreads / g;
+            const int64_t blocks = (d.n_out_el + per - 1) / per;
+            if (blocks < ((int64_t)1 << 31)) {
+                if (g == 8) k_einsum_grouped<T, 8><<<(unsigned)blocks, kThreads, 0, st>>>(d);
+                else if (g == 32) k_einsum_grouped<T, 32><<<(unsigned)blocks, kThreads, 0, st>>>(d);
+                else k_einsum_grouped<T, kThreads><<<(unsigned)blocks, kThreads, 0, st>>>(d);
+                return cudaGetLastError();
+            }
+        }
+    }
     // split the free combinations so that the grid has enough threads
     const int64_t want = (int64_t)152 * 2048;
     int64_t n_split = 1;
@@ -396,7 +485,7 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
 
 template <typename T>
 cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t st) {
-    k_finish<T><<<blocks_for(d.n), kThreads, 0, st>>>(d, u);
+    k_finish<T><<<blocks_for(d.n, kFinEl), kThreads, 0, st>>>(d, u);
     return cudaGetLastError();
 }
 

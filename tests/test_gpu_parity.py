@@ -138,6 +138,28 @@ def test_family_two_sweeps(model_str, dims, prec, ab):
         assert rel(fs[q].cpu().numpy(), ref[q]) < tol, (q, plan.info())
 
 
+@pytest.mark.parametrize("dims", [dict(i=8, j=8, k=2000), dict(i=5, j=300, k=7)])
+def test_generic_long_contractions_fp64(dims):
+    """'ij,jk,ik->ijk' has no fused view: its numerators are einsums over the
+    materialised weights with 2000 (resp. 300) free combinations per output,
+    which run on the grouped contraction kernels (256 and 32 threads per output)."""
+    nef = _nef()
+    model_str = "ij,jk,ik->ijk"
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(21)
+    init = [rng.uniform(0.3, 1.7, m.factor_shape(l)) for l in range(m.n_factors)]
+    y = rng.poisson(np.einsum(model_str, *init)).astype(np.float64)
+    mask = (rng.random(m.y_shape) > 0.2).astype(np.uint8)
+    ref = m.fit(y, mask, init, 1.0, 0.0, 2)
+    plan = nef.Plan(model_str, dims, precision="fp64")
+    assert "generic" in plan.info()
+    fs = [dev(f, torch.float64) for f in init]
+    plan.fit(dev(y, torch.float64), dev(mask, torch.uint8), fs, 1.0, 0.0, 2)
+    plan.check()
+    for q in range(m.n_factors):
+        assert rel(fs[q].cpu().numpy(), ref[q]) < 1e-10
+
+
 # ------------------------------------------------------ tensor-core path
 
 TC_CASES = [
