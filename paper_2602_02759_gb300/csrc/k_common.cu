@@ -88,8 +88,8 @@ __global__ void k_einsum_direct(EinDesc d) {
 // Contraction with G threads per output element: the threads of a group take the
 // free combinations f = sub, sub + G, ... (each decodes its own f) and the group
 // sums its partials in a fixed order (xor shuffles within a warp; for G = 256 the
-// warp sums are added in warp order).  Used where each output has few enough free
-// combinations that G threads cover them in a handful of steps.
+// warp sums are added in warp order).  Used where G threads cover an output's free
+// combinations in a few steps (at most 4 for G = 8 and 32, 64 for G = 256).
 template <typename T, int G>
 __global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
     constexpr int kGroups = kThreads / G;
@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
             dst += v * d.out_st[q];
             for (int k = 0; k < d.n_ops; ++k) base[k] += v * d.ost[k][q];
         }
+#pragma unroll 4
         for (int64_t f = sub; f < d.n_free_el; f += G) {
             int64_t off[kMaxEinOps];
             for (int k = 0; k < d.n_ops; ++k) off[k] = base[k];
@@ -449,7 +450,7 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
     if (d.n_out_el <= 0) return cudaSuccess;
     // few free combinations per output: a group of G threads per output
     if (d.n_free_el > 4 && d.n_free_el < ((int64_t)1 << 31)) {
-        const int g = d.n_free_el <= 64 ? 8 : (d.n_free_el <= 1024 ? 32 : kThreads);
+        const int g = d.n_free_el <= 32 ? 8 : (d.n_free_el <= 128 ? 32 : kThreads);
         const bool part_ok = partial_cap >= 2 * d.n_out_el;
         if (d.n_free_el / g <= 64 || !part_ok) {
             const int64_t per = kThreads / g;

@@ -990,6 +990,35 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             int nvalid, x0, z0;
             tile_info(cur, col0, nvalid, x0, z0);
             for (int k = 0; k < kEpiGroups; ++k) advance(cur);
+            // mask words of both halves, loaded before the waits so that their
+            // latency overlaps them (masked views only; see below for the layouts)
+            uint32_t mw0a = 0u, mw0b = 0u, mw1a = 0u, mw1b = 0u;
+            if constexpr (DEN) {
+                if (prm.mbits) {
+                    const int nv0 = min(32, nvalid), nv1 = min(32, max(0, nvalid - 32));
+                    if (prm.trans) {
+                        if ((v.rows & 31) == 0 && row_ok) {
+                            const int64_t wstride = v.rows >> 5;
+                            const int64_t wb0 = (col0 * v.rows + r0 + 32 * (warp & 3)) >> 5;
+                            const int64_t wb1 = wb0 + 32 * wstride;
+                            if (lane < nv0) mw0a = prm.mbits[wb0 + (int64_t)lane * wstride];
+                            if (lane < nv1) mw1a = prm.mbits[wb1 + (int64_t)lane * wstride];
+                        }
+                    } else if (row_ok) {
+                        // a tile lies inside one c_in block: its block is z0, its offset x0
+                        const int64_t idx0 = ((int64_t)z0 * v.rows + row) * v.c_in + x0;
+                        const int64_t i1 = idx0 + 32;
+                        if (nv0 > 0) {
+                            mw0a = prm.mbits[idx0 >> 5];
+                            if (idx0 & 31) mw0b = prm.mbits[(idx0 >> 5) + 1];
+                        }
+                        if (nv1 > 0) {
+                            mw1a = prm.mbits[i1 >> 5];
+                            if (i1 & 31) mw1b = prm.mbits[(i1 >> 5) + 1];
+                        }
+                    }
+                }
+            }
             if (!wwait(dfull(bd), (i / ND) & 1, 9)) break;
             if (!wwait(yfull(s), (i / NSY) & 1, 10)) break;
             if (!wwait(wempty(b), ((i / NW) & 1) ^ 1, 11)) break;
@@ -1034,28 +1063,23 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 if constexpr (DEN) {
                 if (prm.mbits && prm.trans && (v.rows & 31) == 0) {
                     // rows are the contiguous dimension and a warp's 32 rows are one mask
-                    // word per column: lane c loads the word of column c, and a 32 x 32 bit
+                    // word per column: lane c loaded the word of column c, and a 32 x 32 bit
                     // transpose hands row b its 32 column bits (warp-uniform: nv and, with
                     // rows a multiple of 32, row_ok are the same for every lane)
-                    const int64_t cbase = col0 + 32 * hh;
-                    const int64_t wstride = v.rows >> 5;
-                    const int64_t wbase = (cbase * v.rows + r0 + 32 * (warp & 3)) >> 5;
-                    const uint32_t myw = (lane < nv && row_ok) ? prm.mbits[wbase + (int64_t)lane * wstride] : 0u;
-                    obs &= warp_transpose_bits(myw, lane);
+                    obs &= warp_transpose_bits(hh ? mw1a : mw0a, lane);
                 } else if (prm.mbits && obs) {
-                    const int64_t cbase = col0 + 32 * hh;
                     if (prm.trans) {
+                        const int64_t cbase = col0 + 32 * hh;
                         uint32_t m = 0;
                         for (int c = 0; c < nv; ++c)
                             m |= (uint32_t)mask_bit(prm.mbits, (cbase + c) * v.rows + row) << c;
                         obs &= m;
                     } else {
-                        // a tile lies inside one c_in block: its block is z0, its offset x0
-                        const int64_t idx0 = ((int64_t)z0 * v.rows + row) * v.c_in + x0 + 32 * hh;
-                        const int64_t w0 = idx0 >> 5;
-                        const int sh = (int)(idx0 & 31);
-                        uint64_t m = prm.mbits[w0];
-                        if (sh) m |= (uint64_t)prm.mbits[w0 + 1] << 32;
+                        // bits idx0 .. idx0 + 31 of the row, idx0 = offset of the half's
+                        // first column: one or two words
+                        const int sh = (int)((((int64_t)z0 * v.rows + row) * v.c_in + x0 + 32 * hh) & 31);
+                        uint64_t m = hh ? mw1a : mw0a;
+                        if (sh) m |= (uint64_t)(hh ? mw1b : mw0b) << 32;
                         obs &= (uint32_t)(m >> sh);
                     }
                 }

@@ -138,11 +138,12 @@ def test_family_two_sweeps(model_str, dims, prec, ab):
         assert rel(fs[q].cpu().numpy(), ref[q]) < tol, (q, plan.info())
 
 
-@pytest.mark.parametrize("dims", [dict(i=8, j=8, k=2000), dict(i=5, j=300, k=7)])
+@pytest.mark.parametrize("dims", [dict(i=8, j=8, k=2000), dict(i=5, j=300, k=7), dict(i=6, j=100, k=9)])
 def test_generic_long_contractions_fp64(dims):
     """'ij,jk,ik->ijk' has no fused view: its numerators are einsums over the
-    materialised weights with 2000 (resp. 300) free combinations per output,
-    which run on the grouped contraction kernels (256 and 32 threads per output)."""
+    materialised weights with 2000, 300 or 100 free combinations per output (and
+    7-9 for the other factors), which run on the grouped contraction kernels
+    (256, 32 and 8 threads per output)."""
     nef = _nef()
     model_str = "ij,jk,ik->ijk"
     m = OracleModel(model_str, dims)
