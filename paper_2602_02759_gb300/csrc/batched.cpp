@@ -50,7 +50,10 @@ nef_status bfail(nef_status s, const char* msg) {
 
 int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-constexpr int64_t kTilesPerCta = 16;  // column tiles per CTA of one unit
+#ifndef NEF_BATCH_TILES
+#define NEF_BATCH_TILES 64
+#endif
+constexpr int64_t kTilesPerCta = NEF_BATCH_TILES;  // column tiles per CTA of one unit
 
 struct Prob {
     int64_t d[3], pd[3];
