@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", default="cp_kl",
-                    choices=["cp_kl", "cp_beta05", "custom4", "small", "batched"],
+                    choices=["cp_kl", "cp_beta05", "custom4", "small", "batched", "uber", "icews"],
                     help="cp_kl: the benchmark line (default); the others print one measurement "
                          "line each for the other workloads")
     ap.add_argument("--batched-problems", type=int, default=48)
@@ -555,9 +555,10 @@ def run_workload(args):
     hbm, _, src = load_peaks()
     stream = torch.cuda.current_stream()
     sweeps = max(3, args.steps)
-    if args.workload in ("cp_beta05", "custom4", "small"):
+    if args.workload in ("cp_beta05", "custom4", "small", "uber", "icews"):
         p = {"cp_beta05": lambda: synth.config2(beta=-0.5, n=args.n),
-             "custom4": synth.config3, "small": synth.config1}[args.workload]()
+             "custom4": synth.config3, "small": synth.config1,
+             "uber": synth.config_uber, "icews": synth.config_icews}[args.workload]()
         n_el = p.y.size
         n_fac = len(p.factor_shapes())
         bytes_sweep = n_fac * (4.0 * n_el + (n_el / 8.0 if p.mask is not None else 0.0))
@@ -566,6 +567,8 @@ def run_workload(args):
         precs = ["bf16", "fp32"] + (["fp64"] if args.workload == "small" else [])
         for prec in precs:
             sec, loss, prof, info = time_fit(nef, torch, p, prec, sweeps, args.warmup, stream)
+            if prec == "bf16":
+                out["plan"] = info.strip().splitlines()
             out[prec] = {"sweeps_per_s": 1.0 / sec, "ms_per_sweep": sec * 1e3,
                          "hbm_frac": bytes_sweep / sec / 1e9 / hbm, "loss": loss,
                          "fused_pass_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1]},

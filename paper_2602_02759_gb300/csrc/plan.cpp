@@ -754,6 +754,26 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, int qform, 
     int64_t epi_cost = pp.epi_num.n_out_el * pp.epi_num.n_free_el;
     pp.cost = md.N * 4 + prep_elems * 8 + ns * rows * bond_pad * 8 + epi_cost / 4 +
               (gather ? 0 : ncols * bond_pad * 4 * 4);
+    // rows past the last full tile of tm rows are computed and discarded
+    pp.cost += (int64_t)((double)md.N * 4.0 * ((double)(n_rb * tm) / (double)rows - 1.0));
+    // small kernels per pass (a few microseconds each): every operand that is not a
+    // relabelled copy of one factor is rebuilt, and an epilogue that contracts runs
+    // its own reduction, contractions and update
+    {
+        auto is_copy = [&](const EinRecipe& r) {
+            if (r.ops.size() != 1 || r.ops[0].kind != 0 || !r.free_let.empty()) return false;
+            const int f = r.ops[0].index;
+            if (r.out_let.size() < md.term[f].size()) return false;
+            for (int x : md.term[f])
+                if (std::find(r.out_let.begin(), r.out_let.end(), x) == r.out_let.end()) return false;
+            return true;
+        };
+        int launches = is_copy(pp.P.build) ? 0 : 1;
+        for (auto& q : pp.Q) launches += is_copy(q.build) ? 0 : 1;
+        if (pp.epi_num.ops.size() != 1 || !pp.epi_num.free_let.empty()) launches += 4;
+        constexpr int64_t kLaunchBytes = (int64_t)16 << 20;
+        pp.cost += launches * kLaunchBytes;
+    }
     if (p.prec == NEF_BF16) {
         // the tensor-core pass gathers Q rows per tile where it cannot stage them
         // with TMA, which is slower: weigh that as half a read of Y

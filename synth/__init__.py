@@ -134,6 +134,28 @@ def random_factors(model_str, dims, seed, lo=0.5, hi=1.5):
     return [rng.uniform(lo, hi, size=tuple(dims[c] for c in t)) for t in terms]
 
 
+def config_uber(seed=0, dims=(27, 7, 24, 100, 100), r=10, k=6) -> Problem:
+    """The paper's Uber model 'wr,dr,hr,irk,jrk->wdhij' at the Uber tensor's shape
+    27x7x24x100x100 (45.4 M entries) with R = 10, K = 6 (the ranks of the paper's
+    qualitative Uber fit); Gamma(0.3,1) truth, Poisson data, no mask, KL."""
+    w, d, h, i, j = dims
+    p = make_problem("wr,dr,hr,irk,jrk->wdhij", {"w": w, "d": d, "h": h, "i": i, "j": j, "r": r, "k": k},
+                     seed, gamma=(0.3, 1.0), missing=0.0, alpha=1.0, beta=0.0)
+    p.note = f"uber-shaped wr,dr,hr,irk,jrk->wdhij {dims} R{r} K{k} KL"
+    return p
+
+
+def config_icews(seed=0, dims=(249, 249, 20, 228), r=16, k=4) -> Problem:
+    """The paper's ICEWS model 'ir,jr,ak,kr,tr->ijat' at the ICEWS tensor's shape
+    249x249x20x228 (282.7 M entries) with R = 16, K = 4 (the paper does not state
+    the ranks of its ICEWS fits); Gamma(0.3,1) truth, Poisson data, no mask, KL."""
+    i, j, a, t = dims
+    p = make_problem("ir,jr,ak,kr,tr->ijat", {"i": i, "j": j, "a": a, "t": t, "r": r, "k": k}, seed,
+                     gamma=(0.3, 1.0), missing=0.0, alpha=1.0, beta=0.0)
+    p.note = f"icews-shaped ir,jr,ak,kr,tr->ijat {dims} R{r} K{k} KL"
+    return p
+
+
 def config5(seed=0, n=2048, jk=(128, 128), rank=32, n_train=1536) -> Problem:
     """Fold-in workload: CP 'ir,jr,kr->ijk' n x J x K rank 32, Gamma(0.3,1) truth,
     Poisson data, no mask, KL.  Slices 0..n_train-1 train the model and the

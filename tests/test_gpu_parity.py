@@ -170,6 +170,8 @@ TC_CASES = [
     ("ir,jr,kr->ijk", dict(i=136, j=100, k=68, r=16), 1.0, 0.0, True),
     ("ia,ja,ab,kb,lb->ijkl", dict(i=32, j=40, k=16, l=8, a=16, b=8), 0.5, 0.5, True),
     ("ir,jr,kr->ijk", dict(i=96, j=64, k=128, r=20), 1.0, 1.0, False),
+    ("wr,dr,hr,irk,jrk->wdhij", dict(w=9, d=7, h=8, i=30, j=40, r=5, k=3), 1.0, 0.0, True),
+    ("ir,jr,ak,kr,tr->ijat", dict(i=60, j=50, a=20, t=40, r=8, k=3), 1.0, 0.0, False),
 ]
 
 
@@ -274,6 +276,32 @@ def test_config3_sampled_update():
         expect = m.apply_update(init[l].reshape(-1)[elems], num, den, p.alpha, p.beta)
         np.testing.assert_allclose(got[elems], expect, rtol=2e-3)
         assert np.all(np.isfinite(got)) and np.all(got >= 1e-10)
+
+
+def test_uber_shape_sampled_update():
+    """The Uber model 'wr,dr,hr,irk,jrk->wdhij' at the Uber tensor's shape
+    27x7x24x100x100 (R = 10, K = 6), BF16: the dr update runs on the 4536-row
+    view 'wdh' (a contracted epilogue), the irk update on the 10000-row view 'ij';
+    sampled elements against the oracle."""
+    nef = _nef()
+    p = synth.config_uber()
+    m = OracleModel(p.model_str, p.dims)
+    init = [f.astype(np.float64) for f in p.inits[0]]
+    plan = nef.Plan(p.model_str, p.dims, precision="bf16", profile=True)
+    info = plan.info().splitlines()
+    assert "rows='wdh'" in info[1] and "kernel=tcgen05" in info[1], info
+    Y = dev(p.y)
+    rng = np.random.default_rng(13)
+    for l in (1, 3):
+        fs = [dev(f) for f in init]
+        plan.update(l, Y, None, fs, p.alpha, p.beta)
+        plan.check()
+        assert plan.profile(reset=True)["tcgen05"][1] == 1, plan.info()
+        got = fs[l].cpu().numpy().reshape(-1)
+        elems = rng.choice(got.size, size=2, replace=False)
+        num, den = m.numden_sampled(l, elems, p.y, None, init, p.alpha, p.beta)
+        expect = m.apply_update(init[l].reshape(-1)[elems], num, den, p.alpha, p.beta)
+        np.testing.assert_allclose(got[elems], expect, rtol=2e-3)
 
 
 # ------------------------------------------------------------------ autotune
