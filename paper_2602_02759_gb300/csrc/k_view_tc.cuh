@@ -661,23 +661,30 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         // The whole warp runs the loop; one elected lane issues the copies.
         {
             // Staged source rows (qmode 1) run NSV - 1 tiles ahead of the Y stream.
-            // In qmode 1, c_in is 1 or a multiple of TN, so tile t starts at column
-            // t*TN: the staged row (col mod m, m a multiple of TN) advances by TN per
-            // tile and the constant row ((col / d) mod m, d a multiple of TN) by one
-            // every d / TN tiles, so both are kept as counters.
+            // When c_in is 1 or a multiple of TN, tile t starts at column t*TN: the
+            // staged row (col mod m, m a multiple of TN) advances by TN per tile and
+            // the constant row ((col / d) mod m, d a multiple of TN) by one every
+            // d / TN tiles.  In the block form (c_in > 1 not a multiple of TN) the
+            // tiles restart at every c_in block: the staged row is the tile's offset
+            // in the block (m == c_in) and the constant row advances by one every
+            // d / c_in blocks.  All are kept as counters.
             constexpr int NSV = LY::NSV;
             const bool has_c = prm.q_const >= 0;
-            int64_t vrow = 0, vmod = 1, crow = 0, cmod = 1, cc = 0, per = 1;
+            const bool block = !prm.trans && (v.c_in % TN) != 0;
+            int64_t vrow = 0, vmod = 1, crow = 0, cmod = 1, cc = 0, per = 1, ci = 0;
             if (qmode) {
                 const SrcDesc& dv = v.Q.src[prm.q_var];
                 vmod = dv.mod[0];
-                vrow = (t_lo * TN) % vmod;
+                const int64_t unit = block ? v.c_in : TN;  // columns per step of the constant row
+                const int64_t step = block ? t_lo / prm.n_cib : t_lo;  // blocks (or tiles) before t_lo
+                ci = block ? t_lo - step * prm.n_cib : 0;
+                vrow = block ? ci * TN : (t_lo * TN) % vmod;
                 if (has_c) {
                     const SrcDesc& dc = v.Q.src[prm.q_const];
-                    per = dc.div[0] / TN;
+                    per = dc.div[0] / unit;
                     cmod = dc.mod[0];
-                    const int64_t g = t_lo / per;
-                    cc = t_lo - g * per;
+                    const int64_t g = step / per;
+                    cc = step - g * per;
                     crow = g % cmod;
                 }
             }
@@ -693,9 +700,19 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 mbar_expect_tx_e(vfull(sv), TN * RB + (has_c ? RB : 0));
                 tma_load_2d_e(base + LY::kV + sv * (TN * RB), vmap, 0, (int)vrow, vfull(sv));
                 if (has_c) tma_load_2d_e(base + LY::kG + sv * LY::kGSlot, cmap, 0, (int)crow, vfull(sv));
-                vrow += TN;
-                if (vrow == vmod) vrow = 0;
-                if (++cc == per) {
+                bool next_c = true;
+                if (block) {
+                    vrow += TN;
+                    next_c = ++ci == prm.n_cib;
+                    if (next_c) {
+                        ci = 0;
+                        vrow = 0;
+                    }
+                } else {
+                    vrow += TN;
+                    if (vrow == vmod) vrow = 0;
+                }
+                if (next_c && ++cc == per) {
                     cc = 0;
                     if (++crow == cmod) crow = 0;
                 }
@@ -811,9 +828,10 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             const bool has_c = prm.q_const >= 0;
             long long tp = clock64();
             const bool trl = tr && lane == 0;
-            // Every qmode-1 tile is full (c_in is a multiple of TN, or c_in == 1 and
-            // c_out is a multiple of the staged source's extent), so the build has no
-            // column predicate.
+            // A qmode-1 tile is full (c_in is a multiple of TN, or c_in == 1 and c_out
+            // is a multiple of the staged source's extent) or, in the block form, ends
+            // at its c_in block, where the staged rows past c_in arrive as zeros: the
+            // build has no column predicate.
 #pragma unroll 1
             for (int i = 0; i < T; ++i) {
                 const int s = i % NSV, sq = i % NSQ;

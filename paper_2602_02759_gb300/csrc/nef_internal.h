@@ -249,21 +249,26 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
 bool tc_view_supported(const ViewDesc& v, int need_den);
 
 // The tensor-core pass stages the Q operand's rows with TMA, instead of gathering
-// them per tile, when every tn-column tile starts at a multiple of tn and, within a
-// tile, one source has consecutive rows (one index term, divisor 1, modulus a
-// multiple of tn) and the other, if any, a single row (divisor a multiple of tn).
-// Returns the two sources' indices (q_const = -1 when there is one source).
+// them per tile, when within a tile one source has consecutive rows and the other,
+// if any, a single row.  Tiles of tn columns start at multiples of tn when c_in is
+// 1 or a multiple of tn: then the consecutive source needs one index term, divisor
+// 1 and a modulus that is a multiple of tn, the single-row source a divisor that is
+// a multiple of tn.  Otherwise (block form) the tiles restart at every c_in block
+// and the last one of a block is partial: the consecutive source's modulus must be
+// c_in (its rows are the offsets inside the block; rows past c_in read as zero) and
+// the single-row source's divisor a multiple of c_in.  Returns the two sources'
+// indices (q_const = -1 when there is one source).
 inline bool q_rows_staged(const ViewDesc& v, int tn, int* q_var, int* q_const) {
     if (v.Q.nsrc < 1 || v.Q.nsrc > 2) return false;
-    if (v.c_in != 1 && v.c_in % tn != 0) return false;
+    const bool block = v.c_in != 1 && v.c_in % tn != 0;
     int var = -1, cst = -1;
     for (int s = 0; s < v.Q.nsrc; ++s) {
         const SrcDesc& d = v.Q.src[s];
         if (d.nterm != 1 || d.mul[0] != 1) return false;
-        if (d.div[0] == 1 && d.mod[0] % tn == 0) {
+        if (d.div[0] == 1 && (block ? d.mod[0] == v.c_in : d.mod[0] % tn == 0)) {
             if (var >= 0) return false;
             var = s;
-        } else if (d.div[0] % tn == 0) {
+        } else if (block ? d.div[0] % v.c_in == 0 : d.div[0] % tn == 0) {
             if (cst >= 0) return false;
             cst = s;
         } else {
