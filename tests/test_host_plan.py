@@ -102,6 +102,9 @@ MODELS = [
     ("wr,dr,hr,irk,jrk->wdhij", dict(w=2, d=3, h=2, i=3, j=4, r=2, k=2)),
     ("ri,jr,kr->ijk", dict(i=4, j=3, k=5, r=3)),
     ("ir,js,rs->ij", dict(i=5, j=4, r=2, s=3)),
+    # large enough that the ia / ja passes take one-letter views whose Q operand
+    # includes the contracted group sum_b C K L (an operand source of three factors)
+    ("ia,ja,ab,kb,lb->ijkl", dict(i=12, j=12, k=8, l=8, a=3, b=2)),
 ]
 
 
@@ -193,6 +196,30 @@ def test_planner_views(lib):
     txt = info(lib, h)
     lib.nef_plan_destroy(h)
     assert txt.count("generic") == 3, txt
+
+
+def test_planner_groups_and_row_padding(lib):
+    """Column factors that share a letter outside the bond become one operand
+    source (custom 4-way model: the ia pass runs on the 256-row view 'i' with
+    Q = B o (sum_b C K L), not on the 65536-row view 'ij'), and views whose rows
+    fill a small part of a tile lose to wider views (Uber shape: the dr pass runs
+    on the 4536-row view 'wdh', not on the 7-row view 'd')."""
+    rc, h = make_plan(lib, "ia,ja,ab,kb,lb->ijkl", dict(i=256, j=256, k=64, l=32, a=16, b=8), NEF_BF16)
+    assert rc == 0, lib.nef_last_error()
+    lines = info(lib, h).splitlines()
+    lib.nef_plan_destroy(h)
+    assert "rows='i' (256)" in lines[0] and "Q=gather(2)" in lines[0], lines
+    assert "rows='j' (256)" in lines[1], lines
+    rc, h = make_plan(lib, "wr,dr,hr,irk,jrk->wdhij", dict(w=27, d=7, h=24, i=100, j=100, r=10, k=6), NEF_BF16)
+    assert rc == 0, lib.nef_last_error()
+    lines = info(lib, h).splitlines()
+    lib.nef_plan_destroy(h)
+    assert all("rows='wdh' (4536)" in lines[q] for q in range(3)), lines
+    # small problems keep the one-letter views (extra kernels would cost more than the padding)
+    rc, h = make_plan(lib, "ir,jr,kr->ijk", dict(i=30, j=40, k=50, r=5), NEF_BF16)
+    lines = info(lib, h).splitlines()
+    lib.nef_plan_destroy(h)
+    assert [ln.split("rows='")[1][0] for ln in lines] == ["i", "j", "k"], lines
 
 
 @pytest.mark.parametrize("bad,code", [
