@@ -1,5 +1,5 @@
-"""Build the host test double: the product's plan.cpp and batched.cpp compiled
-with g++ against a fake CUDA runtime and plain-loop launchers (tests only)."""
+"""Build the host test double: the product's plan.cpp, batched.cpp and foldin.cpp
+compiled with g++ against a fake CUDA runtime and plain-loop launchers (tests only)."""
 import os
 import subprocess
 
@@ -12,8 +12,9 @@ LIB = os.path.join(OUT, "libnef_hostcheck.so")
 
 def build():
     os.makedirs(OUT, exist_ok=True)
-    srcs = [os.path.join(CSRC, "plan.cpp"), os.path.join(CSRC, "batched.cpp"),
-            os.path.join(HERE, "mock_launchers.cpp"), os.path.join(HERE, "mock_batched.cpp")]
+    srcs = [os.path.join(CSRC, "plan.cpp"), os.path.join(CSRC, "batched.cpp"), os.path.join(CSRC, "foldin.cpp"),
+            os.path.join(HERE, "mock_launchers.cpp"), os.path.join(HERE, "mock_batched.cpp"),
+            os.path.join(HERE, "mock_foldin.cpp")]
     deps = srcs + [os.path.join(CSRC, f) for f in ("nef_internal.h", "nef_device.cuh", "nef_batched.h")] + \
         [os.path.join(ROOT, "include", "nef.h")] + \
         [os.path.join(HERE, "shim", f) for f in ("cuda_runtime.h", "cuda.h")]
