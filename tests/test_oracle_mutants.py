@@ -4,7 +4,8 @@ Each case copies oracle/nef_oracle.c, plants one plausible slip in the copy (a
 dropped operand, a wrong exponent, a transposed layout, a mask left out, a
 wrong branch of the g-table), builds it on the CPU, and runs the pin suite
 (test_oracle_pins.py) against that build in a child process: some pin must
-fail.  The committed oracle itself is never modified.
+fail.  The same is done for the encoder oracle (oracle/mlp.py against
+test_mlp_oracle.py).  The committed oracle itself is never modified.
 """
 import os
 import subprocess
@@ -83,4 +84,51 @@ def test_unmutated_copy_passes(tmp_path):
                     "-lm"], check=True)
     r = subprocess.run([sys.executable, "-c", CHILD, str(mut_src), str(mut_lib)], cwd=ROOT,
                        capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+MLP_SRC = os.path.join(ROOT, "oracle", "mlp.py")
+
+MLP_MUTANTS = [
+    ("softplus derivative taken as 1", "g_z3 = g_out * sigmoid(z3)", "g_z3 = g_out"),
+    ("relu derivative of layer 2 dropped", "g_z2 = g_h2 * (z2 > 0.0)", "g_z2 = g_h2"),
+    ("square weight gradient transposed", "gW2 = h1.T @ g_z2", "gW2 = g_z2.T @ h1"),
+    ("bias gradient averaged instead of summed", "gb1 = g_z1.sum(axis=0)", "gb1 = g_z1.mean(axis=0)"),
+    ("loss derivative missing the 1 / (1 + out) factor", "g_out = 2.0 * d / (1.0 + out) / n", "g_out = 2.0 * d / n"),
+    ("Adam without bias correction of the second moment", "vh = v / (1.0 - b2 ** t)", "vh = v"),
+    ("forward pass skips the second bias", "z2 = h1 @ W2 + b2", "z2 = h1 @ W2"),
+]
+
+MLP_CHILD = """
+import importlib.util
+import sys
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.mlp", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(mod)
+sys.modules["oracle.mlp"] = mod
+oracle.mlp = mod
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "tests/test_mlp_oracle.py"]))
+"""
+
+
+@pytest.mark.parametrize("name,old,new", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
+def test_mlp_pins_catch_planted_mistake(name, old, new, tmp_path):
+    with open(MLP_SRC) as fh:
+        src = fh.read()
+    assert src.count(old) == 1, f"mutation site not unique: {name}"
+    mut = tmp_path / "mlp.py"
+    mut.write_text(src.replace(old, new))
+    r = subprocess.run([sys.executable, "-c", MLP_CHILD, str(mut)], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 1, f"no pin failed for: {name}\n{r.stdout[-2000:]}\n{r.stderr[-2000:]}"
+
+
+def test_mlp_unmutated_copy_passes(tmp_path):
+    mut = tmp_path / "mlp.py"
+    with open(MLP_SRC) as fh:
+        mut.write_text(fh.read())
+    r = subprocess.run([sys.executable, "-c", MLP_CHILD, str(mut)], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
