@@ -222,6 +222,64 @@ def test_planner_groups_and_row_padding(lib):
     assert [ln.split("rows='")[1][0] for ln in lines] == ["i", "j", "k"], lines
 
 
+def _random_model(rng):
+    """A random valid model string: 2-3 observed letters, 1-3 latent letters,
+    2-5 factors; every observed letter in one factor, every latent letter in
+    1-3 factors (some factors get extra latent letters)."""
+    obs = list("ijkl")[: rng.integers(2, 4)]
+    lat = list("rstu")[: rng.integers(1, 4)]
+    n_fac = int(rng.integers(2, 6))
+    terms = [[] for _ in range(n_fac)]
+    for x in obs:
+        terms[int(rng.integers(n_fac))].append(x)
+    for x in lat:
+        for f in rng.choice(n_fac, size=int(rng.integers(1, min(3, n_fac) + 1)), replace=False):
+            terms[int(f)].append(x)
+    for f in range(n_fac):
+        if lat and rng.random() < 0.3:
+            x = lat[int(rng.integers(len(lat)))]
+            if x not in terms[f]:
+                terms[f].append(x)
+        rng.shuffle(terms[f])
+    terms = [tm for tm in terms if tm]
+    dims = {x: int(rng.integers(2, 7)) for x in obs + lat}
+    if rng.random() < 0.3:
+        for x in obs:
+            dims[x] = int(rng.integers(5, 13))
+    return ",".join("".join(tm) for tm in terms) + "->" + "".join(obs), dims
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_models_match_oracle(lib, seed):
+    """Planner generality: random model strings (views, bond choices, grouped
+    operand sources, merged index terms, contracted epilogues, the generic
+    fallback), one sweep in FP64 and FP32, with and without a mask."""
+    rng = np.random.default_rng(1000 + seed)
+    model_str, dims = _random_model(rng)
+    m = OracleModel(model_str, dims)
+    a, b = [(1.0, 0.0), (0.5, 0.5), (1.0, -0.5)][seed % 3]
+    for prec in (NEF_FP64, NEF_FP32):
+        for masked in (False, True):
+            dt = np.float64 if prec == NEF_FP64 else np.float32
+            fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)).astype(dt) for l in range(m.n_factors)]
+            y = rng.uniform(0.2, 3.0, size=m.y_shape).astype(dt)
+            mask = (rng.random(m.y_shape) > 0.3).astype(np.uint8) if masked else None
+            rc, h = make_plan(lib, model_str, dims, prec)
+            assert rc == 0, (model_str, lib.nef_last_error())
+            try:
+                ref = m.fit(y.astype(np.float64), mask, [f.astype(np.float64) for f in fs], a, b, 1)
+                work = [f.copy() for f in fs]
+                rc = lib.nef_fit(h, y.ctypes.data, None if mask is None else mask.ctypes.data, facs_arr(work),
+                                 a, b, 1)
+                assert rc == 0, (model_str, lib.nef_last_error())
+                tol = 1e-9 if prec == NEF_FP64 else 3e-5
+                for l in range(m.n_factors):
+                    rel = np.linalg.norm(work[l] - ref[l]) / np.linalg.norm(ref[l])
+                    assert rel < tol, (model_str, dims, prec, masked, l, rel, info(lib, h))
+            finally:
+                lib.nef_plan_destroy(h)
+
+
 @pytest.mark.parametrize("bad,code", [
     ("ir,jr,kr", 2), ("ir,jr->ii", 2), ("iir,jr->ij", 2), ("ir,jr->ijk", 2), ("iR,jr->ij", 2),
 ])
