@@ -253,12 +253,14 @@ def _random_model(rng):
 def test_random_models_match_oracle(lib, seed):
     """Planner generality: random model strings (views, bond choices, grouped
     operand sources, merged index terms, contracted epilogues, the generic
-    fallback), one sweep in FP64 and FP32, with and without a mask."""
+    fallback), one sweep with the FP64, FP32 and BF16 plans (the host double
+    runs every view in FP32, so the BF16 plan's choices are checked, not its
+    rounding), with and without a mask."""
     rng = np.random.default_rng(1000 + seed)
     model_str, dims = _random_model(rng)
     m = OracleModel(model_str, dims)
     a, b = [(1.0, 0.0), (0.5, 0.5), (1.0, -0.5)][seed % 3]
-    for prec in (NEF_FP64, NEF_FP32):
+    for prec in (NEF_FP64, NEF_FP32, NEF_BF16):
         for masked in (False, True):
             dt = np.float64 if prec == NEF_FP64 else np.float32
             fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)).astype(dt) for l in range(m.n_factors)]
