@@ -282,6 +282,42 @@ def test_random_models_match_oracle(lib, seed):
                 lib.nef_plan_destroy(h)
 
 
+@pytest.mark.parametrize("prec", [NEF_FP64, NEF_FP32, NEF_BF16])
+def test_edge_cases_match_oracle(lib, prec):
+    """Degenerate inputs: size-1 modes, rank 1, Y with many exact zeros, a fully
+    masked slice (its factor row keeps its value: den = 0), and zero sweeps."""
+    cases = [("ir,jr,kr->ijk", dict(i=1, j=5, k=3, r=2)),
+             ("ir,jr,kr->ijk", dict(i=6, j=1, k=1, r=3)),
+             ("ir,jr->ij", dict(i=7, j=4, r=1)),
+             ("ia,ja,ab,kb,lb->ijkl", dict(i=1, j=3, k=2, l=1, a=2, b=1))]
+    dt = np.float64 if prec == NEF_FP64 else np.float32
+    tol = 1e-10 if prec == NEF_FP64 else 3e-5
+    for model_str, dims in cases:
+        m = OracleModel(model_str, dims)
+        rng = np.random.default_rng(7)
+        fs = [rng.uniform(0.3, 1.7, size=m.factor_shape(l)).astype(dt) for l in range(m.n_factors)]
+        y = rng.poisson(0.3, size=m.y_shape).astype(dt)          # mostly exact zeros
+        mask = np.ones(m.y_shape, np.uint8)
+        mask[0] = 0                                               # slice 0 of the first mode unobserved
+        rc, h = make_plan(lib, model_str, dims, prec)
+        assert rc == 0, lib.nef_last_error()
+        try:
+            work = [f.copy() for f in fs]
+            assert lib.nef_fit(h, y.ctypes.data, mask.ctypes.data, facs_arr(work), 1.0, 0.0, 0) == 0
+            for l in range(m.n_factors):
+                np.testing.assert_array_equal(work[l], fs[l])
+            ref = m.fit(y.astype(np.float64), mask, [f.astype(np.float64) for f in fs], 1.0, 0.0, 2)
+            assert lib.nef_fit(h, y.ctypes.data, mask.ctypes.data, facs_arr(work), 1.0, 0.0, 2) == 0
+            for l in range(m.n_factors):
+                rel = np.linalg.norm(work[l] - ref[l]) / np.linalg.norm(ref[l])
+                assert rel < tol, (model_str, l, rel)
+            # the first factor's rows for the unobserved slice keep their starting value
+            if model_str.startswith("ir,") or model_str.startswith("ia,"):
+                np.testing.assert_array_equal(work[0][0], fs[0][0])
+        finally:
+            lib.nef_plan_destroy(h)
+
+
 @pytest.mark.parametrize("bad,code", [
     ("ir,jr,kr", 2), ("ir,jr->ii", 2), ("iir,jr->ij", 2), ("ir,jr->ijk", 2), ("iR,jr->ij", 2),
 ])
