@@ -89,6 +89,18 @@ def _load():
             lib.or_ginv.restype = ctypes.c_double
             lib.or_ab_supported.argtypes = [ctypes.c_double, ctypes.c_double]
             lib.or_ab_supported.restype = ctypes.c_int
+            lib.or_lik_divergence.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4
+            lib.or_lik_divergence.restype = ctypes.c_double
+            lib.or_lik_weights.argtypes = [ctypes.c_int64, dp, u8p, dp, dp, ctypes.c_int,
+                                           ctypes.c_double, dp, dp]
+            lib.or_lik_loss.argtypes = [sp, dp, u8p, dp, dpp, ctypes.c_int, ctypes.c_double, i64p]
+            lib.or_lik_loss.restype = ctypes.c_double
+            lib.or_lik_update_factor.argtypes = [sp, ctypes.c_int, dp, u8p, dp, dpp, ctypes.c_int,
+                                                 ctypes.c_double, ctypes.c_double, dp, dp]
+            lib.or_lik_update_factor.restype = ctypes.c_int
+            lib.or_lik_fit.argtypes = [sp, dp, u8p, dp, dpp, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, dp]
+            lib.or_lik_fit.restype = ctypes.c_int
             lib.or_num_threads.restype = ctypes.c_int
             lib.or_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -125,6 +137,16 @@ def eta_of(alpha: float, beta: float) -> float:
     else:
         p = alpha
     return 1.0 / p
+
+
+# Likelihood losses of App. B outside the (alpha,beta) family (see nef_oracle.c).
+LIK_KINDS = {"negbin": 1, "binomial": 2, "js": 3}
+
+
+def lik_divergence(kind: str, x: float, y: float, par: float = 0.0, n: float = 1.0) -> float:
+    """D(x, y) of a likelihood loss of App. B: 'negbin' (dispersion par),
+    'binomial' on odds y with n trials (n = 1: Bernoulli), 'js' (Jensen-Shannon)."""
+    return float(_load().or_lik_divergence(LIK_KINDS[kind], float(x), float(y), float(par), float(n)))
 
 
 def _dptr(a: np.ndarray):
@@ -301,6 +323,56 @@ class OracleModel:
             raise ValueError("alpha == 0 with beta != 1 has no decomposition (App. B)")
         if rc:
             raise MemoryError("oracle allocation failed")
+        return (factors, tr) if trace else factors
+
+    def _ntr(self, ntrials):
+        if ntrials is None:
+            return None
+        ntrials = np.ascontiguousarray(ntrials, dtype=np.float64)
+        if ntrials.shape != self.y_shape:
+            raise ValueError("ntrials must have the shape of Y")
+        return ntrials
+
+    def lik_update_factor(self, l, y, mask, factors, kind, par=0.0, ntrials=None, eps=1e-10):
+        """One inner step of Algorithm 1 under a likelihood loss of App. B
+        ('negbin', 'binomial', 'js') on a copy of the factors; returns
+        (new_factors, num, den)."""
+        y, mask, factors = self._check(y, mask, factors)
+        nt = self._ntr(ntrials)
+        factors = [f.copy() for f in factors]
+        num = np.empty(self.factor_shape(l))
+        den = np.empty(self.factor_shape(l))
+        rc = _load().or_lik_update_factor(ctypes.byref(self._spec), int(l), _dptr(y), _u8ptr(mask),
+                                          _dptr(nt) if nt is not None else ctypes.POINTER(ctypes.c_double)(),
+                                          self._fac_ptrs(factors), LIK_KINDS[kind], float(par), float(eps),
+                                          _dptr(num), _dptr(den))
+        if rc:
+            raise ValueError("unknown loss kind" if rc == 1 else "oracle allocation failed")
+        return factors, num, den
+
+    def lik_loss(self, y, mask, factors, kind, par=0.0, ntrials=None):
+        """Sum over observed entries of D(y, yhat) for a likelihood loss; (sum, count)."""
+        y, mask, factors = self._check(y, mask, factors)
+        nt = self._ntr(ntrials)
+        cnt = ctypes.c_int64(0)
+        tot = _load().or_lik_loss(ctypes.byref(self._spec), _dptr(y), _u8ptr(mask),
+                                  _dptr(nt) if nt is not None else ctypes.POINTER(ctypes.c_double)(),
+                                  self._fac_ptrs(factors), LIK_KINDS[kind], float(par), ctypes.byref(cnt))
+        return float(tot), int(cnt.value)
+
+    def lik_fit(self, y, mask, factors, kind, iters, par=0.0, ntrials=None, eps=1e-10, trace=False):
+        """Algorithm 1 under a likelihood loss for `iters` sweeps on copies of the
+        factors; returns new factors (and the loss trace of iters+1 values if asked)."""
+        y, mask, factors = self._check(y, mask, factors)
+        nt = self._ntr(ntrials)
+        factors = [f.copy() for f in factors]
+        tr = np.empty(iters + 1) if trace else None
+        rc = _load().or_lik_fit(ctypes.byref(self._spec), _dptr(y), _u8ptr(mask),
+                                _dptr(nt) if nt is not None else ctypes.POINTER(ctypes.c_double)(),
+                                self._fac_ptrs(factors), LIK_KINDS[kind], float(par), float(eps), int(iters),
+                                _dptr(tr) if trace else ctypes.POINTER(ctypes.c_double)())
+        if rc:
+            raise ValueError("unknown loss kind" if rc == 1 else "oracle allocation failed")
         return (factors, tr) if trace else factors
 
     def numden_sampled(self, l, elems, y, mask, factors, alpha, beta):

@@ -14,13 +14,17 @@
  *   - D_{alpha,beta}(x,y) five-case definition                          (App. B)
  *   - Algorithm 1: Gauss-Seidel over factors in string order, Yhat
  *     recomputed before every factor update                             (Algorithm 1)
+ *   - the likelihood losses of App. B outside the (alpha,beta) family:
+ *     negative binomial, binomial / Bernoulli on odds, Jensen-Shannon,
+ *     with their a, b and g                                             (App. B)
  *
  * Readings where the paper is silent (each listed in the design notes):
  *   - the mask multiplies the weights: W_a = M*a, W_b = M*b (Sec. 6, masked
  *     training loss); a literal M*Y, M*Yhat substitution would leave b(0,0)=1
  *     for KL and count missing entries in the denominator;
  *   - den == 0 leaves theta unchanged (no information about that entry);
- *   - 0 * log 0 = 0 and 0^p = 0 for p > 0 in D and in a(x,y).
+ *   - 0 * log 0 = 0 and 0^p = 0 for p > 0 in D and in a(x,y);
+ *   - the negative binomial dispersion phi is one value for all entries.
  *
  * Layout: Y and the mask are row-major over the observed letters in RHS order;
  * each factor is row-major over its own letters in term order.
@@ -405,6 +409,115 @@ int or_numden_sampled(const or_spec* s, int l, int64_t n_samp, const int64_t* el
         }
         num[q] = sn;
         den[q] = sd;
+    }
+    return 0;
+}
+
+/* ---------------------------------------- likelihood losses of App. B
+ * Losses outside the (alpha,beta) family that have the same convex-concave
+ * structure, each with its a(x,y), b(x,y) and g (App. B):
+ *   kind 1, negative binomial with dispersion par = phi (one value for all
+ *     entries): D = (phi + x) log(phi + y) - x log y,
+ *     a = x / y, b = (phi + x) / (phi + y), g(lambda) = lambda;
+ *   kind 2, binomial on the odds y = p / (1 - p) with n trials per entry
+ *     (ntr, or 1 everywhere = Bernoulli when ntr is NULL):
+ *     D = n log(1 + y) - x log y, a = x / y, b = n / (1 + y), g(lambda) = lambda;
+ *   kind 3, Jensen-Shannon: D = (x log x + y log y) / 2 - (x + y)/2 log((x + y)/2),
+ *     a = log((x + y) / (2 y)), b = 1, g(lambda) = log(lambda), so the update
+ *     multiplies by exp(num / den).
+ * The constant terms of the likelihoods are dropped (0 log 0 = 0). */
+
+static double xlogy(double x, double y) { return x == 0.0 ? 0.0 : x * log(y); }
+
+double or_lik_divergence(int kind, double x, double y, double par, double n) {
+    switch (kind) {
+        case 1: return xlogy(par + x, par + y) - xlogy(x, y);
+        case 2: return n * log1p(y) - xlogy(x, y);
+        case 3: {
+            const double m = 0.5 * (x + y);
+            return 0.5 * (xlogy(x, x) + xlogy(y, y)) - xlogy(m, m);
+        }
+        default: return NAN;
+    }
+}
+
+static void lik_ab(int kind, double x, double y, double par, double n, double* a, double* b) {
+    switch (kind) {
+        case 1: *a = x / y; *b = (par + x) / (par + y); break;
+        case 2: *a = x / y; *b = n / (1.0 + y); break;
+        case 3: *a = log((x + y) / (2.0 * y)); *b = 1.0; break;
+        default: *a = NAN; *b = NAN; break;
+    }
+}
+
+static double lik_ginv(int kind, double z) { return kind == 3 ? exp(z) : z; }
+
+void or_lik_weights(int64_t n, const double* y, const uint8_t* mask, const double* ntr,
+                    const double* yhat, int kind, double par, double* wa, double* wb) {
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n; ++e) {
+        if (mask && !mask[e]) { wa[e] = 0.0; wb[e] = 0.0; continue; }
+        lik_ab(kind, y[e], yhat[e], par, ntr ? ntr[e] : 1.0, &wa[e], &wb[e]);
+    }
+}
+
+double or_lik_loss(const or_spec* s, const double* y, const uint8_t* mask, const double* ntr,
+                   const double* const* fac, int kind, double par, int64_t* cnt) {
+    int64_t n = y_size(s);
+    double* yhat = (double*)malloc(sizeof(double) * n);
+    or_reconstruct(s, fac, yhat);
+    double tot = 0.0;
+    int64_t c = 0;
+    for (int64_t e = 0; e < n; ++e) {
+        if (mask && !mask[e]) continue;
+        tot += or_lik_divergence(kind, y[e], yhat[e], par, ntr ? ntr[e] : 1.0);
+        ++c;
+    }
+    free(yhat);
+    if (cnt) *cnt = c;
+    return tot;
+}
+
+/* One factor update under a likelihood loss: the same three steps as
+ * or_update_factor with the weights and g of the chosen kind. */
+int or_lik_update_factor(const or_spec* s, int l, const double* y, const uint8_t* mask,
+                         const double* ntr, double* const* fac, int kind, double par, double eps,
+                         double* num_out, double* den_out) {
+    if (kind < 1 || kind > 3) return 1;
+    int64_t n = y_size(s);
+    int64_t nl = fac_size(s, l);
+    double* yhat = (double*)malloc(sizeof(double) * n);
+    double* wa = (double*)malloc(sizeof(double) * n);
+    double* wb = (double*)malloc(sizeof(double) * n);
+    double* num = num_out ? num_out : (double*)malloc(sizeof(double) * nl);
+    double* den = den_out ? den_out : (double*)malloc(sizeof(double) * nl);
+    if (!yhat || !wa || !wb || !num || !den) return 2;
+    or_reconstruct(s, (const double* const*)fac, yhat);
+    or_lik_weights(n, y, mask, ntr, yhat, kind, par, wa, wb);
+    or_einstr(s, l, wa, (const double* const*)fac, num);
+    or_einstr(s, l, wb, (const double* const*)fac, den);
+    for (int64_t e = 0; e < nl; ++e) {
+        if (den[e] == 0.0) continue;
+        const double v = fac[l][e] * lik_ginv(kind, num[e] / den[e]);
+        fac[l][e] = v > eps ? v : eps;
+    }
+    free(yhat); free(wa); free(wb);
+    if (!num_out) free(num);
+    if (!den_out) free(den);
+    return 0;
+}
+
+/* Algorithm 1 under a likelihood loss; trace as in or_fit. */
+int or_lik_fit(const or_spec* s, const double* y, const uint8_t* mask, const double* ntr,
+               double* const* fac, int kind, double par, double eps, int iters, double* trace) {
+    if (kind < 1 || kind > 3) return 1;
+    if (trace) trace[0] = or_lik_loss(s, y, mask, ntr, (const double* const*)fac, kind, par, NULL);
+    for (int it = 0; it < iters; ++it) {
+        for (int l = 0; l < s->n_fac; ++l) {
+            int rc = or_lik_update_factor(s, l, y, mask, ntr, fac, kind, par, eps, NULL, NULL);
+            if (rc) return rc;
+        }
+        if (trace) trace[it + 1] = or_lik_loss(s, y, mask, ntr, (const double* const*)fac, kind, par, NULL);
     }
     return 0;
 }

@@ -2,9 +2,9 @@
 
 Each case copies oracle/nef_oracle.c, plants one plausible slip in the copy (a
 dropped operand, a wrong exponent, a transposed layout, a mask left out, a
-wrong branch of the g-table), builds it on the CPU, and runs the pin suite
-(test_oracle_pins.py) against that build in a child process: some pin must
-fail.  The same is done for the encoder oracle (oracle/mlp.py against
+wrong branch of the g-table), builds it on the CPU, and runs the pin suites
+(test_oracle_pins.py, test_oracle_lik_pins.py) against that build in a child
+process: some pin must fail.  The same is done for the encoder oracle (oracle/mlp.py against
 test_mlp_oracle.py).  The committed oracle itself is never modified.
 """
 import os
@@ -42,11 +42,26 @@ MUTANTS = [
      "for (int m = s->n_obs - 1; m >= 0; --m) { st[m] = acc; acc *= s->dim[m]; }",
      "for (int m = 0; m < s->n_obs; ++m) { st[m] = acc; acc *= s->dim[m]; }"),
     ("weights ignore the mask",
-     "if (mask && !mask[e]) { wa[e] = 0.0; wb[e] = 0.0; continue; }",
-     "if (0) { wa[e] = 0.0; wb[e] = 0.0; continue; }"),
+     "if (mask && !mask[e]) { wa[e] = 0.0; wb[e] = 0.0; continue; }\n        ab_weights(",
+     "if (0) { wa[e] = 0.0; wb[e] = 0.0; continue; }\n        ab_weights("),
+    ("likelihood weights ignore the mask",
+     "if (mask && !mask[e]) { wa[e] = 0.0; wb[e] = 0.0; continue; }\n        lik_ab(",
+     "if (0) { wa[e] = 0.0; wb[e] = 0.0; continue; }\n        lik_ab("),
     ("update ignores the epsilon floor",
      "theta[e] = v > eps ? v : eps;",
      "theta[e] = v;"),
+    ("negative binomial b(x, y) inverted",
+     "*b = (par + x) / (par + y); break;",
+     "*b = (par + y) / (par + x); break;"),
+    ("binomial b(x, y) without the trial count",
+     "*b = n / (1.0 + y); break;",
+     "*b = 1.0 / (1.0 + y); break;"),
+    ("Jensen-Shannon a(x, y) without the midpoint's 1/2",
+     "*a = log((x + y) / (2.0 * y)); *b = 1.0; break;",
+     "*a = log((x + y) / y); *b = 1.0; break;"),
+    ("Jensen-Shannon update takes g as the identity",
+     "static double lik_ginv(int kind, double z) { return kind == 3 ? exp(z) : z; }",
+     "static double lik_ginv(int kind, double z) { return z; }"),
 ]
 
 CHILD = """
@@ -55,7 +70,8 @@ import oracle.core as core
 core._SRC = sys.argv[1]
 core._LIB_PATH = sys.argv[2]
 import pytest
-sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "tests/test_oracle_pins.py"]))
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "tests/test_oracle_pins.py",
+                      "tests/test_oracle_lik_pins.py"]))
 """
 
 
