@@ -46,3 +46,16 @@ def test_defaults_and_errors_without_gpu(lib):
     assert b"->" in L.nef_last_error()
     assert L.nef_plan(b"ir,jr,kr->ijk", shapes, 2, ranks, 1, None, ctypes.byref(h)) == 1
     assert L.nef_fit(None, None, None, None, 1.0, 0.0, 1) == 1
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c11"), ("c++", "-std=c++17")])
+def test_headers_are_plain_c(lang, std, tmp_path):
+    """The public headers compile on their own as C11 (pedantic) and as C++:
+    plain types and pointers only, no CUDA, C++ or torch types."""
+    import subprocess
+    src = tmp_path / ("h.c" if lang == "c" else "h.cpp")
+    src.write_text('#include "nef.h"\n#include "nef_debug.h"\nint main(void) { return 0; }\n')
+    cc = "gcc" if lang == "c" else "g++"
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
