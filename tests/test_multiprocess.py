@@ -68,3 +68,43 @@ def test_reference_arm_rank0_only():
     line = json.loads(r0.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def _fake_sampler(lines, window):
+    import bench
+    s = bench.ClockSampler(0)
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    class _Thread:
+        def join(self, timeout=None):
+            pass
+
+    s.proc, s.t, s.lines = _Proc(), _Thread(), lines
+    s.mark(*window)
+    return s
+
+
+CLOCK_LINES = [
+    (0.5, "0, 1500, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"),
+    (1.0, "0, 2070, 2070, 1000.0, 0x4, Not Active, Not Active, Not Active, Active"),
+    (1.5, "0, 2060, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active"),
+    (3.0, "0, 900, 2070, 300.0, 0x8, Active, Not Active, Not Active, Not Active"),
+]
+
+
+def test_clock_summary_uses_only_the_timed_window():
+    """The clocks line reports the median SM clock and the throttle reasons seen
+    inside the timed region only (samples before and after it are dropped)."""
+    out = _fake_sampler(CLOCK_LINES, (0.9, 2.0)).stop()
+    assert out == {"sm_mhz": 2065.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+
+
+def test_clock_summary_short_region_takes_next_sample():
+    out = _fake_sampler(CLOCK_LINES, (1.01, 1.02)).stop()
+    assert out["samples"] == 1 and out["sm_mhz"] == 2060.0 and out["reasons"] == []
