@@ -60,6 +60,32 @@ enum {
     NEF_FP64 = 2   /* CUDA-core FP64 fused sweep                                      */
 };
 
+/*
+ * Loss families (nef_options.loss).  Each has the convex-concave structure of
+ * Thm. 3.1, so Algorithm 1 applies with its own a(x, y), b(x, y) and g (App. B):
+ *   NEF_LOSS_AB        (alpha,beta)-divergence D_{alpha,beta} (App. B, five cases);
+ *                      the alpha, beta arguments of every call select it.
+ *   NEF_LOSS_NEGBIN    negative binomial with dispersion phi = loss_par > 0 (one
+ *                      value for every entry): D = (phi + x) log(phi + y) - x log y,
+ *                      a = x / y, b = (phi + x) / (phi + y), g(l) = l (App. B,
+ *                      negative binomial).
+ *   NEF_LOSS_BINOMIAL  binomial on the odds y = p / (1 - p) with n = loss_par > 0
+ *                      trials per entry (n = 1: Bernoulli): D = n log(1 + y) - x log y,
+ *                      a = x / y, b = n / (1 + y), g(l) = l (App. B, Bernoulli and
+ *                      binomial).  Per-entry trial counts are not supported.
+ *   NEF_LOSS_JS        Jensen-Shannon: D = (x log x + y log y)/2 - m log m with
+ *                      m = (x + y)/2, a = log((x + y) / (2 y)), b = 1, g = log, so the
+ *                      update multiplies by exp(num / den) (App. B, Jensen-Shannon).
+ * The constant terms of the log-likelihoods are dropped from D (0 log 0 = 0).
+ * For the three likelihood families the alpha and beta arguments are ignored.
+ */
+enum {
+    NEF_LOSS_AB = 0,
+    NEF_LOSS_NEGBIN = 1,
+    NEF_LOSS_BINOMIAL = 2,
+    NEF_LOSS_JS = 3
+};
+
 typedef struct {
     int precision;      /* NEF_FP32, NEF_BF16 or NEF_FP64                                   */
     double eps;         /* floor of Eq. 3.1 (paper: "a very small eps > 0"); default 1e-10  */
@@ -77,10 +103,18 @@ typedef struct {
                         /* entries past an early stop are left untouched                    */
     int eager;          /* nonzero: launch every kernel of every sweep directly; zero: from */
                         /* the third sweep on, replay a captured CUDA graph of one sweep    */
+    int loss;           /* NEF_LOSS_AB (default), NEF_LOSS_NEGBIN, NEF_LOSS_BINOMIAL or     */
+                        /* NEF_LOSS_JS: the loss every call on the plan fits and reports    */
+    double loss_par;    /* phi for NEF_LOSS_NEGBIN, trials n for NEF_LOSS_BINOMIAL          */
+    int64_t wait_cycles;/* limit, in SM clock cycles, of every bounded wait inside the      */
+                        /* tensor-core pass; 0 = the default 4e9 (about 2 s).  A wait that  */
+                        /* runs out stops its kernel cleanly and nef_check then reports     */
+                        /* NEF_ETIMEOUT (the results of that call are invalid)              */
 } nef_options;
 
 /* Fill *opt with the defaults: NEF_FP32, eps = 1e-10, no data check, fused, no
- * profiling, stream NULL, tol 0, no loss trace, graph replay. */
+ * profiling, stream NULL, tol 0, no loss trace, graph replay, NEF_LOSS_AB,
+ * loss_par 0, default wait limit. */
 void nef_default_options(nef_options* opt);
 
 /*
@@ -92,8 +126,10 @@ void nef_default_options(nef_options* opt);
  *   opt       : options (host; NULL = defaults); copied into the plan
  *   out       : receives the plan handle (host)
  * Errors: NEF_EPARSE for a malformed string or a repeated letter within a
- * term or on the right; NEF_EINVAL for a count mismatch or a dimension < 1;
- * NEF_ENOMEM / NEF_ECUDA from workspace allocation.  On error *out is NULL.
+ * term or on the right; NEF_EINVAL for a count mismatch, a dimension < 1, an
+ * unknown precision or loss, eps < 0, a loss_par outside its range (phi > 0,
+ * n > 0, both finite) or wait_cycles < 0; NEF_ENOMEM / NEF_ECUDA from workspace
+ * allocation.  On error *out is NULL.
  */
 nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs,
                     const int64_t* ranks, int n_lat, const nef_options* opt,
@@ -116,9 +152,10 @@ void nef_plan_destroy(nef_plan_t plan);
  * it; one extra loss pass follows the last sweep.  With tol > 0 the stream is
  * synchronised once per sweep to read the loss; nef_plan_sweeps reports how
  * many sweeps ran.
- * Errors: NEF_EUNSUPPORTED for alpha == 0 with beta != 1; NEF_EINVAL for a
- * null pointer or iters < 0; NEF_EDATA if check_data found a bad Y entry
- * (factors untouched); NEF_ECUDA for a failed launch.
+ * Errors: NEF_EUNSUPPORTED for alpha == 0 with beta != 1 (NEF_LOSS_AB plans);
+ * NEF_EINVAL for a null pointer, iters < 0 or a non-finite alpha or beta;
+ * NEF_EDATA if check_data found a bad Y entry (factors untouched); NEF_ECUDA
+ * for a failed launch.
  */
 nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask,
                    void* const* factors, double alpha, double beta, int iters);
@@ -163,6 +200,9 @@ nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask
  * with the five-case definition of App. B), with FP64 accumulation.
  *   out : host, 2 doubles: out[0] = the sum, out[1] = the number of observed
  *         entries (so out[0]/out[1] is the mean of Sec. 6.5's metric).
+ * The loss is the plan's family (nef_options.loss).  NEF_BF16 plans reconstruct
+ * Yhat on the tensor cores (BF16 operands, FP32 accumulation), as the loss
+ * trace of nef_fit does; the other precisions on the CUDA cores in FP32/FP64.
  * Synchronises the plan's stream.  Errors as nef_fit.
  */
 nef_status nef_loss(nef_plan_t plan, const void* Y, const uint8_t* mask,
@@ -192,6 +232,27 @@ int nef_plan_launches(nef_plan_t plan, int has_mask);
  * profiling; NEF_ECUDA from the event queries.
  */
 nef_status nef_plan_profile(nef_plan_t plan, double* ms, int* count, int reset);
+
+/*
+ * nef_tc_trace -- (profiling) wait-cycle counters of the tensor-core fused pass, summed over
+ * every CTA of every launch on `plan` since the last reset (plans created with
+ * nef_options.profile = 2, in a library built with -DNEF_TC_TRACE=1; other builds
+ * compile the counters out and leave them zero.  The counters add shared-memory
+ * atomics to every tile, so timings taken with them are not representative).  out (host) receives 32 values: out[0] = summed
+ * CTA lifetimes in SM cycles; out[k], k = 1..12 = cycles spent in bounded waits
+ * at site k: 1 producer waits for a free Y stage, 3 MMA waits for the P tile,
+ * 4 MMA waits for a Q tile, 5 MMA waits for a free yhat buffer, 6 MMA waits for
+ * a W tile, 8 operand warps wait for a free Q stage, 9 epilogue waits for yhat,
+ * 10 epilogue waits for Y, 11 epilogue waits for a free W buffer, 12 epilogue
+ * waits for the final S, 13 operand warps wait for staged source rows, 14
+ * producer waits for a free row stage; busy
+ * phases: 16 operand look-ahead, 17 operand build, 18 operand fence and
+ * arrival, 20 epilogue TMEM load, 21 epilogue Y read, 22 epilogue weights,
+ * 23 epilogue W store, 24 epilogue fence and arrival (waits and phases of the
+ * operand and epilogue warps are counted once per warp).  reset != 0 clears the counters afterwards.  Returns 0, 1 for
+ * a plan without counters, 5 for a CUDA error.  Synchronises the plan's stream.
+ */
+int nef_tc_trace(nef_plan_t plan, unsigned long long* out, int reset);
 
 /*
  * nef_check -- synchronise the plan's stream and report device-side errors
@@ -252,10 +313,17 @@ nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_t* ranks, c
  * factor must satisfy rows x R <= 1,048,576 (rows = I, J or K); larger sizes
  * return NEF_EINVAL.  Every call shares that array: calls that can overlap on
  * the GPU (other streams or host threads) race and must be serialised by the
- * caller.  The first call on each device looks up the array's device address,
- * so make it before any stream capture.  Returns once the work is enqueued.
- * Errors: NEF_EINVAL (null pointer, bad rank, factor index or size),
- * NEF_EUNSUPPORTED (alpha == 0 with beta != 1), NEF_ECUDA (launch failure).
+ * caller.  The first call on each device looks up the array's device address
+ * (and keeps it for later calls), so make it before any stream capture.  A
+ * cudaDeviceReset discards the array's device memory: the kept address is then
+ * stale, so do not call this entry point on a device after resetting it in the
+ * same process.  The launch grid is sized from the device's SM count.  Returns
+ * once the work is enqueued.
+ * Errors: NEF_EINVAL (null pointer, bad rank, factor index or size, alpha or
+ * beta not finite, eps negative or not finite), NEF_EUNSUPPORTED (alpha == 0
+ * with beta != 1), NEF_ECUDA (launch failure).  The C entry point cannot see
+ * the factors' sizes: the caller guarantees factor m has shape[m] x rank
+ * floats (the Python binding checks this before the call).
  */
 nef_status nef_cp3_update_static(const float* Y, const int64_t* shape, int rank,
                                  float* const* factors, int l, double alpha, double beta,

@@ -10,7 +10,6 @@ The work runs in libnef.so (C ABI in include/nef.h); this package only marshals
 arguments.
 """
 from ._nef import (  # noqa: F401
-    DEBUG_EXPORTS,
     EXPORTS,
     LIB_PATH,
     FoldIn,

@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libnef.so")
 
 NEF_FP32, NEF_BF16, NEF_FP64 = 0, 1, 2
+NEF_LOSS_AB, NEF_LOSS_NEGBIN, NEF_LOSS_BINOMIAL, NEF_LOSS_JS = 0, 1, 2, 3
+LOSSES = {"ab": NEF_LOSS_AB, "negbin": NEF_LOSS_NEGBIN, "binomial": NEF_LOSS_BINOMIAL, "js": NEF_LOSS_JS}
 STATUS = {0: "NEF_OK", 1: "NEF_EINVAL", 2: "NEF_EPARSE", 3: "NEF_EUNSUPPORTED", 4: "NEF_ENOMEM",
           5: "NEF_ECUDA", 6: "NEF_EDATA", 7: "NEF_ETIMEOUT"}
 PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
@@ -21,18 +23,18 @@ PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 # every symbol include/nef.h declares
 EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex",
            "nef_plan_sweeps", "nef_plan_autotune", "nef_update", "nef_loss", "nef_plan_info", "nef_plan_launches",
-           "nef_plan_profile", "nef_check", "nef_fit_batched", "nef_cp3_update_static", "nef_last_error",
+           "nef_plan_profile", "nef_tc_trace", "nef_check", "nef_fit_batched", "nef_cp3_update_static",
+           "nef_last_error",
            "nef_foldin_num_params", "nef_foldin_create", "nef_foldin_destroy", "nef_foldin_grad",
            "nef_foldin_train_step", "nef_foldin_predict", "nef_foldin_params"]
-# every symbol include/nef_debug.h declares
-DEBUG_EXPORTS = ["nef_tc_probe", "nef_tc_trace", "nef_tc_gemm"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double),
                 ("check_data", ctypes.c_int), ("force_generic", ctypes.c_int),
                 ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("eager", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("eager", ctypes.c_int),
+                ("loss", ctypes.c_int), ("loss_par", ctypes.c_double), ("wait_cycles", ctypes.c_int64)]
 
 
 class NefError(RuntimeError):
@@ -107,11 +109,6 @@ def load(path: str = LIB_PATH):
     lib.nef_foldin_params.restype = ci
     lib.nef_tc_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
     lib.nef_tc_trace.restype = ctypes.c_int
-    lib.nef_tc_probe.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
-    lib.nef_tc_probe.restype = ctypes.c_int
-    lib.nef_tc_gemm.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
-                                ctypes.c_int, vp, vp]
-    lib.nef_tc_gemm.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -165,15 +162,33 @@ def fit_batched(Ys, masks, factors, alpha, beta, iters, eps=1e-10, stream=None, 
 
 def cp3_update_static(Y, factors, l, alpha, beta, eps=1e-10, stream=None):
     """nef_cp3_update_static: update factor l of 'ir,jr,kr->ijk' in place without any
-    device allocation (see include/nef.h).  Y, factors: contiguous CUDA float32."""
+    device allocation (see include/nef.h).  Y: contiguous CUDA float32 [I, J, K];
+    factors: three contiguous CUDA float32 tensors [I, R], [J, R], [K, R] with one R.
+    The C entry point cannot see the factors' sizes, so they are checked here and a
+    mismatch raises NefError(NEF_EINVAL) before anything is launched."""
     import torch
+    lib = load()
+
+    def bad(msg):
+        raise NefError(1, msg)
+
+    if not isinstance(Y, torch.Tensor) or Y.dim() != 3 or Y.dtype != torch.float32 or not Y.is_cuda \
+            or not Y.is_contiguous():
+        bad("Y must be a contiguous 3-d CUDA float32 tensor")
+    if len(factors) != 3:
+        bad("three factors are needed")
+    rank = int(factors[0].shape[1]) if factors[0].dim() == 2 else -1
+    for m, f in enumerate(factors):
+        if not isinstance(f, torch.Tensor) or f.dtype != torch.float32 or not f.is_cuda or not f.is_contiguous() \
+                or f.dim() != 2 or tuple(f.shape) != (int(Y.shape[m]), rank) or f.device != Y.device:
+            bad(f"factor {m} must be a contiguous CUDA float32 tensor of shape ({int(Y.shape[m])}, R) "
+                f"on Y's device, R the same for all three")
     if stream is None:
         stream = torch.cuda.current_stream()
     shape = (ctypes.c_int64 * 3)(*[int(s) for s in Y.shape])
     arr = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in factors])
-    check(load().nef_cp3_update_static(ctypes.c_void_p(Y.data_ptr()), shape, int(factors[0].shape[1]),
-                                       arr, int(l), float(alpha), float(beta), float(eps),
-                                       ctypes.c_void_p(stream.cuda_stream)))
+    check(lib.nef_cp3_update_static(ctypes.c_void_p(Y.data_ptr()), shape, rank, arr, int(l), float(alpha),
+                                    float(beta), float(eps), ctypes.c_void_p(stream.cuda_stream)))
 
 
 class Plan:
@@ -181,12 +196,16 @@ class Plan:
 
     ``dims`` maps letters to sizes (observed dims and latent ranks).  ``stream``
     is a torch.cuda.Stream (or a raw cudaStream_t integer); None uses torch's
-    current stream at plan time.
+    current stream at plan time.  ``loss`` selects the loss family (App. B):
+    "ab" (the (alpha,beta)-divergence given to each call), "negbin" (dispersion
+    ``loss_par``), "binomial" (``loss_par`` trials; 1 = Bernoulli) or "js".
+    ``wait_cycles`` bounds every wait inside the tensor-core pass (0 = default).
     """
 
     def __init__(self, model_str: str, dims: dict, precision: str = "fp32", eps: float = 1e-10,
                  check_data: bool = False, force_generic: bool = False, profile: int = 0,
-                 stream=None, eager: bool = False):
+                 stream=None, eager: bool = False, loss: str = "ab", loss_par: float = 0.0,
+                 wait_cycles: int = 0):
         lib = load()
         obs, lat, terms = split_model(model_str)
         self.model_str = model_str
@@ -203,6 +222,10 @@ class Plan:
         opt.force_generic = int(bool(force_generic))
         opt.profile = int(profile)
         opt.eager = int(bool(eager))
+        opt.loss = LOSSES[loss]
+        opt.loss_par = float(loss_par)
+        opt.wait_cycles = int(wait_cycles)
+        self.loss_kind = loss
         if stream is None:
             import torch
             stream = torch.cuda.current_stream()
@@ -308,7 +331,7 @@ class Plan:
         return {"tcgen05": (ms[0], cnt[0]), "simt": (ms[1], cnt[1])}
 
     def tc_trace(self, reset: bool = True):
-        """Wait-cycle counters of the tensor-core pass (see include/nef_debug.h)."""
+        """Wait-cycle counters of the tensor-core pass (nef_tc_trace in include/nef.h)."""
         out = (ctypes.c_ulonglong * 32)()
         rc = load().nef_tc_trace(self._h, out, int(bool(reset)))
         if rc:

@@ -14,7 +14,6 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "../../include/nef_debug.h"
 #include "k_view_tc.cuh"
 #include "nef_internal.h"
 
@@ -190,10 +189,3 @@ cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, in
 }
 
 }  // namespace nef
-
-extern "C" int nef_tc_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int M,
-                           int N, int K, int* err, void* stream) {
-    const cudaError_t e =
-        nef::launch_gemm_nt(A, lda, B, ldb, C, ldc, M, N, K, 0, err, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? 0 : 5;
-}

@@ -14,6 +14,7 @@
 // serialised by the caller.  Each call overwrites every element it later reads,
 // so no clearing is needed between calls.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "../../include/nef.h"
@@ -65,9 +66,12 @@ extern "C" nef_status nef_cp3_update_static(const float* Y, const int64_t* shape
         return static_fail(NEF_EINVAL, "NULL argument");
     if (l < 0 || l > 2) return static_fail(NEF_EINVAL, "factor index must be 0, 1 or 2");
     if (rank != 16 && rank != 32 && rank != 64) return static_fail(NEF_EINVAL, "rank must be 16, 32 or 64");
-    if (!(eps >= 0.0)) return static_fail(NEF_EINVAL, "eps must be >= 0");
-    if (alpha == 0.0 && beta != 1.0)
-        return static_fail(NEF_EUNSUPPORTED, "alpha == 0 with beta != 1 has no decomposition");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return static_fail(NEF_EINVAL, "eps must be finite and >= 0");
+    {
+        bool unsupported = false;
+        const char* msg = loss_args_error(LIK_NONE, alpha, beta, 0.0, &unsupported);
+        if (msg) return static_fail(unsupported ? NEF_EUNSUPPORTED : NEF_EINVAL, msg);
+    }
     const int64_t I = shape[0], J = shape[1], K = shape[2];
     if (I < 1 || J < 1 || K < 1) return static_fail(NEF_EINVAL, "dimensions must be >= 1");
     const int64_t dims[3] = {I, J, K};
@@ -110,10 +114,15 @@ extern "C" nef_status nef_cp3_update_static(const float* Y, const int64_t* shape
     float* scratch = nullptr;
     cudaError_t e = scratch_on_current_device(&scratch);
     if (e != cudaSuccess) return static_fail(NEF_ECUDA, cudaGetErrorString(e));
+    // four CTAs of the CUDA-core pass per SM of the current device
+    int dev = 0, n_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return static_fail(NEF_ECUDA, cudaGetErrorString(e));
     const int64_t ncols = v.c_out * v.c_in;
     const int64_t n_rb = (rows + 63) / 64;
     const int64_t tiles = (ncols + 63) / 64;
-    int64_t n_split = std::max<int64_t>(1, (int64_t)608 / n_rb);
+    int64_t n_split = std::max<int64_t>(1, (int64_t)4 * std::max(1, n_sm) / n_rb);
     n_split = std::min<int64_t>(n_split, tiles);
     n_split = std::min<int64_t>(n_split, (kStaticScratchFloats / n_el - 2) / 2);
     n_split = std::max<int64_t>(n_split, 1);

@@ -36,6 +36,18 @@ cudaError_t launch_bp32_g_loss(const CUtensorMap&, const CUtensorMap&, const CUt
                         cudaStream_t);
 cudaError_t launch_bp64_g_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
                         cudaStream_t);
+cudaError_t launch_bp16_lik(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp32_lik(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp64_lik(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                        cudaStream_t);
+cudaError_t launch_bp16_lik_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int,
+                                 int, cudaStream_t);
+cudaError_t launch_bp32_lik_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int,
+                                 int, cudaStream_t);
+cudaError_t launch_bp64_lik_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int,
+                                 int, cudaStream_t);
 cudaError_t launch_batched_bp16(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 cudaError_t launch_batched_bp32(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 }  // namespace tc
@@ -58,6 +70,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int weight_kind(const WeightSpec& w) {
+    switch (w.lik) {
+        case LIK_NEGBIN: return tc::WK_NB;
+        case LIK_BINOMIAL: return tc::WK_BIN;
+        case LIK_JS: return tc::WK_JS;
+        default: break;
+    }
     if (w.log_case) return tc::WK_GEN;
     if (w.y_code == POW_ID && w.a_code == POW_RCP && w.b_code == POW_ONE) return tc::WK_KL;
     if (w.y_code == POW_ID && w.a_code == POW_RSQRT3 && w.b_code == POW_RSQRT) return tc::WK_B05;
@@ -154,6 +172,7 @@ cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v
     p->trace = trace;
     p->loss_part = nullptr;
     p->L = LossSpec{};
+    p->wait_cycles = tc::kWaitCycles;
     *n_rb_out = (int)((v.rows + tc::TM - 1) / tc::TM);
     return cudaSuccess;
 }
@@ -163,7 +182,7 @@ cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v
 cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w,
                            int need_den, int n_split, float* s_num, float* s_den, int* err_flag,
                            cudaStream_t st, TcLaunchInfo* info, unsigned long long* trace, const LossSpec* loss,
-                           double* loss_part) {
+                           double* loss_part, long long wait_cycles) {
     if (!tc_view_supported(v, need_den)) return cudaErrorNotSupported;
     if (mbits && !need_den) return cudaErrorInvalidValue;  // mask code lives in the DEN instances only
     CUtensorMap map, vmap, cmap;
@@ -176,6 +195,7 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         p.loss_part = loss_part;
         p.L = *loss;
     }
+    if (wait_cycles > 0) p.wait_cycles = wait_cycles;
     const int grid = n_rb * n_split;
     if (info) {
         info->n_ctas = grid;
@@ -189,8 +209,16 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         {{tc::launch_bp16_g, tc::launch_bp32_g, tc::launch_bp64_g}, {tc::launch_bp16, tc::launch_bp32, tc::launch_bp64}},
         {{tc::launch_bp16_g_loss, tc::launch_bp32_g_loss, tc::launch_bp64_g_loss},
          {tc::launch_bp16_loss, tc::launch_bp32_loss, tc::launch_bp64_loss}}};
+    // the likelihood families have their own instances for staged Q rows; with
+    // gathered rows they run through the generic weight kind
+    static const LaunchFn lik_table[2][3] = {
+        {tc::launch_bp16_lik, tc::launch_bp32_lik, tc::launch_bp64_lik},
+        {tc::launch_bp16_lik_loss, tc::launch_bp32_lik_loss, tc::launch_bp64_lik_loss}};
     const int bi = v.bond_pad == 16 ? 0 : (v.bond_pad == 32 ? 1 : 2);
-    return table[p.loss_part ? 1 : 0][p.qmode ? 1 : 0][bi](map, vmap, cmap, p, need_den, wk, grid, st);
+    if (wk >= tc::WK_NB && p.qmode)
+        return lik_table[p.loss_part ? 1 : 0][bi](map, vmap, cmap, p, need_den, wk, grid, st);
+    return table[p.loss_part ? 1 : 0][p.qmode ? 1 : 0][bi](map, vmap, cmap, p, need_den, wk >= tc::WK_NB ? tc::WK_GEN : wk,
+                                                          grid, st);
 }
 
 static_assert(sizeof(tc::Params) <= sizeof(TcUnit::prm), "TcUnit parameter area too small");

@@ -70,9 +70,18 @@ constexpr int kEpiWarps = kEpiGroups * kGroupWarps;
 constexpr int kEpiWarp0 = 2 + kOpWarps;  // first epilogue warp
 constexpr int kYStageBytes = TM * TN * 4;   // 32 KB
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+// Default limit of the bounded waits (~2 s at 2 GHz).  The pipeline waits use the
+// launch's limit (Params::wait_cycles); the drains at the end of a CTA, which wait
+// for the CTA's own copies and products already in flight, always use this one,
+// so that no copy into shared memory or product into tensor memory is still
+// running when the CTA frees them, whatever the launch's limit.
+constexpr long long kWaitCycles = 4000000000LL;
 
-enum WeightKind { WK_GEN = 0, WK_KL = 1, WK_B05 = 2, WK_HEL = 3 };
+// Weight kinds with their own instances: the App. B (alpha,beta) cases KL (1,0),
+// (1,-1/2) and (1/2,1/2), the likelihood families negative binomial, binomial on
+// the odds and Jensen-Shannon, and the generic evaluation (any (alpha,beta) or
+// family, selected at run time).
+enum WeightKind { WK_GEN = 0, WK_KL = 1, WK_B05 = 2, WK_HEL = 3, WK_NB = 4, WK_BIN = 5, WK_JS = 6 };
 
 struct Params {
     const uint32_t* mbits;
@@ -95,6 +104,7 @@ struct Params {
     // loss_part[n_ctas + cta]; NULL = not computed
     double* loss_part;
     LossSpec L;
+    long long wait_cycles;    // limit of the pipeline waits (kWaitCycles by default)
 };
 
 constexpr int kTraceSites = 32;   // 0: CTA lifetime cycles, 1..13: wait sites, 16..: busy phases
@@ -133,7 +143,7 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Non-blocking probe of a phase.
-[[maybe_unused]] __device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -145,25 +155,32 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
     return ok;
 }
 
+// Limits below this many cycles poll without suspending and check the clock on
+// every poll (a suspended try_wait can sleep for kSuspendNs, far beyond such a
+// limit); longer limits suspend between polls and check every 16th.
+constexpr long long kShortWait = 1LL << 20;
+
 // Bounded wait.  Returns false (and raises the CTA abort flag) on timeout or
 // when another role already aborted.  With a trace array, the cycles spent
 // waiting are added to trace[code].
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int code, unsigned long long* trace = nullptr) {
+                                          int* err, int code, unsigned long long* trace = nullptr,
+                                          long long limit = kWaitCycles) {
+    const bool fast = limit < kShortWait;
     long long t0 = trace ? clock64() : 0;
-    if (mbar_try(bar, parity)) {
+    if (fast ? mbar_test(bar, parity) : mbar_try(bar, parity)) {
         if (trace) atomicAdd(&trace[code], (unsigned long long)(clock64() - t0));
         return true;
     }
     if (!trace) t0 = clock64();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try(bar, parity)) {
+        if (fast ? mbar_test(bar, parity) : mbar_try(bar, parity)) {
             if (trace) atomicAdd(&trace[code], (unsigned long long)(clock64() - t0));
             return true;
         }
-        if ((it & 15) == 0) {
+        if (fast || (it & 15) == 0) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > kWaitCycles) {
+            if (clock64() - t0 > limit) {
                 *abort_flag = 1;
                 atomicCAS(err, 0, code);
                 return false;
@@ -439,9 +456,15 @@ __device__ __forceinline__ uint32_t warp_transpose_bits(uint32_t x, int lane) {
 
 // One loss term D(y, yhat) in FP32 (App. B).  For KL the weight a = y / yhat
 // is already at hand: D = y log(a) - y + yhat.
+// For Jensen-Shannon a = log((y + yhat) / (2 yhat)) = -log(yhat / m), m = (y + yhat)/2,
+// so D = (y log(y/m) + yhat log(yhat/m)) / 2 = (y log(y/m) - yhat a) / 2.
 template <int WK>
 __device__ __forceinline__ float tc_loss(float y, float yh, float a, const LossSpec& L) {
     if (WK == WK_KL) return (y > 0.f ? y * __logf(a) : 0.f) - y + yh;
+    if (WK == WK_JS) {
+        const float m = 0.5f * (y + yh);
+        return 0.5f * ((y > 0.f ? y * __logf(__fdividef(y, m)) : 0.f) - yh * a);
+    }
     return divergence<float>(y, yh, L);
 }
 
@@ -449,6 +472,16 @@ template <int WK>
 __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& w, float& wa, float& wb) {
     if (WK == WK_KL) {
         wa = __fdividef(y, yh);
+        wb = 1.0f;
+    } else if (WK == WK_NB) {
+        const float phi = (float)w.par;
+        wa = __fdividef(y, yh);
+        wb = __fdividef(phi + y, phi + yh);
+    } else if (WK == WK_BIN) {
+        wa = __fdividef(y, yh);
+        wb = __fdividef((float)w.par, 1.0f + yh);
+    } else if (WK == WK_JS) {
+        wa = __logf(__fdividef(0.5f * (y + yh), yh));
         wb = 1.0f;
     } else if (WK == WK_B05) {
         const float r = rsqrt_approx(yh);
@@ -653,8 +686,10 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
     };
 
     // waits of the warp-uniform producer and MMA loops (every lane polls)
+    const long long wlim = prm.wait_cycles;
     auto uwait = [&](uint32_t bar, uint32_t par, int code) {
-        return __all_sync(0xffffffffu, mbar_wait(bar, par, abort_flag, prm.err, code, lane == 0 ? tr : nullptr));
+        return __all_sync(0xffffffffu,
+                          mbar_wait(bar, par, abort_flag, prm.err, code, lane == 0 ? tr : nullptr, wlim));
     };
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
@@ -836,10 +871,10 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             for (int i = 0; i < T; ++i) {
                 const int s = i % NSV, sq = i % NSQ;
                 if (!__all_sync(0xffffffffu, mbar_wait(vfull(s), (i / NSV) & 1, abort_flag, prm.err, 13,
-                                                       lane == 0 ? tr : nullptr)))
+                                                       lane == 0 ? tr : nullptr, wlim)))
                     break;
                 if (!__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag, prm.err, 8,
-                                                       lane == 0 ? tr : nullptr)))
+                                                       lane == 0 ? tr : nullptr, wlim)))
                     break;
                 if (trl) tp = clock64();
                 const uint8_t* vsrc = sm + LY::kV + s * (TN * RB);
@@ -921,7 +956,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             if (st + 1 < 2 * T) issue((st + 1) & 1);
             const int sq = i % NSQ;
             if (hh == 0 && !__all_sync(0xffffffffu, mbar_wait(qempty(sq), ((i / NSQ) & 1) ^ 1, abort_flag,
-                                                              prm.err, 8, lane == 0 ? tr : nullptr)))
+                                                              prm.err, 8, lane == 0 ? tr : nullptr, wlim)))
                 break;
             uint8_t* qdst = sm + LY::kQ + sq * LY::kQStage;
 #pragma unroll
@@ -970,7 +1005,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         const bool row_ok = row < v.rows;
         const WeightSpec w = prm.w;
         auto wwait = [&](uint32_t bar, uint32_t par, int code) {
-            const bool ok = mbar_wait(bar, par, abort_flag, prm.err, code, lane == 0 ? tr : nullptr);
+            const bool ok = mbar_wait(bar, par, abort_flag, prm.err, code, lane == 0 ? tr : nullptr, wlim);
             return __all_sync(0xffffffffu, ok);
         };
         const bool trl = tr && lane == 0;
@@ -1168,7 +1203,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
             }
         }
         // ---- S readout: group 0 copies S_num, group 1 S_den
-        bool have = (T > 0) && mbar_wait(sfull, 0, abort_flag, prm.err, 12, lane == 0 ? tr : nullptr);
+        bool have = (T > 0) && mbar_wait(sfull, 0, abort_flag, prm.err, 12, lane == 0 ? tr : nullptr, wlim);
         have = __all_sync(0xffffffffu, have);
         tc_fence_after();
         if (h == 0 || (DEN && h == 1)) {

@@ -2,4 +2,3 @@
 #include "k_view_tc_inst.cuh"
 
 NEF_TC_GATHER_INSTANCE(64)
-NEF_TC_GATHER_LOSS_INSTANCE(64)

@@ -34,6 +34,24 @@ cudaError_t launch_bp(const CUtensorMap& map, const CUtensorMap& vmap, const CUt
     }
 }
 
+// The likelihood families' weight kinds (negative binomial and binomial always
+// contract the denominator; Jensen-Shannon has b == 1 and takes the closed form
+// when there is no mask).
+template <int BP, bool LOSS, int QM>
+cudaError_t launch_bp_lik(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p,
+                          int den, int wk, int grid, cudaStream_t st) {
+    if (!den) {
+        if (wk == WK_JS) return launch_one<BP, false, WK_JS, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        return cudaErrorInvalidValue;
+    }
+    switch (wk) {
+        case WK_NB: return launch_one<BP, true, WK_NB, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        case WK_BIN: return launch_one<BP, true, WK_BIN, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        case WK_JS: return launch_one<BP, true, WK_JS, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int BP, bool DEN, int WK>
 cudaError_t launch_batched_one(const TcUnit* units, const TcWork* work, int n_work, cudaStream_t st) {
     auto kern = k_view_tc_batched<BP, DEN, WK>;
@@ -71,6 +89,18 @@ cudaError_t launch_batched_bp(const TcUnit* units, const TcWork* work, int n_wor
     }                                                                                        \
     }                                                                                        \
     }
+#define NEF_TC_LIK_INSTANCE_X(BP, SUFFIX, LOSS)                                               \
+    namespace nef {                                                                          \
+    namespace tc {                                                                           \
+    cudaError_t launch_bp##BP##SUFFIX(const CUtensorMap& map, const CUtensorMap& vmap,        \
+                                      const CUtensorMap& cmap, const Params& p, int den, int wk, \
+                                      int grid, cudaStream_t st) {                           \
+        return launch_bp_lik<BP, LOSS, 1>(map, vmap, cmap, p, den, wk, grid, st);            \
+    }                                                                                        \
+    }                                                                                        \
+    }
+#define NEF_TC_LIK_INSTANCE(BP) NEF_TC_LIK_INSTANCE_X(BP, _lik, false)
+#define NEF_TC_LIK_LOSS_INSTANCE(BP) NEF_TC_LIK_INSTANCE_X(BP, _lik_loss, true)
 #define NEF_TC_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, , false, 1)
 #define NEF_TC_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _loss, true, 1)
 #define NEF_TC_GATHER_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _g, false, 0)

@@ -44,9 +44,31 @@ __device__ __forceinline__ T powz(T x, double p) {
     return pw_code(x, POW_GENERAL, p);
 }
 
+// y log z with 0 log z = 0 (the convention of App. B at y = 0).
+template <typename T>
+__device__ __forceinline__ T xlogy(T y, T z) {
+    return y == T(0) ? T(0) : y * log(z);
+}
+
+// a and b of the likelihood families of App. B (negative binomial, binomial on
+// the odds, Jensen-Shannon); mask handled by the caller.
+template <typename T>
+__device__ __forceinline__ void lik_weights(T y, T yh, const WeightSpec& w, T& wa, T& wb) {
+    const T par = T(w.par);
+    switch (w.lik) {
+        case LIK_NEGBIN: wa = y / yh; wb = (par + y) / (par + yh); break;
+        case LIK_BINOMIAL: wa = y / yh; wb = par / (T(1) + yh); break;
+        default: wa = log((y + yh) / (T(2) * yh)); wb = T(1); break;  // LIK_JS
+    }
+}
+
 // Masked weights of App. B (mask handled by the caller).
 template <typename T>
 __device__ __forceinline__ void ab_weights(T y, T yh, const WeightSpec& w, T& wa, T& wb) {
+    if (w.lik) {
+        lik_weights(y, yh, w, wa, wb);
+        return;
+    }
     if (w.log_case) {
         wa = log(y / yh);
         wb = T(1);
@@ -59,9 +81,28 @@ __device__ __forceinline__ void ab_weights(T y, T yh, const WeightSpec& w, T& wa
     wb = pw_code(yh, w.b_code, w.e_b);
 }
 
-// D_{alpha,beta}(x, y): the five cases of App. B.
+// D(x, y) of a likelihood family of App. B with its constant terms dropped:
+// negative binomial (phi + x) log(phi + y) - x log y; binomial on the odds
+// n log(1 + y) - x log y; Jensen-Shannon (x log x + y log y)/2 - m log m with
+// m = (x + y)/2, evaluated as (x log(x/m) + y log(y/m))/2 (the same value
+// without the cancellation of the first form).
+template <typename T>
+__device__ __forceinline__ T lik_divergence(T x, T y, const LossSpec& L) {
+    const T par = T(L.par);
+    switch (L.lik) {
+        case LIK_NEGBIN: return xlogy(par + x, par + y) - xlogy(x, y);
+        case LIK_BINOMIAL: return par * log1p(y) - xlogy(x, y);
+        default: {  // LIK_JS
+            const T m = T(0.5) * (x + y);
+            return T(0.5) * (xlogy(x, x / m) + xlogy(y, y / m));
+        }
+    }
+}
+
+// D_{alpha,beta}(x, y): the five cases of App. B (or a likelihood family's D).
 template <typename T>
 __device__ __forceinline__ T divergence(T x, T y, const LossSpec& L) {
+    if (L.lik) return lik_divergence(x, y, L);
     const double al = L.alpha, be = L.beta;
     switch (L.kase) {
         case 1: {  // beta = 0

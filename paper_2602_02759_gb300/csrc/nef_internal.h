@@ -39,21 +39,31 @@ enum PowCode : int {
     POW_RCP2 = 8      // x^-2
 };
 
+// Likelihood families of App. B outside the (alpha,beta) family (nef.h NEF_LOSS_*).
+enum LikKind : int { LIK_NONE = 0, LIK_NEGBIN = 1, LIK_BINOMIAL = 2, LIK_JS = 3 };
+
 // Weights of App. B: wa = M * y^alpha * yhat^(beta-1), wb = M * yhat^(alpha+beta-1)
-// (alpha != 0), or wa = M * log(y/yhat), wb = M (alpha = 0, beta = 1).
+// (alpha != 0), or wa = M * log(y/yhat), wb = M (alpha = 0, beta = 1).  With lik
+// set, the likelihood family's a and b instead (negative binomial: y/yhat and
+// (par+y)/(par+yhat); binomial on odds: y/yhat and par/(1+yhat); Jensen-Shannon:
+// log((y+yhat)/(2 yhat)) and 1), par being phi or the trial count.
 struct WeightSpec {
     int log_case;       // 1 for (alpha, beta) = (0, 1)
     int y_code;         // PowCode of y^alpha
     int a_code;         // PowCode of yhat^(beta-1)
-    int b_code;         // PowCode of yhat^(alpha+beta-1)
+    int b_code;         // PowCode of yhat^(alpha+beta-1); POW_ONE whenever b == 1
     double alpha, beta;
     double e_y, e_a, e_b;  // exponents (used by POW_GENERAL)
+    int lik;            // LikKind
+    double par;         // phi (negative binomial) or trials n (binomial)
 };
 
 // Loss cases of App. B.
 struct LossSpec {
     int kase;           // 0 generic, 1 beta=0, 2 alpha=-beta, 3 alpha=0, 4 alpha=beta=0
     double alpha, beta;
+    int lik;            // LikKind: a likelihood family's D instead of D_{alpha,beta}
+    double par;
 };
 
 // Update of Eq. 3.4: theta <- max(eps, theta * ginv(num/den)).
@@ -156,10 +166,22 @@ cudaError_t launch_colsums(const ColsumDesc& d, int64_t max_ld, cudaStream_t st)
 // Message returned by nef_last_error() on this thread.
 void set_last_error(const char* msg);
 
-// Specialisation of the App. B weights, loss and update for given (alpha, beta).
-WeightSpec weight_spec(double alpha, double beta);
-LossSpec loss_spec(double alpha, double beta);
-UpdateSpec update_spec(double alpha, double beta, double eps);
+// Specialisation of the App. B weights, loss and update for given (alpha, beta)
+// (lik = LIK_NONE) or for a likelihood family with parameter par (alpha, beta
+// ignored).
+WeightSpec weight_spec(double alpha, double beta, int lik = LIK_NONE, double par = 0.0);
+LossSpec loss_spec(double alpha, double beta, int lik = LIK_NONE, double par = 0.0);
+UpdateSpec update_spec(double alpha, double beta, double eps, int lik = LIK_NONE);
+
+// Argument check shared by every entry point that takes a loss: returns nullptr
+// when (lik, alpha, beta, par) is valid, else a message; *unsupported is set for
+// alpha == 0 with beta != 1 (no decomposition, App. B).
+const char* loss_args_error(int lik, double alpha, double beta, double par, bool* unsupported);
+
+// True when b(x, y) == 1 for these weights (the closed-form denominator applies).
+inline bool weights_b_is_one(const WeightSpec& w) {
+    return w.lik == LIK_JS || (w.lik == LIK_NONE && (w.log_case || w.b_code == POW_ONE));
+}
 
 // ------------------------------------------------------------- launchers
 // All launchers return cudaGetLastError() after enqueueing on `st`.
@@ -244,7 +266,7 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
                            const WeightSpec& w, int need_den, int n_split, float* s_num,
                            float* s_den, int* err_flag, cudaStream_t st, TcLaunchInfo* info,
                            unsigned long long* trace = nullptr, const LossSpec* loss = nullptr,
-                           double* loss_part = nullptr);
+                           double* loss_part = nullptr, long long wait_cycles = 0);
 
 bool tc_view_supported(const ViewDesc& v, int need_den);
 

@@ -241,9 +241,15 @@ struct nef_plan_s {
     int* loss_count = nullptr;        // device: entries appended to the loss trace
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaGraphExec_t sweep_graph = nullptr;
-    std::vector<const void*> graph_key;  // arguments the captured sweep was recorded with
-    double graph_ab[2] = {0.0, 0.0};
+    // captured sweeps, most recently used last: a fit replays the one recorded with
+    // its arguments (data, mask, factors, loss trace, alpha, beta) or captures anew
+    struct SweepGraph {
+        std::vector<const void*> key;
+        double ab[2];
+        cudaGraphExec_t exec;
+    };
+    std::vector<SweepGraph> graphs;
+    static constexpr size_t kMaxGraphs = 4;
     int last_sweeps = 0;
 };
 
@@ -251,10 +257,19 @@ namespace nef {
 
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
-WeightSpec weight_spec(double al, double be) {
+WeightSpec weight_spec(double al, double be, int lik, double par) {
     WeightSpec w{};
     w.alpha = al;
     w.beta = be;
+    if (lik != LIK_NONE) {
+        // the likelihood families of App. B: b == 1 only for Jensen-Shannon
+        w.lik = lik;
+        w.par = par;
+        w.y_code = POW_ONE;
+        w.a_code = POW_GENERAL;
+        w.b_code = lik == LIK_JS ? POW_ONE : POW_GENERAL;
+        return w;
+    }
     auto code = [](double e) {
         if (e == 0.0) return (int)POW_ONE;
         if (e == 1.0) return (int)POW_ID;
@@ -282,10 +297,13 @@ WeightSpec weight_spec(double al, double be) {
     return w;
 }
 
-LossSpec loss_spec(double al, double be) {
+LossSpec loss_spec(double al, double be, int lik, double par) {
     LossSpec L{};
     L.alpha = al;
     L.beta = be;
+    L.lik = lik;
+    L.par = par;
+    if (lik != LIK_NONE) return L;
     if (al != 0.0 && be != 0.0 && al + be != 0.0) L.kase = 0;
     else if (be == 0.0 && al != 0.0) L.kase = 1;
     else if (al == -be && al != 0.0) L.kase = 2;
@@ -294,9 +312,19 @@ LossSpec loss_spec(double al, double be) {
     return L;
 }
 
-UpdateSpec update_spec(double al, double be, double eps) {
+UpdateSpec update_spec(double al, double be, double eps, int lik) {
     UpdateSpec u{};
     u.eps = eps;
+    if (lik != LIK_NONE) {
+        // g(lambda) = lambda (negative binomial, binomial) or log(lambda) (Jensen-Shannon)
+        if (lik == LIK_JS) {
+            u.log_case = 1;
+        } else {
+            u.eta = 1.0;
+            u.eta_code = POW_ID;
+        }
+        return u;
+    }
     if (al == 0.0 && be == 1.0) {
         u.log_case = 1;
         return u;
@@ -310,6 +338,27 @@ UpdateSpec update_spec(double al, double be, double eps) {
     else if (u.eta == -1.0) u.eta_code = POW_RCP;
     else u.eta_code = POW_GENERAL;
     return u;
+}
+
+const char* loss_args_error(int lik, double al, double be, double par, bool* unsupported) {
+    if (unsupported) *unsupported = false;
+    switch (lik) {
+        case LIK_NONE:
+            if (!std::isfinite(al) || !std::isfinite(be)) return "alpha/beta must be finite";
+            if (al == 0.0 && be != 1.0) {
+                if (unsupported) *unsupported = true;
+                return "alpha == 0 with beta != 1 has no decomposition (App. B)";
+            }
+            return nullptr;
+        case LIK_NEGBIN:
+            return (std::isfinite(par) && par > 0.0) ? nullptr : "negative binomial dispersion phi must be finite and > 0";
+        case LIK_BINOMIAL:
+            return (std::isfinite(par) && par > 0.0) ? nullptr : "binomial trial count n must be finite and > 0";
+        case LIK_JS:
+            return nullptr;
+        default:
+            return "unknown loss family";
+    }
 }
 
 }  // namespace nef
@@ -1024,8 +1073,7 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
                                          ldims.data(), mir, st));
         return after_update<T>(p, pp.l, st);
     }
-    const bool b_is_one = (w.log_case || w.b_code == POW_ONE);
-    const bool closed = pp.den_closed && b_is_one && mbits == nullptr;
+    const bool closed = pp.den_closed && weights_b_is_one(w) && mbits == nullptr;
     const int need_den = closed ? 0 : 1;
     bool use_tc = false;
     if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den);
@@ -1042,7 +1090,8 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
             TcLaunchInfo info{};
             NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den, n_split,
                                     reinterpret_cast<float*>(spn), reinterpret_cast<float*>(spd),
-                                    p->tc_err, st, &info, p->tc_trace, loss, loss ? p->loss_part : nullptr));
+                                    p->tc_err, st, &info, p->tc_trace, loss, loss ? p->loss_part : nullptr,
+                                    p->opt.wait_cycles));
             if (n_part) *n_part = info.n_ctas;
         }
     } else {
@@ -1095,11 +1144,24 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
     return after_update<T>(p, pp.l, st);
 }
 
-nef_status check_ab(double al, double be) {
-    if (!std::isfinite(al) || !std::isfinite(be)) return fail(NEF_EINVAL, "alpha/beta must be finite");
-    if (al == 0.0 && be != 1.0)
-        return fail(NEF_EUNSUPPORTED, "alpha == 0 with beta != 1 has no decomposition (App. B)");
+// The plan's loss family with the call's (alpha, beta) (ignored by the likelihood families).
+nef_status check_ab(nef_plan_t p, double al, double be) {
+    bool unsup = false;
+    const char* msg = loss_args_error(p->opt.loss, al, be, p->opt.loss_par, &unsup);
+    if (msg) return fail(unsup ? NEF_EUNSUPPORTED : NEF_EINVAL, "%s", msg);
     return NEF_OK;
+}
+
+struct Specs {
+    WeightSpec w;
+    UpdateSpec u;
+    LossSpec L;
+};
+
+Specs specs_of(nef_plan_t p, double al, double be) {
+    const int lik = p->opt.loss;
+    const double par = p->opt.loss_par;
+    return Specs{weight_spec(al, be, lik, par), update_spec(al, be, p->opt.eps, lik), loss_spec(al, be, lik, par)};
 }
 
 template <typename T>
@@ -1163,10 +1225,12 @@ nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
     cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
     const uint32_t* mbits = nullptr;
     p->last_sweeps = 0;
+    if (p->opt.loss != NEF_LOSS_AB) al = be = 0.0;  // ignored by the likelihood families
     NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
-    const WeightSpec w = weight_spec(al, be);
-    const UpdateSpec u = update_spec(al, be, p->opt.eps);
-    const LossSpec L = loss_spec(al, be);
+    const Specs sp = specs_of(p, al, be);
+    const WeightSpec& w = sp.w;
+    const UpdateSpec& u = sp.u;
+    const LossSpec& L = sp.L;
     const bool want_loss = only_l < 0 && (trace != nullptr || tol > 0.0);
     const LossSpec* lp = want_loss ? &L : nullptr;
     const T* y = static_cast<const T*>(Y);
@@ -1196,10 +1260,19 @@ nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
             NEF_TRY(ensure_capture_stream(p));
             std::vector<const void*> key = {Y, mbits, trace, reinterpret_cast<const void*>((intptr_t)want_loss)};
             for (int f = 0; f < p->md.L; ++f) key.push_back(factors[f]);
-            if (!p->sweep_graph || key != p->graph_key || p->graph_ab[0] != al || p->graph_ab[1] != be) {
-                if (p->sweep_graph) {
-                    cudaGraphExecDestroy(p->sweep_graph);
-                    p->sweep_graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            for (size_t gi = 0; gi < p->graphs.size(); ++gi) {
+                const auto& ge = p->graphs[gi];
+                if (ge.key == key && ge.ab[0] == al && ge.ab[1] == be) {
+                    exec = ge.exec;
+                    std::rotate(p->graphs.begin() + gi, p->graphs.begin() + gi + 1, p->graphs.end());
+                    break;
+                }
+            }
+            if (!exec) {
+                if (p->graphs.size() >= nef_plan_s::kMaxGraphs) {
+                    cudaGraphExecDestroy(p->graphs.front().exec);
+                    p->graphs.erase(p->graphs.begin());
                 }
                 NEF_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
                 const nef_status rs = sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, -1, p->cap_stream);
@@ -1210,17 +1283,15 @@ nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
                     return rs;
                 }
                 NEF_CUDA(ec);
-                const cudaError_t ei = cudaGraphInstantiate(&p->sweep_graph, g, 0);
+                const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
                 cudaGraphDestroy(g);
                 NEF_CUDA(ei);
-                p->graph_key = key;
-                p->graph_ab[0] = al;
-                p->graph_ab[1] = be;
+                p->graphs.push_back({key, {al, be}, exec});
             }
             NEF_CUDA(cudaEventRecord(p->ev_fork, st));
             NEF_CUDA(cudaStreamWaitEvent(p->cap_stream, p->ev_fork, 0));
             while (done < iters) {
-                NEF_CUDA(cudaGraphLaunch(p->sweep_graph, p->cap_stream));
+                NEF_CUDA(cudaGraphLaunch(exec, p->cap_stream));
                 ++done;
                 if (tol > 0.0) {
                     double h[2];
@@ -1281,17 +1352,20 @@ nef_status loss_pass(nef_plan_t p, const T* y, const uint32_t* mbits, void* cons
         return NEF_OK;
     }
     PassPlan& pp = p->pass[vl];
+    // the partial products are discarded: the denominator contraction runs only
+    // where the instance needs it (masked views, b != 1)
+    const int need_den = (mbits || !weights_b_is_one(w)) ? 1 : 0;
     bool use_tc = false;
-    if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), 1);
+    if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den);
     NEF_TRY(refresh_sources<T>(p, pp, factors, st, use_tc));
     if (use_tc) {
         if constexpr (sizeof(T) == 4) {
             ViewDesc v = bind_view(p, pp, true);
             TcLaunchInfo info{};
-            NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, 1, pp.n_split,
+            NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den, pp.n_split,
                                     static_cast<float*>(buf_ptr(p, B_SPART_N)),
                                     static_cast<float*>(buf_ptr(p, B_SPART_D)), p->tc_err, st, &info, nullptr, &L,
-                                    p->loss_part));
+                                    p->loss_part, p->opt.wait_cycles));
             *n_part = info.n_ctas;
         }
         return NEF_OK;
@@ -1310,8 +1384,9 @@ nef_status loss_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* con
     cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
     const uint32_t* mbits = nullptr;
     NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
-    const WeightSpec w = weight_spec(al, be);
-    const LossSpec L = loss_spec(al, be);
+    const Specs sp = specs_of(p, al, be);
+    const WeightSpec& w = sp.w;
+    const LossSpec& L = sp.L;
     const T* y = static_cast<const T*>(Y);
     int n_part = 0;
     // the first factor with a view serves as the reconstruction route
@@ -1319,14 +1394,10 @@ nef_status loss_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* con
     for (int l = 0; l < p->md.L; ++l)
         if (!p->pass[l].generic) { vl = l; break; }
     if (vl >= 0) {
-        PassPlan& pp = p->pass[vl];
+        // the fused pass of the first viewable factor with its products discarded:
+        // tensor cores for NEF_BF16 plans, CUDA cores otherwise
         NEF_TRY(init_sources<T>(p, factors, st));
-        NEF_TRY(refresh_sources<T>(p, pp, factors, st, false));
-        ViewDesc v = bind_view(p, pp, false);
-        const int64_t tm = sizeof(T) == 8 ? 32 : 64;
-        const int64_t n_rb = (v.rows + tm - 1) / tm;
-        int ns = (int)std::max<int64_t>(1, std::min<int64_t>(pp.n_split, p->loss_part_cap / 2 / n_rb));
-        NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, 0, ns, nullptr, nullptr, &L, p->loss_part, st, &n_part));
+        NEF_TRY(loss_pass<T>(p, y, mbits, factors, w, L, st, &n_part));
     } else {
         GenericRecon g{};
         const Model& md = p->md;
@@ -1357,10 +1428,11 @@ nef_status alloc(nef_plan_t p, int id, size_t bytes);
 // bond), precision, weight kind, denominator mode, mask and the SM count.
 std::string tune_key(nef_plan_t p, const PassPlan& pp, const WeightSpec& w, int need_den, bool masked) {
     char k[512];
-    snprintf(k, sizeof(k), "view rows=%lld c_out=%lld c_in=%lld bond_pad=%lld nq=%d prec=%d ab=%.17g,%.17g den=%d mask=%d "
-             "sm=%lld",
+    snprintf(k, sizeof(k), "view rows=%lld c_out=%lld c_in=%lld bond_pad=%lld nq=%d prec=%d ab=%.17g,%.17g lik=%d,%.17g "
+             "den=%d mask=%d sm=%lld",
              (long long)pp.view.rows, (long long)pp.view.c_out, (long long)pp.view.c_in, (long long)pp.view.bond_pad,
-             (int)pp.Q.size(), p->prec, w.alpha, w.beta, need_den, masked ? 1 : 0, (long long)p->n_sm);
+             (int)pp.Q.size(), p->prec, w.lik ? 0.0 : w.alpha, w.lik ? 0.0 : w.beta, w.lik, w.par, need_den,
+             masked ? 1 : 0, (long long)p->n_sm);
     return k;
 }
 
@@ -1394,7 +1466,7 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
     cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
     const uint32_t* mbits = nullptr;
     NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
-    const WeightSpec w = weight_spec(al, be);
+    const WeightSpec w = specs_of(p, al, be).w;
     const T* y = static_cast<const T*>(Y);
     std::map<std::string, int> cache;
     if (cache_path) {
@@ -1418,8 +1490,7 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
         PassPlan& pp = p->pass[l];
         if (splits) splits[l] = -1;
         if (pp.generic) continue;
-        const bool b_is_one = (w.log_case || w.b_code == POW_ONE);
-        const bool closed = pp.den_closed && b_is_one && mbits == nullptr;
+        const bool closed = pp.den_closed && weights_b_is_one(w) && mbits == nullptr;
         const int need_den = closed ? 0 : 1;
         bool use_tc = false;
         if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den);
@@ -1457,7 +1528,7 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
                         TcLaunchInfo info{};
                         return launch_view_tc(reinterpret_cast<const float*>(y), mbits, bind_view(p, pp, true), w,
                                               need_den, c, reinterpret_cast<float*>(spn), reinterpret_cast<float*>(spd),
-                                              p->tc_err, st, &info);
+                                              p->tc_err, st, &info, nullptr, nullptr, nullptr, p->opt.wait_cycles);
                     }
                     return cudaErrorNotSupported;
                 }
@@ -1506,10 +1577,8 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
         info += pp.desc + "\n";
     }
     p->info = info;
-    if (p->sweep_graph) {  // recorded with the old splits
-        cudaGraphExecDestroy(p->sweep_graph);
-        p->sweep_graph = nullptr;
-    }
+    for (auto& ge : p->graphs) cudaGraphExecDestroy(ge.exec);  // recorded with the old splits
+    p->graphs.clear();
     if (cache_path) {
         FILE* f = fopen(cache_path, "w");
         if (!f) return fail(NEF_EINVAL, "cannot write the autotune cache %s", cache_path);
@@ -1548,7 +1617,7 @@ void destroy(nef_plan_t p) {
     if (p->tc_err) cudaFree(p->tc_err);
     if (p->tc_trace) cudaFree(p->tc_trace);
     if (p->loss_count) cudaFree(p->loss_count);
-    if (p->sweep_graph) cudaGraphExecDestroy(p->sweep_graph);
+    for (auto& ge : p->graphs) cudaGraphExecDestroy(ge.exec);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -1740,6 +1809,10 @@ nef_status build_plan(nef_plan_t p) {
 
 }  // namespace
 
+static_assert(NEF_LOSS_AB == LIK_NONE && NEF_LOSS_NEGBIN == LIK_NEGBIN && NEF_LOSS_BINOMIAL == LIK_BINOMIAL &&
+                  NEF_LOSS_JS == LIK_JS,
+              "loss families of the ABI and of the kernels");
+
 // ================================================================== C ABI
 extern "C" {
 
@@ -1754,6 +1827,9 @@ void nef_default_options(nef_options* opt) {
     opt->tol = 0.0;
     opt->loss_trace = nullptr;
     opt->eager = 0;
+    opt->loss = NEF_LOSS_AB;
+    opt->loss_par = 0.0;
+    opt->wait_cycles = 0;
 }
 
 nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, const int64_t* ranks,
@@ -1768,9 +1844,20 @@ nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, con
         delete p;
         return fail(NEF_EINVAL, "unknown precision %d", p->opt.precision);
     }
-    if (!(p->opt.eps >= 0.0)) {
+    if (!(p->opt.eps >= 0.0) || !std::isfinite(p->opt.eps)) {
         delete p;
-        return fail(NEF_EINVAL, "eps must be >= 0");
+        return fail(NEF_EINVAL, "eps must be finite and >= 0");
+    }
+    if (p->opt.loss != NEF_LOSS_AB) {
+        const char* msg = loss_args_error(p->opt.loss, 1.0, 0.0, p->opt.loss_par, nullptr);
+        if (msg) {
+            delete p;
+            return fail(NEF_EINVAL, "%s", msg);
+        }
+    }
+    if (p->opt.wait_cycles < 0) {
+        delete p;
+        return fail(NEF_EINVAL, "wait_cycles must be >= 0");
     }
     p->prec = p->opt.precision;
     p->esz = p->prec == NEF_FP64 ? 8 : 4;
@@ -1804,7 +1891,7 @@ nef_status nef_fit_ex(nef_plan_t plan, const void* Y, const uint8_t* mask, void*
     if (!plan) return fail(NEF_EINVAL, "plan is NULL");
     if (iters < 0) return fail(NEF_EINVAL, "iters must be >= 0");
     if (!(tol >= 0.0)) return fail(NEF_EINVAL, "tol must be >= 0");
-    NEF_TRY(check_ab(alpha, beta));
+    NEF_TRY(check_ab(plan, alpha, beta));
     const nef_status r = plan->prec == NEF_FP64
                              ? fit_impl<double>(plan, Y, mask, factors, alpha, beta, iters, -1, tol, loss_trace)
                              : fit_impl<float>(plan, Y, mask, factors, alpha, beta, iters, -1, tol, loss_trace);
@@ -1827,7 +1914,7 @@ nef_status nef_plan_autotune(nef_plan_t plan, const void* Y, const uint8_t* mask
                              double alpha, double beta, const char* cache_path, int* splits) {
     g_err.clear();
     if (!plan) return fail(NEF_EINVAL, "plan is NULL");
-    NEF_TRY(check_ab(alpha, beta));
+    NEF_TRY(check_ab(plan, alpha, beta));
     if (plan->prec == NEF_FP64)
         return autotune_impl<double>(plan, Y, mask, factors, alpha, beta, cache_path, splits);
     return autotune_impl<float>(plan, Y, mask, factors, alpha, beta, cache_path, splits);
@@ -1838,7 +1925,7 @@ nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask
     g_err.clear();
     if (!plan) return fail(NEF_EINVAL, "plan is NULL");
     if (l < 0 || l >= plan->md.L) return fail(NEF_EINVAL, "factor index %d out of range", l);
-    NEF_TRY(check_ab(alpha, beta));
+    NEF_TRY(check_ab(plan, alpha, beta));
     if (plan->prec == NEF_FP64) return fit_impl<double>(plan, Y, mask, factors, alpha, beta, 1, l);
     return fit_impl<float>(plan, Y, mask, factors, alpha, beta, 1, l);
 }
@@ -1848,7 +1935,7 @@ nef_status nef_loss(nef_plan_t plan, const void* Y, const uint8_t* mask, void* c
     g_err.clear();
     if (!plan) return fail(NEF_EINVAL, "plan is NULL");
     if (!out) return fail(NEF_EINVAL, "out is NULL");
-    NEF_TRY(check_ab(alpha, beta));
+    NEF_TRY(check_ab(plan, alpha, beta));
     if (plan->prec == NEF_FP64) return loss_impl<double>(plan, Y, mask, factors, alpha, beta, out);
     return loss_impl<float>(plan, Y, mask, factors, alpha, beta, out);
 }

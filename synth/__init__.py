@@ -45,8 +45,24 @@ class Problem:
         return [tuple(self.dims[c] for c in t) for t in terms]
 
 
+def draw_data(mean, rng, data="poisson", noise=(2.0, 0.5), par=1.0):
+    """Data around a nonnegative mean tensor: Poisson(mean) counts; mean *
+    Gamma(k, theta) multiplicative noise (positive values); negative binomial
+    counts Poisson(mean * Gamma(par, 1/par)) with dispersion par; or binomial
+    counts Binomial(n = par, mean / (1 + mean)), mean being the odds."""
+    if data == "poisson":
+        return rng.poisson(mean)
+    if data == "gamma_noise":
+        return mean * rng.gamma(noise[0], noise[1], size=mean.shape)
+    if data == "negbin":
+        return rng.poisson(mean * rng.gamma(par, 1.0 / par, size=mean.shape))
+    if data == "binomial":
+        return rng.binomial(int(par), mean / (1.0 + mean))
+    raise ValueError(data)
+
+
 def make_problem(model_str: str, dims: dict, seed: int = 0, *,
-                 gamma=(0.3, 1.0), data="poisson", noise=(2.0, 0.5),
+                 gamma=(0.3, 1.0), data="poisson", noise=(2.0, 0.5), par=1.0,
                  missing=0.0, restarts=1, init=(0.5, 1.5), alpha=1.0, beta=0.0,
                  y_dtype=np.float32) -> Problem:
     terms, rhs = parse_terms(model_str)
@@ -56,12 +72,7 @@ def make_problem(model_str: str, dims: dict, seed: int = 0, *,
         shp = tuple(int(dims[c]) for c in t)
         truth.append(rng.gamma(gamma[0], gamma[1], size=shp))
     mean = np.einsum(model_str, *truth, optimize=True)
-    if data == "poisson":
-        y = rng.poisson(mean).astype(y_dtype)
-    elif data == "gamma_noise":
-        y = (mean * rng.gamma(noise[0], noise[1], size=mean.shape)).astype(y_dtype)
-    else:
-        raise ValueError(data)
+    y = draw_data(mean, rng, data, noise, par).astype(y_dtype)
     del mean
     mask = None
     if missing > 0.0:
@@ -109,6 +120,31 @@ def config3(seed=0, shape=(256, 256, 64, 32), a=16, b=8) -> Problem:
                      gamma=(0.5, 1.0), data="gamma_noise", noise=(2.0, 0.5),
                      missing=0.30, alpha=0.5, beta=0.5)
     p.note = f"ia,ja,ab,kb,lb->ijkl {shape} a{a} b{b} (0.5,0.5) 30% missing"
+    return p
+
+
+# loss families of the 512^3 CP workload beyond KL: the data each one models
+LOSS_WORKLOADS = {
+    "rkl": dict(data="gamma_noise", alpha=0.0, beta=1.0, loss="ab", par=0.0,
+                note="reverse KL (0,1), Y = mean * Gamma(2, 0.5)"),
+    "negbin": dict(data="negbin", alpha=1.0, beta=0.0, loss="negbin", par=2.0,
+                   note="negative binomial phi = 2, Y ~ Poisson(mean * Gamma(2, 1/2))"),
+    "bernoulli": dict(data="binomial", alpha=1.0, beta=0.0, loss="binomial", par=1.0,
+                      note="Bernoulli on the odds, Y ~ Bernoulli(mean / (1 + mean))"),
+    "js": dict(data="poisson", alpha=1.0, beta=0.0, loss="js", par=0.0,
+               note="Jensen-Shannon, Y ~ Poisson(mean)"),
+}
+
+
+def config2_loss(kind, seed=0, n=512, rank=64) -> Problem:
+    """The 512^3 rank-64 CP workload (Gamma(0.3,1) truth, no mask) with the data
+    of loss family `kind` (LOSS_WORKLOADS); p.loss / p.loss_par name the family."""
+    w = LOSS_WORKLOADS[kind]
+    p = make_problem("ir,jr,kr->ijk", {"i": n, "j": n, "k": n, "r": rank}, seed,
+                     gamma=(0.3, 1.0), data=w["data"], par=w["par"], missing=0.0,
+                     alpha=w["alpha"], beta=w["beta"])
+    p.loss, p.loss_par = w["loss"], w["par"]
+    p.note = f"cp {n}^3 R{rank} {w['note']}"
     return p
 
 

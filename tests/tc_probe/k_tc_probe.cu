@@ -3,7 +3,7 @@
 // (K-major A, MN-major B) on caller-given BF16 tiles, with the A operands
 // either in shared memory (128B-swizzled) or in tensor memory (written by the
 // threads with tcgen05.st, one row per lane).
-#include "../../include/nef_debug.h"
+#include "nef_probe.h"
 #include "k_view_tc.cuh"
 
 namespace nef {

@@ -19,6 +19,17 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+
+def _probe():
+    """The test-only probe library (tests/tc_probe): layout probe and GEMM alone."""
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tc_probe", "build.py")
+    spec = importlib.util.spec_from_file_location("nef_probe_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.load()
+
 def _nef():
     import paper_2602_02759_gb300 as nef
     return nef
@@ -38,7 +49,7 @@ def test_tc_gemm(M, N, K):
     tB = torch.as_tensor(B).cuda().to(torch.bfloat16).contiguous()
     C = torch.full((M, N), float("nan"), device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rc = nef.load().nef_tc_gemm(tA.data_ptr(), K, tB.data_ptr(), K, C.data_ptr(), N, M, N, K, err.data_ptr(),
+    rc = _probe().nef_tc_gemm(tA.data_ptr(), K, tB.data_ptr(), K, C.data_ptr(), N, M, N, K, err.data_ptr(),
                                 torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert rc == 0 and int(err.item()) == 0

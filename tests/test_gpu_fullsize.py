@@ -1,0 +1,133 @@
+"""Full-size parity in the launch configuration the benchmark times: every element
+of every updated factor against the FP64 oracle (Algorithm 1, Eq. 3.4, App. B).
+
+  * CP 'ir,jr,kr->ijk' 512^3, R = 64, Poisson data, no mask, (alpha, beta) = (1, 0)
+    and (1, -1/2): one update of each factor from the same start, NEF_BF16 and
+    NEF_FP32, compared element by element with the oracle's update_factor.
+  * The same workload, NEF_BF16, fitted for 3 sweeps: the final loss within 1e-3
+    relative of the oracle's loss trace (the BF16 path's stated tolerance).
+  * The custom 4-way model 'ia,ja,ab,kb,lb->ijkl' 256x256x64x32 (a = 16, b = 8),
+    (1/2, 1/2), 30 % missing, NEF_BF16: one update of each of the five factors.
+
+Tolerances (elementwise, relative to the oracle's value):
+  * NEF_FP32: 1e-5 relative in the Frobenius norm per factor (the stated one-sweep
+    FP32 tolerance) and 3e-5 per element.  Each num/den element is a sum of
+    262,144 positive FP32 products, accumulated in sequential chains of ~3,500
+    terms per thread and then over the column splits; with round-to-nearest the
+    relative error of such a sum behaves like a random walk, about sqrt(3500) *
+    2^-24 ~ 4e-6 per chain, and the largest of 32,768 elements lies a few of
+    those above; 3e-5 leaves room for num and den together.
+  * NEF_BF16: 2e-3 per element.  The operands are rounded to BF16 (relative
+    2^-9 each); the rounding of the updated factor's own row enters every entry
+    of its row of Yhat with the same sign, so it does not average out over the
+    contraction: a weighted mean of 64 row roundings, a few 1e-4, times the
+    update exponent.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import OracleModel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+_ORACLE = {}
+
+
+def _nef():
+    import paper_2602_02759_gb300 as nef
+    return nef
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _frob(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _problem(beta):
+    key = ("p2", beta)
+    if key not in _ORACLE:
+        _ORACLE[key] = synth.config2(beta=beta)
+    return _ORACLE[key]
+
+
+def _oracle_update(beta, l):
+    key = ("u2", beta, l)
+    if key not in _ORACLE:
+        p = _problem(beta)
+        m = OracleModel(p.model_str, p.dims)
+        init = [f.astype(np.float64) for f in p.inits[0]]
+        _ORACLE[key] = m.update_factor(l, p.y, None, init, 1.0, beta)[0][l]
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("beta", [0.0, -0.5])
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_config2_every_element_after_one_update(prec, beta):
+    nef = _nef()
+    p = _problem(beta)
+    plan = nef.Plan(p.model_str, p.dims, precision=prec, profile=True)
+    Y = dev(p.y)
+    for l in range(3):
+        ref = _oracle_update(beta, l)
+        fs = [dev(f) for f in p.inits[0]]
+        plan.update(l, Y, None, fs, 1.0, beta)
+        plan.check()
+        assert plan.profile()["tcgen05" if prec == "bf16" else "simt"][1] == 1
+        got = fs[l].double().cpu().numpy()
+        err = np.abs(got - ref) / np.abs(ref)
+        print(f"cfg2 {prec} beta={beta} l={l}: frob {_frob(got, ref):.3e} max el {err.max():.3e} "
+              f"p99.9 {np.quantile(err, 0.999):.3e}")
+        if prec == "fp32":
+            assert _frob(got, ref) < 1e-5, (l, _frob(got, ref))
+            np.testing.assert_allclose(got, ref, rtol=3e-5, atol=0)
+        else:
+            np.testing.assert_allclose(got, ref, rtol=2e-3, atol=0)
+        for q in range(3):
+            if q != l:
+                assert torch.equal(fs[q].cpu(), torch.from_numpy(p.inits[0][q]))
+
+
+def test_config2_bf16_fit_loss_within_1e3():
+    """Three BF16 sweeps at 512^3 (KL): the final loss within 1e-3 relative of the
+    FP64 oracle's trace, and the loss trace summed inside the passes as well."""
+    nef = _nef()
+    p = _problem(0.0)
+    m = OracleModel(p.model_str, p.dims)
+    iters = 3
+    _, trace = m.fit(p.y, None, [f.astype(np.float64) for f in p.inits[0]], 1.0, 0.0, iters, trace=True)
+    plan = nef.Plan(p.model_str, p.dims, precision="bf16")
+    Y = dev(p.y)
+    fs = [dev(f) for f in p.inits[0]]
+    tr = torch.zeros(iters + 1, dtype=torch.float64, device="cuda")
+    plan.fit(Y, None, fs, 1.0, 0.0, iters, loss_trace=tr)
+    plan.check()
+    lo, cnt = plan.loss(Y, None, fs, 1.0, 0.0)
+    assert cnt == p.y.size
+    got = tr.cpu().numpy()
+    print("cfg2 bf16 trace", got, "oracle", trace)
+    assert lo == pytest.approx(trace[-1], rel=1e-3)
+    np.testing.assert_allclose(got, trace, rtol=1e-3)
+
+
+def test_config3_every_element_after_one_update():
+    nef = _nef()
+    p = synth.config3()
+    m = OracleModel(p.model_str, p.dims)
+    init = [f.astype(np.float64) for f in p.inits[0]]
+    plan = nef.Plan(p.model_str, p.dims, precision="bf16", profile=True)
+    Y, M = dev(p.y), dev(p.mask, torch.uint8)
+    for l in range(5):
+        ref = m.update_factor(l, p.y, p.mask, init, p.alpha, p.beta)[0][l]
+        fs = [dev(f) for f in p.inits[0]]
+        plan.update(l, Y, M, fs, p.alpha, p.beta)
+        plan.check()
+        assert plan.profile(reset=True)["tcgen05"][1] == 1, plan.info()
+        got = fs[l].double().cpu().numpy()
+        err = np.abs(got - ref) / np.abs(ref)
+        print(f"cfg3 bf16 l={l}: frob {_frob(got, ref):.3e} max el {err.max():.3e}")
+        np.testing.assert_allclose(got, ref, rtol=2e-3, atol=0)

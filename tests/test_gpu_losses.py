@@ -1,0 +1,197 @@
+"""GPU parity of the loss families beyond the (alpha, beta) cases of the main
+parity suite, through the C ABI against the FP64 oracle:
+
+  * reverse KL, (alpha, beta) = (0, 1): a = log(x / yhat), b = 1, the exponential
+    update of App. B's g-table (g = log);
+  * the likelihood families of App. B: negative binomial (dispersion phi),
+    binomial on the odds (n trials; n = 1 is Bernoulli) and Jensen-Shannon
+    (exponential update), selected by nef_options.loss.
+
+Tolerances as in the main parity suite: FP64 plans 1e-10, FP32 plans 3e-5
+(relative Frobenius, two sweeps), BF16 one update 2e-3 per element and the
+loss after several sweeps within 1e-3 of the oracle's trace.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import OracleModel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _nef():
+    import paper_2602_02759_gb300 as nef
+    return nef
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _data(kind, mean, rng, par):
+    """Data suited to each family: positive (Gamma-noise) values for reverse KL,
+    whose a = log(x / yhat) needs x > 0; Poisson-Gamma counts (negative binomial
+    with dispersion par) for the negative binomial; Binomial(n, yhat / (1 + yhat))
+    counts for the binomial on the odds; Poisson counts for Jensen-Shannon."""
+    if kind == "rkl":
+        return (mean * rng.gamma(2.0, 0.5, mean.shape)).astype(np.float32)
+    if kind == "negbin":
+        return rng.poisson(mean * rng.gamma(par, 1.0 / par, mean.shape)).astype(np.float32)
+    if kind == "binomial":
+        return rng.binomial(int(par), mean / (1.0 + mean)).astype(np.float32)
+    return rng.poisson(mean).astype(np.float32)
+
+
+MODELS = [
+    ("ir,jr,kr->ijk", dict(i=136, j=100, k=68, r=16)),         # staged Q rows, bond 16
+    ("ir,jr,kr->ijk", dict(i=160, j=96, k=192, r=64)),         # bond 64
+    ("ia,ja,ab,kb,lb->ijkl", dict(i=32, j=40, k=16, l=8, a=16, b=8)),
+    ("wr,dr,hr,irk,jrk->wdhij", dict(w=9, d=7, h=8, i=30, j=40, r=5, k=3)),  # gathered Q sources
+]
+KINDS = [("rkl", 0.0), ("negbin", 2.0), ("binomial", 1.0), ("binomial", 5.0), ("js", 0.0)]
+
+
+def _oracle_fit(m, kind, par, y, mask, init, iters, trace=False):
+    if kind == "rkl":
+        return m.fit(y, mask, init, 0.0, 1.0, iters, trace=trace)
+    ntr = np.full(m.y_shape, par) if kind == "binomial" else None
+    return m.lik_fit(y, mask, init, kind, iters, par=par, ntrials=ntr, trace=trace)
+
+
+def _oracle_update(m, kind, par, l, y, mask, init):
+    if kind == "rkl":
+        return m.update_factor(l, y, mask, init, 0.0, 1.0)[0][l]
+    ntr = np.full(m.y_shape, par) if kind == "binomial" else None
+    return m.lik_update_factor(l, y, mask, init, kind, par=par, ntrials=ntr)[0][l]
+
+
+def _plan(nef, model_str, dims, prec, kind, par, **kw):
+    if kind == "rkl":
+        return nef.Plan(model_str, dims, precision=prec, **kw)
+    return nef.Plan(model_str, dims, precision=prec, loss=kind, loss_par=par, **kw)
+
+
+def _ab(kind):
+    return (0.0, 1.0) if kind == "rkl" else (float("nan"), float("nan"))
+
+
+def _setup(model_str, dims, kind, par, seed, masked):
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(seed)
+    truth = [rng.gamma(0.5, 1.0, m.factor_shape(l)) for l in range(m.n_factors)]
+    y = _data(kind, np.einsum(model_str, *truth), rng, par)
+    mask = (rng.random(m.y_shape) > 0.2).astype(np.uint8) if masked else None
+    init = [rng.uniform(0.5, 1.5, m.factor_shape(l)) for l in range(m.n_factors)]
+    return m, y, mask, init
+
+
+@pytest.mark.parametrize("kind,par", KINDS)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("masked", [False, True])
+def test_cuda_core_two_sweeps(kind, par, prec, masked):
+    nef = _nef()
+    model_str, dims = "ia,ja,ab,kb,lb->ijkl", dict(i=9, j=30, k=13, l=20, a=5, b=3)
+    m, y, mask, init = _setup(model_str, dims, kind, par, 3, masked)
+    ref = _oracle_fit(m, kind, par, y, mask, init, 2)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = _plan(nef, model_str, dims, prec, kind, par)
+    fs = [dev(f, dt) for f in init]
+    a, b = _ab(kind)
+    plan.fit(dev(y, dt), None if mask is None else dev(mask, torch.uint8), fs, a, b, 2)
+    plan.check()
+    tol = 1e-10 if prec == "fp64" else 3e-5
+    for q in range(m.n_factors):
+        assert rel(fs[q].cpu().numpy(), ref[q]) < tol, (q, rel(fs[q].cpu().numpy(), ref[q]))
+
+
+@pytest.mark.parametrize("model_str,dims", MODELS)
+@pytest.mark.parametrize("kind,par", KINDS)
+def test_bf16_single_updates(model_str, dims, kind, par):
+    nef = _nef()
+    masked = model_str.startswith("ia") or model_str.startswith("wr")
+    m, y, mask, init = _setup(model_str, dims, kind, par, 7, masked)
+    plan = _plan(nef, model_str, dims, "bf16", kind, par, profile=True)
+    assert "generic" not in plan.info() and "simt" not in plan.info(), plan.info()
+    Y = dev(y)
+    M = None if mask is None else dev(mask, torch.uint8)
+    a, b = _ab(kind)
+    for l in range(m.n_factors):
+        ref = _oracle_update(m, kind, par, l, y, mask, init)
+        fs = [dev(f) for f in init]
+        plan.update(l, Y, M, fs, a, b)
+        plan.check()
+        assert plan.profile()["tcgen05"][1] == 1, "the tensor-core pass did not run"
+        got = fs[l].double().cpu().numpy()
+        assert np.all(np.isfinite(got))
+        np.testing.assert_allclose(got, ref, rtol=2e-3, atol=0, err_msg=f"factor {l}\n{plan.info()}")
+
+
+@pytest.mark.parametrize("kind,par", KINDS)
+def test_bf16_fit_loss_matches_oracle(kind, par):
+    nef = _nef()
+    model_str, dims = "ir,jr,kr->ijk", dict(i=200, j=132, k=256, r=32)
+    m, y, mask, init = _setup(model_str, dims, kind, par, 8, True)
+    iters = 12
+    _, trace = _oracle_fit(m, kind, par, y, mask, init, iters, trace=True)
+    plan = _plan(nef, model_str, dims, "bf16", kind, par)
+    fs = [dev(f) for f in init]
+    Y, M = dev(y), dev(mask, torch.uint8)
+    tr = torch.zeros(iters + 1, dtype=torch.float64, device="cuda")
+    a, b = _ab(kind)
+    plan.fit(Y, M, fs, a, b, iters, loss_trace=tr)
+    plan.check()
+    lo, cnt = plan.loss(Y, M, fs, a, b)
+    assert cnt == int(mask.sum())
+    assert lo == pytest.approx(trace[-1], rel=1e-3)
+    np.testing.assert_allclose(tr.cpu().numpy(), trace, rtol=1e-3)
+
+
+@pytest.mark.parametrize("kind,par", [("negbin", 2.0), ("binomial", 1.0), ("js", 0.0)])
+def test_likelihood_512cube_whole_factor(kind, par):
+    """512^3 rank-64 CP (the benchmark's shape) under each likelihood family:
+    one update of factor A, every element against the oracle."""
+    nef = _nef()
+    p = synth.config2()
+    m = OracleModel(p.model_str, p.dims)
+    rng = np.random.default_rng(17)
+    mean = np.einsum(p.model_str, *p.truth, optimize=True)
+    y = _data(kind, mean, rng, par)
+    del mean
+    init = [f.astype(np.float64) for f in p.inits[0]]
+    ref = _oracle_update(m, kind, par, 0, y, None, init)
+    plan = _plan(nef, p.model_str, p.dims, "bf16", kind, par, profile=True)
+    fs = [dev(f) for f in p.inits[0]]
+    plan.update(0, dev(y), None, fs, float("nan"), float("nan"))
+    plan.check()
+    assert plan.profile()["tcgen05"][1] == 1
+    got = fs[0].double().cpu().numpy()
+    err = np.abs(got - ref) / np.abs(ref)
+    print(f"512^3 {kind}: max el {err.max():.3e}")
+    np.testing.assert_allclose(got, ref, rtol=2e-3, atol=0)
+
+
+def test_bf16_loss_runs_on_tensor_cores():
+    """nef_loss of a BF16 plan reconstructs on the tensor cores (one tcgen05 pass)
+    and agrees with the oracle's loss to well inside 1e-3."""
+    nef = _nef()
+    model_str, dims = "ir,jr,kr->ijk", dict(i=200, j=132, k=256, r=32)
+    m, y, mask, init = _setup(model_str, dims, "negbin", 2.0, 9, False)
+    for kind, par, ab in (("ab", 0.0, (1.0, 0.0)), ("negbin", 2.0, (0.0, 0.0)), ("js", 0.0, (0.0, 0.0))):
+        plan = nef.Plan(model_str, dims, precision="bf16", profile=True, loss=kind, loss_par=par)
+        fs = [dev(f) for f in init]
+        lo, cnt = plan.loss(dev(y), None, fs, *ab)
+        assert plan.profile()["tcgen05"][1] == 1
+        if kind == "ab":
+            ref, rc = m.loss(y, None, init, *ab)
+        else:
+            ref, rc = m.lik_loss(y, None, init, kind, par=par)
+        assert cnt == rc
+        assert lo == pytest.approx(ref, rel=1e-5), kind

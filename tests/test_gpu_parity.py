@@ -19,6 +19,17 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+
+def _probe():
+    """The test-only probe library (tests/tc_probe): layout probe and GEMM alone."""
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tc_probe", "build.py")
+    spec = importlib.util.spec_from_file_location("nef_probe_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.load()
+
 def _nef():
     import paper_2602_02759_gb300 as nef
     return nef
@@ -53,7 +64,7 @@ def test_tc_probe_layouts(bp, a_in_tmem):
     D1 = torch.zeros(128, 64, device="cuda")
     D2 = torch.zeros(128, bp, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    lib = nef.load()
+    lib = _probe()
     rc = lib.nef_tc_probe(bp, a_in_tmem, tP.data_ptr(), tQ.data_ptr(), tW.data_ptr(), D1.data_ptr(), D2.data_ptr(),
                           err.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()

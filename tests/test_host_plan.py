@@ -22,11 +22,8 @@ from oracle import OracleModel  # noqa: E402
 NEF_FP32, NEF_BF16, NEF_FP64 = 0, 1, 2
 
 
-class Opt(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double),
-                ("check_data", ctypes.c_int), ("force_generic", ctypes.c_int),
-                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("eager", ctypes.c_int)]
+# the options struct of include/nef.h, as the binding declares it (one layout for both)
+from paper_2602_02759_gb300._nef import Options as Opt  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -464,5 +461,90 @@ def test_autotune_cache_roundtrip(lib, tmp_path):
         ref = m.fit(y, None, [f.copy() for f in fs], 1.0, 0.0, 3)
         for l in range(3):
             assert np.linalg.norm(work[l] - ref[l]) / np.linalg.norm(ref[l]) < 1e-10
+    finally:
+        lib.nef_plan_destroy(h)
+
+
+LIK = {"negbin": 1, "binomial": 2, "js": 3}
+
+
+def make_lik_plan(lib, model_str, dims, prec, kind, par):
+    obs, lat, _ = split(model_str)
+    shapes = (ctypes.c_int64 * max(1, len(obs)))(*[dims[c] for c in obs])
+    ranks = (ctypes.c_int64 * max(1, len(lat)))(*[dims[c] for c in lat])
+    o = Opt()
+    lib.nef_default_options(ctypes.byref(o))
+    o.precision = prec
+    o.loss = LIK[kind]
+    o.loss_par = par
+    h = ctypes.c_void_p()
+    rc = lib.nef_plan(model_str.encode(), shapes, len(obs), ranks, len(lat), ctypes.byref(o), ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("model_str,dims", [MODELS[0], MODELS[4], MODELS[5], MODELS[8]])
+@pytest.mark.parametrize("prec", [NEF_FP64, NEF_FP32])
+@pytest.mark.parametrize("kind,par", [("negbin", 2.5), ("binomial", 1.0), ("binomial", 6.0), ("js", 0.0)])
+@pytest.mark.parametrize("masked", [False, True])
+def test_likelihood_fit_matches_oracle(lib, model_str, dims, prec, kind, par, masked):
+    """The likelihood families of App. B (negative binomial, binomial on the odds,
+    Jensen-Shannon) through the planner and sweep driver: two sweeps and the loss
+    against the oracle's or_lik_fit / or_lik_loss (the alpha, beta arguments are
+    ignored by these families)."""
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(hash((model_str, kind, par, masked)) % 2**32)
+    dt = np.float64 if prec == NEF_FP64 else np.float32
+    fs = [rng.uniform(0.3, 1.2, size=m.factor_shape(l)).astype(dt) for l in range(m.n_factors)]
+    if kind == "binomial":
+        y = rng.integers(0, int(par) + 1, size=m.y_shape).astype(dt)
+    else:
+        y = rng.poisson(1.5, size=m.y_shape).astype(dt)
+    mask = (rng.random(m.y_shape) > 0.3).astype(np.uint8) if masked else None
+    ntr = None if kind != "binomial" else np.full(m.y_shape, par)
+    rc, h = make_lik_plan(lib, model_str, dims, prec, kind, par)
+    assert rc == 0, lib.nef_last_error()
+    try:
+        ref = m.lik_fit(y, mask, [f.astype(np.float64) for f in fs], kind, 2, par=par, ntrials=ntr)
+        work = [f.copy() for f in fs]
+        rc = lib.nef_fit(h, y.ctypes.data, None if mask is None else mask.ctypes.data, facs_arr(work),
+                         float("nan"), float("nan"), 2)
+        assert rc == 0, lib.nef_last_error()
+        tol = 1e-10 if prec == NEF_FP64 else 3e-5
+        for l in range(m.n_factors):
+            rel = np.linalg.norm(work[l] - ref[l]) / np.linalg.norm(ref[l])
+            assert rel < tol, (l, rel, info(lib, h))
+        out = (ctypes.c_double * 2)()
+        assert lib.nef_loss(h, y.ctypes.data, None if mask is None else mask.ctypes.data, facs_arr(work),
+                            0.0, 0.0, out) == 0, lib.nef_last_error()
+        lref, cnt = m.lik_loss(y, mask, [w.astype(np.float64) for w in work], kind, par=par, ntrials=ntr)
+        assert out[1] == cnt
+        assert out[0] == pytest.approx(lref, rel=1e-9 if prec == NEF_FP64 else 1e-5)
+    finally:
+        lib.nef_plan_destroy(h)
+
+
+def test_likelihood_plan_argument_checks(lib):
+    """A dispersion or trial count outside (0, inf) and an unknown family are
+    rejected at plan time; the (alpha, beta) family still checks its arguments."""
+    for kind, par in (("negbin", 0.0), ("negbin", -1.0), ("binomial", 0.0), ("binomial", float("inf"))):
+        rc, h = make_lik_plan(lib, "ir,jr,kr->ijk", dict(i=3, j=3, k=3, r=2), NEF_FP64, kind, par)
+        assert rc == 1 and not h.value, (kind, par)
+    o = Opt()
+    lib.nef_default_options(ctypes.byref(o))
+    assert o.loss == 0 and o.loss_par == 0.0 and o.wait_cycles == 0
+    o.loss = 9
+    h = ctypes.c_void_p()
+    shapes = (ctypes.c_int64 * 3)(3, 3, 3)
+    ranks = (ctypes.c_int64 * 1)(2)
+    assert lib.nef_plan(b"ir,jr,kr->ijk", shapes, 3, ranks, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    o.loss = 0
+    o.wait_cycles = -1
+    assert lib.nef_plan(b"ir,jr,kr->ijk", shapes, 3, ranks, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    rc, h = make_plan(lib, "ir,jr,kr->ijk", dict(i=3, j=3, k=3, r=2), NEF_FP64)
+    try:
+        y = np.ones((3, 3, 3))
+        fs = [np.ones((3, 2)) for _ in range(3)]
+        assert lib.nef_fit(h, y.ctypes.data, None, facs_arr(fs), float("nan"), 0.0, 1) == 1
+        assert lib.nef_fit(h, y.ctypes.data, None, facs_arr(fs), 0.0, 0.5, 1) == 3
     finally:
         lib.nef_plan_destroy(h)
