@@ -1358,6 +1358,8 @@ nef_status loss_pass(nef_plan_t p, const T* y, const uint32_t* mbits, void* cons
     bool use_tc = false;
     if constexpr (sizeof(T) == 4) use_tc = p->prec == NEF_BF16 && tc_view_supported(bind_view(p, pp, true), need_den);
     NEF_TRY(refresh_sources<T>(p, pp, factors, st, use_tc));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->opt.profile) NEF_TRY(prof_begin(p, st, &e0, &e1));
     if (use_tc) {
         if constexpr (sizeof(T) == 4) {
             ViewDesc v = bind_view(p, pp, true);
@@ -1368,13 +1370,17 @@ nef_status loss_pass(nef_plan_t p, const T* y, const uint32_t* mbits, void* cons
                                     p->loss_part, p->opt.wait_cycles));
             *n_part = info.n_ctas;
         }
-        return NEF_OK;
+    } else {
+        ViewDesc v = bind_view(p, pp, false);
+        const int64_t tm = sizeof(T) == 8 ? 32 : 64;
+        const int64_t n_rb = (v.rows + tm - 1) / tm;
+        int ns = (int)std::max<int64_t>(1, std::min<int64_t>(pp.n_split, p->loss_part_cap / 2 / n_rb));
+        NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, 0, ns, nullptr, nullptr, &L, p->loss_part, st, n_part));
     }
-    ViewDesc v = bind_view(p, pp, false);
-    const int64_t tm = sizeof(T) == 8 ? 32 : 64;
-    const int64_t n_rb = (v.rows + tm - 1) / tm;
-    int ns = (int)std::max<int64_t>(1, std::min<int64_t>(pp.n_split, p->loss_part_cap / 2 / n_rb));
-    NEF_CUDA(launch_view_simt<T>(y, mbits, v, w, 0, ns, nullptr, nullptr, &L, p->loss_part, st, n_part));
+    if (p->opt.profile) {
+        NEF_CUDA(cudaEventRecord(e1, st));
+        p->ev_used.push_back({use_tc ? 0 : 1, {e0, e1}});
+    }
     return NEF_OK;
 }
 
