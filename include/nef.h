@@ -149,8 +149,8 @@ void nef_plan_destroy(nef_plan_t plan);
  *   iters   : number of sweeps (0 is a no-op)
  * The loss of the current factors is summed inside the first pass of every
  * sweep (its Yhat is already on chip) when opt.loss_trace or opt.tol asks for
- * it; one extra loss pass follows the last sweep.  With tol > 0 the stream is
- * synchronised once per sweep to read the loss; nef_plan_sweeps reports how
+ * it; one extra loss pass follows the last sweep.  With tol > 0 the stopping
+ * rule runs on the device (as in nef_fit_ctl); nef_plan_sweeps reports how
  * many sweeps ran.
  * Errors: NEF_EUNSUPPORTED for alpha == 0 with beta != 1 (NEF_LOSS_AB plans);
  * NEF_EINVAL for a null pointer, iters < 0 or a non-finite alpha or beta;
@@ -171,7 +171,48 @@ nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask,
 nef_status nef_fit_ex(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
                       double alpha, double beta, int iters, double tol, double* loss_trace, int* sweeps);
 
-/* Number of sweeps the last nef_fit on `plan` ran (iters unless tol stopped it). */
+/*
+ * Stopping rules of App. B evaluated on the device, for nef_fit_ctl:
+ *   tol          > 0: stop after the first sweep k >= 2 whose preceding relative
+ *                training-loss decrease (L[k-2] - L[k-1]) / L[k-2] is below tol,
+ *                L[k] being Eq. 3.1's objective after k sweeps (as nef_options.tol);
+ *   val_mask     device, N bytes (nonzero = validation entry), or NULL: the
+ *                held-out entries whose loss V[k] (sum of D over them, after k
+ *                sweeps) is evaluated after every sweep; normally disjoint from
+ *                the training mask;
+ *   val_patience > 0 (with val_mask): stop after the sweep k whose V[k] exceeded
+ *                V[k-1] for the val_patience-th time in a row (App. B uses 5);
+ *   loss_trace   device, iters + 1 doubles, or NULL: L[0..]; entries past the
+ *                stop are left untouched;
+ *   val_trace    device, iters + 1 doubles, or NULL: V[0..] (needs val_mask).
+ * The iteration cap is nef_fit_ctl's iters.  Each validation evaluation is one
+ * more pass over Y per sweep.
+ */
+typedef struct {
+    double tol;
+    double* loss_trace;
+    const uint8_t* val_mask;
+    int val_patience;
+    double* val_trace;
+} nef_fit_control;
+
+/*
+ * nef_fit_ctl -- nef_fit under the stopping rules of *ctl (NULL = none: exactly
+ * iters sweeps).  With a rule, the loop runs entirely on the device: sweeps 2..
+ * are the body of a CUDA-graph conditional (while) node whose last kernel
+ * applies the rules and ends the loop, so the host does not wait between
+ * sweeps (with opt.eager the host reads the decision after every sweep).
+ *   sweeps : host, receives the number of sweeps run, or NULL (reading it
+ *            synchronises the stream; nef_plan_sweeps gives it later)
+ * Errors as nef_fit, plus NEF_EINVAL for tol < 0, val_patience < 0, or
+ * val_trace / val_patience without val_mask.
+ */
+nef_status nef_fit_ctl(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors, double alpha,
+                       double beta, int iters, const nef_fit_control* ctl, int* sweeps);
+
+/* Number of sweeps the last nef_fit on `plan` ran (iters unless a stopping rule
+ * ended it earlier).  Synchronises the plan's stream when the count is still on
+ * the device (fits with a stopping rule). */
 int nef_plan_sweeps(nef_plan_t plan);
 
 /*

@@ -21,7 +21,7 @@ STATUS = {0: "NEF_OK", 1: "NEF_EINVAL", 2: "NEF_EPARSE", 3: "NEF_EUNSUPPORTED", 
 PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 
 # every symbol include/nef.h declares
-EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex",
+EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex", "nef_fit_ctl",
            "nef_plan_sweeps", "nef_plan_autotune", "nef_update", "nef_loss", "nef_plan_info", "nef_plan_launches",
            "nef_plan_profile", "nef_tc_trace", "nef_check", "nef_fit_batched", "nef_cp3_update_static",
            "nef_last_error",
@@ -35,6 +35,11 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("eager", ctypes.c_int),
                 ("loss", ctypes.c_int), ("loss_par", ctypes.c_double), ("wait_cycles", ctypes.c_int64)]
+
+
+class FitControl(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("val_mask", ctypes.c_void_p),
+                ("val_patience", ctypes.c_int), ("val_trace", ctypes.c_void_p)]
 
 
 class NefError(RuntimeError):
@@ -66,6 +71,9 @@ def load(path: str = LIB_PATH):
     lib.nef_fit_ex.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
                                ctypes.c_int, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int)]
     lib.nef_fit_ex.restype = ctypes.c_int
+    lib.nef_fit_ctl.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                                ctypes.c_int, ctypes.POINTER(FitControl), ctypes.POINTER(ctypes.c_int)]
+    lib.nef_fit_ctl.restype = ctypes.c_int
     lib.nef_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
                                       ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
     lib.nef_plan_autotune.restype = ctypes.c_int
@@ -280,20 +288,33 @@ class Plan:
                 raise ValueError(f"factor {t} must be a contiguous CUDA {want} tensor of shape {shp}")
 
     # -------------------------------------------------------------- ABI
-    def fit(self, Y, mask, factors, alpha, beta, iters, tol: float = 0.0, loss_trace=None):
-        """Run `iters` sweeps (nef_fit_ex).  ``loss_trace``: a float64 CUDA tensor of
-        at least iters + 1 entries that receives the loss after each sweep;
-        ``tol`` > 0 stops early.  Returns the number of sweeps run."""
+    def fit(self, Y, mask, factors, alpha, beta, iters, tol: float = 0.0, loss_trace=None,
+            val_mask=None, val_patience: int = 0, val_trace=None, sweeps: bool = True):
+        """Run up to `iters` sweeps (nef_fit_ctl).  ``loss_trace`` / ``val_trace``:
+        float64 CUDA tensors of at least iters + 1 entries receiving the training
+        loss / the loss over ``val_mask`` (a uint8 CUDA tensor shaped like Y) after
+        each sweep; ``tol`` > 0 and ``val_patience`` > 0 are App. B's stopping rules,
+        evaluated on the device.  Returns the number of sweeps run (reading it
+        synchronises the stream; ``sweeps=False`` returns None without waiting)."""
+        import torch
+        self._check_args(Y, val_mask, factors)
         self._check_args(Y, mask, factors)
-        if loss_trace is not None:
-            import torch
-            if loss_trace.dtype != torch.float64 or not loss_trace.is_cuda or loss_trace.numel() < int(iters) + 1:
-                raise ValueError("loss_trace must be a float64 CUDA tensor with iters + 1 entries")
+        for name, tr in (("loss_trace", loss_trace), ("val_trace", val_trace)):
+            if tr is not None and (tr.dtype != torch.float64 or not tr.is_cuda or tr.numel() < int(iters) + 1):
+                raise ValueError(f"{name} must be a float64 CUDA tensor with iters + 1 entries")
+        def addr(t):
+            return None if t is None else t.data_ptr()
+
+        ctl = FitControl(float(tol), addr(loss_trace), addr(val_mask), int(val_patience), addr(val_trace))
         done = ctypes.c_int(0)
-        check(load().nef_fit_ex(self._h, self._ptr(Y), self._ptr(mask), self._facs(factors),
-                                float(alpha), float(beta), int(iters), float(tol),
-                                self._ptr(loss_trace), ctypes.byref(done)))
-        return int(done.value)
+        check(load().nef_fit_ctl(self._h, self._ptr(Y), self._ptr(mask), self._facs(factors),
+                                 float(alpha), float(beta), int(iters), ctypes.byref(ctl),
+                                 ctypes.byref(done) if sweeps else None))
+        return int(done.value) if sweeps else None
+
+    def sweeps(self) -> int:
+        """Sweeps run by the last fit (nef_plan_sweeps)."""
+        return int(load().nef_plan_sweeps(self._h))
 
     def autotune(self, Y, mask, factors, alpha, beta, cache=None):
         """Time candidate column splits of every fused pass (nef_plan_autotune);

@@ -248,13 +248,17 @@ __global__ void k_loss_append(const double* __restrict__ part, int n, double* tr
     }
 }
 
-__global__ void k_convert_bf16(const float* __restrict__ src, int64_t n, uint16_t* __restrict__ dst) {
+// BF16 copy of an operand, and the FP32 operand replaced by the same rounded
+// values, so that whatever else reads the FP32 copy (closed-form denominators,
+// epilogue contractions) sees exactly the operand the tensor cores multiply.
+__global__ void k_convert_bf16(float* __restrict__ src, int64_t n, uint16_t* __restrict__ dst) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     // round to nearest even
     uint32_t u = __float_as_uint(src[e]);
     uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);
     dst[e] = (uint16_t)(r >> 16);
+    src[e] = __uint_as_float(r & 0xffff0000u);
 }
 
 // Unfused path: yhat at every entry by a loop over all latent combinations,
@@ -337,13 +341,23 @@ __device__ __forceinline__ void decode_letters(int64_t e, int nlet, const int64_
     }
 }
 
+// The factor's operand copies.  A copy with a BF16 twin (BF16 plans) holds the
+// BF16-rounded value in its own element type too, so that the closed-form
+// denominators and contracted operands built from it see exactly the factor the
+// tensor cores multiply (otherwise the rounding of a whole factor column biases
+// num/den of that column, and the exponential updates scale the bias by num/den).
 template <typename T>
 __device__ __forceinline__ void write_mirrors(const MirrorDesc& m, const int64_t* idx, int nlet, T v) {
     for (int k = 0; k < m.n; ++k) {
         int64_t off = 0;
         for (int q = 0; q < nlet; ++q) off += idx[q] * m.st[k][q];
-        static_cast<T*>(m.p32[k])[off] = v;
-        if (m.p16[k]) m.p16[k][off] = bf16_bits((float)v);
+        if (m.p16[k]) {
+            const uint16_t b = bf16_bits((float)v);
+            m.p16[k][off] = b;
+            static_cast<T*>(m.p32[k])[off] = (T)__uint_as_float((uint32_t)b << 16);
+        } else {
+            static_cast<T*>(m.p32[k])[off] = v;
+        }
     }
 }
 
@@ -559,7 +573,30 @@ cudaError_t launch_loss_append(const double* part, int n, double* trace, int* co
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st) {
+// The stopping rules of App. B on the device (one thread, fit_rule_step); inside
+// a graph loop the result also becomes the loop's condition.
+__global__ void k_fit_check(FitCtlState* s, const double* out_loss, const double* out_val,
+                            cudaGraphConditionalHandle handle, int set_handle, int mode) {
+    const int cont = fit_rule_step(s, out_loss, out_val, mode);
+    if (set_handle && mode == 0) cudaGraphSetConditional(handle, cont ? 1u : 0u);
+}
+
+__global__ void k_fit_set_cond(const FitCtlState* s, cudaGraphConditionalHandle handle) {
+    cudaGraphSetConditional(handle, s->cont ? 1u : 0u);
+}
+
+cudaError_t launch_fit_check(FitCtlState* s, const double* out_loss, const double* out_val,
+                             cudaGraphConditionalHandle handle, int set_handle, int mode, cudaStream_t st) {
+    k_fit_check<<<1, 1, 0, st>>>(s, out_loss, out_val, handle, set_handle, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_set_cond(const FitCtlState* s, cudaGraphConditionalHandle handle, cudaStream_t st) {
+    k_fit_set_cond<<<1, 1, 0, st>>>(s, handle);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_bf16(float* src, int64_t n, uint16_t* dst, cudaStream_t st) {
     k_convert_bf16<<<blocks_for(n), kThreads, 0, st>>>(src, n, dst);
     return cudaGetLastError();
 }

@@ -76,7 +76,7 @@ int weight_kind(const WeightSpec& w) {
         case LIK_JS: return tc::WK_JS;
         default: break;
     }
-    if (w.log_case) return tc::WK_GEN;
+    if (w.log_case) return tc::WK_RKL;
     if (w.y_code == POW_ID && w.a_code == POW_RCP && w.b_code == POW_ONE) return tc::WK_KL;
     if (w.y_code == POW_ID && w.a_code == POW_RSQRT3 && w.b_code == POW_RSQRT) return tc::WK_B05;
     if (w.y_code == POW_SQRT && w.a_code == POW_RSQRT && w.b_code == POW_ONE) return tc::WK_HEL;
@@ -209,8 +209,8 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         {{tc::launch_bp16_g, tc::launch_bp32_g, tc::launch_bp64_g}, {tc::launch_bp16, tc::launch_bp32, tc::launch_bp64}},
         {{tc::launch_bp16_g_loss, tc::launch_bp32_g_loss, tc::launch_bp64_g_loss},
          {tc::launch_bp16_loss, tc::launch_bp32_loss, tc::launch_bp64_loss}}};
-    // the likelihood families have their own instances for staged Q rows; with
-    // gathered rows they run through the generic weight kind
+    // reverse KL and the likelihood families have their own instances for staged Q
+    // rows; with gathered rows they run through the generic weight kind
     static const LaunchFn lik_table[2][3] = {
         {tc::launch_bp16_lik, tc::launch_bp32_lik, tc::launch_bp64_lik},
         {tc::launch_bp16_lik_loss, tc::launch_bp32_lik_loss, tc::launch_bp64_lik_loss}};

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "nef_batched.h"
 #include "nef_device.cuh"
@@ -81,7 +82,7 @@ constexpr long long kWaitCycles = 4000000000LL;
 // (1,-1/2) and (1/2,1/2), the likelihood families negative binomial, binomial on
 // the odds and Jensen-Shannon, and the generic evaluation (any (alpha,beta) or
 // family, selected at run time).
-enum WeightKind { WK_GEN = 0, WK_KL = 1, WK_B05 = 2, WK_HEL = 3, WK_NB = 4, WK_BIN = 5, WK_JS = 6 };
+enum WeightKind { WK_GEN = 0, WK_KL = 1, WK_B05 = 2, WK_HEL = 3, WK_NB = 4, WK_BIN = 5, WK_JS = 6, WK_RKL = 7 };
 
 struct Params {
     const uint32_t* mbits;
@@ -456,22 +457,23 @@ __device__ __forceinline__ uint32_t warp_transpose_bits(uint32_t x, int lane) {
 
 // One loss term D(y, yhat) in FP32 (App. B).  For KL the weight a = y / yhat
 // is already at hand: D = y log(a) - y + yhat.
-// For Jensen-Shannon a = log((y + yhat) / (2 yhat)) = -log(yhat / m), m = (y + yhat)/2,
-// so D = (y log(y/m) + yhat log(yhat/m)) / 2 = (y log(y/m) - yhat a) / 2.
-template <int WK>
-__device__ __forceinline__ float tc_loss(float y, float yh, float a, const LossSpec& L) {
-    if (WK == WK_KL) return (y > 0.f ? y * __logf(a) : 0.f) - y + yh;
-    if (WK == WK_JS) {
-        const float m = 0.5f * (y + yh);
-        return 0.5f * ((y > 0.f ? y * __logf(__fdividef(y, m)) : 0.f) - yh * a);
-    }
-    return divergence<float>(y, yh, L);
+// log2 by one SFU operation, subnormals flushed; the loss terms built from it are
+// summed over many entries in FP64, far beyond what its ~2^-22 error can change.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
+constexpr float kLn2 = 0.69314718056f;
+constexpr float kTiny = 1.17549435e-38f;  // smallest normal float
 
 template <int WK>
 __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& w, float& wa, float& wb) {
     if (WK == WK_KL) {
         wa = __fdividef(y, yh);
+        wb = 1.0f;
+    } else if (WK == WK_RKL) {
+        wa = kLn2 * lg2_approx(__fdividef(y, yh));
         wb = 1.0f;
     } else if (WK == WK_NB) {
         const float phi = (float)w.par;
@@ -481,7 +483,7 @@ __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& 
         wa = __fdividef(y, yh);
         wb = __fdividef((float)w.par, 1.0f + yh);
     } else if (WK == WK_JS) {
-        wa = __logf(__fdividef(0.5f * (y + yh), yh));
+        wa = kLn2 * lg2_approx(__fdividef(0.5f * (y + yh), yh));
         wb = 1.0f;
     } else if (WK == WK_B05) {
         const float r = rsqrt_approx(yh);
@@ -493,6 +495,40 @@ __device__ __forceinline__ void tc_weights(float y, float yh, const WeightSpec& 
     } else {
         ab_weights(y, yh, w, wa, wb);
     }
+}
+
+// One loss term D(y, yhat) in FP32 (App. B), from the weights already at hand
+// where the kind allows (a, b: the FP32 weights of tc_weights):
+//   KL (1,0):        D = y ln(y/yhat) - y + yhat, a = y/yhat (a floored at the
+//                    smallest normal float, so y = 0 gives 0 * finite = 0);
+//   reverse KL (0,1): D = yhat ln(yhat/y) - yhat + y = y - yhat (1 + a), a = ln(y/yhat);
+//   (1,-1/2):        D = 2y/sqrt(yhat) + 2 sqrt(yhat) - 4 sqrt(y) = 2 b (y + yhat) - 4 sqrt(y),
+//                    b = 1/sqrt(yhat);
+//   (1/2,1/2):       D = 2 (sqrt(y) - sqrt(yhat))^2 = 2 (y + yhat (1 - 2a)), a = sqrt(y/yhat);
+//   Jensen-Shannon:  a = ln((y + yhat)/(2 yhat)) = -ln(yhat/m), m = (y + yhat)/2, so
+//                    D = (y ln(y/m) + yhat ln(yhat/m))/2 = (y ln(y/m) - yhat a)/2;
+//   negative binomial: D = (phi + y) ln(phi + yhat) - y ln yhat;
+//   binomial on odds:  D = n ln(1 + yhat) - y ln yhat;
+//   otherwise the generic five-case divergence.
+template <int WK>
+__device__ __forceinline__ float tc_loss(float y, float yh, float a, float b, const LossSpec& L) {
+    if (WK == WK_KL) return fmaf(y * kLn2, lg2_approx(fmaxf(a, kTiny)), yh - y);
+    if (WK == WK_RKL) return fmaf(-yh, 1.0f + a, y);
+    if (WK == WK_B05) return fmaf(2.0f * b, y + yh, -4.0f * sqrt_approx(y));
+    if (WK == WK_HEL) return 2.0f * fmaf(yh, fmaf(-2.0f, a, 1.0f), y);
+    if (WK == WK_JS) {
+        const float m = 0.5f * (y + yh);
+        const float ly = y > 0.f ? y * (kLn2 * lg2_approx(__fdividef(y, m))) : 0.f;
+        return 0.5f * (ly - yh * a);
+    }
+    if (WK == WK_NB) {
+        const float phi = (float)L.par;
+        return kLn2 * ((phi + y) * lg2_approx(phi + yh) - (y > 0.f ? y * lg2_approx(yh) : 0.f));
+    }
+    if (WK == WK_BIN) {
+        return kLn2 * ((float)L.par * lg2_approx(1.0f + yh) - (y > 0.f ? y * lg2_approx(yh) : 0.f));
+    }
+    return divergence<float>(y, yh, L);
 }
 
 __device__ __forceinline__ int64_t src_row_tc(const SrcDesc& s, int64_t i) {
@@ -1139,20 +1175,34 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 }
                 uint32_t wa2[16], wb2[16];
                 float t = 0.f;  // loss terms of the observed entries (FP32 within the half)
+                // weights of the 32 entries (and their loss terms); a half whose entries are
+                // all observed and in range (every full tile of an unmasked view) sums the
+                // loss terms without a per-entry test
+                auto weights_half = [&](auto all_tag) {
+                    constexpr bool ALL = decltype(all_tag)::value;
 #pragma unroll
-                for (int c = 0; c < 32; c += 2) {
-                    float a0, b0, a1, b1;
-                    tc_weights<WK>(yv[c], __uint_as_float(yh[c]), w, a0, b0);
-                    tc_weights<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), w, a1, b1);
-                    wa2[c >> 1] = pack_bf16(a0, a1);
-                    if (DEN) wb2[c >> 1] = pack_bf16(b0, b1);
-                    if (do_loss) {
-                        const float d0 = tc_loss<WK>(yv[c], __uint_as_float(yh[c]), a0, prm.L);
-                        const float d1 = tc_loss<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), a1, prm.L);
-                        t += ((obs >> c) & 1u) ? d0 : 0.f;
-                        t += ((obs >> (c + 1)) & 1u) ? d1 : 0.f;
+                    for (int c = 0; c < 32; c += 2) {
+                        float a0, b0, a1, b1;
+                        tc_weights<WK>(yv[c], __uint_as_float(yh[c]), w, a0, b0);
+                        tc_weights<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), w, a1, b1);
+                        wa2[c >> 1] = pack_bf16(a0, a1);
+                        if (DEN) wb2[c >> 1] = pack_bf16(b0, b1);
+                        if (do_loss) {
+                            const float d0 = tc_loss<WK>(yv[c], __uint_as_float(yh[c]), a0, b0, prm.L);
+                            const float d1 = tc_loss<WK>(yv[c + 1], __uint_as_float(yh[c + 1]), a1, b1, prm.L);
+                            if constexpr (ALL) {
+                                t += d0 + d1;
+                            } else {
+                                t += ((obs >> c) & 1u) ? d0 : 0.f;
+                                t += ((obs >> (c + 1)) & 1u) ? d1 : 0.f;
+                            }
+                        }
                     }
-                }
+                };
+                if (do_loss && !DEN && obs == 0xffffffffu)
+                    weights_half(std::true_type{});
+                else
+                    weights_half(std::false_type{});
                 if (do_loss) {
                     lsum += (double)t;
                     lcnt += (double)__popc(obs);

@@ -34,20 +34,25 @@ cudaError_t launch_bp(const CUtensorMap& map, const CUtensorMap& vmap, const CUt
     }
 }
 
-// The likelihood families' weight kinds (negative binomial and binomial always
-// contract the denominator; Jensen-Shannon has b == 1 and takes the closed form
+// The weight kinds of the other loss families: reverse KL (0,1) and the
+// likelihood families (negative binomial and binomial always contract the
+// denominator; Jensen-Shannon and reverse KL have b == 1 and take the closed form
 // when there is no mask).
 template <int BP, bool LOSS, int QM>
 cudaError_t launch_bp_lik(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p,
                           int den, int wk, int grid, cudaStream_t st) {
     if (!den) {
-        if (wk == WK_JS) return launch_one<BP, false, WK_JS, LOSS, QM>(map, vmap, cmap, p, grid, st);
-        return cudaErrorInvalidValue;
+        switch (wk) {
+            case WK_JS: return launch_one<BP, false, WK_JS, LOSS, QM>(map, vmap, cmap, p, grid, st);
+            case WK_RKL: return launch_one<BP, false, WK_RKL, LOSS, QM>(map, vmap, cmap, p, grid, st);
+            default: return cudaErrorInvalidValue;
+        }
     }
     switch (wk) {
         case WK_NB: return launch_one<BP, true, WK_NB, LOSS, QM>(map, vmap, cmap, p, grid, st);
         case WK_BIN: return launch_one<BP, true, WK_BIN, LOSS, QM>(map, vmap, cmap, p, grid, st);
         case WK_JS: return launch_one<BP, true, WK_JS, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        case WK_RKL: return launch_one<BP, true, WK_RKL, LOSS, QM>(map, vmap, cmap, p, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }

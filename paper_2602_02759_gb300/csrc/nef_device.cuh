@@ -127,6 +127,38 @@ __device__ __forceinline__ T divergence(T x, T y, const LossSpec& L) {
     }
 }
 
+// The stopping rules of App. B applied after one sweep (mode 0) or recording V[0]
+// before the first sweep (mode 1); returns the loop's new condition (1 = go on).
+// Training loss: stop once the relative decrease (L[k-2] - L[k-1]) / L[k-2] falls
+// below tol; validation loss: stop once it rose `patience` sweeps in a row; and
+// the sweep cap.
+__host__ __device__ inline int fit_rule_step(FitCtlState* s, const double* out_loss, const double* out_val,
+                                             int mode) {
+    if (mode == 1) {
+        s->prev_val = out_val[0];
+        s->have_val = 1;
+        return s->cont;
+    }
+    s->done += 1;
+    bool stop = s->done >= s->iters;
+    if (out_loss) {
+        const double l = out_loss[0];
+        if (s->tol > 0.0 && s->have_loss && s->prev_loss != 0.0 && (s->prev_loss - l) / s->prev_loss < s->tol)
+            stop = true;
+        s->prev_loss = l;
+        s->have_loss = 1;
+    }
+    if (out_val) {
+        const double v = out_val[0];
+        s->rises = (s->have_val && v > s->prev_val) ? s->rises + 1 : 0;
+        if (s->patience > 0 && s->rises >= s->patience) stop = true;
+        s->prev_val = v;
+        s->have_val = 1;
+    }
+    s->cont = stop ? 0 : 1;
+    return s->cont;
+}
+
 // Eq. 3.4 for one element; den == 0 keeps theta.
 template <typename T>
 __device__ __forceinline__ T mu_update(T theta, T num, T den, const UpdateSpec& u) {

@@ -233,7 +233,8 @@ struct TcLaunchInfo {
     int smem_bytes;
 };
 
-cudaError_t launch_convert_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st);
+// BF16 copy dst of src; src is replaced by the same rounded values.
+cudaError_t launch_convert_bf16(float* src, int64_t n, uint16_t* dst, cudaStream_t st);
 
 // Tensor-core GEMM C[M x N] (=, or += with accumulate) A[M x K] . B[N x K]^T; A and B
 // row-major BF16 (pitches lda, ldb elements, multiples of 8; 16-byte aligned bases),
@@ -256,6 +257,30 @@ cudaError_t launch_fi_adam(float* p, const float* g, float* m, float* v, int64_t
                            float eps, float bc1, float bc2, cudaStream_t st);
 cudaError_t launch_fi_weight_copy(const float* w, int rows, int cols, uint16_t* dst, uint16_t* dst_t,
                                   cudaStream_t st);
+
+// Device state of a fit whose stopping rules (App. B) are evaluated on the device.
+struct FitCtlState {
+    int iters;          // sweep cap
+    int done;           // sweeps run so far
+    int cont;           // 1 while the loop goes on
+    int rises;          // consecutive sweeps whose validation loss rose
+    int patience;       // stop once rises reaches this (0: no validation rule)
+    int have_loss;      // prev_loss holds L[done - 1]
+    int have_val;       // prev_val holds V[done]
+    int pad;
+    double tol;         // relative training-loss decrease threshold (0: off)
+    double prev_loss, prev_val;
+};
+
+// After sweep done+1: done += 1, apply the rules to the training loss out_loss[0]
+// (L[done - 1], summed inside that sweep's first pass) and the validation loss
+// out_val[0] (V[done], or null), set cont and, when set_handle, the conditional
+// handle of the enclosing graph loop.  mode 1 only records out_val[0] as V[0].
+cudaError_t launch_fit_check(FitCtlState* s, const double* out_loss, const double* out_val,
+                             cudaGraphConditionalHandle handle, int set_handle, int mode, cudaStream_t st);
+
+// Set the loop's conditional handle from s->cont (the first node of the graph).
+cudaError_t launch_fit_set_cond(const FitCtlState* s, cudaGraphConditionalHandle handle, cudaStream_t st);
 
 // Sum per-CTA loss partials (part[0..n): loss, part[n..2n): count) into out[0..1];
 // also append the loss to trace[*count] when trace is set, and increment *count.

@@ -239,7 +239,14 @@ struct nef_plan_s {
     int64_t n_sm = 152;               // SMs of the plan's device (grid sizing)
     // per-sweep loss and graph replay of sweeps
     int* loss_count = nullptr;        // device: entries appended to the loss trace
+    // stopping rules on the device: state, validation-loss outputs, packed validation mask
+    FitCtlState* ctl = nullptr;
+    double* val_out = nullptr;
+    int* val_count = nullptr;
+    uint32_t* val_bits = nullptr;
+    bool sweeps_on_device = false;    // last_sweeps still to be read from ctl->done
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t body_stream = nullptr;  // captures the body of a conditional loop
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // captured sweeps, most recently used last: a fit replays the one recorded with
     // its arguments (data, mask, factors, loss trace, alpha, beta) or captures anew
@@ -1006,7 +1013,7 @@ nef_status refresh_sources(nef_plan_t p, PassPlan& pp, void* const* factors, cud
         NEF_TRY(run_ein<T>(p, sp.build, factors, st));
         if constexpr (sizeof(T) == 4) {
             if (bf16)
-                NEF_CUDA(launch_convert_bf16(static_cast<const float*>(buf_ptr(p, sp.buf)),
+                NEF_CUDA(launch_convert_bf16(static_cast<float*>(buf_ptr(p, sp.buf)),
                                              sp.n_rows * pp.view.bond_pad, p->src_bf16[sp.buf], st));
         }
         sp.built_at.clear();
@@ -1214,51 +1221,82 @@ nef_status loss_pass(nef_plan_t p, const T* y, const uint32_t* mbits, void* cons
 nef_status ensure_capture_stream(nef_plan_t p) {
     if (p->cap_stream) return NEF_OK;
     NEF_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    NEF_CUDA(cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking));
     NEF_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     NEF_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     return NEF_OK;
 }
 
+// A fit of Algorithm 1: `iters` sweeps (or the single update only_l), with the
+// optional stopping rules of App. B evaluated on the device (tol on the training
+// loss, val_patience on the loss over the validation mask).
 template <typename T>
 nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* const* factors,
-                    double al, double be, int iters, int only_l, double tol = 0.0, double* trace = nullptr) {
+                    double al, double be, int iters, int only_l, double tol = 0.0, double* trace = nullptr,
+                    const uint8_t* val_mask = nullptr, int patience = 0, double* val_trace = nullptr) {
     cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
     const uint32_t* mbits = nullptr;
     p->last_sweeps = 0;
+    p->sweeps_on_device = false;
     if (p->opt.loss != NEF_LOSS_AB) al = be = 0.0;  // ignored by the likelihood families
     NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
     const Specs sp = specs_of(p, al, be);
     const WeightSpec& w = sp.w;
     const UpdateSpec& u = sp.u;
     const LossSpec& L = sp.L;
+    const bool want_val = only_l < 0 && val_mask != nullptr && (patience > 0 || val_trace != nullptr);
+    const bool ctl = only_l < 0 && (tol > 0.0 || (want_val && patience > 0));
     const bool want_loss = only_l < 0 && (trace != nullptr || tol > 0.0);
     const LossSpec* lp = want_loss ? &L : nullptr;
     const T* y = static_cast<const T*>(Y);
     if (iters <= 0) return NEF_OK;
     NEF_TRY(init_sources<T>(p, factors, st));
     if (want_loss) NEF_CUDA(cudaMemsetAsync(p->loss_count, 0, sizeof(int), st));
-    std::vector<double> hist;  // losses read back for the tol rule
-    auto converged = [&]() -> nef_status {
-        double h[2];
-        NEF_CUDA(cudaMemcpyAsync(h, p->loss_out, sizeof(h), cudaMemcpyDeviceToHost, st));
-        NEF_CUDA(cudaStreamSynchronize(st));
-        hist.push_back(h[0]);
+    // V[k]: the loss over the validation entries after k sweeps
+    auto val_pass = [&](cudaStream_t s) -> nef_status {
+        int n_part = 0;
+        NEF_TRY(loss_pass<T>(p, y, p->val_bits, factors, w, L, s, &n_part));
+        NEF_CUDA(launch_loss_append(p->loss_part, n_part, val_trace, p->val_count, p->val_out, s));
         return NEF_OK;
     };
-    auto stop_now = [&]() {
-        const size_t k = hist.size();
-        return tol > 0.0 && k >= 2 && hist[k - 2] != 0.0 && (hist[k - 2] - hist[k - 1]) / hist[k - 2] < tol;
+    if (want_val) {
+        if (!p->val_bits) NEF_CUDA(cudaMalloc(&p->val_bits, ((p->md.N + 31) / 32 + 1) * sizeof(uint32_t)));
+        NEF_CUDA(launch_pack_mask(val_mask, p->md.N, p->val_bits, st));
+        NEF_CUDA(cudaMemsetAsync(p->val_count, 0, sizeof(int), st));
+        NEF_TRY(val_pass(st));
+    }
+    if (ctl) {
+        FitCtlState h{};
+        h.iters = iters;
+        h.cont = 1;
+        h.patience = want_val ? patience : 0;
+        h.tol = tol;
+        NEF_CUDA(cudaMemcpyAsync(p->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+        if (want_val) NEF_CUDA(launch_fit_check(p->ctl, nullptr, p->val_out, 0, 0, 1, st));
+    }
+    // one sweep, the validation loss after it and the stopping rules (set_handle:
+    // the loop's conditional handle, inside the graph body)
+    auto iteration = [&](cudaStream_t s, bool in_graph, cudaGraphConditionalHandle hnd) -> nef_status {
+        NEF_TRY(sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, in_graph ? -1 : only_l, s));
+        if (want_val) NEF_TRY(val_pass(s));
+        if (ctl)
+            NEF_CUDA(launch_fit_check(p->ctl, want_loss ? p->loss_out : nullptr, want_val ? p->val_out : nullptr,
+                                      hnd, in_graph ? 1 : 0, 0, s));
+        return NEF_OK;
     };
     // sweep 1 runs directly (it also settles which contracted operands each pass rebuilds)
-    NEF_TRY(sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, only_l, st));
+    NEF_TRY(iteration(st, false, 0));
     int done = 1;
-    if (tol > 0.0) NEF_TRY(converged());
-    const bool graph = !p->opt.eager && !p->opt.profile && only_l < 0 && iters >= 3;
-    if (done < iters && !stop_now()) {
+    const bool graph = !p->opt.eager && !p->opt.profile && only_l < 0 && iters >= (ctl ? 2 : 3);
+    if (done < iters) {
         if (graph) {
-            // sweeps 2.. replay one captured sweep on the plan's capture stream
+            // sweeps 2.. replay a captured sweep on the plan's capture stream: a plain
+            // fit launches it iters - 1 times; a fit with stopping rules launches once a
+            // graph whose conditional (while) node repeats it until the rules end the loop
             NEF_TRY(ensure_capture_stream(p));
-            std::vector<const void*> key = {Y, mbits, trace, reinterpret_cast<const void*>((intptr_t)want_loss)};
+            std::vector<const void*> key = {Y, mbits, trace, reinterpret_cast<const void*>((intptr_t)want_loss),
+                                            reinterpret_cast<const void*>((intptr_t)ctl),
+                                            want_val ? p->val_bits : nullptr, val_trace};
             for (int f = 0; f < p->md.L; ++f) key.push_back(factors[f]);
             cudaGraphExec_t exec = nullptr;
             for (size_t gi = 0; gi < p->graphs.size(); ++gi) {
@@ -1274,9 +1312,41 @@ nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
                     cudaGraphExecDestroy(p->graphs.front().exec);
                     p->graphs.erase(p->graphs.begin());
                 }
-                NEF_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
-                const nef_status rs = sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, -1, p->cap_stream);
                 cudaGraph_t g = nullptr;
+                NEF_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+                nef_status rs = NEF_OK;
+                if (!ctl) {
+                    rs = iteration(p->cap_stream, true, 0);
+                } else {
+                    rs = [&]() -> nef_status {
+                        cudaStreamCaptureStatus cs;
+                        cudaGraph_t cg = nullptr;
+                        NEF_CUDA(cudaStreamGetCaptureInfo(p->cap_stream, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+                        cudaGraphConditionalHandle hnd = 0;
+                        NEF_CUDA(cudaGraphConditionalHandleCreate(&hnd, cg, 0, cudaGraphCondAssignDefault));
+                        NEF_CUDA(launch_fit_set_cond(p->ctl, hnd, p->cap_stream));
+                        const cudaGraphNode_t* deps = nullptr;
+                        size_t n_deps = 0;
+                        NEF_CUDA(cudaStreamGetCaptureInfo(p->cap_stream, &cs, nullptr, &cg, &deps, nullptr, &n_deps));
+                        cudaGraphNodeParams np{};
+                        np.type = cudaGraphNodeTypeConditional;
+                        np.conditional.handle = hnd;
+                        np.conditional.type = cudaGraphCondTypeWhile;
+                        np.conditional.size = 1;
+                        cudaGraphNode_t loop = nullptr;
+                        NEF_CUDA(cudaGraphAddNode(&loop, cg, deps, nullptr, n_deps, &np));
+                        NEF_CUDA(cudaStreamUpdateCaptureDependencies(p->cap_stream, &loop, nullptr, 1,
+                                                                     cudaStreamSetCaptureDependencies));
+                        NEF_CUDA(cudaStreamBeginCaptureToGraph(p->body_stream, np.conditional.phGraph_out[0], nullptr,
+                                                               nullptr, 0, cudaStreamCaptureModeRelaxed));
+                        const nef_status rb = iteration(p->body_stream, true, hnd);
+                        cudaGraph_t body = nullptr;
+                        const cudaError_t eb = cudaStreamEndCapture(p->body_stream, &body);
+                        NEF_TRY(rb);
+                        NEF_CUDA(eb);
+                        return NEF_OK;
+                    }();
+                }
                 const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &g);
                 if (rs != NEF_OK) {
                     if (g) cudaGraphDestroy(g);
@@ -1290,16 +1360,10 @@ nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
             }
             NEF_CUDA(cudaEventRecord(p->ev_fork, st));
             NEF_CUDA(cudaStreamWaitEvent(p->cap_stream, p->ev_fork, 0));
-            while (done < iters) {
+            if (ctl) {
                 NEF_CUDA(cudaGraphLaunch(exec, p->cap_stream));
-                ++done;
-                if (tol > 0.0) {
-                    double h[2];
-                    NEF_CUDA(cudaMemcpyAsync(h, p->loss_out, sizeof(h), cudaMemcpyDeviceToHost, p->cap_stream));
-                    NEF_CUDA(cudaStreamSynchronize(p->cap_stream));
-                    hist.push_back(h[0]);
-                    if (stop_now()) break;
-                }
+            } else {
+                for (; done < iters; ++done) NEF_CUDA(cudaGraphLaunch(exec, p->cap_stream));
             }
             NEF_CUDA(cudaEventRecord(p->ev_join, p->cap_stream));
             NEF_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
@@ -1308,16 +1372,19 @@ nef_status fit_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
             for (int f = 0; f < p->md.L; ++f) p->fac_version[f] = ++p->version_counter;
         } else {
             while (done < iters) {
-                NEF_TRY(sweep_once<T>(p, y, mbits, factors, w, u, lp, trace, only_l, st));
-                ++done;
-                if (tol > 0.0) {
-                    NEF_TRY(converged());
-                    if (stop_now()) break;
+                if (ctl) {  // the decision of the last check, read back
+                    int c = 0;
+                    NEF_CUDA(cudaMemcpyAsync(&c, &p->ctl->cont, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    NEF_CUDA(cudaStreamSynchronize(st));
+                    if (!c) break;
                 }
+                NEF_TRY(iteration(st, false, 0));
+                ++done;
             }
         }
     }
     p->last_sweeps = done;
+    p->sweeps_on_device = ctl;
     if (want_loss) {
         // the loss after the last sweep
         int n_part = 0;
@@ -1623,6 +1690,11 @@ void destroy(nef_plan_t p) {
     if (p->tc_err) cudaFree(p->tc_err);
     if (p->tc_trace) cudaFree(p->tc_trace);
     if (p->loss_count) cudaFree(p->loss_count);
+    if (p->ctl) cudaFree(p->ctl);
+    if (p->val_out) cudaFree(p->val_out);
+    if (p->val_count) cudaFree(p->val_count);
+    if (p->val_bits) cudaFree(p->val_bits);
+    if (p->body_stream) cudaStreamDestroy(p->body_stream);
     for (auto& ge : p->graphs) cudaGraphExecDestroy(ge.exec);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
@@ -1803,6 +1875,9 @@ nef_status build_plan(nef_plan_t p) {
     NEF_CUDA(cudaMalloc(&p->loss_out, 2 * sizeof(double)));
     NEF_CUDA(cudaMalloc(&p->loss_count, sizeof(int)));
     NEF_CUDA(cudaMemset(p->loss_count, 0, sizeof(int)));
+    NEF_CUDA(cudaMalloc(&p->ctl, sizeof(FitCtlState)));
+    NEF_CUDA(cudaMalloc(&p->val_out, 2 * sizeof(double)));
+    NEF_CUDA(cudaMalloc(&p->val_count, sizeof(int)));
     NEF_CUDA(cudaMalloc(&p->flag, sizeof(int)));
     NEF_CUDA(cudaMalloc(&p->tc_err, sizeof(int)));
     NEF_CUDA(cudaMemset(p->tc_err, 0, sizeof(int)));
@@ -1890,19 +1965,35 @@ nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, con
 
 void nef_plan_destroy(nef_plan_t plan) { destroy(plan); }
 
-nef_status nef_fit_ex(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors, double alpha,
-                      double beta, int iters, double tol, double* loss_trace, int* sweeps) {
+nef_status nef_fit_ctl(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors, double alpha,
+                       double beta, int iters, const nef_fit_control* ctl, int* sweeps) {
     g_err.clear();
     if (sweeps) *sweeps = 0;
     if (!plan) return fail(NEF_EINVAL, "plan is NULL");
     if (iters < 0) return fail(NEF_EINVAL, "iters must be >= 0");
-    if (!(tol >= 0.0)) return fail(NEF_EINVAL, "tol must be >= 0");
+    nef_fit_control c{};
+    if (ctl) c = *ctl;
+    if (!(c.tol >= 0.0)) return fail(NEF_EINVAL, "tol must be >= 0");
+    if (c.val_patience < 0) return fail(NEF_EINVAL, "val_patience must be >= 0");
+    if (!c.val_mask && (c.val_patience > 0 || c.val_trace))
+        return fail(NEF_EINVAL, "val_patience and val_trace need val_mask");
     NEF_TRY(check_ab(plan, alpha, beta));
-    const nef_status r = plan->prec == NEF_FP64
-                             ? fit_impl<double>(plan, Y, mask, factors, alpha, beta, iters, -1, tol, loss_trace)
-                             : fit_impl<float>(plan, Y, mask, factors, alpha, beta, iters, -1, tol, loss_trace);
-    if (sweeps) *sweeps = plan->last_sweeps;
+    const nef_status r =
+        plan->prec == NEF_FP64
+            ? fit_impl<double>(plan, Y, mask, factors, alpha, beta, iters, -1, c.tol, c.loss_trace, c.val_mask,
+                               c.val_patience, c.val_trace)
+            : fit_impl<float>(plan, Y, mask, factors, alpha, beta, iters, -1, c.tol, c.loss_trace, c.val_mask,
+                              c.val_patience, c.val_trace);
+    if (sweeps && r == NEF_OK) *sweeps = nef_plan_sweeps(plan);
     return r;
+}
+
+nef_status nef_fit_ex(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors, double alpha,
+                      double beta, int iters, double tol, double* loss_trace, int* sweeps) {
+    nef_fit_control c{};
+    c.tol = tol;
+    c.loss_trace = loss_trace;
+    return nef_fit_ctl(plan, Y, mask, factors, alpha, beta, iters, &c, sweeps);
 }
 
 nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
@@ -1914,7 +2005,21 @@ nef_status nef_fit(nef_plan_t plan, const void* Y, const uint8_t* mask, void* co
     return nef_fit_ex(plan, Y, mask, factors, alpha, beta, iters, plan->opt.tol, plan->opt.loss_trace, nullptr);
 }
 
-int nef_plan_sweeps(nef_plan_t plan) { return plan ? plan->last_sweeps : 0; }
+int nef_plan_sweeps(nef_plan_t plan) {
+    if (!plan) return 0;
+    if (plan->sweeps_on_device) {
+        cudaStream_t st = static_cast<cudaStream_t>(plan->opt.stream);
+        int d = 0;
+        if (cudaMemcpyAsync(&d, &plan->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess) {
+            plan->last_sweeps = d;
+            plan->sweeps_on_device = false;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return plan->last_sweeps;
+}
 
 nef_status nef_plan_autotune(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,
                              double alpha, double beta, const char* cache_path, int* splits) {

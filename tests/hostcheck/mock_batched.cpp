@@ -12,6 +12,7 @@
 #include <vector>
 
 #define __device__
+#define __host__
 #define __forceinline__ inline
 #define __shfl_xor_sync(m, v, o) (v)
 static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }

@@ -9,6 +9,7 @@
 #include <vector>
 
 #define __device__
+#define __host__
 #define __forceinline__ inline
 #define __shfl_xor_sync(m, v, o) (v)
 static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
@@ -167,7 +168,7 @@ cudaError_t launch_sum_f64(const double* part, int n, double* out, cudaStream_t)
     });
 }
 
-cudaError_t launch_convert_bf16(const float*, int64_t, uint16_t*, cudaStream_t) {
+cudaError_t launch_convert_bf16(float*, int64_t, uint16_t*, cudaStream_t) {
     return cudaErrorNotSupported;
 }
 
@@ -219,13 +220,22 @@ static uint16_t bf16_bits_host(float x) {
     return (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
 }
 
+// A copy with a BF16 twin holds the BF16-rounded value in its own type too.
 template <typename T>
 static void write_mirrors_host(const MirrorDesc& m, const int64_t* idx, int nlet, T v) {
     for (int k = 0; k < m.n; ++k) {
         int64_t off = 0;
         for (int q = 0; q < nlet; ++q) off += idx[q] * m.st[k][q];
-        static_cast<T*>(m.p32[k])[off] = v;
-        if (m.p16[k]) m.p16[k][off] = bf16_bits_host((float)v);
+        if (m.p16[k]) {
+            const uint16_t b = bf16_bits_host((float)v);
+            m.p16[k][off] = b;
+            const uint32_t u = (uint32_t)b << 16;
+            float f;
+            std::memcpy(&f, &u, 4);
+            static_cast<T*>(m.p32[k])[off] = (T)f;
+        } else {
+            static_cast<T*>(m.p32[k])[off] = v;
+        }
     }
 }
 
@@ -309,6 +319,22 @@ cudaError_t launch_view_tc(const float*, const uint32_t*, const ViewDesc&, const
                            int, float*, float*, int*, cudaStream_t, TcLaunchInfo*, unsigned long long*,
                            const LossSpec*, double*, long long) {
     return cudaErrorNotSupported;
+}
+
+cudaError_t launch_fit_check(FitCtlState* s, const double* out_loss, const double* out_val,
+                             cudaGraphConditionalHandle handle, int set_handle, int mode, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
+        const int cont = fit_rule_step(s, out_loss, out_val, mode);
+        if (set_handle && mode == 0) *reinterpret_cast<unsigned*>(handle) = cont ? 1u : 0u;
+        return cudaSuccess;
+    });
+}
+
+cudaError_t launch_fit_set_cond(const FitCtlState* s, cudaGraphConditionalHandle handle, cudaStream_t) {
+    return host_submit([=]() -> cudaError_t {
+        *reinterpret_cast<unsigned*>(handle) = s->cont ? 1u : 0u;
+        return cudaSuccess;
+    });
 }
 
 cudaError_t launch_loss_append(const double* part, int n, double* trace, int* count, double* out, cudaStream_t) {

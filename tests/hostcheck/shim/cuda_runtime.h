@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <memory>
 #include <vector>
 
 typedef int cudaError_t;
@@ -28,15 +29,20 @@ inline cudaError_t cudaFree(void* p) { std::free(p); return cudaSuccess; }
 inline cudaError_t cudaMemset(void* p, int v, size_t n) { std::memset(p, v, n); return cudaSuccess; }
 // Stream capture: while a capture is open, launches and async copies are
 // recorded instead of run; a graph launch replays them in order.
+// Captures nest (a conditional node's body is captured while its parent graph's
+// capture is open): the innermost open capture receives the work.  A while node
+// is one operation of its graph that runs the body's operations while its
+// condition value (set by the mock kernels) is nonzero.
 struct HostGraph {
-    std::vector<std::function<void()>> ops;
+    std::vector<std::function<void()>> ops;  // a while node's operation shares its body
 };
 typedef HostGraph* cudaGraph_t;
 typedef HostGraph* cudaGraphExec_t;
-inline HostGraph*& host_capture() {
-    static HostGraph* g = nullptr;
+inline std::vector<HostGraph*>& host_captures() {
+    static std::vector<HostGraph*> g;
     return g;
 }
+inline HostGraph* host_capture() { return host_captures().empty() ? nullptr : host_captures().back(); }
 template <class F>
 inline cudaError_t host_submit(F f) {
     if (host_capture()) {
@@ -49,12 +55,73 @@ enum cudaStreamCaptureMode { cudaStreamCaptureModeGlobal = 0, cudaStreamCaptureM
                              cudaStreamCaptureModeRelaxed = 2 };
 enum { cudaStreamNonBlocking = 1, cudaEventDisableTiming = 2 };
 inline cudaError_t cudaStreamBeginCapture(cudaStream_t, cudaStreamCaptureMode) {
-    host_capture() = new HostGraph;
+    host_captures().push_back(new HostGraph);
     return cudaSuccess;
 }
 inline cudaError_t cudaStreamEndCapture(cudaStream_t, cudaGraph_t* g) {
-    *g = host_capture();
-    host_capture() = nullptr;
+    HostGraph* top = host_captures().back();
+    host_captures().pop_back();
+    if (g) *g = top;
+    return cudaSuccess;
+}
+typedef unsigned long long cudaGraphConditionalHandle;
+typedef struct HostNode* cudaGraphNode_t;
+struct cudaGraphEdgeData;
+enum cudaStreamCaptureStatus { cudaStreamCaptureStatusNone = 0, cudaStreamCaptureStatusActive = 1 };
+enum { cudaStreamAddCaptureDependencies = 0, cudaStreamSetCaptureDependencies = 1 };
+enum { cudaGraphCondAssignDefault = 1 };
+enum cudaGraphConditionalNodeType { cudaGraphCondTypeIf = 0, cudaGraphCondTypeWhile = 1 };
+enum cudaGraphNodeType { cudaGraphNodeTypeKernel = 0, cudaGraphNodeTypeConditional = 0x0d };
+struct cudaConditionalNodeParams {
+    cudaGraphConditionalHandle handle;
+    cudaGraphConditionalNodeType type;
+    unsigned int size;
+    cudaGraph_t* phGraph_out;
+};
+struct cudaGraphNodeParams {
+    cudaGraphNodeType type;
+    cudaConditionalNodeParams conditional;
+};
+inline cudaError_t cudaStreamGetCaptureInfo(cudaStream_t, cudaStreamCaptureStatus* status, unsigned long long*,
+                                            cudaGraph_t* graph, const cudaGraphNode_t** deps,
+                                            const cudaGraphEdgeData**, size_t* n_deps) {
+    if (status) *status = host_capture() ? cudaStreamCaptureStatusActive : cudaStreamCaptureStatusNone;
+    if (graph) *graph = host_capture();
+    if (deps) *deps = nullptr;
+    if (n_deps) *n_deps = 0;
+    return cudaSuccess;
+}
+// a handle is the address of its condition value
+inline cudaError_t cudaGraphConditionalHandleCreate(cudaGraphConditionalHandle* h, cudaGraph_t, unsigned def,
+                                                    unsigned) {
+    static std::vector<unsigned*> values;
+    values.push_back(new unsigned(def));
+    *h = reinterpret_cast<cudaGraphConditionalHandle>(values.back());
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphAddNode(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t*,
+                                    const cudaGraphEdgeData*, size_t, cudaGraphNodeParams* np) {
+    if (np->type != cudaGraphNodeTypeConditional || np->conditional.type != cudaGraphCondTypeWhile)
+        return cudaErrorNotSupported;
+    auto body = std::make_shared<HostGraph>();
+    static cudaGraph_t out[1];
+    out[0] = body.get();
+    np->conditional.phGraph_out = out;
+    unsigned* v = reinterpret_cast<unsigned*>(np->conditional.handle);
+    g->ops.push_back([v, body]() {
+        while (*v)
+            for (auto& f : body->ops) f();
+    });
+    *node = nullptr;
+    return cudaSuccess;
+}
+inline cudaError_t cudaStreamUpdateCaptureDependencies(cudaStream_t, cudaGraphNode_t*, const cudaGraphEdgeData*,
+                                                       size_t, unsigned) {
+    return cudaSuccess;
+}
+inline cudaError_t cudaStreamBeginCaptureToGraph(cudaStream_t, cudaGraph_t g, const cudaGraphNode_t*,
+                                                 const cudaGraphEdgeData*, size_t, cudaStreamCaptureMode) {
+    host_captures().push_back(g);
     return cudaSuccess;
 }
 inline cudaError_t cudaGraphInstantiate(cudaGraphExec_t* e, cudaGraph_t g, unsigned long long) {

@@ -80,3 +80,65 @@ def test_tol_stop_bf16():
     for k in range(2, done):
         assert (t[k - 2] - t[k - 1]) / t[k - 2] >= tol
     assert np.all(np.isfinite(t[: done + 1])) and np.all(np.isnan(t[done + 1:]))
+
+
+def _overfit_problem(seed=41):
+    """A CP model of rank 6 on a small noisy Poisson tensor with half of the entries
+    held out: the training loss keeps falling while the validation loss turns up."""
+    model_str, dims = "ir,jr,kr->ijk", dict(i=36, j=32, k=40, r=12)
+    m = OracleModel(model_str, dims)
+    rng = np.random.default_rng(seed)
+    truth = [rng.gamma(2.0, 0.5, m.factor_shape(l)) for l in range(3)]
+    y = rng.poisson(np.einsum(model_str, *truth) * 0.02).astype(np.float64)
+    u = rng.random(m.y_shape)
+    train = (u < 0.5).astype(np.uint8)
+    val = (u >= 0.5).astype(np.uint8)
+    init = [rng.uniform(0.5, 1.5, m.factor_shape(l)) for l in range(3)]
+    return model_str, dims, m, y, train, val, init
+
+
+def _oracle_traces(m, y, train, val, init, iters):
+    fs = [f.astype(np.float64) for f in init]
+    L, V = [m.loss(y, train, fs, 1.0, 0.0)[0]], [m.loss(y, val, fs, 1.0, 0.0)[0]]
+    for _ in range(iters):
+        fs = m.fit(y, train, fs, 1.0, 0.0, 1)
+        L.append(m.loss(y, train, fs, 1.0, 0.0)[0])
+        V.append(m.loss(y, val, fs, 1.0, 0.0)[0])
+    return np.array(L), np.array(V)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_device_stopping_rules_stop_where_the_oracle_predicts(prec):
+    """App. B's two stopping rules, evaluated by the check kernel at the end of
+    each sweep inside a conditional (while) graph loop: the training-loss rule
+    (relative decrease below tol) and the validation rule (the loss over held-out
+    entries rising 5 sweeps in a row) stop at the sweep the FP64 oracle's traces
+    predict, and the traces match the oracle's."""
+    import paper_2602_02759_gb300 as nef
+    model_str, dims, m, y, train, val, init = _overfit_problem()
+    iters = 80
+    L, V = _oracle_traces(m, y, train, val, init, iters)
+    tol = 2e-3
+    k_tol = next((k for k in range(2, iters + 1) if (L[k - 2] - L[k - 1]) / L[k - 2] < tol), iters)
+    rises, k_val = 0, iters
+    for k in range(1, iters + 1):
+        rises = rises + 1 if V[k] > V[k - 1] else 0
+        if rises >= 5:
+            k_val = k
+            break
+    assert 2 < k_tol < iters and 5 < k_val < iters, (k_tol, k_val)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Y, T, Vm = _dev(y, dt), _dev(train, torch.uint8), _dev(val, torch.uint8)
+    rtol = 1e-10 if prec == "fp64" else 1e-5
+    for tol_s, pat, want in ((tol, 0, k_tol), (0.0, 5, k_val)):
+        plan = nef.Plan(model_str, dims, precision=prec)
+        fs = [_dev(f, dt) for f in init]
+        lt = torch.full((iters + 1,), float("nan"), dtype=torch.float64, device="cuda")
+        vt = torch.full((iters + 1,), float("nan"), dtype=torch.float64, device="cuda")
+        done = plan.fit(Y, T, fs, 1.0, 0.0, iters, tol=tol_s, loss_trace=lt, val_mask=Vm, val_patience=pat,
+                        val_trace=vt)
+        plan.check()
+        assert done == want, (tol_s, pat, done, want)
+        np.testing.assert_allclose(lt.cpu().numpy()[: want + 1], L[: want + 1], rtol=rtol)
+        np.testing.assert_allclose(vt.cpu().numpy()[: want + 1], V[: want + 1], rtol=rtol)
+        assert np.all(np.isnan(lt.cpu().numpy()[want + 1:]))
