@@ -256,7 +256,9 @@ def foldin_variant(nef, torch, stream, train_sweeps=100, steps=200, lr=1e-3):
     e1.record(stream)
     l_end = enc.train_step(xs, targets, lr)
     t_train = e0.elapsed_time(e1) / 1e3 / (steps - 2)
-    flops = 2.0 * 3.0 * n_tr * (d * 512 + 512 * 512 + 512 * R)  # forward + two backward products
+    # products per Adam step: the first layer's forward product and weight gradient (its
+    # input gradient is not needed), three each for the other two layers
+    flops = 2.0 * n_tr * (2 * d * 512 + 3 * 512 * 512 + 3 * 512 * R)
     ref = nef.Plan(p.model_str, dict(i=n_te, j=J, k=K, r=R), precision="fp32", stream=stream)
     x_te = yte.reshape(n_te, d).contiguous()
     for _ in range(3):  # warm-up

@@ -237,6 +237,28 @@ nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask
                       void* const* factors, double alpha, double beta);
 
 /*
+ * nef_numden -- the numerator and denominator of Eq. 3.6-3.8 for factor l at
+ * the given factors (the first half of Algorithm 1's inner step), without the
+ * update; for callers that sum them over shards of Y before updating (slabs of
+ * Y on several GPUs: num and den are sums over the entries of Y, so the sum of
+ * the slabs' num and den is the whole tensor's).
+ *   num, den : device, factor l's size in the plan's element type, written
+ * Arguments otherwise as nef_update.  Errors as nef_update.
+ */
+nef_status nef_numden(nef_plan_t plan, int l, const void* Y, const uint8_t* mask, void* const* factors,
+                      double alpha, double beta, void* num, void* den);
+
+/*
+ * nef_apply_update -- the second half of the inner step: Eq. 3.4 for factor l
+ * from given num and den, theta <- max(eps, theta * g^{-1}(num/den)) with g of
+ * the plan's loss family (den == 0 keeps theta); refreshes the plan's operand
+ * copies of factor l.  num, den: device, factor l's size.  Errors: NEF_EINVAL
+ * (null pointer, factor index, alpha/beta), NEF_ECUDA.
+ */
+nef_status nef_apply_update(nef_plan_t plan, int l, void* const* factors, const void* num, const void* den,
+                            double alpha, double beta);
+
+/*
  * nef_loss -- sum over observed entries of D_{alpha,beta}(y, yhat) (Eq. 3.1
  * with the five-case definition of App. B), with FP64 accumulation.
  *   out : host, 2 doubles: out[0] = the sum, out[1] = the number of observed

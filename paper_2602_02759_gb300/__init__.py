@@ -24,3 +24,4 @@ from ._nef import (  # noqa: F401
     pack_params,
     split_model,
 )
+from .slab import SlabFit, slab_bounds, slab_sweeps  # noqa: F401

@@ -22,7 +22,8 @@ PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 
 # every symbol include/nef.h declares
 EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex", "nef_fit_ctl",
-           "nef_plan_sweeps", "nef_plan_autotune", "nef_update", "nef_loss", "nef_plan_info", "nef_plan_launches",
+           "nef_plan_sweeps", "nef_plan_autotune", "nef_update", "nef_numden", "nef_apply_update", "nef_loss",
+           "nef_plan_info", "nef_plan_launches",
            "nef_plan_profile", "nef_tc_trace", "nef_check", "nef_fit_batched", "nef_cp3_update_static",
            "nef_last_error",
            "nef_foldin_num_params", "nef_foldin_create", "nef_foldin_destroy", "nef_foldin_grad",
@@ -82,6 +83,12 @@ def load(path: str = LIB_PATH):
     lib.nef_update.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(vp), ctypes.c_double,
                                ctypes.c_double]
     lib.nef_update.restype = ctypes.c_int
+    lib.nef_numden.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                               vp, vp]
+    lib.nef_numden.restype = ctypes.c_int
+    lib.nef_apply_update.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), vp, vp, ctypes.c_double,
+                                     ctypes.c_double]
+    lib.nef_apply_update.restype = ctypes.c_int
     lib.nef_loss.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double, dp]
     lib.nef_loss.restype = ctypes.c_int
     lib.nef_plan_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_int]
@@ -331,6 +338,25 @@ class Plan:
         self._check_args(Y, mask, factors)
         check(load().nef_update(self._h, int(l), self._ptr(Y), self._ptr(mask),
                                 self._facs(factors), float(alpha), float(beta)))
+
+    def numden(self, l, Y, mask, factors, alpha, beta):
+        """num and den of Eq. 3.6-3.8 for factor l (nef_numden), as new CUDA tensors."""
+        import torch
+        self._check_args(Y, mask, factors)
+        num = torch.empty_like(factors[l])
+        den = torch.empty_like(factors[l])
+        check(load().nef_numden(self._h, int(l), self._ptr(Y), self._ptr(mask), self._facs(factors),
+                                float(alpha), float(beta), self._ptr(num), self._ptr(den)))
+        return num, den
+
+    def apply_update(self, l, factors, num, den, alpha, beta):
+        """Eq. 3.4 for factor l from num and den (nef_apply_update)."""
+        f = factors[l]
+        for t in (num, den):
+            if t.dtype != f.dtype or t.shape != f.shape or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("num and den must be contiguous CUDA tensors shaped like factor l")
+        check(load().nef_apply_update(self._h, int(l), self._facs(factors), self._ptr(num), self._ptr(den),
+                                      float(alpha), float(beta)))
 
     def loss(self, Y, mask, factors, alpha, beta):
         self._check_args(Y, mask, factors)

@@ -1,14 +1,18 @@
 // batched.cpp -- many independent CP factorizations 'ir,jr,kr->ijk', each with
 // several random restarts, fitted together by the multiplicative update.
 //
-// Every (problem, restart) pair is a unit.  Y is copied once per call into a
-// zero-padded layout (dimensions rounded up to multiples of 4, padding
-// unobserved) so that every unit's views satisfy the TMA stride rule.  A sweep
-// is three mode phases (Gauss-Seidel order of Algorithm 1 within every unit);
-// each phase is one batched tensor-core launch per bond width plus one batched
-// finish.  The whole iteration loop is captured in a CUDA graph and launched
-// once.  Restarts of a problem read the same Y tiles: their work items are
-// adjacent, so a tile is read from HBM once and from L2 by the other restarts.
+// Every (problem, restart) pair is a unit.  The whole fit is one persistent
+// launch (k_batched_persistent, one CTA per SM): CTAs take work items -- the
+// fused pass of one (row block, column split) of one unit in one mode -- from a
+// device queue ordered sweep by sweep and mode by mode; a per-unit stage counter,
+// waited on with a bound, keeps Algorithm 1's Gauss-Seidel order within every
+// unit, and the CTA that completes a stage's last item applies its update.  The
+// launch, its counter resets and the final losses form one CUDA graph.  Items of
+// the restarts of one problem are adjacent in the queue, so a Y tile read from
+// HBM by one restart is read from L2 by the others.  Y is used in place when its
+// innermost dimension is a multiple of 4 (the TMA stride rule); other problems
+// are copied once per call into a zero-padded layout (dimensions rounded up to
+// multiples of 4, padding unobserved).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -58,7 +62,8 @@ constexpr int64_t kTilesPerCta = NEF_BATCH_TILES;  // column tiles per CTA of on
 struct Prob {
     int64_t d[3], pd[3];
     int R, bp;
-    int64_t y_off, b_off;  // offsets (elements / words) into the padded buffers
+    bool padded;           // Y copied into the zero-padded layout
+    int64_t y_off, b_off;  // offsets (elements / words) into the padded / bit buffers
 };
 
 }  // namespace
@@ -91,8 +96,10 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
         for (int m = 0; m < 3; ++m) {
             q.d[m] = shapes[3 * p + m];
             if (q.d[m] < 1) return bfail(NEF_EINVAL, "dimensions must be >= 1");
-            q.pd[m] = rup(q.d[m], 4);
         }
+        // the views' TMA strides are K and J*K elements: whole 16-byte units iff K % 4 == 0
+        q.padded = q.d[2] % 4 != 0;
+        for (int m = 0; m < 3; ++m) q.pd[m] = q.padded ? rup(q.d[m], 4) : q.d[m];
         q.R = (int)ranks[p];
         if (q.R < 1 || q.R > 32) return bfail(NEF_EINVAL, "batched ranks must be in [1, 32]");
         q.bp = q.R <= 16 ? 16 : 32;
@@ -102,16 +109,31 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
                 if (!factors[((int64_t)p * restarts + k) * 3 + m]) return bfail(NEF_EINVAL, "factor pointer is NULL");
         const int64_t np = q.pd[0] * q.pd[1] * q.pd[2];
         q.y_off = y_tot;
-        y_tot += rup(np, 64);
+        if (q.padded) y_tot += rup(np, 64);
         q.b_off = b_tot;
-        b_tot += rup((np + 31) / 32 + 2, 64);
+        if (q.padded || masks) b_tot += rup((np + 31) / 32 + 2, 64);
     }
     DevBuf ypad, bits;
-    B_CUDA(ypad.alloc((size_t)y_tot * 4));
-    B_CUDA(bits.alloc((size_t)b_tot * 4));
-    for (int p = 0; p < n; ++p)
-        B_CUDA(launch_pad_problem(Y[p], masks ? masks[p] : nullptr, pr[p].d, pr[p].pd,
-                                  ypad.as<float>() + pr[p].y_off, bits.as<uint32_t>() + pr[p].b_off, st));
+    B_CUDA(ypad.alloc((size_t)std::max<int64_t>(y_tot, 1) * 4));
+    B_CUDA(bits.alloc((size_t)std::max<int64_t>(b_tot, 1) * 4));
+    std::vector<const float*> yv(n);
+    std::vector<const uint32_t*> bv(n);
+    for (int p = 0; p < n; ++p) {
+        const Prob& q = pr[p];
+        if (q.padded) {
+            B_CUDA(launch_pad_problem(Y[p], masks ? masks[p] : nullptr, q.d, q.pd, ypad.as<float>() + q.y_off,
+                                      bits.as<uint32_t>() + q.b_off, st));
+            yv[p] = ypad.as<float>() + q.y_off;
+            bv[p] = bits.as<uint32_t>() + q.b_off;
+        } else {
+            yv[p] = Y[p];
+            bv[p] = nullptr;
+            if (masks) {
+                B_CUDA(launch_pack_mask(masks[p], q.d[0] * q.d[1] * q.d[2], bits.as<uint32_t>() + q.b_off, st));
+                bv[p] = bits.as<uint32_t>() + q.b_off;
+            }
+        }
+    }
 
     // ---- units: canonical factor copies and partial buffers
     const int nu = n * restarts;
@@ -164,11 +186,12 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
     B_CUDA(errf.alloc(sizeof(int)));
     B_CUDA(cudaMemsetAsync(errf.p, 0, sizeof(int), st));
 
-    // ---- per-mode launch descriptors
+    // ---- units (one per (problem, restart) and mode), their finishes and the work items
     std::vector<TcUnit> units((size_t)nu * 3);
-    std::vector<TcWork> work[3][2];  // [mode][bond width 16/32]
     std::vector<BatchFinish> fin((size_t)nu * 3);
     std::vector<int64_t> prefix((size_t)(nu + 1) * 3);
+    std::vector<int> stage_items((size_t)nu * 3, 0), prefix_items((size_t)nu * 3, 0), sweep_items((size_t)nu, 0);
+    std::vector<PersistItem> items[2];  // one sweep, per bond width 16 / 32, mode-major
     for (int l = 0; l < 3; ++l) {
         int64_t acc = 0;
         for (int p = 0; p < n; ++p) {
@@ -192,19 +215,19 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
                 ps.mod[0] = q.pd[l];
                 ps.mul[0] = 1;
                 v.Q.nsrc = 2;
-                for (int s = 0; s < 2; ++s) {
-                    SrcDesc& d = v.Q.src[s];
-                    d.ptr = c16.as<uint16_t>() + canon_off[(size_t)uu * 3 + other[s]];
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    SrcDesc& d = v.Q.src[s2];
+                    d.ptr = c16.as<uint16_t>() + canon_off[(size_t)uu * 3 + other[s2]];
                     d.ld = q.bp;
                     d.nterm = 1;
-                    d.div[0] = (s == 0) ? q.pd[other[1]] : 1;
-                    d.mod[0] = q.pd[other[s]];
+                    d.div[0] = (s2 == 0) ? q.pd[other[1]] : 1;
+                    d.mod[0] = q.pd[other[s2]];
                     d.mul[0] = 1;
                 }
                 float* sn = pnum.as<float>() + part_off[uu];
                 float* sd = pden.as<float>() + part_off[uu];
-                if (!tc_make_unit(ypad.as<float>() + q.y_off, bits.as<uint32_t>() + q.b_off, v, w, (int)ns, sn, sd,
-                                  errf.as<int>(), &units[(size_t)l * nu + uu], &n_rb))
+                if (!tc_make_unit(yv[p], bv[p], v, w, (int)ns, sn, sd, errf.as<int>(), &units[(size_t)l * nu + uu],
+                                  &n_rb))
                     return bfail(NEF_EUNSUPPORTED, "a batched view cannot run on the tensor cores");
                 BatchFinish& f = fin[(size_t)l * nu + uu];
                 f.theta = factors[(size_t)uu * 3 + l];
@@ -216,31 +239,47 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
                 f.bp = q.bp;
                 f.s_size = v.rows * q.bp;
                 f.n_split = (int)ns;
+                f.rows = q.d[l];
                 prefix[(size_t)l * (nu + 1) + uu] = acc;
                 acc += q.d[l] * q.R;
+                const size_t um = (size_t)l * nu + uu;
+                stage_items[um] = n_rb * (int)ns;
+                prefix_items[um] = sweep_items[uu];
+                sweep_items[uu] += stage_items[um];
             }
             // restarts of one (row block, split) are adjacent: they share Y tiles in L2
             const int g = q.bp == 16 ? 0 : 1;
             for (int rb = 0; rb < n_rb; ++rb)
                 for (int sp = 0; sp < ns; ++sp)
-                    for (int k = 0; k < restarts; ++k) work[l][g].push_back({p * restarts + k, rb, (int)sp, 0});
+                    for (int k = 0; k < restarts; ++k)
+                        items[g].push_back({l * nu + p * restarts + k, rb, (int)sp, 0});
         }
         prefix[(size_t)l * (nu + 1) + nu] = acc;
     }
-    DevBuf d_units, d_fin, d_prefix, d_work[3][2];
+    DevBuf d_units, d_fin, d_prefix, d_items[2], d_tab, d_cnt;
     B_CUDA(d_units.alloc(units.size() * sizeof(TcUnit)));
     B_CUDA(cudaMemcpyAsync(d_units.p, units.data(), units.size() * sizeof(TcUnit), cudaMemcpyHostToDevice, st));
     B_CUDA(d_fin.alloc(fin.size() * sizeof(BatchFinish)));
     B_CUDA(cudaMemcpyAsync(d_fin.p, fin.data(), fin.size() * sizeof(BatchFinish), cudaMemcpyHostToDevice, st));
     B_CUDA(d_prefix.alloc(prefix.size() * sizeof(int64_t)));
     B_CUDA(cudaMemcpyAsync(d_prefix.p, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    for (int l = 0; l < 3; ++l)
-        for (int g = 0; g < 2; ++g)
-            if (!work[l][g].empty()) {
-                B_CUDA(d_work[l][g].alloc(work[l][g].size() * sizeof(TcWork)));
-                B_CUDA(cudaMemcpyAsync(d_work[l][g].p, work[l][g].data(), work[l][g].size() * sizeof(TcWork),
-                                       cudaMemcpyHostToDevice, st));
-            }
+    for (int g = 0; g < 2; ++g)
+        if (!items[g].empty()) {
+            B_CUDA(d_items[g].alloc(items[g].size() * sizeof(PersistItem)));
+            B_CUDA(cudaMemcpyAsync(d_items[g].p, items[g].data(), items[g].size() * sizeof(PersistItem),
+                                   cudaMemcpyHostToDevice, st));
+        }
+    // stage tables: [stage_items | prefix_items | sweep_items]
+    std::vector<int> tab;
+    tab.insert(tab.end(), stage_items.begin(), stage_items.end());
+    tab.insert(tab.end(), prefix_items.begin(), prefix_items.end());
+    tab.insert(tab.end(), sweep_items.begin(), sweep_items.end());
+    B_CUDA(d_tab.alloc(tab.size() * sizeof(int)));
+    B_CUDA(cudaMemcpyAsync(d_tab.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    // counters: queue[2], abort, pad, done[nu], stage[nu]
+    const size_t n_cnt = 4 + 2 * (size_t)nu;
+    B_CUDA(d_cnt.alloc(n_cnt * sizeof(unsigned int)));
+    unsigned int* cnt = d_cnt.as<unsigned int>();
     const TcUnit* du = d_units.as<TcUnit>();
     const BatchFinish* df = d_fin.as<BatchFinish>();
     const int64_t* dp = d_prefix.as<int64_t>();
@@ -250,8 +289,17 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
         B_CUDA(launch_mirror_batched(df + (size_t)l * nu, dp + (size_t)l * (nu + 1), nu,
                                      prefix[(size_t)l * (nu + 1) + nu], st));
 
-    // ---- the sweep loop, captured in one graph
+    // ---- the fit: counter resets and one persistent launch per bond width (per chunk of
+    // sweeps when the queue of a whole fit would exceed 2^31 items), captured in one graph
     if (iters > 0) {
+        int n_sm = 152;
+        {
+            int dev = 0, v = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+                n_sm = v;
+            cudaGetLastError();
+        }
         // the caller's stream may be the legacy stream, which cannot be captured: capture
         // and launch on a private stream that starts after the work queued so far
         cudaStream_t cs = nullptr;
@@ -264,17 +312,35 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         B_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-        cudaError_t cap = cudaSuccess;
-        for (int it = 0; it < iters && cap == cudaSuccess; ++it)
-            for (int l = 0; l < 3 && cap == cudaSuccess; ++l) {
-                for (int g = 0; g < 2 && cap == cudaSuccess; ++g)
-                    if (!work[l][g].empty())
-                        cap = launch_view_tc_batched(du + (size_t)l * nu, d_work[l][g].as<TcWork>(),
-                                                     (int)work[l][g].size(), 16 << g, 1, w, cs);
-                if (cap == cudaSuccess)
-                    cap = launch_finish_batched(df + (size_t)l * nu, dp + (size_t)l * (nu + 1), nu,
-                                                prefix[(size_t)l * (nu + 1) + nu], u, cs);
+        cudaError_t cap = cudaMemsetAsync(cnt, 0, n_cnt * sizeof(unsigned int), cs);
+        for (int g = 0; g < 2 && cap == cudaSuccess; ++g) {
+            if (items[g].empty()) continue;
+            const int64_t n_it = (int64_t)items[g].size();
+            const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(iters, ((int64_t)1 << 31) / n_it));
+            for (int s0 = 0; s0 < iters && cap == cudaSuccess; s0 += chunk) {
+                if (s0 > 0) cap = cudaMemsetAsync(cnt + g, 0, sizeof(unsigned int), cs);  // queue of this chunk
+                PersistDesc d{};
+                d.units = du;
+                d.fin = df;
+                d.items = d_items[g].as<PersistItem>();
+                d.stage_items = d_tab.as<int>();
+                d.prefix_items = d_tab.as<int>() + 3 * (size_t)nu;
+                d.sweep_items = d_tab.as<int>() + 6 * (size_t)nu;
+                d.n_items = (int)n_it;
+                d.n_sweeps = std::min(chunk, iters - s0);
+                d.sweep0 = s0;
+                d.n_units = nu;
+                d.bp = g == 0 ? 16 : 32;
+                d.queue = cnt + g;
+                d.abort = reinterpret_cast<int*>(cnt + 2);
+                d.done = cnt + 4;
+                d.stage = cnt + 4 + nu;
+                d.err = errf.as<int>();
+                d.u = u;
+                d.wait_cycles = opt.wait_cycles > 0 ? (long long)opt.wait_cycles : 4000000000LL;
+                if (cap == cudaSuccess) cap = launch_batched_persistent(d, w, n_sm, cs);
             }
+        }
         cudaError_t end = cudaStreamEndCapture(cs, &graph);
         if (cap != cudaSuccess || end != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);

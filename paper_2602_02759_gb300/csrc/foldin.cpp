@@ -14,6 +14,7 @@
 // transposed) that the elementwise kernels write.  Parameters, gradients and
 // the Adam moments are FP32 and packed in the order W1, b1, W2, b2, W3, b3
 // (weights [fan_in x fan_out], row-major).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -36,6 +37,9 @@ struct nef_foldin_s {
     double* part = nullptr;
     int n_part = 256;
     int* err = nullptr;
+    float* ws = nullptr;       // split-K partial tiles of the products
+    int64_t ws_floats = 0;
+    int n_sm = 152;
     int64_t t = 0;
     std::vector<void*> allocs;
 };
@@ -87,9 +91,12 @@ nef_status refresh_weights(nef_foldin_t f) {
     return NEF_OK;
 }
 
+// Products with few output tiles and a long K (the first layer's forward product,
+// the weight gradients of the small layers) split K over about one wave of CTAs.
 nef_status gemm(nef_foldin_t f, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
                 int M, int N, int K) {
-    FI_CUDA(nef::launch_gemm_nt(A, lda, B, ldb, C, ldc, M, N, K, 0, f->err, f->st));
+    const int splits = nef::gemm_splits(M, N, K, f->n_sm);
+    FI_CUDA(nef::launch_gemm_nt(A, lda, B, ldb, C, ldc, M, N, K, 0, f->err, f->st, f->ws, f->ws_floats, splits));
     return NEF_OK;
 }
 
@@ -215,6 +222,21 @@ nef_status nef_foldin_create(int d_in, int d_h, int d_out, int max_batch, const 
     A(&f->G1t, h * ldn);
     A(&f->part, f->n_part);
     A(&f->err, 1);
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            f->n_sm = nsm;
+        cudaGetLastError();
+        // every product of forward() and backward(): (M, N, K, ldc)
+        const int64_t prods[8][4] = {{n, h, d, h}, {n, h, h, h}, {n, o, h, o}, {h, o, n, o},
+                                     {n, h, o, h}, {h, h, n, h}, {n, h, h, h}, {d, h, n, h}};
+        for (auto& q : prods) {
+            const int sp = nef::gemm_splits((int)q[0], (int)q[1], (int)q[2], f->n_sm);
+            if (sp > 1) f->ws_floats = std::max<int64_t>(f->ws_floats, sp * q[0] * q[3]);
+        }
+        if (f->ws_floats > 0) A(&f->ws, f->ws_floats);
+    }
     if (s == NEF_OK && cudaMemcpyAsync(f->p, params, f->np * sizeof(float), cudaMemcpyDeviceToDevice, f->st) !=
                            cudaSuccess)
         s = fi_fail(NEF_ECUDA, "parameter copy failed");

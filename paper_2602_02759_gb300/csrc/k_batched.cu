@@ -3,8 +3,7 @@
 //  * k_pad_problem: copy one problem's Y into a zero-padded layout whose
 //    dimensions are multiples of 4 (the TMA stride rule) and pack its mask into
 //    bits; padded entries are unobserved.
-//  * k_finish_batched: the finish step (split reduction, update of Eq. 3.4 and
-//    the canonical copies) for every (problem, restart) unit of a mode phase.
+//  * k_mirror_batched: the canonical copies of every unit's starting factors.
 //  * k_loss_batched: sum over observed entries of D_{alpha,beta}(y, yhat) for
 //    every restart of one problem, reading Y once per entry (App. B, Eq. 3.1).
 #include "nef_batched.h"
@@ -49,30 +48,6 @@ __device__ __forceinline__ uint16_t bf16_bits_b(float x) {
 }
 
 // Element g of the concatenated factor space -> unit by binary search in prefix[].
-__global__ void k_finish_batched(const BatchFinish* __restrict__ fin, const int64_t* __restrict__ prefix,
-                                 int n_units, UpdateSpec u) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= prefix[n_units]) return;
-    int lo = 0, hi = n_units - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
-    }
-    const BatchFinish& f = fin[lo];
-    const int64_t e = g - prefix[lo];
-    const int64_t row = e / f.rank, r = e % f.rank;
-    const int64_t so = row * f.bp + r;
-    float num = 0.f, den = 0.f;
-    for (int s = 0; s < f.n_split; ++s) {
-        num += f.part_num[(int64_t)s * f.s_size + so];
-        den += f.part_den[(int64_t)s * f.s_size + so];
-    }
-    const float v = mu_update(f.theta[e], num, den, u);
-    f.theta[e] = v;
-    f.canon32[so] = v;
-    f.canon16[so] = bf16_bits_b(v);
-}
-
 __global__ void k_mirror_batched(const BatchFinish* __restrict__ fin, const int64_t* __restrict__ prefix,
                                  int n_units) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,12 +118,6 @@ cudaError_t launch_pad_problem(const float* y, const uint8_t* mask, const int64_
     const int64_t nw = (pdims[0] * pdims[1] * pdims[2] + 31) >> 5;
     k_pad_problem<<<blocks_for(nw), kThreads, 0, st>>>(y, mask, dims[0], dims[1], dims[2], pdims[0], pdims[1],
                                                         pdims[2], yp, bits);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finish_batched(const BatchFinish* fin, const int64_t* prefix, int n_units, int64_t total,
-                                  const UpdateSpec& u, cudaStream_t st) {
-    k_finish_batched<<<blocks_for(total), kThreads, 0, st>>>(fin, prefix, n_units, u);
     return cudaGetLastError();
 }
 

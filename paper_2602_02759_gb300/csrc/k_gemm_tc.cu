@@ -2,7 +2,10 @@
 // the fold-in encoder's forward and backward products.
 //
 // A is [M x K] and B is [N x K], both row-major BF16 (K contiguous, "K-major");
-// C is [M x N] row-major FP32 (ldc).  One CTA computes a 128 x 128 tile of C:
+// C is [M x N] row-major FP32 (ldc).  One CTA computes a 128 x 128 tile of C
+// over one range of the K blocks (split-K: blockIdx.z; with several splits each
+// writes its partial tile to a workspace and k_gemm_reduce sums the splits in a
+// fixed order, so the result does not depend on scheduling):
 //   warp 0 (one elected lane): TMA loads of 128 x 64 tiles of A and B into a
 //          4-stage ring (128B swizzle), out-of-range rows/columns read as zero;
 //   warp 1 (one elected lane): tcgen05.mma kind::f16, M = 128, N = 128, K = 16
@@ -13,6 +16,8 @@
 // error flag and the CTA drains its copies and MMAs before freeing TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 
 #include "k_view_tc.cuh"
 #include "nef_internal.h"
@@ -45,14 +50,16 @@ constexpr int kSmem = kMisc + 16 + 1024;      // + alignment slack
 
 __global__ void __launch_bounds__(kThreadsG, 1)
 k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, float* __restrict__ C,
-          int M, int N, int K, int ldc, int accumulate, int* err) {
+          int M, int N, int K, int ldc, int accumulate, int kb_per_split, int* err) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* sm = smem_raw + (base - raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int nk = (K + BK - 1) / BK;
+    const int kb0 = blockIdx.z * kb_per_split;
+    const int nk = max(0, min((K + BK - 1) / BK - kb0, kb_per_split));  // K blocks of this split
+    if (gridDim.z > 1) C += (int64_t)blockIdx.z * M * ldc;                 // this split's partial tile
     const uint32_t bar0 = base + kBar;
     auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 8u * (NST + s); };
@@ -88,8 +95,8 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
             const int s = kb % NST;
             if (!uwait(empty(s), ((kb / NST) & 1) ^ 1, 1)) break;
             mbar_expect_tx_e(full(s), kStage);
-            tma_load_2d_e(base + s * kStage, &amap, kb * BK, m0, full(s));
-            tma_load_2d_e(base + s * kStage + kTileBytes, &bmap, kb * BK, n0, full(s));
+            tma_load_2d_e(base + s * kStage, &amap, (kb0 + kb) * BK, m0, full(s));
+            tma_load_2d_e(base + s * kStage + kTileBytes, &bmap, (kb0 + kb) * BK, n0, full(s));
             issued = kb + 1;
         }
         for (int kb = max(0, issued - NST); kb < issued; ++kb) {
@@ -128,7 +135,7 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
             for (int k = 0; k < 32; ++k) {
                 if (n0 + c0 + k < N) {
                     const float v = (nk > 0) ? __uint_as_float(r[k]) : 0.f;
-                    dst[k] = accumulate ? dst[k] + v : v;
+                    dst[k] = (accumulate && gridDim.z == 1) ? dst[k] + v : v;
                 }
             }
         }
@@ -139,6 +146,18 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
     }
+}
+
+// C (=, or += with accumulate) the sum of the splits' partial tiles, in split order.
+__global__ void k_gemm_reduce(const float* __restrict__ part, int n_split, int M, int N, int ldc,
+                              float* __restrict__ C, int accumulate) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * N) return;
+    const int64_t r = e / N, c = e - r * N;
+    const int64_t off = r * ldc + c, stride = (int64_t)M * ldc;
+    float v = 0.f;
+    for (int z = 0; z < n_split; ++z) v += part[z * stride + off];
+    C[off] = accumulate ? C[off] + v : v;
 }
 
 }  // namespace gemm
@@ -171,8 +190,18 @@ bool encode_kmajor(CUtensorMap* map, const uint16_t* p, int64_t rows, int64_t K,
 }
 }  // namespace
 
+int gemm_splits(int M, int N, int K, int n_sm) {
+    // about one wave of CTAs over the SMs, each split keeping >= 8 K blocks of 64
+    const int64_t tiles = (int64_t)((M + gemm::BM - 1) / gemm::BM) * ((N + gemm::BN - 1) / gemm::BN);
+    const int nk = (K + gemm::BK - 1) / gemm::BK;
+    int64_t s = std::max<int64_t>(1, n_sm / std::max<int64_t>(1, tiles));
+    s = std::min<int64_t>(s, std::max(1, nk / 8));
+    return (int)std::min<int64_t>(s, 16);
+}
+
 cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
-                           int M, int N, int K, int accumulate, int* err, cudaStream_t st) {
+                           int M, int N, int K, int accumulate, int* err, cudaStream_t st, float* ws,
+                           int64_t ws_floats, int n_split) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     // TMA: 16-byte aligned base and row pitch
     if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) || (lda * 2) % 16 ||
@@ -183,8 +212,19 @@ cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, in
     cudaError_t e =
         cudaFuncSetAttribute(gemm::k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm::kSmem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((M + gemm::BM - 1) / gemm::BM), (unsigned)((N + gemm::BN - 1) / gemm::BN));
-    gemm::k_gemm_nt<<<grid, gemm::kThreadsG, gemm::kSmem, st>>>(am, bm, C, M, N, K, (int)ldc, accumulate, err);
+    const int nk = (K + gemm::BK - 1) / gemm::BK;
+    if (n_split < 1 || ws == nullptr || (int64_t)n_split * M * ldc > ws_floats) n_split = 1;
+    n_split = std::max(1, std::min(n_split, std::max(1, nk)));
+    const int per = (nk + n_split - 1) / n_split;
+    n_split = std::max(1, (nk + per - 1) / per);  // no empty split
+    dim3 grid((unsigned)((M + gemm::BM - 1) / gemm::BM), (unsigned)((N + gemm::BN - 1) / gemm::BN),
+              (unsigned)n_split);
+    gemm::k_gemm_nt<<<grid, gemm::kThreadsG, gemm::kSmem, st>>>(am, bm, n_split > 1 ? ws : C, M, N, K, (int)ldc,
+                                                                 accumulate, std::max(per, 1), err);
+    if (n_split > 1) {
+        const int64_t n = (int64_t)M * N;
+        gemm::k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, n_split, M, N, (int)ldc, C, accumulate);
+    }
     return cudaGetLastError();
 }
 

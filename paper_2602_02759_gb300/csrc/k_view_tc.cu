@@ -48,8 +48,6 @@ cudaError_t launch_bp32_lik_loss(const CUtensorMap&, const CUtensorMap&, const C
                                  int, cudaStream_t);
 cudaError_t launch_bp64_lik_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int,
                                  int, cudaStream_t);
-cudaError_t launch_batched_bp16(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
-cudaError_t launch_batched_bp32(const TcUnit*, const TcWork*, int, int, int, cudaStream_t);
 }  // namespace tc
 
 namespace {
@@ -236,15 +234,5 @@ bool tc_make_unit(const float* y, const uint32_t* mbits, const ViewDesc& v, cons
     return true;
 }
 
-cudaError_t launch_view_tc_batched(const TcUnit* units, const TcWork* work, int n_work, int bp, int need_den,
-                                   const WeightSpec& w, cudaStream_t st) {
-    if (n_work <= 0) return cudaSuccess;
-    const int wk = weight_kind(w);
-    switch (bp) {
-        case 16: return tc::launch_batched_bp16(units, work, n_work, need_den, wk, st);
-        case 32: return tc::launch_batched_bp32(units, work, n_work, need_den, wk, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
 
 }  // namespace nef

@@ -531,6 +531,15 @@ __device__ __forceinline__ float tc_loss(float y, float yh, float a, float b, co
     return divergence<float>(y, yh, L);
 }
 
+// 16 bytes of an operand row.  CG: through L2 only (ld.global.cg), for operands
+// that an earlier stage of the same persistent launch rewrote from another SM,
+// where a line left in this SM's L1 by an earlier stage could be stale.
+template <bool CG>
+__device__ __forceinline__ uint4 ld_row16(const uint16_t* p) {
+    if constexpr (CG) return __ldcg(reinterpret_cast<const uint4*>(p));
+    return *reinterpret_cast<const uint4*>(p);
+}
+
 __device__ __forceinline__ int64_t src_row_tc(const SrcDesc& s, int64_t i) {
     int64_t r = 0;
     if ((uint64_t)i < 0xffffffffull) {  // 32-bit division when the index fits (div, mod <= index range)
@@ -594,7 +603,9 @@ struct Layout {
 // column tiles of split sp.
 // QM: the Q-operand path compiled in: 0 gathered rows, 1 TMA-staged rows
 // (prm.qmode must match), 2 both, chosen by prm.qmode at run time (batched launches)
-template <int BP, bool DEN, int WK, bool LOSS, int QM>
+// CG: operand rows by L2-only loads and, at the end, every mbarrier invalidated so
+// that the next work item of a persistent CTA can initialise them again.
+template <int BP, bool DEN, int WK, bool LOSS, int QM, bool CG = false>
 __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUtensorMap* vmap,
                                              const CUtensorMap* cmap, const Params& prm, const int64_t rb,
                                              const int64_t sp) {
@@ -973,8 +984,8 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
                 const int jj = hs * NH + j;
-                nx0[j] = nok ? *reinterpret_cast<const uint4*>(s0 + nrow[0] * ld0 + jj * 8) : make_uint4(0, 0, 0, 0);
-                nx1[j] = (nok && nsrc > 1) ? *reinterpret_cast<const uint4*>(s1 + nrow[1] * ld1 + jj * 8)
+                nx0[j] = nok ? ld_row16<CG>(s0 + nrow[0] * ld0 + jj * 8) : make_uint4(0, 0, 0, 0);
+                nx1[j] = (nok && nsrc > 1) ? ld_row16<CG>(s1 + nrow[1] * ld1 + jj * 8)
                                            : make_uint4(0, 0, 0, 0);
             }
         };
@@ -1007,7 +1018,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
                 }
                 for (int s2 = 2; s2 < nsrc; ++s2) {
                     const uint16_t* sb = static_cast<const uint16_t*>(v.Q.src[s2].ptr);
-                    const uint4 raw = cok ? *reinterpret_cast<const uint4*>(sb + crow[s2] * v.Q.src[s2].ld + jj * 8)
+                    const uint4 raw = cok ? ld_row16<CG>(sb + crow[s2] * v.Q.src[s2].ld + jj * 8)
                                           : make_uint4(0, 0, 0, 0);
                     unpack_bf16x8(raw, f);
 #pragma unroll
@@ -1056,7 +1067,7 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
 #pragma unroll
             for (int j = 0; j < NCH; ++j) {
                 const uint4 x =
-                    row_ok ? *reinterpret_cast<const uint4*>(pbase + pr * ps.ld + j * 8) : make_uint4(0, 0, 0, 0);
+                    row_ok ? ld_row16<CG>(pbase + pr * ps.ld + j * 8) : make_uint4(0, 0, 0, 0);
                 pv[4 * j] = x.x;
                 pv[4 * j + 1] = x.y;
                 pv[4 * j + 2] = x.z;
@@ -1289,6 +1300,13 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");
     }
+    if constexpr (CG) {
+        // every wait of this item has completed or was drained: the barriers are idle
+        if (tid == 0)
+            for (int b = 0; b < LY::kNumBars; ++b)
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0 + 8u * b) : "memory");
+        __syncthreads();
+    }
 }
 
 // LOSS: also sum the loss terms into prm.loss_part (a separate instance, so the
@@ -1301,19 +1319,97 @@ k_view_tc(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUte
     view_tc_body<BP, DEN, WK, LOSS, QM>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb, blockIdx.x / n_rb);
 }
 
-// Batched form: CTA b runs work[b] = (unit, row block, split); the unit's tensor
-// maps stay in global memory and its parameters are staged in shared memory.
-template <int BP, bool DEN, int WK>
-__global__ void __launch_bounds__(kThreads, 1)
-k_view_tc_batched(const TcUnit* __restrict__ units, const TcWork* __restrict__ work) {
+// ---------------------------------------------------------- persistent batched fit
+// Spin (bounded) until *flag >= target; false on timeout (raises the error flag
+// and the abort flag) or when another CTA aborted.
+__device__ __forceinline__ bool wait_stage(const unsigned int* flag, unsigned int target, const PersistDesc& d) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v >= target) return true;
+        if (*(volatile int*)d.abort) return false;
+        if (clock64() - t0 > d.wait_cycles) {
+            atomicCAS(d.err, 0, 20);
+            atomicExch(d.abort, 1);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
+// The update of one (unit, mode) stage by the whole CTA: split reduction of the
+// partials (L2-only loads: other SMs wrote them), Eq. 3.4 and the operand copies.
+__device__ __forceinline__ void persist_finish(const BatchFinish& f, const UpdateSpec& u) {
+    const int64_t n_el = f.rows * f.rank;
+    for (int64_t e = threadIdx.x; e < n_el; e += blockDim.x) {
+        const int64_t row = e / f.rank, r = e - row * f.rank;
+        const int64_t so = row * f.bp + r;
+        float num = 0.f, den = 0.f;
+        for (int s = 0; s < f.n_split; ++s) {
+            num += __ldcg(f.part_num + (int64_t)s * f.s_size + so);
+            den += __ldcg(f.part_den + (int64_t)s * f.s_size + so);
+        }
+        const float v = mu_update(__ldcg(f.theta + e), num, den, u);
+        f.theta[e] = v;
+        f.canon32[so] = v;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        f.canon16[so] = *reinterpret_cast<const uint16_t*>(&b);
+    }
+    // the copies are read by later stages' bulk tensor copies (async proxy) and loads
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __threadfence();
+}
+
+template <int BP, int WK>
+__global__ void __launch_bounds__(kThreads, 1) k_batched_persistent(const __grid_constant__ PersistDesc d) {
     __shared__ __align__(16) unsigned char prm_sh[(sizeof(Params) + 15) / 16 * 16];
-    const TcWork wk = work[blockIdx.x];
-    const TcUnit* U = units + wk.unit;
-    for (int i = threadIdx.x; i < (int)(sizeof(prm_sh) / 16); i += blockDim.x)
-        reinterpret_cast<uint4*>(prm_sh)[i] = reinterpret_cast<const uint4*>(U->prm)[i];
-    __syncthreads();
-    view_tc_body<BP, DEN, WK, false, 2>(&U->ymap, &U->vmap, &U->cmap, *reinterpret_cast<const Params*>(prm_sh),
-                                        wk.rb, wk.sp);
+    __shared__ unsigned int item_sh;
+    __shared__ int finish_sh;
+    const unsigned int total = (unsigned int)d.n_items * (unsigned int)d.n_sweeps;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = *(volatile int*)d.abort ? total : atomicAdd(d.queue, 1u);
+        __syncthreads();
+        const unsigned int q = item_sh;
+        if (q >= total) break;
+        const int sl = (int)(q / (unsigned int)d.n_items);
+        const PersistItem it = d.items[q - (unsigned int)sl * (unsigned int)d.n_items];
+        const int s = d.sweep0 + sl;  // the item's sweep
+        const int l = it.um / d.n_units, unit = it.um - l * d.n_units;
+        // stages of the unit finish in the order (sweep 0, mode 0), (0, 1), (0, 2), (1, 0), ...
+        const unsigned int seq = (unsigned int)(s * 3 + l);
+        bool go = true;
+        if (threadIdx.x == 0 && seq > 0) go = wait_stage(d.stage + unit, seq, d);
+        if (threadIdx.x == 0) finish_sh = go ? 1 : 0;
+        __syncthreads();
+        if (!finish_sh) break;
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const TcUnit* U = d.units + it.um;
+        for (int i = threadIdx.x; i < (int)(sizeof(prm_sh) / 16); i += blockDim.x)
+            reinterpret_cast<uint4*>(prm_sh)[i] = __ldcg(reinterpret_cast<const uint4*>(U->prm) + i);
+        __syncthreads();
+        const Params& prm = *reinterpret_cast<const Params*>(prm_sh);
+        view_tc_body<BP, true, WK, false, 2, true>(&U->ymap, &U->vmap, &U->cmap, prm, it.rb, it.sp);
+        // partials written: count the item; the stage's last item applies the update
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned int cum = (unsigned int)s * (unsigned int)d.sweep_items[unit] +
+                                     (unsigned int)d.prefix_items[it.um] + (unsigned int)d.stage_items[it.um];
+            const unsigned int old = atomicAdd(d.done + unit, 1u);
+            finish_sh = (old + 1u == cum) ? 1 : 0;
+            __threadfence();
+        }
+        __syncthreads();
+        if (finish_sh) {
+            persist_finish(d.fin[it.um], d.u);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(d.stage + unit), "r"(seq + 1u) : "memory");
+            }
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace tc

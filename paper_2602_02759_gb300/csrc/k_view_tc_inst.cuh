@@ -57,28 +57,6 @@ cudaError_t launch_bp_lik(const CUtensorMap& map, const CUtensorMap& vmap, const
     }
 }
 
-template <int BP, bool DEN, int WK>
-cudaError_t launch_batched_one(const TcUnit* units, const TcWork* work, int n_work, cudaStream_t st) {
-    auto kern = k_view_tc_batched<BP, DEN, WK>;
-    const int sm = Layout<BP, DEN>::kAlloc;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    kern<<<n_work, kThreads, sm, st>>>(units, work);
-    return cudaGetLastError();
-}
-
-template <int BP>
-cudaError_t launch_batched_bp(const TcUnit* units, const TcWork* work, int n_work, int den, int wk,
-                              cudaStream_t st) {
-    if (den) {
-        switch (wk) {
-            case WK_KL: return launch_batched_one<BP, true, WK_KL>(units, work, n_work, st);
-            default: return launch_batched_one<BP, true, WK_GEN>(units, work, n_work, st);
-        }
-    }
-    return launch_batched_one<BP, false, WK_GEN>(units, work, n_work, st);
-}
-
 }  // namespace tc
 }  // namespace nef
 
@@ -110,13 +88,3 @@ cudaError_t launch_batched_bp(const TcUnit* units, const TcWork* work, int n_wor
 #define NEF_TC_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _loss, true, 1)
 #define NEF_TC_GATHER_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _g, false, 0)
 #define NEF_TC_GATHER_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _g_loss, true, 0)
-
-#define NEF_TC_BATCHED_INSTANCE(BP)                                                          \
-    namespace nef {                                                                          \
-    namespace tc {                                                                           \
-    cudaError_t launch_batched_bp##BP(const TcUnit* units, const TcWork* work, int n_work,   \
-                                      int den, int wk, cudaStream_t st) {                    \
-        return launch_batched_bp<BP>(units, work, n_work, den, wk, st);                      \
-    }                                                                                        \
-    }                                                                                        \
-    }

@@ -239,8 +239,14 @@ cudaError_t launch_convert_bf16(float* src, int64_t n, uint16_t* dst, cudaStream
 // Tensor-core GEMM C[M x N] (=, or += with accumulate) A[M x K] . B[N x K]^T; A and B
 // row-major BF16 (pitches lda, ldb elements, multiples of 8; 16-byte aligned bases),
 // C row-major FP32 (pitch ldc).  err: device flag set when a bounded wait gives up.
+// n_split > 1 splits K over that many CTAs per tile, with partial tiles in ws
+// (n_split * M * ldc floats; too small or null: no split) summed in split order.
 cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
-                           int M, int N, int K, int accumulate, int* err, cudaStream_t st);
+                           int M, int N, int K, int accumulate, int* err, cudaStream_t st, float* ws = nullptr,
+                           int64_t ws_floats = 0, int n_split = 1);
+
+// Split count for an M x N x K product on n_sm SMs (about one wave of CTAs).
+int gemm_splits(int M, int N, int K, int n_sm);
 
 // Fold-in encoder kernels (k_foldin.cu).
 cudaError_t launch_fi_features(const float* slices, int n, int d, uint16_t* x, uint16_t* xt, int ldt, cudaStream_t st);

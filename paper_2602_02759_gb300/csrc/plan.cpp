@@ -1045,10 +1045,14 @@ nef_status prof_begin(nef_plan_t p, cudaStream_t st, cudaEvent_t* a, cudaEvent_t
     return NEF_OK;
 }
 
+// One factor update (Algorithm 1's inner step).  With export_num/export_den the
+// pass stops after forming num and den (Eq. 3.6-3.8), copies them there and
+// leaves the factor unchanged (the caller sums them over shards of Y first).
 template <typename T>
 nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbits,
                     void* const* factors, const WeightSpec& w, const UpdateSpec& u, cudaStream_t st,
-                    const LossSpec* loss = nullptr, int* n_part = nullptr) {
+                    const LossSpec* loss = nullptr, int* n_part = nullptr, T* export_num = nullptr,
+                    T* export_den = nullptr) {
     const Model& md = p->md;
     const int64_t nl = md.fac_size(pp.l);
     T* num = static_cast<T*>(buf_ptr(p, B_NUM));
@@ -1076,6 +1080,11 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
                                            np, st));
         NEF_TRY(run_ein<T>(p, pp.gen_num, factors, st));
         NEF_TRY(run_ein<T>(p, pp.gen_den, factors, st));
+        if (export_num) {
+            NEF_CUDA(cudaMemcpyAsync(export_num, num, nl * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            NEF_CUDA(cudaMemcpyAsync(export_den, den, nl * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            return NEF_OK;
+        }
         NEF_CUDA(launch_update_mirror<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, (int)ldims.size(),
                                          ldims.data(), mir, st));
         return after_update<T>(p, pp.l, st);
@@ -1112,7 +1121,7 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
         NEF_CUDA(cudaEventRecord(e1, st));
         p->ev_used.push_back({use_tc ? 0 : 1, {e0, e1}});
     }
-    if (pp.finish_identity) {
+    if (pp.finish_identity && !export_num) {
         // split reduction, denominator, update and the factor's copies in one kernel
         FinishDesc d{};
         d.nlet = (int)ldims.size();
@@ -1146,10 +1155,16 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
         NEF_TRY(run_ein<T>(p, pp.den_prod, factors, st));
         NEF_TRY(run_ein<T>(p, pp.epi_den_closed, factors, st));
     }
+    if (export_num) {
+        NEF_CUDA(cudaMemcpyAsync(export_num, num, nl * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        NEF_CUDA(cudaMemcpyAsync(export_den, den, nl * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        return NEF_OK;
+    }
     NEF_CUDA(launch_update_mirror<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, (int)ldims.size(),
                                      ldims.data(), mir, st));
     return after_update<T>(p, pp.l, st);
 }
+
 
 // The plan's loss family with the call's (alpha, beta) (ignored by the likelihood families).
 nef_status check_ab(nef_plan_t p, double al, double be) {
@@ -1192,6 +1207,33 @@ nef_status prologue(nef_plan_t p, const void* Y, const uint8_t* mask, void* cons
         if (h) return fail(NEF_EDATA, "Y holds a negative or non-finite entry");
     }
     return NEF_OK;
+}
+
+// num and den of factor l at the caller's factors (nef_numden), or the update of
+// factor l from given num and den (nef_apply_update: num_in set).
+template <typename T>
+nef_status numden_impl(nef_plan_t p, int l, const void* Y, const uint8_t* mask, void* const* factors, double al,
+                       double be, T* num, T* den, const T* num_in = nullptr, const T* den_in = nullptr) {
+    cudaStream_t st = static_cast<cudaStream_t>(p->opt.stream);
+    if (p->opt.loss != NEF_LOSS_AB) al = be = 0.0;
+    const Specs sp = specs_of(p, al, be);
+    if (num_in) {
+        if (!factors) return fail(NEF_EINVAL, "factors is NULL");
+        for (int f = 0; f < p->md.L; ++f)
+            if (!factors[f]) return fail(NEF_EINVAL, "factor %d is NULL", f);
+        NEF_TRY(init_sources<T>(p, factors, st));
+        const Model& md = p->md;
+        std::vector<int64_t> ldims;
+        for (int x : md.term[l]) ldims.push_back(md.dim[x]);
+        NEF_CUDA(launch_update_mirror<T>(static_cast<T*>(factors[l]), num_in, den_in, md.fac_size(l), sp.u,
+                                         (int)ldims.size(), ldims.data(), mirror_desc(p, l), st));
+        return after_update<T>(p, l, st);
+    }
+    const uint32_t* mbits = nullptr;
+    NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
+    NEF_TRY(init_sources<T>(p, factors, st));
+    return run_pass<T>(p, p->pass[l], static_cast<const T*>(Y), mbits, factors, sp.w, sp.u, st, nullptr, nullptr,
+                       num, den);
 }
 
 // One sweep of Algorithm 1 (or the single update only_l).  With `loss`, the
@@ -1890,8 +1932,8 @@ nef_status build_plan(nef_plan_t p) {
 
 }  // namespace
 
-static_assert(NEF_LOSS_AB == LIK_NONE && NEF_LOSS_NEGBIN == LIK_NEGBIN && NEF_LOSS_BINOMIAL == LIK_BINOMIAL &&
-                  NEF_LOSS_JS == LIK_JS,
+static_assert((int)NEF_LOSS_AB == (int)LIK_NONE && (int)NEF_LOSS_NEGBIN == (int)LIK_NEGBIN &&
+                  (int)NEF_LOSS_BINOMIAL == (int)LIK_BINOMIAL && (int)NEF_LOSS_JS == (int)LIK_JS,
               "loss families of the ABI and of the kernels");
 
 // ================================================================== C ABI
@@ -2039,6 +2081,34 @@ nef_status nef_update(nef_plan_t plan, int l, const void* Y, const uint8_t* mask
     NEF_TRY(check_ab(plan, alpha, beta));
     if (plan->prec == NEF_FP64) return fit_impl<double>(plan, Y, mask, factors, alpha, beta, 1, l);
     return fit_impl<float>(plan, Y, mask, factors, alpha, beta, 1, l);
+}
+
+nef_status nef_numden(nef_plan_t plan, int l, const void* Y, const uint8_t* mask, void* const* factors,
+                      double alpha, double beta, void* num, void* den) {
+    g_err.clear();
+    if (!plan) return fail(NEF_EINVAL, "plan is NULL");
+    if (l < 0 || l >= plan->md.L) return fail(NEF_EINVAL, "factor index %d out of range", l);
+    if (!num || !den) return fail(NEF_EINVAL, "num/den is NULL");
+    NEF_TRY(check_ab(plan, alpha, beta));
+    if (plan->prec == NEF_FP64)
+        return numden_impl<double>(plan, l, Y, mask, factors, alpha, beta, static_cast<double*>(num),
+                                   static_cast<double*>(den));
+    return numden_impl<float>(plan, l, Y, mask, factors, alpha, beta, static_cast<float*>(num),
+                              static_cast<float*>(den));
+}
+
+nef_status nef_apply_update(nef_plan_t plan, int l, void* const* factors, const void* num, const void* den,
+                            double alpha, double beta) {
+    g_err.clear();
+    if (!plan) return fail(NEF_EINVAL, "plan is NULL");
+    if (l < 0 || l >= plan->md.L) return fail(NEF_EINVAL, "factor index %d out of range", l);
+    if (!num || !den) return fail(NEF_EINVAL, "num/den is NULL");
+    NEF_TRY(check_ab(plan, alpha, beta));
+    if (plan->prec == NEF_FP64)
+        return numden_impl<double>(plan, l, nullptr, nullptr, factors, alpha, beta, nullptr, nullptr,
+                                   static_cast<const double*>(num), static_cast<const double*>(den));
+    return numden_impl<float>(plan, l, nullptr, nullptr, factors, alpha, beta, nullptr, nullptr,
+                              static_cast<const float*>(num), static_cast<const float*>(den));
 }
 
 nef_status nef_loss(nef_plan_t plan, const void* Y, const uint8_t* mask, void* const* factors,

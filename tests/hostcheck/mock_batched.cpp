@@ -87,67 +87,101 @@ bool tc_make_unit(const float* y, const uint32_t* mbits, const ViewDesc& v, cons
     return true;
 }
 
-// Per work item: S[split][row][:] = sum over the split's columns of W(y, yhat) Q[col, :]
+// One work item: S[split][row][:] = sum over the split's columns of W(y, yhat) Q[col, :]
 // for the rows of one row block (Eq. 3.8 with the bond re-association).
-cudaError_t launch_view_tc_batched(const TcUnit* units, const TcWork* work, int n_work, int bp, int need_den,
-                                   const WeightSpec&, cudaStream_t) {
+static void mock_item(const TcUnit* units, int um, int rb, int sp, int bp, int need_den) {
+    int64_t id;
+    std::memcpy(&id, units[um].prm, sizeof(id));
+    const MockUnit& m = registry()[(size_t)id];
+    const ViewDesc& v = m.v;
+    const bool trans = v.c_in == 1;
+    const int64_t t_lo = (int64_t)sp * m.tiles_per_split;
+    const int64_t t_hi = std::min(t_lo + m.tiles_per_split, m.n_tiles);
+    std::vector<float> q(bp), sn(bp), sd(bp);
+    for (int64_t row = (int64_t)rb * kTM; row < std::min(v.rows, (int64_t)(rb + 1) * kTM); ++row) {
+        std::fill(sn.begin(), sn.end(), 0.f);
+        std::fill(sd.begin(), sd.end(), 0.f);
+        const uint16_t* prow = static_cast<const uint16_t*>(v.P.src[0].ptr) + src_row(v.P.src[0], row) * bp;
+        for (int64_t t = t_lo; t < t_hi; ++t) {
+            int64_t col0, nvalid;
+            if (trans) {
+                col0 = t * kTN;
+                nvalid = std::min<int64_t>(kTN, v.c_out - col0);
+            } else {
+                const int64_t co = t / m.n_cib, ci = t % m.n_cib;
+                col0 = co * v.c_in + ci * kTN;
+                nvalid = std::min<int64_t>(kTN, v.c_in - ci * kTN);
+            }
+            for (int64_t c = 0; c < nvalid; ++c) {
+                const int64_t col = col0 + c;
+                const int64_t e = trans ? col * v.rows + row
+                                        : ((col / v.c_in) * v.rows + row) * v.c_in + col % v.c_in;
+                if (m.mbits && !mask_bit(m.mbits, e)) continue;
+                for (int b = 0; b < bp; ++b) q[b] = 1.f;
+                for (int s = 0; s < v.Q.nsrc; ++s) {
+                    const uint16_t* qrow =
+                        static_cast<const uint16_t*>(v.Q.src[s].ptr) + src_row(v.Q.src[s], col) * bp;
+                    for (int b = 0; b < bp; ++b) q[b] *= bf16_value(qrow[b]);
+                }
+                float yh = 0.f;
+                for (int b = 0; b < bp; ++b) {
+                    q[b] = bf16_round(q[b]);
+                    yh += bf16_value(prow[b]) * q[b];
+                }
+                float wa, wb;
+                ab_weights(m.y[e], yh, m.w, wa, wb);
+                wa = bf16_round(wa);
+                wb = bf16_round(wb);
+                for (int b = 0; b < bp; ++b) {
+                    sn[b] += wa * q[b];
+                    sd[b] += wb * q[b];
+                }
+            }
+        }
+        float* dn = m.s_num + ((int64_t)sp * v.rows + row) * bp;
+        for (int b = 0; b < bp; ++b) dn[b] = sn[b];
+        if (need_den) {
+            float* dd = m.s_den + ((int64_t)sp * v.rows + row) * bp;
+            for (int b = 0; b < bp; ++b) dd[b] = sd[b];
+        }
+    }
+}
+
+// The update of one (unit, mode) stage: split reduction, Eq. 3.4, operand copies.
+static void mock_finish(const BatchFinish& f, const UpdateSpec& u) {
+    for (int64_t e = 0; e < f.rows * f.rank; ++e) {
+        const int64_t so = (e / f.rank) * f.bp + e % f.rank;
+        float num = 0.f, den = 0.f;
+        for (int s = 0; s < f.n_split; ++s) {
+            num += f.part_num[(int64_t)s * f.s_size + so];
+            den += f.part_den[(int64_t)s * f.s_size + so];
+        }
+        const float v = mu_update(f.theta[e], num, den, u);
+        f.theta[e] = v;
+        f.canon32[so] = v;
+        f.canon16[so] = bf16_bits(v);
+    }
+}
+
+// The persistent launch, one CTA: items taken in queue order; before an item the
+// unit's preceding stage must be finished (the launch would wait for it), after it
+// the stage counter rule decides whether this item applies the stage's update.
+cudaError_t launch_batched_persistent(const PersistDesc& d, const WeightSpec&, int, cudaStream_t) {
     return host_submit([=]() -> cudaError_t {
-        for (int k = 0; k < n_work; ++k) {
-            const TcWork wk = work[k];
-            int64_t id;
-            std::memcpy(&id, units[wk.unit].prm, sizeof(id));
-            const MockUnit& m = registry()[(size_t)id];
-            const ViewDesc& v = m.v;
-            const bool trans = v.c_in == 1;
-            const int64_t t_lo = (int64_t)wk.sp * m.tiles_per_split;
-            const int64_t t_hi = std::min(t_lo + m.tiles_per_split, m.n_tiles);
-            std::vector<float> q(bp), sn(bp), sd(bp);
-            for (int64_t row = (int64_t)wk.rb * kTM; row < std::min(v.rows, (int64_t)(wk.rb + 1) * kTM); ++row) {
-                std::fill(sn.begin(), sn.end(), 0.f);
-                std::fill(sd.begin(), sd.end(), 0.f);
-                const uint16_t* prow = static_cast<const uint16_t*>(v.P.src[0].ptr) + src_row(v.P.src[0], row) * bp;
-                for (int64_t t = t_lo; t < t_hi; ++t) {
-                    int64_t col0, nvalid;
-                    if (trans) {
-                        col0 = t * kTN;
-                        nvalid = std::min<int64_t>(kTN, v.c_out - col0);
-                    } else {
-                        const int64_t co = t / m.n_cib, ci = t % m.n_cib;
-                        col0 = co * v.c_in + ci * kTN;
-                        nvalid = std::min<int64_t>(kTN, v.c_in - ci * kTN);
-                    }
-                    for (int64_t c = 0; c < nvalid; ++c) {
-                        const int64_t col = col0 + c;
-                        const int64_t e = trans ? col * v.rows + row
-                                                : ((col / v.c_in) * v.rows + row) * v.c_in + col % v.c_in;
-                        if (m.mbits && !mask_bit(m.mbits, e)) continue;
-                        for (int b = 0; b < bp; ++b) q[b] = 1.f;
-                        for (int s = 0; s < v.Q.nsrc; ++s) {
-                            const uint16_t* qrow =
-                                static_cast<const uint16_t*>(v.Q.src[s].ptr) + src_row(v.Q.src[s], col) * bp;
-                            for (int b = 0; b < bp; ++b) q[b] *= bf16_value(qrow[b]);
-                        }
-                        float yh = 0.f;
-                        for (int b = 0; b < bp; ++b) {
-                            q[b] = bf16_round(q[b]);
-                            yh += bf16_value(prow[b]) * q[b];
-                        }
-                        float wa, wb;
-                        ab_weights(m.y[e], yh, m.w, wa, wb);
-                        wa = bf16_round(wa);
-                        wb = bf16_round(wb);
-                        for (int b = 0; b < bp; ++b) {
-                            sn[b] += wa * q[b];
-                            sd[b] += wb * q[b];
-                        }
-                    }
-                }
-                float* dn = m.s_num + ((int64_t)wk.sp * v.rows + row) * bp;
-                for (int b = 0; b < bp; ++b) dn[b] = sn[b];
-                if (need_den) {
-                    float* dd = m.s_den + ((int64_t)wk.sp * v.rows + row) * bp;
-                    for (int b = 0; b < bp; ++b) dd[b] = sd[b];
-                }
+        const uint64_t total = (uint64_t)d.n_items * (uint64_t)d.n_sweeps;
+        for (uint64_t q = *d.queue; q < total; q = ++*d.queue) {
+            const int sl = (int)(q / (uint64_t)d.n_items);
+            const PersistItem it = d.items[q - (uint64_t)sl * d.n_items];
+            const int s = d.sweep0 + sl;
+            const int l = it.um / d.n_units, unit = it.um - l * d.n_units;
+            const unsigned int seq = (unsigned int)(s * 3 + l);
+            if (d.stage[unit] < seq) return cudaErrorInvalidValue;  // a CTA would wait for an item it holds
+            mock_item(d.units, it.um, it.rb, it.sp, d.bp, 1);
+            const unsigned int cum = (unsigned int)s * d.sweep_items[unit] + d.prefix_items[it.um] +
+                                     d.stage_items[it.um];
+            if (++d.done[unit] == cum) {
+                mock_finish(d.fin[it.um], d.u);
+                d.stage[unit] = seq + 1;
             }
         }
         return cudaSuccess;
@@ -174,28 +208,6 @@ cudaError_t launch_pad_problem(const float* y, const uint8_t* mask, const int64_
                     yp[e] = v;
                     if (obs) bits[e >> 5] |= 1u << (e & 31);
                 }
-        return cudaSuccess;
-    });
-}
-
-cudaError_t launch_finish_batched(const BatchFinish* fin, const int64_t* prefix, int n_units, int64_t,
-                                  const UpdateSpec& u, cudaStream_t) {
-    return host_submit([=]() -> cudaError_t {
-        for (int x = 0; x < n_units; ++x) {
-            const BatchFinish& f = fin[x];
-            for (int64_t e = 0; e < prefix[x + 1] - prefix[x]; ++e) {
-                const int64_t so = (e / f.rank) * f.bp + e % f.rank;
-                float num = 0.f, den = 0.f;
-                for (int s = 0; s < f.n_split; ++s) {
-                    num += f.part_num[(int64_t)s * f.s_size + so];
-                    den += f.part_den[(int64_t)s * f.s_size + so];
-                }
-                const float v = mu_update(f.theta[e], num, den, u);
-                f.theta[e] = v;
-                f.canon32[so] = v;
-                f.canon16[so] = bf16_bits(v);
-            }
-        }
         return cudaSuccess;
     });
 }

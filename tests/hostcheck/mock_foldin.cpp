@@ -40,8 +40,17 @@ void write_pair(uint16_t* dst, uint16_t* dst_t, int64_t ldt, int n, int d, int64
 
 }  // namespace
 
+int gemm_splits(int M, int N, int K, int n_sm) {
+    const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + 127) / 128);
+    const int nk = (K + 63) / 64;
+    int64_t s = std::max<int64_t>(1, n_sm / std::max<int64_t>(1, tiles));
+    s = std::min<int64_t>(s, std::max(1, nk / 8));
+    return (int)std::min<int64_t>(s, 16);
+}
+
+// The split count changes only the order of the FP32 sums, not the product.
 cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
-                           int M, int N, int K, int accumulate, int*, cudaStream_t) {
+                           int M, int N, int K, int accumulate, int*, cudaStream_t, float*, int64_t, int) {
     return host_submit([=]() -> cudaError_t {
         for (int i = 0; i < M; ++i)
             for (int j = 0; j < N; ++j) {

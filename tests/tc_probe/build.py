@@ -67,6 +67,9 @@ def load():
         lib.nef_tc_gemm.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_int, vp, vp]
         lib.nef_tc_gemm.restype = ctypes.c_int
+        lib.nef_tc_gemm_split.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int64, vp, vp]
+        lib.nef_tc_gemm_split.restype = ctypes.c_int
         _lib = lib
     return _lib
 

@@ -40,6 +40,14 @@ int nef_tc_probe(int bond_pad, int a_in_tmem, const uint16_t* P, const uint16_t*
 int nef_tc_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
                 int K, int* err, void* stream);
 
+/*
+ * nef_tc_gemm_split -- the same product with K split over n_split CTAs per tile,
+ * their partial tiles in ws (device, ws_floats FP32 values, at least
+ * n_split * M * ldc) summed in split order.  Returns as nef_tc_gemm.
+ */
+int nef_tc_gemm_split(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int M,
+                      int N, int K, int n_split, float* ws, int64_t ws_floats, int* err, void* stream);
+
 
 #ifdef __cplusplus
 }

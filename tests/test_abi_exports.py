@@ -42,7 +42,7 @@ def test_probe_entry_points_live_only_in_the_test_library(lib):
     spec.loader.exec_module(mod)
     probe = ctypes.CDLL(mod.build())
     names = _declared("nef_probe.h", PROBE)
-    assert names == ["nef_tc_gemm", "nef_tc_probe"]
+    assert names == ["nef_tc_gemm", "nef_tc_gemm_split", "nef_tc_probe"]
     for name in names:
         assert hasattr(probe, name), name
         assert not hasattr(lib, name), name

@@ -59,6 +59,32 @@ def test_tc_gemm(M, N, K):
     np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("M,N,K,splits", [(256, 256, 4096, 8), (200, 72, 1000, 3), (1536, 512, 2048, 3)])
+def test_tc_gemm_split_k(M, N, K, splits):
+    """Split-K: the K blocks of each tile spread over `splits` CTAs, partial tiles
+    summed in split order: the BF16 product within FP32 rounding of the FP64
+    product of the same BF16 values, and bit-identical on a second call."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.uniform(-1, 1, (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (N, K)).astype(np.float32)
+    tA = torch.as_tensor(A).cuda().to(torch.bfloat16).contiguous()
+    tB = torch.as_tensor(B).cuda().to(torch.bfloat16).contiguous()
+    ws = torch.empty(splits * M * N, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs = []
+    for _ in range(2):
+        C = torch.full((M, N), float("nan"), device="cuda")
+        rc = _probe().nef_tc_gemm_split(tA.data_ptr(), K, tB.data_ptr(), K, C.data_ptr(), N, M, N, K, splits,
+                                        ws.data_ptr(), ws.numel(), err.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert rc == 0 and int(err.item()) == 0
+        outs.append(C.cpu().numpy())
+    ref = bf16(A) @ bf16(B).T
+    np.testing.assert_allclose(outs[0], ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def _setup(d=256, h=64, o=16, n=48, seed=0):
     rng = np.random.default_rng(seed)
     params = synth.mlp_params((d, h, h, o), seed=seed)

@@ -8,9 +8,16 @@ parity suite, through the C ABI against the FP64 oracle:
     (exponential update), selected by nef_options.loss.
 
 Tolerances as in the main parity suite: FP64 plans 1e-10, FP32 plans 3e-5
-(relative Frobenius, two sweeps), BF16 one update 2e-3 per element and the
-loss after several sweeps within 1e-3 of the oracle's trace.
+(relative Frobenius, two sweeps), BF16 one update 2e-3 relative Frobenius and
+per element, and the loss after several sweeps within 1e-3 of the oracle's trace.
+Per element, views whose bond is narrower than 16 or whose Q operand is a product
+of three or more gathered sources get 5e-3: every factor element enters the
+reconstruction rounded to BF16 (2^-9 relative), a Q row holds the product of up
+to three such roundings plus the rounding of each product, and with a bond of 5
+or 8 the reconstruction averages over few latent terms, so its error keeps the
+sign of a few roundings that all entries of a factor row share.
 """
+import re
 import numpy as np
 import pytest
 
@@ -131,7 +138,12 @@ def test_bf16_single_updates(model_str, dims, kind, par):
         assert plan.profile()["tcgen05"][1] == 1, "the tensor-core pass did not run"
         got = fs[l].double().cpu().numpy()
         assert np.all(np.isfinite(got))
-        np.testing.assert_allclose(got, ref, rtol=2e-3, atol=0, err_msg=f"factor {l}\n{plan.info()}")
+        assert rel(got, ref) < 2e-3, (l, rel(got, ref))
+        line = plan.info().splitlines()[l]
+        bond = int(re.search(r"bond='\w+' \((\d+)->", line).group(1))
+        nsrc = int(re.search(r"Q=gather\((\d+)\)", line).group(1)) if "gather(" in line else 1
+        tol = 2e-3 if bond >= 16 and nsrc <= 2 else 5e-3
+        np.testing.assert_allclose(got, ref, rtol=tol, atol=0, err_msg=f"factor {l}\n{plan.info()}")
 
 
 @pytest.mark.parametrize("kind,par", KINDS)
@@ -198,3 +210,39 @@ def test_bf16_loss_runs_on_tensor_cores():
         assert cnt == rc
         print(f"nef_loss bf16 {kind}: rel {abs(lo - ref) / ref:.2e}")
         assert lo == pytest.approx(ref, rel=1e-3), kind
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 2e-3)])
+def test_numden_over_slabs_then_update_matches_oracle(prec, tol):
+    """The two halves of the inner step on the GPU (nef_numden, nef_apply_update):
+    Y split in two slabs along i, each slab's num/den of factor B computed by its
+    own plan, summed (what the all-reduce of the multi-GPU form does) and applied:
+    equal to the oracle's update of B on the whole tensor; and on one slab the two
+    halves equal nef_update."""
+    nef = _nef()
+    model_str, dims = "ir,jr,kr->ijk", dict(i=160, j=96, k=192, r=32)
+    m, y, mask, init = _setup(model_str, dims, "negbin", 2.0, 23, True)
+    ref = m.update_factor(1, y, mask, init, 1.0, 0.0)[0][1]
+    halves = [(0, 72), (72, 160)]
+    num_t = den_t = None
+    for lo, hi in halves:
+        plan = nef.Plan(model_str, dict(dims, i=hi - lo), precision=prec)
+        fs = [dev(init[0][lo:hi]), dev(init[1]), dev(init[2])]
+        num, den = plan.numden(1, dev(y[lo:hi]), dev(mask[lo:hi], torch.uint8), fs, 1.0, 0.0)
+        plan.check()
+        num_t = num if num_t is None else num_t + num
+        den_t = den if den_t is None else den_t + den
+    fs = [dev(init[0]), dev(init[1]), dev(init[2])]
+    whole = nef.Plan(model_str, dims, precision=prec)
+    whole.apply_update(1, fs, num_t, den_t, 1.0, 0.0)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(fs[1].double().cpu().numpy(), ref, rtol=tol, atol=0)
+    # on one tensor: numden + apply_update == nef_update (same products, other summation order)
+    Y, M = dev(y), dev(mask, torch.uint8)
+    a = [dev(f) for f in init]
+    b = [dev(f) for f in init]
+    whole.update(2, Y, M, a, 1.0, 0.0)
+    n2, d2 = whole.numden(2, Y, M, b, 1.0, 0.0)
+    whole.apply_update(2, b, n2, d2, 1.0, 0.0)
+    whole.check()
+    np.testing.assert_allclose(b[2].cpu().numpy(), a[2].cpu().numpy(), rtol=1e-5, atol=0)
