@@ -130,12 +130,25 @@ __global__ void k_fi_relu_grad(float* __restrict__ g, const float* __restrict__ 
 }
 
 // out[c] = sum over rows of g[r][c] (fixed order), one thread per column.
-__global__ void k_fi_colsum(const float* __restrict__ g, int n, int h, float* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= h) return;
+// Column sums of g [n x h]: a block per 32 columns; its 32 warps take rows
+// w, w + 32, ... of their column (lane), then warp 0 adds the 32 partial sums in
+// warp order (a fixed order: the result does not depend on scheduling).
+constexpr int kColsumWarps = 32;
+__global__ void __launch_bounds__(32 * kColsumWarps) k_fi_colsum(const float* __restrict__ g, int n, int h,
+                                                                 float* __restrict__ out) {
+    __shared__ float part[kColsumWarps][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int r = 0; r < n; ++r) s += g[(int64_t)r * h + c];
-    out[c] = s;
+    if (c < h)
+        for (int r = w; r < n; r += kColsumWarps) s += g[(int64_t)r * h + c];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && c < h) {
+        float t = 0.f;
+        for (int k = 0; k < kColsumWarps; ++k) t += part[k][lane];
+        out[c] = t;
+    }
 }
 
 // Adam (Kingma & Ba) on the packed parameters; bc1 = 1 - b1^t, bc2 = 1 - b2^t.
@@ -210,7 +223,7 @@ cudaError_t launch_fi_convert(const float* src, int n, int d, uint16_t* dst, uin
 }
 
 cudaError_t launch_fi_colsum(const float* g, int n, int h, float* out, cudaStream_t st) {
-    k_fi_colsum<<<(h + kT - 1) / kT, kT, 0, st>>>(g, n, h, out);
+    k_fi_colsum<<<(h + 31) / 32, 32 * kColsumWarps, 0, st>>>(g, n, h, out);
     return cudaGetLastError();
 }
 

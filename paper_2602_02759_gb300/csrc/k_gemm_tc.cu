@@ -40,17 +40,27 @@ __device__ __forceinline__ void tc_mma_ss_e(uint32_t d_tmem, uint64_t a_desc, ui
         : "memory");
 }
 
-constexpr int BM = 128, BN = 128, BK = 64, NST = 4;
+constexpr int BM = 128, BK = 64, NST = 4;
 constexpr int kThreadsG = 128;
-constexpr int kTileBytes = BM * BK * 2;  // 16 KB (A and B tiles alike)
-constexpr int kStage = 2 * kTileBytes;
-constexpr int kBar = NST * kStage;            // full[NST], empty[NST], done
-constexpr int kMisc = kBar + (2 * NST + 1) * 8;
-constexpr int kSmem = kMisc + 16 + 1024;      // + alignment slack
+constexpr int kTileBytes = BM * BK * 2;  // 16 KB: the A tile, and each 128-row half of the B tile
 
+// Shared layout of a CTA computing a 128 x BN tile (BN = 128 or 256).
+template <int BN>
+struct GemmLayout {
+    static constexpr int kStage = kTileBytes * (1 + BN / 128);
+    static constexpr int kBar = NST * kStage;            // full[NST], empty[NST], done
+    static constexpr int kMisc = kBar + (2 * NST + 1) * 8;
+    static constexpr int kSmem = kMisc + 16 + 1024;      // + alignment slack
+    static_assert(kSmem <= 232448, "shared memory per CTA");
+};
+
+template <int BN>
 __global__ void __launch_bounds__(kThreadsG, 1)
 k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, float* __restrict__ C,
           int M, int N, int K, int ldc, int accumulate, int kb_per_split, int* err) {
+    constexpr int kStage = GemmLayout<BN>::kStage;
+    constexpr int kBar = GemmLayout<BN>::kBar;
+    constexpr int kMisc = GemmLayout<BN>::kMisc;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -77,7 +87,7 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(128u)
+                     "r"((uint32_t)BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -96,7 +106,10 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
             if (!uwait(empty(s), ((kb / NST) & 1) ^ 1, 1)) break;
             mbar_expect_tx_e(full(s), kStage);
             tma_load_2d_e(base + s * kStage, &amap, (kb0 + kb) * BK, m0, full(s));
-            tma_load_2d_e(base + s * kStage + kTileBytes, &bmap, (kb0 + kb) * BK, n0, full(s));
+#pragma unroll
+            for (int hb = 0; hb < BN / 128; ++hb)  // B rows n0 + 128 hb .. (consecutive 128-row boxes)
+                tma_load_2d_e(base + s * kStage + kTileBytes * (1 + hb), &bmap, (kb0 + kb) * BK, n0 + 128 * hb,
+                              full(s));
             issued = kb + 1;
         }
         for (int kb = max(0, issued - NST); kb < issued; ++kb) {
@@ -144,7 +157,7 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
     }
 }
 
@@ -190,9 +203,13 @@ bool encode_kmajor(CUtensorMap* map, const uint16_t* p, int64_t rows, int64_t K,
 }
 }  // namespace
 
+// 128 x 256 tiles for products at least 256 wide (half the re-reads of A), else 128 x 128.
+inline int gemm_bn(int N) { return N >= 256 ? 256 : 128; }
+
 int gemm_splits(int M, int N, int K, int n_sm) {
     // about one wave of CTAs over the SMs, each split keeping >= 8 K blocks of 64
-    const int64_t tiles = (int64_t)((M + gemm::BM - 1) / gemm::BM) * ((N + gemm::BN - 1) / gemm::BN);
+    const int bn = gemm_bn(N);
+    const int64_t tiles = (int64_t)((M + gemm::BM - 1) / gemm::BM) * ((N + bn - 1) / bn);
     const int nk = (K + gemm::BK - 1) / gemm::BK;
     int64_t s = std::max<int64_t>(1, n_sm / std::max<int64_t>(1, tiles));
     s = std::min<int64_t>(s, std::max(1, nk / 8));
@@ -209,18 +226,19 @@ cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, in
         return cudaErrorInvalidValue;
     CUtensorMap am, bm;
     if (!encode_kmajor(&am, A, M, K, lda) || !encode_kmajor(&bm, B, N, K, ldb)) return cudaErrorInvalidValue;
-    cudaError_t e =
-        cudaFuncSetAttribute(gemm::k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm::kSmem);
+    const int bn = gemm_bn(N);
+    auto kern = bn == 256 ? gemm::k_gemm_nt<256> : gemm::k_gemm_nt<128>;
+    const int smem = bn == 256 ? gemm::GemmLayout<256>::kSmem : gemm::GemmLayout<128>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int nk = (K + gemm::BK - 1) / gemm::BK;
     if (n_split < 1 || ws == nullptr || (int64_t)n_split * M * ldc > ws_floats) n_split = 1;
     n_split = std::max(1, std::min(n_split, std::max(1, nk)));
     const int per = (nk + n_split - 1) / n_split;
     n_split = std::max(1, (nk + per - 1) / per);  // no empty split
-    dim3 grid((unsigned)((M + gemm::BM - 1) / gemm::BM), (unsigned)((N + gemm::BN - 1) / gemm::BN),
-              (unsigned)n_split);
-    gemm::k_gemm_nt<<<grid, gemm::kThreadsG, gemm::kSmem, st>>>(am, bm, n_split > 1 ? ws : C, M, N, K, (int)ldc,
-                                                                 accumulate, std::max(per, 1), err);
+    dim3 grid((unsigned)((M + gemm::BM - 1) / gemm::BM), (unsigned)((N + bn - 1) / bn), (unsigned)n_split);
+    kern<<<grid, gemm::kThreadsG, smem, st>>>(am, bm, n_split > 1 ? ws : C, M, N, K, (int)ldc, accumulate,
+                                               std::max(per, 1), err);
     if (n_split > 1) {
         const int64_t n = (int64_t)M * N;
         gemm::k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, n_split, M, N, (int)ldc, C, accumulate);

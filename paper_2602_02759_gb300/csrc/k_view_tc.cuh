@@ -683,7 +683,9 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        // a CTA that gives up its allocation permit may not allocate again: a persistent
+        // CTA (CG), which allocates once per work item, keeps it
+        if constexpr (!CG) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();

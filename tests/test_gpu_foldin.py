@@ -190,3 +190,51 @@ def test_foldin_gain_over_plain_foldin():
         # the gap to the converged fold-in shrinks by at least 2x
         assert (le - full) < 0.5 * (lp - full), (k, le, lp, full)
     assert held_out_loss(A_enc, 20) == pytest.approx(full, rel=1e-2)
+
+
+def test_foldin_gain_at_benchmark_size():
+    """The fold-in workload at its full size: CP 'ir,jr,kr->ijk' 2048 x 128 x 128,
+    R = 32, KL; B, C from a BF16 MU fit of the 1536 training slices; the encoder
+    16384 -> 512 -> 512 -> 32 trained by 200 Adam steps on (slice, component count
+    mass) pairs; the 512 held-out slices folded in from the encoder's loadings and
+    from the plain initialisation, each refined by k MU passes on mode 0 with B, C
+    fixed.  The encoder's gap to the converged fold-in (500 passes) is below the
+    plain initialisation's after k = 0, 1, 2 and 5 passes."""
+    nef = _nef()
+    p = synth.config5()
+    n, J, K = p.y.shape
+    R, n_tr = p.dims["r"], 1536
+    n_te, d = n - n_tr, J * K
+    y = torch.from_numpy(p.y).cuda()
+    ytr, yte = y[:n_tr].contiguous(), y[n_tr:].contiguous()
+    A0, B0, C0 = (torch.from_numpy(f).cuda() for f in p.inits[0])
+    fs = [A0[:n_tr].contiguous(), B0.clone(), C0.clone()]
+    nef.Plan(p.model_str, dict(i=n_tr, j=J, k=K, r=R), precision="bf16").fit(ytr, None, fs, 1.0, 0.0, 100)
+    A_tr, B, C = fs
+    mass = (B.sum(0) * C.sum(0))[None, :]
+    enc = nef.FoldIn(d, 512, R, n_tr,
+                     torch.from_numpy(nef.pack_params(synth.mlp_params((d, 512, 512, R), 3))).cuda())
+    xs = ytr.reshape(n_tr, d).contiguous()
+    targets = (A_tr * mass).contiguous()
+    first = enc.train_step(xs, targets, 1e-3)
+    for _ in range(198):
+        enc.train_step(xs, targets, 1e-3, want_loss=False)
+    last = enc.train_step(xs, targets, 1e-3)
+    assert last < 0.5 * first, (first, last)
+    ref = nef.Plan(p.model_str, dict(i=n_te, j=J, k=K, r=R), precision="fp32")
+    A_enc = (enc.predict(yte.reshape(n_te, d).contiguous()) / mass).contiguous()
+    A_plain = A0[n_tr:].contiguous()
+
+    def held_out_loss(A, k):
+        fs2 = [A.clone(), B, C]
+        for _ in range(k):
+            ref.update(0, yte, None, fs2, 1.0, 0.0)
+        return ref.loss(yte, None, fs2, 1.0, 0.0)[0]
+
+    full = held_out_loss(A_plain, 500)
+    gaps = {}
+    for k in (0, 1, 2, 5):
+        le, lp = held_out_loss(A_enc, k), held_out_loss(A_plain, k)
+        gaps[k] = ((le - full) / full, (lp - full) / full)
+        assert le - full < lp - full, (k, gaps)
+    print("fold-in gaps (encoder, plain) by passes:", gaps)
