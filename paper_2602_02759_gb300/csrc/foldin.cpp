@@ -83,9 +83,10 @@ void fi_free(nef_foldin_t f) {
     f->allocs.clear();
 }
 
-// BF16 copies of the weights used by the products.
-nef_status refresh_weights(nef_foldin_t f) {
-    FI_CUDA(nef::launch_fi_weight_copy(f->p + f->oW1, f->d, f->h, nullptr, f->W1t, f->st));
+// BF16 copies of the weights used by the products (with_w1: also W1's, which the
+// Adam step otherwise writes itself).
+nef_status refresh_weights(nef_foldin_t f, bool with_w1 = true) {
+    if (with_w1) FI_CUDA(nef::launch_fi_weight_copy(f->p + f->oW1, f->d, f->h, nullptr, f->W1t, f->st));
     FI_CUDA(nef::launch_fi_weight_copy(f->p + f->oW2, f->h, f->h, f->W2n, f->W2t, f->st));
     FI_CUDA(nef::launch_fi_weight_copy(f->p + f->oW3, f->h, f->o, f->W3n, f->W3t, f->st));
     return NEF_OK;
@@ -279,9 +280,13 @@ nef_status nef_foldin_train_step(nef_foldin_t f, const float* slices, const floa
     FI_TRY(backward(f, targets, n));
     f->t += 1;
     const double bc1 = 1.0 - std::pow(beta1, (double)f->t), bc2 = 1.0 - std::pow(beta2, (double)f->t);
-    FI_CUDA(nef::launch_fi_adam(f->p, f->g, f->m, f->v, f->np, (float)lr, (float)beta1, (float)beta2, (float)eps,
-                                (float)bc1, (float)bc2, f->st));
-    FI_TRY(refresh_weights(f));
+    // W1 (the bulk of the parameters) in tiles that also write its BF16 transposed
+    // copy; the rest of the packed parameters elementwise; then the small copies
+    FI_CUDA(nef::launch_fi_adam_t(f->p + f->oW1, f->g + f->oW1, f->m + f->oW1, f->v + f->oW1, f->d, f->h, (float)lr,
+                                  (float)beta1, (float)beta2, (float)eps, (float)bc1, (float)bc2, f->W1t, f->st));
+    FI_CUDA(nef::launch_fi_adam(f->p + f->ob1, f->g + f->ob1, f->m + f->ob1, f->v + f->ob1, f->np - f->ob1,
+                                (float)lr, (float)beta1, (float)beta2, (float)eps, (float)bc1, (float)bc2, f->st));
+    FI_TRY(refresh_weights(f, false));
     if (loss) FI_TRY(read_loss(f, n, loss));
     return NEF_OK;
 }

@@ -165,6 +165,38 @@ __global__ void k_fi_adam(float* __restrict__ p, const float* __restrict__ g, fl
     p[e] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
 }
 
+// Adam on a row-major [rows x cols] weight block, in 32 x 32 tiles, that also writes
+// the BF16 transposed copy of the updated weights (dst_t [cols x rows]) through
+// shared memory, so the copy costs no second read of the weights.
+__global__ void k_fi_adam_t(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int rows, int cols, float lr, float b1, float b2, float eps,
+                            float bc1, float bc2, uint16_t* __restrict__ dst_t) {
+    __shared__ uint16_t tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int k = ty; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + tx;
+        uint16_t b = 0;
+        if (r < rows && c < cols) {
+            const int64_t e = (int64_t)r * cols + c;
+            const float gg = g[e];
+            const float mm = b1 * m[e] + (1.f - b1) * gg;
+            const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+            m[e] = mm;
+            v[e] = vv;
+            const float np = p[e] - lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+            p[e] = np;
+            b = to_bf16(np);
+        }
+        tile[k][tx] = b;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + tx;
+        if (c < cols && r < rows) dst_t[(int64_t)c * rows + r] = tile[tx][k];
+    }
+}
+
 // BF16 copy of a row-major [rows x cols] FP32 matrix: straight (dst, ld cols) and/or
 // transposed (dst_t [cols x rows], ld rows).
 __global__ void k_fi_weight_copy(const float* __restrict__ w, int rows, int cols, uint16_t* __restrict__ dst,
@@ -191,10 +223,62 @@ __global__ void k_fi_weight_copy(const float* __restrict__ w, int rows, int cols
 
 dim3 tiles32(int rows, int cols) { return dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)); }
 
+// The features x = log1p(slice) in BF16, row-major and transposed, for d % 4 == 0 and
+// ldt % 16 == 0 (16-byte stores): a block of 256 threads covers 32 rows x 128
+// columns; each thread reads four consecutive columns of four rows (float4, 512
+// bytes per warp row) and writes their BF16 values (8 bytes); the transposed copy
+// goes through shared memory, each thread writing 16 consecutive rows of one
+// column of xt (32 bytes, one sector).
+constexpr int kFeatRows = 32, kFeatCols = 128;
+__global__ void __launch_bounds__(256) k_fi_features_v(const float* __restrict__ src, int n, int d,
+                                                       uint16_t* __restrict__ dst, uint16_t* __restrict__ dst_t,
+                                                       int ldt) {
+    __shared__ uint16_t tile[kFeatRows][kFeatCols + 8];
+    const int c0 = blockIdx.x * kFeatCols, r0 = blockIdx.y * kFeatRows;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int c = c0 + 4 * tx;
+#pragma unroll
+    for (int k = 0; k < kFeatRows / 8; ++k) {
+        const int rr = ty + 8 * k, r = r0 + rr;
+        uint2 packed = make_uint2(0u, 0u);
+        if (r < n && c < d) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src + (int64_t)r * d + c));
+            packed.x = (uint32_t)to_bf16(log1pf(v.x)) | ((uint32_t)to_bf16(log1pf(v.y)) << 16);
+            packed.y = (uint32_t)to_bf16(log1pf(v.z)) | ((uint32_t)to_bf16(log1pf(v.w)) << 16);
+            if (dst) *reinterpret_cast<uint2*>(dst + (int64_t)r * d + c) = packed;
+        }
+        *reinterpret_cast<uint2*>(&tile[rr][4 * tx]) = packed;
+    }
+    if (!dst_t) return;
+    __syncthreads();
+    // thread t: column c0 + (t >> 1), rows r0 + 16 * (t & 1) .. + 15
+    const int cc = threadIdx.x >> 1, half = threadIdx.x & 1;
+    const int col = c0 + cc, rbase = r0 + 16 * half;
+    if (col >= d) return;
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        w[q] = (uint32_t)tile[16 * half + 2 * q][cc] | ((uint32_t)tile[16 * half + 2 * q + 1][cc] << 16);
+    uint16_t* out = dst_t + (int64_t)col * ldt + rbase;
+    if (rbase + 16 <= n) {
+        reinterpret_cast<uint4*>(out)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4*>(out)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+        for (int q = 0; q < 16 && rbase + q < n; ++q) out[q] = (uint16_t)(w[q >> 1] >> (16 * (q & 1)));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_fi_features(const float* slices, int n, int d, uint16_t* x, uint16_t* xt, int ldt, cudaStream_t st) {
-    k_fi_convert_t<1><<<tiles32(n, d), kT, 0, st>>>(slices, n, d, x, xt, ldt);
+    const bool vec = d % 4 == 0 && ldt % 8 == 0 && (reinterpret_cast<uintptr_t>(slices) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(x) & 7) == 0 && (reinterpret_cast<uintptr_t>(xt) & 15) == 0;
+    if (vec) {
+        const dim3 grid((unsigned)((d + kFeatCols - 1) / kFeatCols), (unsigned)((n + kFeatRows - 1) / kFeatRows));
+        k_fi_features_v<<<grid, 256, 0, st>>>(slices, n, d, x, xt, ldt);
+    } else {
+        k_fi_convert_t<1><<<tiles32(n, d), kT, 0, st>>>(slices, n, d, x, xt, ldt);
+    }
     return cudaGetLastError();
 }
 
@@ -230,6 +314,12 @@ cudaError_t launch_fi_colsum(const float* g, int n, int h, float* out, cudaStrea
 cudaError_t launch_fi_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
                            float eps, float bc1, float bc2, cudaStream_t st) {
     k_fi_adam<<<(unsigned)((n + kT - 1) / kT), kT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fi_adam_t(float* p, const float* g, float* m, float* v, int rows, int cols, float lr, float b1,
+                             float b2, float eps, float bc1, float bc2, uint16_t* dst_t, cudaStream_t st) {
+    k_fi_adam_t<<<tiles32(rows, cols), kT, 0, st>>>(p, g, m, v, rows, cols, lr, b1, b2, eps, bc1, bc2, dst_t);
     return cudaGetLastError();
 }
 

@@ -203,18 +203,33 @@ bool encode_kmajor(CUtensorMap* map, const uint16_t* p, int64_t rows, int64_t K,
 }
 }  // namespace
 
-// 128 x 256 tiles for products at least 256 wide (half the re-reads of A), else 128 x 128.
-inline int gemm_bn(int N) { return N >= 256 ? 256 : 128; }
-
-int gemm_splits(int M, int N, int K, int n_sm) {
-    // about one wave of CTAs over the SMs, each split keeping >= 8 K blocks of 64
-    const int bn = gemm_bn(N);
+namespace {
+// Splits for tiles of width bn: about one wave of CTAs over the SMs, each split
+// keeping >= 8 K blocks of 64.
+int splits_for(int M, int N, int K, int n_sm, int bn) {
     const int64_t tiles = (int64_t)((M + gemm::BM - 1) / gemm::BM) * ((N + bn - 1) / bn);
     const int nk = (K + gemm::BK - 1) / gemm::BK;
     int64_t s = std::max<int64_t>(1, n_sm / std::max<int64_t>(1, tiles));
     s = std::min<int64_t>(s, std::max(1, nk / 8));
     return (int)std::min<int64_t>(s, 16);
 }
+
+int64_t ctas_for(int M, int N, int K, int n_sm, int bn) {
+    return (int64_t)((M + gemm::BM - 1) / gemm::BM) * ((N + bn - 1) / bn) * splits_for(M, N, K, n_sm, bn);
+}
+}  // namespace
+
+// 128 x 256 tiles (half the re-reads of A) where they give at least as many CTAs,
+// up to one wave, as 128 x 128 tiles; else 128 x 128 (short products with few
+// tiles are latency-bound and want more CTAs).
+int gemm_bn(int M, int N, int K, int n_sm) {
+    if (N < 256) return 128;
+    const int64_t c256 = std::min<int64_t>(ctas_for(M, N, K, n_sm, 256), n_sm);
+    const int64_t c128 = std::min<int64_t>(ctas_for(M, N, K, n_sm, 128), n_sm);
+    return c256 >= c128 ? 256 : 128;
+}
+
+int gemm_splits(int M, int N, int K, int n_sm) { return splits_for(M, N, K, n_sm, gemm_bn(M, N, K, n_sm)); }
 
 cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
                            int M, int N, int K, int accumulate, int* err, cudaStream_t st, float* ws,
@@ -226,7 +241,14 @@ cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, in
         return cudaErrorInvalidValue;
     CUtensorMap am, bm;
     if (!encode_kmajor(&am, A, M, K, lda) || !encode_kmajor(&bm, B, N, K, ldb)) return cudaErrorInvalidValue;
-    const int bn = gemm_bn(N);
+    int n_sm = 152;
+    {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n_sm = v;
+    }
+    const int bn = gemm_bn(M, N, K, n_sm);
     auto kern = bn == 256 ? gemm::k_gemm_nt<256> : gemm::k_gemm_nt<128>;
     const int smem = bn == 256 ? gemm::GemmLayout<256>::kSmem : gemm::GemmLayout<128>::kSmem;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

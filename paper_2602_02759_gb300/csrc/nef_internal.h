@@ -263,6 +263,9 @@ cudaError_t launch_fi_adam(float* p, const float* g, float* m, float* v, int64_t
                            float eps, float bc1, float bc2, cudaStream_t st);
 cudaError_t launch_fi_weight_copy(const float* w, int rows, int cols, uint16_t* dst, uint16_t* dst_t,
                                   cudaStream_t st);
+// Adam on a [rows x cols] weight block plus its BF16 transposed copy dst_t [cols x rows].
+cudaError_t launch_fi_adam_t(float* p, const float* g, float* m, float* v, int rows, int cols, float lr, float b1,
+                             float b2, float eps, float bc1, float bc2, uint16_t* dst_t, cudaStream_t st);
 
 // Device state of a fit whose stopping rules (App. B) are evaluated on the device.
 struct FitCtlState {
@@ -310,7 +313,9 @@ bool tc_view_supported(const ViewDesc& v, int need_den);
 // and the last one of a block is partial: the consecutive source's modulus must be
 // c_in (its rows are the offsets inside the block; rows past c_in read as zero) and
 // the single-row source's divisor a multiple of c_in.  Returns the two sources'
-// indices (q_const = -1 when there is one source).
+// indices (q_const = -1 when there is one source).  A single source whose rows
+// are the columns of a view with c_in == 1 (mod == c_out) is staged too: its rows
+// never wrap, and the rows past c_out of the last, partial tile read as zeros.
 inline bool q_rows_staged(const ViewDesc& v, int tn, int* q_var, int* q_const) {
     if (v.Q.nsrc < 1 || v.Q.nsrc > 2) return false;
     const bool block = v.c_in != 1 && v.c_in % tn != 0;
@@ -318,7 +323,8 @@ inline bool q_rows_staged(const ViewDesc& v, int tn, int* q_var, int* q_const) {
     for (int s = 0; s < v.Q.nsrc; ++s) {
         const SrcDesc& d = v.Q.src[s];
         if (d.nterm != 1 || d.mul[0] != 1) return false;
-        if (d.div[0] == 1 && (block ? d.mod[0] == v.c_in : d.mod[0] % tn == 0)) {
+        const bool whole = v.Q.nsrc == 1 && v.c_in == 1 && d.mod[0] == v.c_out;
+        if (d.div[0] == 1 && (block ? d.mod[0] == v.c_in : (d.mod[0] % tn == 0 || whole))) {
             if (var >= 0) return false;
             var = s;
         } else if (block ? d.div[0] % v.c_in == 0 : d.div[0] % tn == 0) {

@@ -532,7 +532,9 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, int qform, 
     // qform 0 takes each column factor as its own group (it must carry exactly the
     // bond latents) and falls back to the dense operand; qform 1 joins factors that
     // share a letter outside the bond, and is tried only where qform 0 would not
-    // gather.
+    // gather; qform 2 takes the dense operand where qform 0 would gather (a small
+    // dense operand is one TMA-staged source where the gathered form needs three or
+    // four per tile), and the cost decides.
     std::vector<std::vector<int>> groups;
     auto is_bond = [&](int x) { return std::find(bond.begin(), bond.end(), x) != bond.end(); };
     bool gather = (int)colf.size() <= kMaxSrc;
@@ -554,7 +556,9 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, int qform, 
         }
         if ((int)seen_obs.size() != (int)cols.size()) gather = false;
     }
-    if (qform == 0) {
+    if (qform == 2) {
+        if (!gather) return false;  // qform 0 already builds the dense operand
+    } else if (qform == 0) {
         if (gather)
             for (int f : colf) groups.push_back({f});
     } else {
@@ -799,10 +803,25 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, int qform, 
     const int64_t tiles = (ncols + tn - 1) / tn;
     // one wave: one tensor-core CTA per SM (its shared memory fills the SM), four
     // CUDA-core CTAs per SM
+    // CUDA-core CTAs per SM; the split count fills the waves of CTAs best (the
+    // fraction of the last wave in use), preferring fewer splits on a tie, among
+    // up to four times one wave's worth
     const int64_t target = (p.prec == NEF_BF16) ? p.n_sm : p.n_sm * 4;
-    int64_t ns = std::max<int64_t>(1, target / std::max<int64_t>(1, n_rb));
-    ns = std::min<int64_t>(ns, tiles);
-    ns = std::max<int64_t>(ns, 1);
+    int64_t ns = 1;
+    {
+        const int64_t rbs = std::max<int64_t>(1, n_rb);
+        const int64_t hi = std::max<int64_t>(1, std::min<int64_t>(tiles, 4 * ((target + rbs - 1) / rbs)));
+        double best = -1.0;
+        for (int64_t c = 1; c <= hi; ++c) {
+            const int64_t ctas = rbs * c;
+            const int64_t waves = (ctas + target - 1) / target;
+            const double eff = (double)ctas / (double)(waves * target);
+            if (eff > best + 1e-9) {
+                best = eff;
+                ns = c;
+            }
+        }
+    }
     pp.n_split = (int)ns;
     pp.view.P.nsrc = 1;
     pp.view.Q.nsrc = (int)pp.Q.size();
@@ -1760,7 +1779,7 @@ nef_status build_plan(nef_plan_t p) {
                         if (md.is_obs(x) && !(x >= s && x < e)) ok_run = false;
                     if (!ok_run) continue;
                   for (int assign = 0; assign < 64; ++assign)
-                  for (int qform = 0; qform < 2; ++qform) {
+                  for (int qform = 0; qform < 3; ++qform) {
                     PassPlan cand;
                     int nb = next_buf;
                     if (!plan_view(*p, l, s, e, assign, qform, cand, nb)) continue;

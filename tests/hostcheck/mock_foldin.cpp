@@ -41,6 +41,7 @@ void write_pair(uint16_t* dst, uint16_t* dst_t, int64_t ldt, int n, int d, int64
 }  // namespace
 
 int gemm_splits(int M, int N, int K, int n_sm) {
+    // the split count changes nothing in the host double's product; any value will do
     const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + 127) / 128);
     const int nk = (K + 63) / 64;
     int64_t s = std::max<int64_t>(1, n_sm / std::max<int64_t>(1, tiles));
@@ -143,6 +144,14 @@ cudaError_t launch_fi_adam(float* p, const float* g, float* m, float* v, int64_t
         }
         return cudaSuccess;
     });
+}
+
+cudaError_t launch_fi_adam_t(float* p, const float* g, float* m, float* v, int rows, int cols, float lr, float b1,
+                             float b2, float eps, float bc1, float bc2, uint16_t* dst_t, cudaStream_t st) {
+    const int64_t n = (int64_t)rows * cols;
+    cudaError_t e = launch_fi_adam(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2, st);
+    if (e != cudaSuccess) return e;
+    return launch_fi_weight_copy(p, rows, cols, nullptr, dst_t, st);
 }
 
 cudaError_t launch_fi_weight_copy(const float* w, int rows, int cols, uint16_t* dst, uint16_t* dst_t,
