@@ -36,6 +36,12 @@ cudaError_t launch_bp32_g_loss(const CUtensorMap&, const CUtensorMap&, const CUt
                         cudaStream_t);
 cudaError_t launch_bp64_g_loss(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
                         cudaStream_t);
+cudaError_t launch_bp16_r1(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                           cudaStream_t);
+cudaError_t launch_bp32_r1(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                           cudaStream_t);
+cudaError_t launch_bp64_r1(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
+                           cudaStream_t);
 cudaError_t launch_bp16_lik(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
                         cudaStream_t);
 cudaError_t launch_bp32_lik(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const Params&, int, int, int,
@@ -104,7 +110,8 @@ namespace {
 // Kernel parameters and tensor maps of one view pass.
 cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w, int n_split,
                         float* s_num, float* s_den, int* err_flag, unsigned long long* trace, CUtensorMap* map,
-                        CUtensorMap* vmap, CUtensorMap* cmap, tc::Params* p, int* n_rb_out) {
+                        CUtensorMap* vmap, CUtensorMap* cmap, tc::Params* p, int* n_rb_out,
+                        bool force_gather = false) {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const bool trans = (v.c_in == 1);
@@ -131,7 +138,7 @@ cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v
     *vmap = *map;  // unused unless the Q operand is TMA-staged
     *cmap = *map;
     int q_var = -1, q_const = -1;
-    if (getenv("NEF_TC_GATHER") == nullptr && q_rows_staged(v, tc::TN, &q_var, &q_const)) {
+    if (!force_gather && q_rows_staged(v, tc::TN, &q_var, &q_const)) {
         const SrcDesc& d = v.Q.src[q_var];
         cuuint64_t vd[2] = {(cuuint64_t)d.ld, (cuuint64_t)d.mod[0]};
         cuuint64_t vs[1] = {(cuuint64_t)d.ld * 2};
@@ -180,14 +187,14 @@ cudaError_t make_params(const float* y, const uint32_t* mbits, const ViewDesc& v
 cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc& v, const WeightSpec& w,
                            int need_den, int n_split, float* s_num, float* s_den, int* err_flag,
                            cudaStream_t st, TcLaunchInfo* info, unsigned long long* trace, const LossSpec* loss,
-                           double* loss_part, long long wait_cycles) {
+                           double* loss_part, long long wait_cycles, const TcTileConfig* cfg) {
     if (!tc_view_supported(v, need_den)) return cudaErrorNotSupported;
     if (mbits && !need_den) return cudaErrorInvalidValue;  // mask code lives in the DEN instances only
     CUtensorMap map, vmap, cmap;
     tc::Params p;
     int n_rb = 0;
-    cudaError_t e =
-        make_params(y, mbits, v, w, n_split, s_num, s_den, err_flag, trace, &map, &vmap, &cmap, &p, &n_rb);
+    cudaError_t e = make_params(y, mbits, v, w, n_split, s_num, s_den, err_flag, trace, &map, &vmap, &cmap, &p,
+                                &n_rb, cfg && cfg->gather);
     if (e != cudaSuccess) return e;
     if (loss) {
         p.loss_part = loss_part;
@@ -198,6 +205,7 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
     if (info) {
         info->n_ctas = grid;
         info->smem_bytes = 0;
+        info->staged = p.qmode ? 1 : 0;
     }
     const int wk = weight_kind(w);
     using LaunchFn = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, const tc::Params&,
@@ -213,6 +221,13 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
         {tc::launch_bp16_lik, tc::launch_bp32_lik, tc::launch_bp64_lik},
         {tc::launch_bp16_lik_loss, tc::launch_bp32_lik_loss, tc::launch_bp64_lik_loss}};
     const int bi = v.bond_pad == 16 ? 0 : (v.bond_pad == 32 ? 1 : 2);
+    if (info) info->ring = 0;
+    if (cfg && cfg->ring == 1 && p.qmode && !p.loss_part && wk < tc::WK_NB) {
+        // the alternative ring depths exist for the staged instances of the sweep's passes
+        static const LaunchFn r1[3] = {tc::launch_bp16_r1, tc::launch_bp32_r1, tc::launch_bp64_r1};
+        if (info) info->ring = 1;
+        return r1[bi](map, vmap, cmap, p, need_den, wk, grid, st);
+    }
     if (wk >= tc::WK_NB && p.qmode)
         return lik_table[p.loss_part ? 1 : 0][bi](map, vmap, cmap, p, need_den, wk, grid, st);
     return table[p.loss_part ? 1 : 0][p.qmode ? 1 : 0][bi](map, vmap, cmap, p, need_den, wk >= tc::WK_NB ? tc::WK_GEN : wk,

@@ -556,16 +556,27 @@ __device__ __forceinline__ int64_t src_row_tc(const SrcDesc& s, int64_t i) {
 }
 
 // ---------------------------------------------------------- shared layout
-template <int BP, bool DEN>
+// Ring depths of a layout: configuration 0 (the default) and configuration 1 (an
+// alternative the autotuner may choose per view: one more Y stage at the cost of
+// the staged-row and Q rings where shared memory allows, else deeper operand rings).
+template <int BP, int CFG>
+struct Rings {
+    static constexpr int NSY = CFG == 0 ? ((BP == 64) ? NEF_TC_NSY64 : (BP == 32 ? 5 : 6))
+                                        : ((BP == 64) ? 5 : (BP == 32 ? 6 : 5));
+    static constexpr int NSV = CFG == 0 ? ((BP == 64) ? NEF_TC_NSV64 : 8) : ((BP == 64) ? 3 : (BP == 32 ? 4 : 12));
+    static constexpr int NSQ = CFG == 0 ? ((BP == 64) ? NEF_TC_NSQ64 : 6) : ((BP == 64) ? 4 : (BP == 32 ? 4 : 8));
+};
+
+template <int BP, bool DEN, int CFG = 0>
 struct Layout {
     // Shared memory holds only what the async proxy brings in (Y, staged source
     // rows) and the Q operand; the A operands of both products (P, W) live in
     // tensor memory, so the shared-memory bandwidth of a tile goes to the Y
     // stream.  Ring depths: as many Y stages (bytes in flight towards HBM
     // latency) as fit next to the Q stages.
-    static constexpr int NSY = (BP == 64) ? NEF_TC_NSY64 : (BP == 32 ? 5 : 6);  // Y stages
-    static constexpr int NSV = (BP == 64) ? NEF_TC_NSV64 : 8;                    // staged source-row stages
-    static constexpr int NSQ = (BP == 64) ? NEF_TC_NSQ64 : 6;                    // Q stages
+    static constexpr int NSY = Rings<BP, CFG>::NSY;  // Y stages
+    static constexpr int NSV = Rings<BP, CFG>::NSV;  // staged source-row stages
+    static constexpr int NSQ = Rings<BP, CFG>::NSQ;  // Q stages
     static constexpr int NW = DEN ? (BP == 16 ? 3 : 2) : NEF_TC_NW;              // W buffers (TMEM)
     static constexpr int ND = DEN ? (BP == 64 ? 3 : 4) : NEF_TC_ND;             // yhat buffers (TMEM)
     static constexpr int RB = BP * 2;                        // bytes per bond row (BF16)
@@ -605,11 +616,11 @@ struct Layout {
 // (prm.qmode must match), 2 both, chosen by prm.qmode at run time (batched launches)
 // CG: operand rows by L2-only loads and, at the end, every mbarrier invalidated so
 // that the next work item of a persistent CTA can initialise them again.
-template <int BP, bool DEN, int WK, bool LOSS, int QM, bool CG = false>
+template <int BP, bool DEN, int WK, bool LOSS, int QM, bool CG = false, int CFG = 0>
 __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUtensorMap* vmap,
                                              const CUtensorMap* cmap, const Params& prm, const int64_t rb,
                                              const int64_t sp) {
-    using LY = Layout<BP, DEN>;
+    using LY = Layout<BP, DEN, CFG>;
     constexpr int RB = LY::RB;
     constexpr int NSY = LY::NSY;
     constexpr int NSQ = LY::NSQ;
@@ -1313,12 +1324,13 @@ __device__ __forceinline__ void view_tc_body(const CUtensorMap* ymap, const CUte
 
 // LOSS: also sum the loss terms into prm.loss_part (a separate instance, so the
 // plain pass carries none of that code).
-template <int BP, bool DEN, int WK, bool LOSS, int QM>
+template <int BP, bool DEN, int WK, bool LOSS, int QM, int CFG = 0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_view_tc(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap vmap,
           const __grid_constant__ CUtensorMap cmap, const __grid_constant__ Params prm) {
     const int64_t n_rb = (prm.v.rows + TM - 1) / TM;
-    view_tc_body<BP, DEN, WK, LOSS, QM>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb, blockIdx.x / n_rb);
+    view_tc_body<BP, DEN, WK, LOSS, QM, false, CFG>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb,
+                                                    blockIdx.x / n_rb);
 }
 
 // ---------------------------------------------------------- persistent batched fit

@@ -5,32 +5,32 @@
 namespace nef {
 namespace tc {
 
-template <int BP, bool DEN, int WK, bool LOSS, int QM>
+template <int BP, bool DEN, int WK, bool LOSS, int QM, int CFG = 0>
 cudaError_t launch_one(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int grid,
                        cudaStream_t st) {
-    auto kern = k_view_tc<BP, DEN, WK, LOSS, QM>;
-    const int sm = Layout<BP, DEN>::kAlloc;
+    auto kern = k_view_tc<BP, DEN, WK, LOSS, QM, CFG>;
+    const int sm = Layout<BP, DEN, CFG>::kAlloc;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, sm, st>>>(map, vmap, cmap, p);
     return cudaGetLastError();
 }
 
-template <int BP, bool LOSS, int QM>
+template <int BP, bool LOSS, int QM, int CFG = 0>
 cudaError_t launch_bp(const CUtensorMap& map, const CUtensorMap& vmap, const CUtensorMap& cmap, const Params& p, int den,
                       int wk, int grid, cudaStream_t st) {
     if (den) {
         switch (wk) {
-            case WK_KL: return launch_one<BP, true, WK_KL, LOSS, QM>(map, vmap, cmap, p, grid, st);
-            case WK_B05: return launch_one<BP, true, WK_B05, LOSS, QM>(map, vmap, cmap, p, grid, st);
-            case WK_HEL: return launch_one<BP, true, WK_HEL, LOSS, QM>(map, vmap, cmap, p, grid, st);
-            default: return launch_one<BP, true, WK_GEN, LOSS, QM>(map, vmap, cmap, p, grid, st);
+            case WK_KL: return launch_one<BP, true, WK_KL, LOSS, QM, CFG>(map, vmap, cmap, p, grid, st);
+            case WK_B05: return launch_one<BP, true, WK_B05, LOSS, QM, CFG>(map, vmap, cmap, p, grid, st);
+            case WK_HEL: return launch_one<BP, true, WK_HEL, LOSS, QM, CFG>(map, vmap, cmap, p, grid, st);
+            default: return launch_one<BP, true, WK_GEN, LOSS, QM, CFG>(map, vmap, cmap, p, grid, st);
         }
     }
     switch (wk) {
-        case WK_KL: return launch_one<BP, false, WK_KL, LOSS, QM>(map, vmap, cmap, p, grid, st);
-        case WK_HEL: return launch_one<BP, false, WK_HEL, LOSS, QM>(map, vmap, cmap, p, grid, st);
-        default: return launch_one<BP, false, WK_GEN, LOSS, QM>(map, vmap, cmap, p, grid, st);
+        case WK_KL: return launch_one<BP, false, WK_KL, LOSS, QM, CFG>(map, vmap, cmap, p, grid, st);
+        case WK_HEL: return launch_one<BP, false, WK_HEL, LOSS, QM, CFG>(map, vmap, cmap, p, grid, st);
+        default: return launch_one<BP, false, WK_GEN, LOSS, QM, CFG>(map, vmap, cmap, p, grid, st);
     }
 }
 
@@ -84,6 +84,16 @@ cudaError_t launch_bp_lik(const CUtensorMap& map, const CUtensorMap& vmap, const
     }
 #define NEF_TC_LIK_INSTANCE(BP) NEF_TC_LIK_INSTANCE_X(BP, _lik, false)
 #define NEF_TC_LIK_LOSS_INSTANCE(BP) NEF_TC_LIK_INSTANCE_X(BP, _lik_loss, true)
+#define NEF_TC_RING1_INSTANCE(BP)                                                            \
+    namespace nef {                                                                          \
+    namespace tc {                                                                           \
+    cudaError_t launch_bp##BP##_r1(const CUtensorMap& map, const CUtensorMap& vmap,           \
+                                   const CUtensorMap& cmap, const Params& p, int den, int wk, \
+                                   int grid, cudaStream_t st) {                              \
+        return launch_bp<BP, false, 1, 1>(map, vmap, cmap, p, den, wk, grid, st);            \
+    }                                                                                        \
+    }                                                                                        \
+    }
 #define NEF_TC_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, , false, 1)
 #define NEF_TC_LOSS_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _loss, true, 1)
 #define NEF_TC_GATHER_INSTANCE(BP) NEF_TC_INSTANCE_X(BP, _g, false, 0)

@@ -231,6 +231,16 @@ cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint
 struct TcLaunchInfo {
     int n_ctas;
     int smem_bytes;
+    int staged;   // 1: Q rows staged by TMA, 0: gathered per tile
+    int ring;     // ring-depth configuration launched
+};
+
+// Per-pass choices of the tensor-core pass beyond the split (the autotuner's):
+// ring-depth configuration 0 or 1 of the staged instances, and gathered Q rows
+// even where they could be staged.
+struct TcTileConfig {
+    int ring;
+    bool gather;
 };
 
 // BF16 copy dst of src; src is replaced by the same rounded values.
@@ -300,7 +310,8 @@ cudaError_t launch_view_tc(const float* y, const uint32_t* mbits, const ViewDesc
                            const WeightSpec& w, int need_den, int n_split, float* s_num,
                            float* s_den, int* err_flag, cudaStream_t st, TcLaunchInfo* info,
                            unsigned long long* trace = nullptr, const LossSpec* loss = nullptr,
-                           double* loss_part = nullptr, long long wait_cycles = 0);
+                           double* loss_part = nullptr, long long wait_cycles = 0,
+                           const TcTileConfig* cfg = nullptr);
 
 bool tc_view_supported(const ViewDesc& v, int need_den);
 

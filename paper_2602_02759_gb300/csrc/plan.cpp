@@ -194,6 +194,7 @@ struct PassPlan {
     EinRecipe den_prod;               // product of the column sums -> B_DENVEC
     EinRecipe epi_den_closed;         // den_l from the broadcast den vector
     int n_split = 1;
+    TcTileConfig tc{0, false};        // ring-depth configuration and Q path of the tensor-core pass
     int64_t cost = 0;
     std::string desc;
     bool finish_identity = false;     // epilogue is a relabelling of S: fused finish kernel
@@ -1126,7 +1127,7 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
             NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den, n_split,
                                     reinterpret_cast<float*>(spn), reinterpret_cast<float*>(spd),
                                     p->tc_err, st, &info, p->tc_trace, loss, loss ? p->loss_part : nullptr,
-                                    p->opt.wait_cycles));
+                                    p->opt.wait_cycles, &pp.tc));
             if (n_part) *n_part = info.n_ctas;
         }
     } else {
@@ -1495,7 +1496,7 @@ nef_status loss_pass(nef_plan_t p, const T* y, const uint32_t* mbits, void* cons
             NEF_CUDA(launch_view_tc(reinterpret_cast<const float*>(y), mbits, v, w, need_den, pp.n_split,
                                     static_cast<float*>(buf_ptr(p, B_SPART_N)),
                                     static_cast<float*>(buf_ptr(p, B_SPART_D)), p->tc_err, st, &info, nullptr, &L,
-                                    p->loss_part, p->opt.wait_cycles));
+                                    p->loss_part, p->opt.wait_cycles, &pp.tc));
             *n_part = info.n_ctas;
         }
     } else {
@@ -1594,6 +1595,23 @@ nef_status ensure_split_buffers(nef_plan_t p) {
     return NEF_OK;
 }
 
+// The tensor-core pass's tile configuration as it runs: the deeper-ring instances
+// exist for staged Q rows only, so a gathered pass runs the default ring.
+static TcTileConfig tc_tile_normalise(const ViewDesc& v, TcTileConfig c) {
+    int qv = 0, qc = 0;
+    const bool staged = !c.gather && q_rows_staged(v, kTcTileN, &qv, &qc);
+    if (!staged) c.ring = 0;
+    return c;
+}
+
+static std::string tc_tile_desc(const ViewDesc& v, const TcTileConfig& c0) {
+    const TcTileConfig c = tc_tile_normalise(v, c0);
+    int qv = 0, qc = 0;
+    const bool staged = !c.gather && q_rows_staged(v, kTcTileN, &qv, &qc);
+    return std::string(" tile=128x") + std::to_string(kTcTileN) + " ring=" + std::to_string(c.ring) +
+           (staged ? " q=staged" : " q=gathered");
+}
+
 template <typename T>
 nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void* const* factors, double al,
                          double be, const char* cache_path, int* splits) {
@@ -1602,7 +1620,7 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
     NEF_TRY(prologue<T>(p, Y, mask, factors, st, &mbits));
     const WeightSpec w = specs_of(p, al, be).w;
     const T* y = static_cast<const T*>(Y);
-    std::map<std::string, int> cache;
+    std::map<std::string, std::string> cache;  // key -> "split ring gather" 
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
             char line[1024];
@@ -1610,7 +1628,7 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
                 char* tab = strrchr(line, '\t');
                 if (!tab) continue;
                 *tab = 0;
-                cache[line] = atoi(tab + 1);
+                cache[line] = tab + 1;
             }
             fclose(f);
         }
@@ -1635,7 +1653,11 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
         const std::string key = tune_key(p, pp, w, need_den, mbits != nullptr);
         auto hit = cache.find(key);
         if (hit != cache.end()) {
-            pp.n_split = (int)std::max<int64_t>(1, std::min<int64_t>(hit->second, tiles));
+            int sv = 1, rv = 0, gv = 0;
+            sscanf(hit->second.c_str(), "%d %d %d", &sv, &rv, &gv);
+            pp.n_split = (int)std::max<int64_t>(1, std::min<int64_t>(sv, tiles));
+            pp.tc = use_tc ? tc_tile_normalise(bind_view(p, pp, true), TcTileConfig{rv == 1 ? 1 : 0, gv != 0})
+                           : TcTileConfig{0, false};
             if (splits) splits[l] = pp.n_split;
             continue;
         }
@@ -1655,6 +1677,18 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
         T* spd = static_cast<T*>(buf_ptr(p, B_SPART_D));
         double best_ms = 1e300;
         int best = keep;
+        TcTileConfig best_tc{0, false};
+        // tensor-core passes: the ring-depth configurations of the staged instances and,
+        // where the Q rows can be staged, the gathered path too
+        std::vector<TcTileConfig> tcs = {TcTileConfig{0, false}};
+        if (use_tc) {
+            int qv, qc;
+            if (q_rows_staged(bind_view(p, pp, true), kTcTileN, &qv, &qc)) {
+                tcs.push_back(TcTileConfig{1, false});
+                tcs.push_back(TcTileConfig{0, true});
+            }
+        }
+        for (const TcTileConfig& tcc : tcs)
         for (int c : cand) {
             auto launch = [&]() -> cudaError_t {
                 if (use_tc) {
@@ -1662,7 +1696,7 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
                         TcLaunchInfo info{};
                         return launch_view_tc(reinterpret_cast<const float*>(y), mbits, bind_view(p, pp, true), w,
                                               need_den, c, reinterpret_cast<float*>(spn), reinterpret_cast<float*>(spd),
-                                              p->tc_err, st, &info, nullptr, nullptr, nullptr, p->opt.wait_cycles);
+                                              p->tc_err, st, &info, nullptr, nullptr, nullptr, p->opt.wait_cycles, &tcc);
                     }
                     return cudaErrorNotSupported;
                 }
@@ -1689,17 +1723,22 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
             if (ms[1] < best_ms) {
                 best_ms = ms[1];
                 best = c;
+                best_tc = tcc;
             }
         }
+        if (rs != NEF_OK) break;
         pp.n_split = best;
-        cache[key] = best;
+        pp.tc = best_tc;
+        char v[64];
+        snprintf(v, sizeof(v), "%d %d %d", best, best_tc.ring, best_tc.gather ? 1 : 0);
+        cache[key] = v;
         if (splits) splits[l] = best;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     NEF_TRY(rs);
     NEF_TRY(ensure_split_buffers(p));
-    // the plan description carries the splits
+    // the plan description carries the splits and the tensor-core tile configuration
     std::string info;
     for (auto& pp : p->pass) {
         const size_t at = pp.desc.find("splits=");
@@ -1707,6 +1746,11 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
             const size_t end = pp.desc.find(' ', at);
             pp.desc = pp.desc.substr(0, at) + "splits=" + std::to_string(pp.n_split) +
                       (end == std::string::npos ? std::string() : pp.desc.substr(end));
+        }
+        if (pp.desc.find("kernel=tcgen05") != std::string::npos) {
+            const size_t t = pp.desc.find(" tile=");
+            if (t != std::string::npos) pp.desc.resize(t);
+            pp.desc += tc_tile_desc(bind_view(p, pp, true), pp.tc);
         }
         info += pp.desc + "\n";
     }
@@ -1716,7 +1760,7 @@ nef_status autotune_impl(nef_plan_t p, const void* Y, const uint8_t* mask, void*
     if (cache_path) {
         FILE* f = fopen(cache_path, "w");
         if (!f) return fail(NEF_EINVAL, "cannot write the autotune cache %s", cache_path);
-        for (auto& kv : cache) fprintf(f, "%s\t%d\n", kv.first.c_str(), kv.second);
+        for (auto& kv : cache) fprintf(f, "%s\t%s\n", kv.first.c_str(), kv.second.c_str());
         fclose(f);
     }
     return NEF_OK;
@@ -1821,8 +1865,8 @@ nef_status build_plan(nef_plan_t p) {
         }
         if (!best.generic) {
             bool tc = false;
+            ViewDesc vv = best.view;
             if (p->prec == NEF_BF16) {
-                ViewDesc vv = best.view;
                 vv.P.nsrc = 1;
                 vv.P.src[0] = best.P.desc;
                 vv.Q.nsrc = (int)best.Q.size();
@@ -1830,6 +1874,7 @@ nef_status build_plan(nef_plan_t p) {
                 tc = tc_view_supported(vv, 1);
             }
             best.desc += tc ? " kernel=tcgen05" : (p->prec == NEF_FP64 ? " kernel=simt-fp64" : " kernel=simt-fp32");
+            if (tc) best.desc += tc_tile_desc(vv, best.tc);
         }
         info += best.desc + "\n";
         p->pass.push_back(best);

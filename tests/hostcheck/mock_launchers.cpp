@@ -317,7 +317,7 @@ cudaError_t launch_colsums(const ColsumDesc& d, int64_t, cudaStream_t) {
 bool tc_view_supported(const ViewDesc&, int) { return false; }
 cudaError_t launch_view_tc(const float*, const uint32_t*, const ViewDesc&, const WeightSpec&, int,
                            int, float*, float*, int*, cudaStream_t, TcLaunchInfo*, unsigned long long*,
-                           const LossSpec*, double*, long long) {
+                           const LossSpec*, double*, long long, const TcTileConfig*) {
     return cudaErrorNotSupported;
 }
 

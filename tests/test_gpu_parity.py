@@ -335,6 +335,7 @@ def test_autotune_bf16_then_fit(tmp_path):
     assert all(s >= 1 for s in splits), splits
     plan2 = nef.Plan(model_str, dims, precision="bf16")
     assert plan2.autotune(Y, None, [dev(f) for f in init], 1.0, 0.0, cache=cache) == splits
+    assert all("ring=" in ln for ln in plan.info().splitlines() if "kernel=tcgen05" in ln), plan.info()
     iters = 10
     _, trace = m.fit(y, None, init, 1.0, 0.0, iters, trace=True)
     fs = [dev(f) for f in init]
@@ -342,3 +343,20 @@ def test_autotune_bf16_then_fit(tmp_path):
     plan.check()
     lo, _ = plan.loss(Y, None, fs, 1.0, 0.0)
     assert lo == pytest.approx(trace[-1], rel=1e-3)
+    # every tile configuration the tuner may choose (the deeper-ring instances and
+    # the gathered Q path), forced through the cache, fits like the oracle
+    lines = cache.read_text().strip().splitlines()
+    for ring, gather in ((1, 0), (0, 1)):
+        cache.write_text("".join(ln.split("\t")[0] + f"\t2 {ring} {gather}\n" for ln in lines))
+        forced = nef.Plan(model_str, dims, precision="bf16", profile=True)
+        forced.autotune(Y, None, [dev(f) for f in init], 1.0, 0.0, cache=cache)
+        tc_lines = [ln for ln in forced.info().splitlines() if "kernel=tcgen05" in ln]
+        assert tc_lines and all(f"ring={ring}" in ln for ln in tc_lines), forced.info()
+        assert all(("q=gathered" in ln) == bool(gather) for ln in tc_lines), forced.info()
+        fs = [dev(f) for f in init]
+        forced.profile(reset=True)
+        forced.fit(Y, None, fs, 1.0, 0.0, iters)
+        forced.check()
+        assert forced.profile(reset=True)["tcgen05"][1] >= iters
+        lo, _ = forced.loss(Y, None, fs, 1.0, 0.0)
+        assert lo == pytest.approx(trace[-1], rel=1e-3), (ring, gather)
