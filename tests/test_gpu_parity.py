@@ -351,8 +351,13 @@ def test_autotune_bf16_then_fit(tmp_path):
         forced = nef.Plan(model_str, dims, precision="bf16", profile=True)
         forced.autotune(Y, None, [dev(f) for f in init], 1.0, 0.0, cache=cache)
         tc_lines = [ln for ln in forced.info().splitlines() if "kernel=tcgen05" in ln]
-        assert tc_lines and all(f"ring={ring}" in ln for ln in tc_lines), forced.info()
-        assert all(("q=gathered" in ln) == bool(gather) for ln in tc_lines), forced.info()
+        # the deeper rings exist for staged Q rows; a pass with gathered rows keeps ring 0
+        staged = [ln for ln in tc_lines if "q=staged" in ln]
+        assert staged or gather, forced.info()
+        assert all(f"ring={ring}" in ln for ln in staged), forced.info()
+        assert all("ring=0" in ln for ln in tc_lines if "q=gathered" in ln), forced.info()
+        if gather:
+            assert all("q=gathered" in ln for ln in tc_lines), forced.info()
         fs = [dev(f) for f in init]
         forced.profile(reset=True)
         forced.fit(Y, None, fs, 1.0, 0.0, iters)
