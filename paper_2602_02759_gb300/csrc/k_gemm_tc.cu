@@ -10,7 +10,13 @@
 //          4-stage ring (128B swizzle), out-of-range rows/columns read as zero;
 //   warp 1 (one elected lane): tcgen05.mma kind::f16, M = 128, N = 128, K = 16
 //          steps, accumulator in TMEM (128 columns);
-//   all four warps: epilogue, TMEM lane = tile row, FP32 stores (guarded).
+//   all four warps: epilogue, TMEM lane = tile row.  Each warp stages 32 x 32
+//          FP32 blocks of its rows in shared memory (128B swizzle, two buffers)
+//          and writes them with TMA tensor stores, which clip the edges of C;
+//          the accumulate form and row pitches TMA cannot address use guarded
+//          per-element stores instead.
+//   The producer also prefetches the K block NST ahead into L2, so the ring's
+//   loads mostly hit L2.
 // The operand layouts and descriptors are those of the fused pass's first
 // product (yhat = P . Q^T).  Every mbarrier wait is bounded; a timeout sets the
 // error flag and the CTA drains its copies and MMAs before freeing TMEM.
@@ -18,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "k_view_tc.cuh"
 #include "nef_internal.h"
@@ -40,9 +47,46 @@ __device__ __forceinline__ void tc_mma_ss_e(uint32_t d_tmem, uint64_t a_desc, ui
         : "memory");
 }
 
+__device__ __forceinline__ void tma_prefetch_2d_e(const CUtensorMap* map, int x, int y) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n\t}" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y)
+        : "memory");
+}
+
+// TMA tensor stores from shared memory (bulk-group completion), issued by one thread.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one group still reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every group complete (writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
 constexpr int BM = 128, BK = 64, NST = 4;
 constexpr int kThreadsG = 128;
 constexpr int kTileBytes = BM * BK * 2;  // 16 KB: the A tile, and each 128-row half of the B tile
+constexpr int kEpiBlock = 32 * 32 * 4;   // one staged 32 x 32 FP32 block (4 KB)
+
+// C's store path: guarded per-element stores, TMA stores into C ([M x N], pitch
+// ldc), or TMA stores into the split partials ([n_split][M][ldc]).
+enum GemmStore { kStoreElem = 0, kStoreTma2d = 1, kStoreTma3d = 2 };
 
 // Shared layout of a CTA computing a 128 x BN tile (BN = 128 or 256).
 template <int BN>
@@ -50,17 +94,20 @@ struct GemmLayout {
     static constexpr int kStage = kTileBytes * (1 + BN / 128);
     static constexpr int kBar = NST * kStage;            // full[NST], empty[NST], done
     static constexpr int kMisc = kBar + (2 * NST + 1) * 8;
-    static constexpr int kSmem = kMisc + 16 + 1024;      // + alignment slack
+    static constexpr int kEpi = (kMisc + 16 + 1023) / 1024 * 1024;  // 4 warps x 2 staged blocks
+    static constexpr int kSmem = kEpi + 4 * 2 * kEpiBlock + 1024;   // + alignment slack
     static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 
 template <int BN>
 __global__ void __launch_bounds__(kThreadsG, 1)
-k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, float* __restrict__ C,
-          int M, int N, int K, int ldc, int accumulate, int kb_per_split, int* err) {
+k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+          const __grid_constant__ CUtensorMap cmap, float* __restrict__ C, int M, int N, int K, int ldc,
+          int accumulate, int kb_per_split, int store, int* err) {
     constexpr int kStage = GemmLayout<BN>::kStage;
     constexpr int kBar = GemmLayout<BN>::kBar;
     constexpr int kMisc = GemmLayout<BN>::kMisc;
+    constexpr int kEpi = GemmLayout<BN>::kEpi;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -110,6 +157,11 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
             for (int hb = 0; hb < BN / 128; ++hb)  // B rows n0 + 128 hb .. (consecutive 128-row boxes)
                 tma_load_2d_e(base + s * kStage + kTileBytes * (1 + hb), &bmap, (kb0 + kb) * BK, n0 + 128 * hb,
                               full(s));
+            if (kb + NST < nk) {  // the block this stage takes next, into L2
+                tma_prefetch_2d_e(&amap, (kb0 + kb + NST) * BK, m0);
+#pragma unroll
+                for (int hb = 0; hb < BN / 128; ++hb) tma_prefetch_2d_e(&bmap, (kb0 + kb + NST) * BK, n0 + 128 * hb);
+            }
             issued = kb + 1;
         }
         for (int kb = max(0, issued - NST); kb < issued; ++kb) {
@@ -137,8 +189,45 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
     tc_fence_after();
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    if (store != kStoreElem) {
+        // staged blocks: row `lane` of a 32 x 32 block at lane * 128 bytes, its 16-byte
+        // chunk j at chunk j ^ (lane & 7) (the tensor map's 128B swizzle)
+        const uint32_t stage0 = base + kEpi + (uint32_t)warp * 2u * kEpiBlock;
+        const bool rows_in = m0 + warp * 32 < M;  // warp-uniform; the store clips rows >= M
+        int nb = 0;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + lane_off + c0, r);
+            tmem_wait_ld();
+            if (!ok || !rows_in || n0 + c0 >= N) break;  // warp-uniform
+            if (nk == 0) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) r[k] = 0u;
+            }
+            const uint32_t sb = stage0 + (uint32_t)(nb & 1) * kEpiBlock;
+            if (nb >= 2) {  // the store issued from this buffer two blocks ago has read it
+                if (lane == 0) bulk_wait_read1();
+                __syncwarp();
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                st_shared_v4(sb + (uint32_t)lane * 128u + ((uint32_t)(j ^ (lane & 7)) << 4), r[4 * j], r[4 * j + 1],
+                             r[4 * j + 2], r[4 * j + 3]);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                if (store == kStoreTma3d) tma_store_3d(&cmap, n0 + c0, m0 + warp * 32, (int)blockIdx.z, sb);
+                else tma_store_2d(&cmap, n0 + c0, m0 + warp * 32, sb);
+                bulk_commit();
+            }
+            ++nb;
+        }
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
+    }
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN && store == kStoreElem; c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tmem + lane_off + c0, r);
         tmem_wait_ld();
@@ -201,6 +290,20 @@ bool encode_kmajor(CUtensorMap* map, const uint16_t* p, int64_t rows, int64_t K,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+// Tensor map of FP32 C for the TMA-store epilogue: [M x N] with row pitch ldc, or the
+// split partials [n_split][M][ldc] (3-d); box 32 x 32 (x 1), 128B swizzle.
+bool encode_c(CUtensorMap* map, float* p, int64_t M, int64_t N, int64_t ldc, int n_split) {
+    auto enc = gemm_encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)M, (cuuint64_t)n_split};
+    cuuint64_t strides[2] = {(cuuint64_t)ldc * 4, (cuuint64_t)(M * ldc * 4)};
+    cuuint32_t box[3] = {32, 32, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, n_split > 1 ? 3 : 2, p, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 }  // namespace
 
 namespace {
@@ -259,8 +362,17 @@ cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, in
     const int per = (nk + n_split - 1) / n_split;
     n_split = std::max(1, (nk + per - 1) / per);  // no empty split
     dim3 grid((unsigned)((M + gemm::BM - 1) / gemm::BM), (unsigned)((N + bn - 1) / bn), (unsigned)n_split);
-    kern<<<grid, gemm::kThreadsG, smem, st>>>(am, bm, n_split > 1 ? ws : C, M, N, K, (int)ldc, accumulate,
-                                               std::max(per, 1), err);
+    // TMA stores need a 16-byte aligned destination and a row pitch of whole 16-byte units
+    float* out = n_split > 1 ? ws : C;
+    CUtensorMap cm;
+    std::memset(&cm, 0, sizeof(cm));
+    int store = gemm::kStoreElem;
+    if (!accumulate || n_split > 1) {
+        if ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && ldc % 4 == 0 && encode_c(&cm, out, M, N, ldc, n_split))
+            store = n_split > 1 ? gemm::kStoreTma3d : gemm::kStoreTma2d;
+    }
+    kern<<<grid, gemm::kThreadsG, smem, st>>>(am, bm, cm, out, M, N, K, (int)ldc, accumulate, std::max(per, 1), store,
+                                               err);
     if (n_split > 1) {
         const int64_t n = (int64_t)M * N;
         gemm::k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, n_split, M, N, (int)ldc, C, accumulate);

@@ -59,6 +59,29 @@ def test_tc_gemm(M, N, K):
     np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("M,N,K,ldc", [(200, 72, 96, 80), (50, 30, 64, 30), (50, 30, 64, 33), (300, 40, 128, 44)])
+def test_tc_gemm_row_pitch(M, N, K, ldc):
+    """C with a row pitch wider than N: the tile stores (TMA stores where the pitch is a
+    whole number of 16-byte units, per-element stores otherwise) write the M x N block
+    and leave the columns between N and the pitch untouched."""
+    nef = _nef()
+    rng = np.random.default_rng(M + 3 * N + K + ldc)
+    A = rng.uniform(-1, 1, (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (N, K)).astype(np.float32)
+    tA = torch.as_tensor(A).cuda().to(torch.bfloat16).contiguous()
+    tB = torch.as_tensor(B).cuda().to(torch.bfloat16).contiguous()
+    C = torch.full((M, ldc), -7.0, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = _probe().nef_tc_gemm(tA.data_ptr(), K, tB.data_ptr(), K, C.data_ptr(), ldc, M, N, K, err.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert rc == 0 and int(err.item()) == 0
+    got = C.cpu().numpy()
+    ref = bf16(A) @ bf16(B).T
+    np.testing.assert_allclose(got[:, :N], ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+    assert np.all(got[:, N:] == -7.0)
+
+
 @pytest.mark.parametrize("M,N,K,splits", [(256, 256, 4096, 8), (200, 72, 1000, 3), (1536, 512, 2048, 3)])
 def test_tc_gemm_split_k(M, N, K, splits):
     """Split-K: the K blocks of each tile spread over `splits` CTAs, partial tiles
