@@ -281,7 +281,9 @@ int nef_plan_info(nef_plan_t plan, char* buf, int cap);
 
 /*
  * nef_plan_launches -- number of kernel launches one sweep of nef_fit enqueues
- * for the given mask presence (used to report launch counts).
+ * for the given mask presence (used to report launch counts): the count taken
+ * when the plan last ran or recorded a sweep of that kind, or before the first
+ * such sweep the planner's estimate.
  */
 int nef_plan_launches(nef_plan_t plan, int has_mask);
 

@@ -4,11 +4,15 @@
 // unfused fallback that materialises yhat, a(Y,Yhat), b(Y,Yhat) (Algorithm 1 as
 // written) for model strings the fused view cannot express.
 #include <algorithm>
+#include <type_traits>
 
 #include "nef_device.cuh"
 #include "nef_internal.h"
+#include "nef_launch.cuh"
 
 namespace nef {
+
+long long kernel_launches() { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -16,6 +20,8 @@ constexpr int kThreads = 256;
 
 template <typename T>
 __global__ void k_einsum_part(EinDesc d, int64_t chunk, T* partial) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int sp = blockIdx.y;
     if (o >= d.n_out_el) return;
@@ -52,9 +58,42 @@ __global__ void k_einsum_part(EinDesc d, int64_t chunk, T* partial) {
     partial[(int64_t)sp * d.n_out_el + o] = acc;
 }
 
-// Single-split contraction written straight to the destination layout.
+// Destination write of a contraction: out (= or +=), and with out16 the BF16 copy
+// and the FP32 value rounded to it (round to nearest even).
 template <typename T>
+__device__ __forceinline__ void ein_store(const EinDesc& d, void* outp, int64_t dst, T acc) {
+    T* out = static_cast<T*>(outp);
+    if constexpr (std::is_same<T, float>::value) {
+        if (d.out16) {
+            const uint32_t u = __float_as_uint(acc);
+            const uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);
+            d.out16[dst] = (uint16_t)(r >> 16);
+            out[dst] = __uint_as_float(r & 0xffff0000u);
+            return;
+        }
+    }
+    out[dst] = d.accumulate ? out[dst] + acc : acc;
+}
+
+// Product of the operands at one free combination: all of them into acc, or (DUAL)
+// operand 0 times the rest into acc and operand 0b times the rest into accb.
+template <typename T, bool DUAL>
+__device__ __forceinline__ void ein_term(const EinDesc& d, const int64_t* off, T& acc, T& accb) {
+    T p = T(1);
+    for (int k = DUAL ? 1 : 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
+    if constexpr (DUAL) {
+        acc += static_cast<const T*>(d.op[0])[off[0]] * p;
+        accb += static_cast<const T*>(d.op0b)[off[0]] * p;
+    } else {
+        acc += p;
+    }
+}
+
+// Single-split contraction written straight to the destination layout.
+template <typename T, bool DUAL>
 __global__ void k_einsum_direct(EinDesc d) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= d.n_out_el) return;
     int64_t off[kMaxEinOps];
@@ -68,11 +107,9 @@ __global__ void k_einsum_direct(EinDesc d) {
     }
     int64_t idx[kMaxEinLet];
     for (int q = d.n_out; q < d.n_out + d.n_free; ++q) idx[q] = 0;
-    T acc = T(0);
+    T acc = T(0), accb = T(0);
     for (int64_t f = 0; f < d.n_free_el; ++f) {
-        T p = T(1);
-        for (int k = 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
-        acc += p;
+        ein_term<T, DUAL>(d, off, acc, accb);
         for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
             idx[q] += 1;
             for (int k = 0; k < d.n_ops; ++k) off[k] += d.ost[k][q];
@@ -81,22 +118,43 @@ __global__ void k_einsum_direct(EinDesc d) {
             idx[q] = 0;
         }
     }
-    T* out = static_cast<T*>(d.out);
-    out[dst] = d.accumulate ? out[dst] + acc : acc;
+    ein_store<T>(d, d.out, dst, acc);
+    if constexpr (DUAL) ein_store<T>(d, d.outb, dst, accb);
+}
+
+// Sum over the G threads of a group in a fixed order (xor shuffles within a warp; for
+// G = 256 the warp sums are added in warp order).
+template <typename T, int G>
+__device__ __forceinline__ T group_sum(T acc, T* sh) {
+    if constexpr (G <= 32) {
+#pragma unroll
+        for (int w = G / 2; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    } else {
+        static_assert(G == kThreads, "group size");
+        acc = warp_sum(acc);
+        __syncthreads();  // sh free from a previous use
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        acc = T(0);
+        for (int k = 0; k < kThreads / 32; ++k) acc += sh[k];
+    }
+    return acc;
 }
 
 // Contraction with G threads per output element: the threads of a group take the
 // free combinations f = sub, sub + G, ... (each decodes its own f) and the group
-// sums its partials in a fixed order (xor shuffles within a warp; for G = 256 the
-// warp sums are added in warp order).  Used where G threads cover an output's free
-// combinations in a few steps (at most 4 for G = 8 and 32, 64 for G = 256).
-template <typename T, int G>
+// sums its partials.  Used where G threads cover an output's free combinations in a
+// few steps (at most 4 for G = 8 and 32, 64 for G = 256).
+template <typename T, int G, bool DUAL>
 __global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int kGroups = kThreads / G;
+    __shared__ T sh[kThreads / 32];
     const int sub = (int)(threadIdx.x % G);
     const int64_t o = (int64_t)blockIdx.x * kGroups + threadIdx.x / G;
     const bool ok = o < d.n_out_el;
-    T acc = T(0);
+    T acc = T(0), accb = T(0);
     int64_t dst = 0;
     if (ok) {
         int64_t base[kMaxEinOps];
@@ -119,31 +177,21 @@ __global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
                 r /= dq;
                 for (int k = 0; k < d.n_ops; ++k) off[k] += (int64_t)v * d.ost[k][q];
             }
-            T p = T(1);
-            for (int k = 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
-            acc += p;
+            ein_term<T, DUAL>(d, off, acc, accb);
         }
     }
-    if constexpr (G <= 32) {
-#pragma unroll
-        for (int w = G / 2; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
-    } else {
-        static_assert(G == kThreads, "group size");
-        __shared__ T sh[kThreads / 32];
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        acc = T(0);
-        for (int k = 0; k < kThreads / 32; ++k) acc += sh[k];
-    }
+    acc = group_sum<T, G>(acc, sh);
+    if constexpr (DUAL) accb = group_sum<T, G>(accb, sh);
     if (ok && sub == 0) {
-        T* out = static_cast<T*>(d.out);
-        out[dst] = d.accumulate ? out[dst] + acc : acc;
+        ein_store<T>(d, d.out, dst, acc);
+        if constexpr (DUAL) ein_store<T>(d, d.outb, dst, accb);
     }
 }
 
 template <typename T>
 __global__ void k_einsum_final(EinDesc d, int n_split, const T* partial) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= d.n_out_el) return;
     T acc = T(0);
@@ -153,11 +201,12 @@ __global__ void k_einsum_final(EinDesc d, int n_split, const T* partial) {
         dst += (rem % d.dim[q]) * d.out_st[q];
         rem /= d.dim[q];
     }
-    T* out = static_cast<T*>(d.out);
-    out[dst] = d.accumulate ? out[dst] + acc : acc;
+    ein_store<T>(d, d.out, dst, acc);
 }
 
 __global__ void k_pack_mask(const uint8_t* __restrict__ m, int64_t n, uint32_t* __restrict__ bits) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nw = (n + 31) >> 5;
     if (w >= nw) return;
@@ -172,6 +221,8 @@ __global__ void k_pack_mask(const uint8_t* __restrict__ m, int64_t n, uint32_t* 
 
 template <typename T>
 __global__ void k_check_data(const T* __restrict__ y, int64_t n, int* flag) {
+    pdl_wait();
+    pdl_trigger();
     int bad = 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -183,6 +234,8 @@ __global__ void k_check_data(const T* __restrict__ y, int64_t n, int* flag) {
 
 template <typename T>
 __global__ void k_reduce_splits(const T* __restrict__ part, int n_split, int64_t n, T* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     T acc = T(0);
@@ -191,8 +244,25 @@ __global__ void k_reduce_splits(const T* __restrict__ part, int n_split, int64_t
 }
 
 template <typename T>
+__global__ void k_reduce_splits2(const T* __restrict__ part_a, const T* __restrict__ part_b, int n_split, int64_t n,
+                                 T* __restrict__ out_a, T* __restrict__ out_b) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * n) return;
+    const bool b = e >= n;
+    const int64_t i = b ? e - n : e;
+    const T* part = b ? part_b : part_a;
+    T acc = T(0);
+    for (int s = 0; s < n_split; ++s) acc += part[(int64_t)s * n + i];
+    (b ? out_b : out_a)[i] = acc;
+}
+
+template <typename T>
 __global__ void k_update(T* __restrict__ theta, const T* __restrict__ num, const T* __restrict__ den,
                          int64_t n, UpdateSpec u) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     theta[e] = mu_update(theta[e], num[e], den[e], u);
@@ -200,11 +270,15 @@ __global__ void k_update(T* __restrict__ theta, const T* __restrict__ num, const
 
 template <typename T>
 __global__ void k_fill(T* p, int64_t n, T v) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) p[e] = v;
 }
 
 __global__ void k_sum_f64(const double* __restrict__ part, int n, double* out) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[32];
     double acc = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) acc += part[k];
@@ -221,6 +295,8 @@ __global__ void k_sum_f64(const double* __restrict__ part, int n, double* out) {
 // out[0..1] = sums of part[0..n) and part[n..2n) (loss, observed count); the
 // loss is also written to trace[*count] (if trace) and *count is incremented.
 __global__ void k_loss_append(const double* __restrict__ part, int n, double* trace, int* count, double* out) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[2][32];
     double a = 0.0, c = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -252,6 +328,8 @@ __global__ void k_loss_append(const double* __restrict__ part, int n, double* tr
 // values, so that whatever else reads the FP32 copy (closed-form denominators,
 // epilogue contractions) sees exactly the operand the tensor cores multiply.
 __global__ void k_convert_bf16(float* __restrict__ src, int64_t n, uint16_t* __restrict__ dst) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     // round to nearest even
@@ -267,6 +345,8 @@ template <typename T>
 __global__ void k_generic_weights(GenericRecon g, const T* __restrict__ y, const uint32_t* mbits,
                                   WeightSpec w, T* __restrict__ wa, T* __restrict__ wb,
                                   int has_loss, LossSpec L, double* loss_part) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh_loss[kThreads / 32];
     __shared__ double sh_cnt[kThreads / 32];
     double lsum = 0.0, lcnt = 0.0;
@@ -368,6 +448,8 @@ constexpr int kFinEl = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_finish(FinishDesc d, UpdateSpec u) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int kGrp = kThreads / kFinEl;
     __shared__ T sn[kGrp][kFinEl], sd[kGrp][kFinEl];
     const int lane = (int)(threadIdx.x % kFinEl), g = (int)(threadIdx.x / kFinEl);
@@ -415,6 +497,8 @@ struct LetterDims {
 template <typename T>
 __global__ void k_update_mirror(T* __restrict__ theta, const T* __restrict__ num, const T* __restrict__ den,
                                 int64_t n, UpdateSpec u, int nlet, LetterDims dim, MirrorDesc m) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const T v = mu_update(theta[e], num[e], den[e], u);
@@ -426,6 +510,8 @@ __global__ void k_update_mirror(T* __restrict__ theta, const T* __restrict__ num
 
 template <typename T>
 __global__ void k_mirror_init(const T* __restrict__ theta, int64_t n, int nlet, LetterDims dim, MirrorDesc m) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     int64_t idx[kMaxFacLet];
@@ -436,6 +522,8 @@ __global__ void k_mirror_init(const T* __restrict__ theta, int64_t n, int nlet, 
 // Column sums of canonical operands: block (job, column).
 template <typename T>
 __global__ void k_colsums(ColsumDesc d) {
+    pdl_wait();
+    pdl_trigger();
     const ColsumJob& j = d.job[blockIdx.x];
     const int64_t b = blockIdx.y;
     if (b >= j.ld) return;
@@ -462,6 +550,7 @@ inline unsigned blocks_for(int64_t n, int threads = kThreads) {
 template <typename T>
 cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cudaStream_t st) {
     if (d.n_out_el <= 0) return cudaSuccess;
+    const bool dual = d.op0b != nullptr && d.outb != nullptr && d.n_ops >= 1;
     // few free combinations per output: a group of G threads per output
     if (d.n_free_el > 4 && d.n_free_el < ((int64_t)1 << 31)) {
         const int g = d.n_free_el <= 32 ? 8 : (d.n_free_el <= 128 ? 32 : kThreads);
@@ -470,9 +559,15 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
             const int64_t per = kThreads / g;
             const int64_t blocks = (d.n_out_el + per - 1) / per;
             if (blocks < ((int64_t)1 << 31)) {
-                if (g == 8) k_einsum_grouped<T, 8><<<(unsigned)blocks, kThreads, 0, st>>>(d);
-                else if (g == 32) k_einsum_grouped<T, 32><<<(unsigned)blocks, kThreads, 0, st>>>(d);
-                else k_einsum_grouped<T, kThreads><<<(unsigned)blocks, kThreads, 0, st>>>(d);
+                if (dual) {
+                    if (g == 8) launch_pdl(k_einsum_grouped<T, 8, true>, (unsigned)blocks, kThreads, 0, st, d);
+                    else if (g == 32) launch_pdl(k_einsum_grouped<T, 32, true>, (unsigned)blocks, kThreads, 0, st, d);
+                    else launch_pdl(k_einsum_grouped<T, kThreads, true>, (unsigned)blocks, kThreads, 0, st, d);
+                } else {
+                    if (g == 8) launch_pdl(k_einsum_grouped<T, 8, false>, (unsigned)blocks, kThreads, 0, st, d);
+                    else if (g == 32) launch_pdl(k_einsum_grouped<T, 32, false>, (unsigned)blocks, kThreads, 0, st, d);
+                    else launch_pdl(k_einsum_grouped<T, kThreads, false>, (unsigned)blocks, kThreads, 0, st, d);
+                }
                 return cudaGetLastError();
             }
         }
@@ -488,19 +583,32 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
     }
     if (n_split == 1) {
         // one pass straight into the destination
-        k_einsum_direct<T><<<blocks_for(d.n_out_el), kThreads, 0, st>>>(d);
+        if (dual) launch_pdl(k_einsum_direct<T, true>, blocks_for(d.n_out_el), kThreads, 0, st, d);
+        else launch_pdl(k_einsum_direct<T, false>, blocks_for(d.n_out_el), kThreads, 0, st, d);
         return cudaGetLastError();
+    }
+    if (dual) {
+        // the split form computes one contraction: the two, one after the other
+        EinDesc a = d, b = d;
+        a.op0b = nullptr;
+        a.outb = nullptr;
+        b.op[0] = d.op0b;
+        b.out = d.outb;
+        b.op0b = nullptr;
+        b.outb = nullptr;
+        cudaError_t e = launch_einsum<T>(a, partial, partial_cap, st);
+        return e != cudaSuccess ? e : launch_einsum<T>(b, partial, partial_cap, st);
     }
     const int64_t chunk = (d.n_free_el + n_split - 1) / n_split;
     dim3 grid(blocks_for(d.n_out_el), (unsigned)n_split);
-    k_einsum_part<T><<<grid, kThreads, 0, st>>>(d, chunk, partial);
-    k_einsum_final<T><<<blocks_for(d.n_out_el), kThreads, 0, st>>>(d, (int)n_split, partial);
+    launch_pdl(k_einsum_part<T>, grid, kThreads, 0, st, d, chunk, partial);
+    launch_pdl(k_einsum_final<T>, blocks_for(d.n_out_el), kThreads, 0, st, d, (int)n_split, partial);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t st) {
-    k_finish<T><<<blocks_for(d.n, kFinEl), kThreads, 0, st>>>(d, u);
+    launch_pdl(k_finish<T>, blocks_for(d.n, kFinEl), kThreads, 0, st, d, u);
     return cudaGetLastError();
 }
 
@@ -509,7 +617,7 @@ cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n
                                  int nlet, const int64_t* dim, const MirrorDesc& m, cudaStream_t st) {
     LetterDims ld{};
     for (int q = 0; q < nlet; ++q) ld.d[q] = dim[q];
-    k_update_mirror<T><<<blocks_for(n), kThreads, 0, st>>>(theta, num, den, n, u, nlet, ld, m);
+    launch_pdl(k_update_mirror<T>, blocks_for(n), kThreads, 0, st, theta, num, den, n, u, nlet, ld, m);
     return cudaGetLastError();
 }
 
@@ -519,57 +627,65 @@ cudaError_t launch_mirror_init(const T* theta, int64_t n, int nlet, const int64_
     if (m.n == 0) return cudaSuccess;
     LetterDims ld{};
     for (int q = 0; q < nlet; ++q) ld.d[q] = dim[q];
-    k_mirror_init<T><<<blocks_for(n), kThreads, 0, st>>>(theta, n, nlet, ld, m);
+    launch_pdl(k_mirror_init<T>, blocks_for(n), kThreads, 0, st, theta, n, nlet, ld, m);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_colsums(const ColsumDesc& d, int64_t max_ld, cudaStream_t st) {
     if (d.n == 0) return cudaSuccess;
-    k_colsums<T><<<dim3((unsigned)d.n, (unsigned)max_ld), kThreads, 0, st>>>(d);
+    launch_pdl(k_colsums<T>, dim3((unsigned)d.n, (unsigned)max_ld), kThreads, 0, st, d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_mask(const uint8_t* mask, int64_t n, uint32_t* bits, cudaStream_t st) {
     const int64_t nw = (n + 31) >> 5;
-    k_pack_mask<<<blocks_for(nw), kThreads, 0, st>>>(mask, n, bits);
+    launch_pdl(k_pack_mask, blocks_for(nw), kThreads, 0, st, mask, n, bits);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_check_data(const T* y, int64_t n, int* flag, cudaStream_t st) {
     unsigned nb = (unsigned)std::min<int64_t>(blocks_for(n), 152 * 8);
-    k_check_data<T><<<nb, kThreads, 0, st>>>(y, n, flag);
+    launch_pdl(k_check_data<T>, nb, kThreads, 0, st, y, n, flag);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_reduce_splits(const T* part, int n_split, int64_t n, T* out, cudaStream_t st) {
-    k_reduce_splits<T><<<blocks_for(n), kThreads, 0, st>>>(part, n_split, n, out);
+    launch_pdl(k_reduce_splits<T>, blocks_for(n), kThreads, 0, st, part, n_split, n, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce_splits2(const T* part_a, const T* part_b, int n_split, int64_t n, T* out_a, T* out_b,
+                                  cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    launch_pdl(k_reduce_splits2<T>, blocks_for(2 * n), kThreads, 0, st, part_a, part_b, n_split, n, out_a, out_b);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_update(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
                           cudaStream_t st) {
-    k_update<T><<<blocks_for(n), kThreads, 0, st>>>(theta, num, den, n, u);
+    launch_pdl(k_update<T>, blocks_for(n), kThreads, 0, st, theta, num, den, n, u);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fill(T* p, int64_t n, T v, cudaStream_t st) {
-    k_fill<T><<<blocks_for(n), kThreads, 0, st>>>(p, n, v);
+    launch_pdl(k_fill<T>, blocks_for(n), kThreads, 0, st, p, n, v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sum_f64(const double* part, int n, double* out, cudaStream_t st) {
-    k_sum_f64<<<1, 1024, 0, st>>>(part, n, out);
+    launch_pdl(k_sum_f64, 1, 1024, 0, st, part, n, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_loss_append(const double* part, int n, double* trace, int* count, double* out,
                                cudaStream_t st) {
-    k_loss_append<<<1, 1024, 0, st>>>(part, n, trace, count, out);
+    launch_pdl(k_loss_append, 1, 1024, 0, st, part, n, trace, count, out);
     return cudaGetLastError();
 }
 
@@ -577,27 +693,31 @@ cudaError_t launch_loss_append(const double* part, int n, double* trace, int* co
 // a graph loop the result also becomes the loop's condition.
 __global__ void k_fit_check(FitCtlState* s, const double* out_loss, const double* out_val,
                             cudaGraphConditionalHandle handle, int set_handle, int mode) {
+    pdl_wait();
+    pdl_trigger();
     const int cont = fit_rule_step(s, out_loss, out_val, mode);
     if (set_handle && mode == 0) cudaGraphSetConditional(handle, cont ? 1u : 0u);
 }
 
 __global__ void k_fit_set_cond(const FitCtlState* s, cudaGraphConditionalHandle handle) {
+    pdl_wait();
+    pdl_trigger();
     cudaGraphSetConditional(handle, s->cont ? 1u : 0u);
 }
 
 cudaError_t launch_fit_check(FitCtlState* s, const double* out_loss, const double* out_val,
                              cudaGraphConditionalHandle handle, int set_handle, int mode, cudaStream_t st) {
-    k_fit_check<<<1, 1, 0, st>>>(s, out_loss, out_val, handle, set_handle, mode);
+    launch_pdl(k_fit_check, 1, 1, 0, st, s, out_loss, out_val, handle, set_handle, mode);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fit_set_cond(const FitCtlState* s, cudaGraphConditionalHandle handle, cudaStream_t st) {
-    k_fit_set_cond<<<1, 1, 0, st>>>(s, handle);
+    launch_pdl(k_fit_set_cond, 1, 1, 0, st, s, handle);
     return cudaGetLastError();
 }
 
 cudaError_t launch_convert_bf16(float* src, int64_t n, uint16_t* dst, cudaStream_t st) {
-    k_convert_bf16<<<blocks_for(n), kThreads, 0, st>>>(src, n, dst);
+    launch_pdl(k_convert_bf16, blocks_for(n), kThreads, 0, st, src, n, dst);
     return cudaGetLastError();
 }
 
@@ -608,7 +728,7 @@ cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint
     const unsigned nb = loss ? (unsigned)n_part : (unsigned)std::min<int64_t>(blocks_for(g.n), 152 * 16);
     LossSpec L{};
     if (loss) L = *loss;
-    k_generic_weights<T><<<nb, kThreads, 0, st>>>(g, y, mbits, w, wa, wb, loss ? 1 : 0, L, loss_part);
+    launch_pdl(k_generic_weights<T>, nb, kThreads, 0, st, g, y, mbits, w, wa, wb, loss ? 1 : 0, L, loss_part);
     return cudaGetLastError();
 }
 
@@ -616,6 +736,7 @@ cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint
     template cudaError_t launch_einsum<T>(const EinDesc&, T*, int64_t, cudaStream_t);        \
     template cudaError_t launch_check_data<T>(const T*, int64_t, int*, cudaStream_t);        \
     template cudaError_t launch_reduce_splits<T>(const T*, int, int64_t, T*, cudaStream_t);  \
+    template cudaError_t launch_reduce_splits2<T>(const T*, const T*, int, int64_t, T*, T*, cudaStream_t); \
     template cudaError_t launch_update<T>(T*, const T*, const T*, int64_t, const UpdateSpec&, \
                                           cudaStream_t);                                     \
     template cudaError_t launch_fill<T>(T*, int64_t, T, cudaStream_t);                       \

@@ -9,6 +9,7 @@
 
 #include "nef_device.cuh"
 #include "nef_internal.h"
+#include "nef_launch.cuh"
 
 namespace nef {
 
@@ -29,6 +30,8 @@ __device__ __forceinline__ float sigmoid_f(float z) { return 1.f / (1.f + __expf
 template <int OP>
 __global__ void k_fi_convert_t(const float* __restrict__ src, int n, int d, uint16_t* __restrict__ dst,
                                uint16_t* __restrict__ dst_t, int ldt) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint16_t tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
@@ -54,6 +57,8 @@ __global__ void k_fi_convert_t(const float* __restrict__ src, int n, int d, uint
 // act 2: out = softplus(z) (FP32).
 __global__ void k_fi_bias_act(float* __restrict__ z, const float* __restrict__ b, int n, int h, int act,
                               uint16_t* __restrict__ hb, uint16_t* __restrict__ ht, int ldt, float* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint16_t tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -85,6 +90,8 @@ __global__ void k_fi_bias_act(float* __restrict__ z, const float* __restrict__ b
 // per-block sums of d^2 into part[block].
 __global__ void k_fi_out_grad(const float* __restrict__ out, const float* __restrict__ t, const float* __restrict__ z,
                               int64_t n_el, float inv_count, float* __restrict__ g, double* __restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[kT / 32];
     double acc = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
@@ -106,6 +113,8 @@ __global__ void k_fi_out_grad(const float* __restrict__ out, const float* __rest
 // g *= (z > 0) (relu backward), in place; BF16 copies row-major (gb) and transposed (gt).
 __global__ void k_fi_relu_grad(float* __restrict__ g, const float* __restrict__ z, int n, int h,
                                uint16_t* __restrict__ gb, uint16_t* __restrict__ gt, int ldt) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint16_t tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -136,6 +145,8 @@ __global__ void k_fi_relu_grad(float* __restrict__ g, const float* __restrict__ 
 constexpr int kColsumWarps = 32;
 __global__ void __launch_bounds__(32 * kColsumWarps) k_fi_colsum(const float* __restrict__ g, int n, int h,
                                                                  float* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float part[kColsumWarps][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + lane;
@@ -155,6 +166,8 @@ __global__ void __launch_bounds__(32 * kColsumWarps) k_fi_colsum(const float* __
 __global__ void k_fi_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                           float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float bc1,
                           float bc2) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const float gg = g[e];
@@ -171,6 +184,8 @@ __global__ void k_fi_adam(float* __restrict__ p, const float* __restrict__ g, fl
 __global__ void k_fi_adam_t(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, int rows, int cols, float lr, float b1, float b2, float eps,
                             float bc1, float bc2, uint16_t* __restrict__ dst_t) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint16_t tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -201,6 +216,8 @@ __global__ void k_fi_adam_t(float* __restrict__ p, const float* __restrict__ g, 
 // transposed (dst_t [cols x rows], ld rows).
 __global__ void k_fi_weight_copy(const float* __restrict__ w, int rows, int cols, uint16_t* __restrict__ dst,
                                  uint16_t* __restrict__ dst_t) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint16_t tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -233,6 +250,8 @@ constexpr int kFeatRows = 32, kFeatCols = 128;
 __global__ void __launch_bounds__(256) k_fi_features_v(const float* __restrict__ src, int n, int d,
                                                        uint16_t* __restrict__ dst, uint16_t* __restrict__ dst_t,
                                                        int ldt) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint16_t tile[kFeatRows][kFeatCols + 8];
     const int c0 = blockIdx.x * kFeatCols, r0 = blockIdx.y * kFeatRows;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -275,57 +294,57 @@ cudaError_t launch_fi_features(const float* slices, int n, int d, uint16_t* x, u
                      (reinterpret_cast<uintptr_t>(x) & 7) == 0 && (reinterpret_cast<uintptr_t>(xt) & 15) == 0;
     if (vec) {
         const dim3 grid((unsigned)((d + kFeatCols - 1) / kFeatCols), (unsigned)((n + kFeatRows - 1) / kFeatRows));
-        k_fi_features_v<<<grid, 256, 0, st>>>(slices, n, d, x, xt, ldt);
+        launch_pdl(k_fi_features_v, grid, 256, 0, st, slices, n, d, x, xt, ldt);
     } else {
-        k_fi_convert_t<1><<<tiles32(n, d), kT, 0, st>>>(slices, n, d, x, xt, ldt);
+        launch_pdl(k_fi_convert_t<1>, tiles32(n, d), kT, 0, st, slices, n, d, x, xt, ldt);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_bias_act(float* z, const float* b, int n, int h, int act, uint16_t* hb, uint16_t* ht, int ldt,
                                float* out, cudaStream_t st) {
-    k_fi_bias_act<<<tiles32(n, h), kT, 0, st>>>(z, b, n, h, act, hb, ht, ldt, out);
+    launch_pdl(k_fi_bias_act, tiles32(n, h), kT, 0, st, z, b, n, h, act, hb, ht, ldt, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_out_grad(const float* out, const float* t, const float* z, int64_t n_el, float inv_count,
                                float* g, double* part, int n_part, cudaStream_t st) {
-    k_fi_out_grad<<<n_part, kT, 0, st>>>(out, t, z, n_el, inv_count, g, part);
+    launch_pdl(k_fi_out_grad, n_part, kT, 0, st, out, t, z, n_el, inv_count, g, part);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_relu_grad(float* g, const float* z, int n, int h, uint16_t* gb, uint16_t* gt, int ldt,
                                 cudaStream_t st) {
-    k_fi_relu_grad<<<tiles32(n, h), kT, 0, st>>>(g, z, n, h, gb, gt, ldt);
+    launch_pdl(k_fi_relu_grad, tiles32(n, h), kT, 0, st, g, z, n, h, gb, gt, ldt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_convert(const float* src, int n, int d, uint16_t* dst, uint16_t* dst_t, int ldt,
                               cudaStream_t st) {
-    k_fi_convert_t<0><<<tiles32(n, d), kT, 0, st>>>(src, n, d, dst, dst_t, ldt);
+    launch_pdl(k_fi_convert_t<0>, tiles32(n, d), kT, 0, st, src, n, d, dst, dst_t, ldt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_colsum(const float* g, int n, int h, float* out, cudaStream_t st) {
-    k_fi_colsum<<<(h + 31) / 32, 32 * kColsumWarps, 0, st>>>(g, n, h, out);
+    launch_pdl(k_fi_colsum, (h + 31) / 32, 32 * kColsumWarps, 0, st, g, n, h, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
                            float eps, float bc1, float bc2, cudaStream_t st) {
-    k_fi_adam<<<(unsigned)((n + kT - 1) / kT), kT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+    launch_pdl(k_fi_adam, (unsigned)((n + kT - 1) / kT), kT, 0, st, p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_adam_t(float* p, const float* g, float* m, float* v, int rows, int cols, float lr, float b1,
                              float b2, float eps, float bc1, float bc2, uint16_t* dst_t, cudaStream_t st) {
-    k_fi_adam_t<<<tiles32(rows, cols), kT, 0, st>>>(p, g, m, v, rows, cols, lr, b1, b2, eps, bc1, bc2, dst_t);
+    launch_pdl(k_fi_adam_t, tiles32(rows, cols), kT, 0, st, p, g, m, v, rows, cols, lr, b1, b2, eps, bc1, bc2, dst_t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fi_weight_copy(const float* w, int rows, int cols, uint16_t* dst, uint16_t* dst_t,
                                   cudaStream_t st) {
-    k_fi_weight_copy<<<tiles32(rows, cols), kT, 0, st>>>(w, rows, cols, dst, dst_t);
+    launch_pdl(k_fi_weight_copy, tiles32(rows, cols), kT, 0, st, w, rows, cols, dst, dst_t);
     return cudaGetLastError();
 }
 

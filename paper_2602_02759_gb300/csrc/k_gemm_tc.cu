@@ -28,6 +28,7 @@
 
 #include "k_view_tc.cuh"
 #include "nef_internal.h"
+#include "nef_launch.cuh"
 
 namespace nef {
 namespace gemm {
@@ -104,6 +105,8 @@ __global__ void __launch_bounds__(kThreadsG, 1)
 k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
           const __grid_constant__ CUtensorMap cmap, float* __restrict__ C, int M, int N, int K, int ldc,
           int accumulate, int kb_per_split, int store, int* err) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int kStage = GemmLayout<BN>::kStage;
     constexpr int kBar = GemmLayout<BN>::kBar;
     constexpr int kMisc = GemmLayout<BN>::kMisc;
@@ -253,6 +256,8 @@ k_gemm_nt(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
 // C (=, or += with accumulate) the sum of the splits' partial tiles, in split order.
 __global__ void k_gemm_reduce(const float* __restrict__ part, int n_split, int M, int N, int ldc,
                               float* __restrict__ C, int accumulate) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)M * N) return;
     const int64_t r = e / N, c = e - r * N;
@@ -371,11 +376,11 @@ cudaError_t launch_gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, in
         if ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && ldc % 4 == 0 && encode_c(&cm, out, M, N, ldc, n_split))
             store = n_split > 1 ? gemm::kStoreTma3d : gemm::kStoreTma2d;
     }
-    kern<<<grid, gemm::kThreadsG, smem, st>>>(am, bm, cm, out, M, N, K, (int)ldc, accumulate, std::max(per, 1), store,
+    launch_pdl(kern, grid, gemm::kThreadsG, smem, st, am, bm, cm, out, M, N, K, (int)ldc, accumulate, std::max(per, 1), store,
                                                err);
     if (n_split > 1) {
         const int64_t n = (int64_t)M * N;
-        gemm::k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, n_split, M, N, (int)ldc, C, accumulate);
+        launch_pdl(gemm::k_gemm_reduce, (unsigned)((n + 255) / 256), 256, 0, st, ws, n_split, M, N, (int)ldc, C, accumulate);
     }
     return cudaGetLastError();
 }

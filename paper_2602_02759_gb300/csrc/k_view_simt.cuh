@@ -12,6 +12,7 @@
 
 #include "nef_device.cuh"
 #include "nef_internal.h"
+#include "nef_launch.cuh"
 
 namespace nef {
 
@@ -40,6 +41,8 @@ __global__ void __launch_bounds__(kThreads)
 k_view_simt(const T* __restrict__ y, const uint32_t* __restrict__ mbits, ViewDesc v, WeightSpec w,
             LossSpec L, int64_t cols_per_split, T* __restrict__ s_num, T* __restrict__ s_den,
             double* __restrict__ loss_part) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int PAD = 4;
     constexpr int MR = TM / 16, NR = TN / 16;
     constexpr int SR = (TM * BP) / 1024;
@@ -228,7 +231,7 @@ cudaError_t run(const T* y, const uint32_t* mbits, const ViewDesc& v, const Weig
     if (e != cudaSuccess) return e;
     const int64_t n_ctas = n_rb * n_split;
     if (n_ctas_out) *n_ctas_out = (int)n_ctas;
-    kern<<<(unsigned)n_ctas, kThreads, sm, st>>>(y, mbits, v, w, L, cols_per_split, s_num, s_den,
+    launch_pdl(kern, (unsigned)n_ctas, kThreads, sm, st, y, mbits, v, w, L, cols_per_split, s_num, s_den,
                                                   loss_part);
     return cudaGetLastError();
 }

@@ -34,6 +34,7 @@
 #include "nef_batched.h"
 #include "nef_device.cuh"
 #include "nef_internal.h"
+#include "nef_launch.cuh"
 
 #ifndef NEF_TC_TRACE
 #define NEF_TC_TRACE 0  // 1: per-site wait and phase cycle counters (nef_tc_trace; slows the pass)
@@ -1328,6 +1329,8 @@ template <int BP, bool DEN, int WK, bool LOSS, int QM, int CFG = 0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_view_tc(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap vmap,
           const __grid_constant__ CUtensorMap cmap, const __grid_constant__ Params prm) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t n_rb = (prm.v.rows + TM - 1) / TM;
     view_tc_body<BP, DEN, WK, LOSS, QM, false, CFG>(&ymap, &vmap, &cmap, prm, blockIdx.x % n_rb,
                                                     blockIdx.x / n_rb);

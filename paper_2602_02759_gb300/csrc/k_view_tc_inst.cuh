@@ -12,7 +12,7 @@ cudaError_t launch_one(const CUtensorMap& map, const CUtensorMap& vmap, const CU
     const int sm = Layout<BP, DEN, CFG>::kAlloc;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, sm, st>>>(map, vmap, cmap, p);
+    launch_pdl(kern, grid, kThreads, sm, st, map, vmap, cmap, p);
     return cudaGetLastError();
 }
 

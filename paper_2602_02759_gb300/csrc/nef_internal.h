@@ -104,6 +104,13 @@ struct EinDesc {
     int64_t n_out_el, n_free_el;
     void* out;
     int accumulate;                        // 1: out += result, 0: out = result
+    // FP32 only, with accumulate = 0: also write the BF16 copy of the result here (same
+    // offsets) and store the FP32 result rounded to it (round to nearest even)
+    uint16_t* out16;
+    // optional second contraction of the same shape that reads op0b in place of op[0]
+    // and writes outb (the two share every other operand read)
+    const void* op0b;
+    void* outb;
 };
 
 // ----------------------------------------------------- finishing a pass
@@ -200,6 +207,13 @@ cudaError_t launch_view_simt(const T* y, const uint32_t* mbits, const ViewDesc& 
                              T* s_num, T* s_den, const LossSpec* loss, double* loss_part,
                              cudaStream_t st, int* n_ctas_out);
 
+// Kernels this library has launched in this process (a counter kept by the launchers).
+long long kernel_launches();
+
+// Both split reductions of a pass (numerator and denominator partials) in one launch.
+template <typename T>
+cudaError_t launch_reduce_splits2(const T* part_a, const T* part_b, int n_split, int64_t n, T* out_a, T* out_b,
+                                  cudaStream_t st);
 template <typename T>
 cudaError_t launch_reduce_splits(const T* part, int n_split, int64_t n, T* out, cudaStream_t st);
 

@@ -164,6 +164,30 @@ struct EinRecipe {
     int64_t n_out_el = 1, n_free_el = 1;
 };
 
+// Recipes that compute the same tensor into the same layout (destinations aside).
+bool same_recipe(const EinRecipe& a, const EinRecipe& b) {
+    if (a.out_let != b.out_let || a.free_let != b.free_let || a.out_st != b.out_st || a.out_kind != b.out_kind ||
+        a.n_out_el != b.n_out_el || a.n_free_el != b.n_free_el || a.ops.size() != b.ops.size())
+        return false;
+    for (size_t k = 0; k < a.ops.size(); ++k)
+        if (a.ops[k].kind != b.ops[k].kind || a.ops[k].index != b.ops[k].index || a.ops[k].st != b.ops[k].st)
+            return false;
+    return true;
+}
+
+// Recipes of one contraction over two different buffers in operand 0 (numerator and
+// denominator epilogues): one dual launch computes both.
+bool dual_pair(const EinRecipe& a, const EinRecipe& b) {
+    if (a.out_let != b.out_let || a.free_let != b.free_let || a.out_st != b.out_st || a.out_kind != b.out_kind ||
+        a.ops.empty() || a.ops.size() != b.ops.size() || a.ops[0].kind != 1 || b.ops[0].kind != 1 ||
+        a.ops[0].st != b.ops[0].st)
+        return false;
+    for (size_t k = 1; k < a.ops.size(); ++k)
+        if (a.ops[k].kind != b.ops[k].kind || a.ops[k].index != b.ops[k].index || a.ops[k].st != b.ops[k].st)
+            return false;
+    return true;
+}
+
 enum BufId { B_NUM = 0, B_DEN, B_SNUM, B_SDEN, B_SPART_N, B_SPART_D, B_DENVEC, B_COLSUM0,
              B_WA = 20, B_WB, B_SRC0 = 32, B_CS0 = 4096 };
 
@@ -174,8 +198,8 @@ struct SourcePlan {
     SrcDesc desc;          // index terms (ptr bound at run time)
     int copy_of = -1;      // factor whose relabelled copy this is (kept current by its update)
     std::vector<int> deps;             // factors the build reads
-    std::vector<int64_t> built_at;     // their versions when last built (empty = stale)
     int cs_buf = -1;       // column sums of this operand (closed-form denominators), or -1
+    bool shared = false;   // same recipe as an earlier pass's operand: reads that pass's buffer
 };
 
 struct PassPlan {
@@ -198,6 +222,7 @@ struct PassPlan {
     int64_t cost = 0;
     std::string desc;
     bool finish_identity = false;     // epilogue is a relabelling of S: fused finish kernel
+    bool dual_epi = false;            // epi_num and epi_den differ only in the S they read
     // generic
     EinRecipe gen_num, gen_den;
 };
@@ -236,6 +261,10 @@ struct nef_plan_s {
     std::vector<std::vector<std::pair<int, int>>> mirrors_of;   // factor -> (pass, source: -1 = P)
     std::vector<int64_t> fac_version;
     int64_t version_counter = 0;
+    // per source buffer: versions of the factors its build read when it was last built
+    // (empty = stale); buffers are shared by passes whose operands have one recipe
+    std::vector<std::vector<int64_t>> src_built;
+    int sweep_launches[2] = {0, 0};   // kernels of one sweep without / with a mask, as last counted
     int64_t max_ld = 16;
     int64_t n_sm = 152;               // SMs of the plan's device (grid sizing)
     // per-sweep loss and graph replay of sweeps
@@ -999,9 +1028,10 @@ ColsumDesc colsum_jobs(nef_plan_t p, int f) {
 
 bool source_stale(nef_plan_t p, const SourcePlan& sp) {
     if (sp.copy_of >= 0) return false;
-    if (sp.built_at.size() != sp.deps.size()) return true;
+    const std::vector<int64_t>& built = p->src_built[sp.buf];
+    if (built.size() != sp.deps.size()) return true;
     for (size_t k = 0; k < sp.deps.size(); ++k)
-        if (sp.built_at[k] != p->fac_version[sp.deps[k]]) return true;
+        if (built[k] != p->fac_version[sp.deps[k]]) return true;
     return false;
 }
 
@@ -1030,14 +1060,16 @@ nef_status refresh_sources(nef_plan_t p, PassPlan& pp, void* const* factors, cud
     for (int k = -1; k < (int)pp.Q.size(); ++k) {
         SourcePlan& sp = source_ref(pp, k);
         if (!source_stale(p, sp)) continue;
-        NEF_TRY(run_ein<T>(p, sp.build, factors, st));
+        // the build also writes the BF16 copy the tensor-core pass reads (and rounds the
+        // FP32 values to it); the copy's padding columns stay zero from allocation
+        EinDesc d = bind(p, sp.build, factors);
         if constexpr (sizeof(T) == 4) {
-            if (bf16)
-                NEF_CUDA(launch_convert_bf16(static_cast<float*>(buf_ptr(p, sp.buf)),
-                                             sp.n_rows * pp.view.bond_pad, p->src_bf16[sp.buf], st));
+            if (bf16) d.out16 = p->src_bf16[sp.buf];
         }
-        sp.built_at.clear();
-        for (int g : sp.deps) sp.built_at.push_back(p->fac_version[g]);
+        NEF_CUDA(launch_einsum<T>(d, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
+        std::vector<int64_t>& built = p->src_built[sp.buf];
+        built.clear();
+        for (int g : sp.deps) built.push_back(p->fac_version[g]);
     }
     return NEF_OK;
 }
@@ -1164,13 +1196,28 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
         NEF_CUDA(launch_finish<T>(d, u, st));
         return after_update<T>(p, pp.l, st);
     }
-    NEF_CUDA(launch_reduce_splits<T>(spn, n_split, sz, static_cast<T*>(buf_ptr(p, B_SNUM)), st));
-    if (need_den)
-        NEF_CUDA(launch_reduce_splits<T>(spd, n_split, sz, static_cast<T*>(buf_ptr(p, B_SDEN)), st));
-    NEF_TRY(run_ein<T>(p, pp.epi_num, factors, st));
-    if (need_den) {
-        NEF_TRY(run_ein<T>(p, pp.epi_den, factors, st));
+    // S = the sum of the split partials (one split: the partials are S); numerator and
+    // denominator reduced in one launch, and contracted by one dual epilogue where
+    // their recipes differ only in which S they read
+    T* snum = n_split == 1 ? spn : static_cast<T*>(buf_ptr(p, B_SNUM));
+    T* sden = n_split == 1 ? spd : static_cast<T*>(buf_ptr(p, B_SDEN));
+    if (n_split > 1) {
+        if (need_den) NEF_CUDA(launch_reduce_splits2<T>(spn, spd, n_split, sz, snum, sden, st));
+        else NEF_CUDA(launch_reduce_splits<T>(spn, n_split, sz, snum, st));
+    }
+    EinDesc en = bind(p, pp.epi_num, factors);
+    en.op[0] = snum;
+    if (need_den && pp.dual_epi) {
+        en.op0b = sden;
+        en.outb = buf_ptr(p, B_DEN);
+        NEF_CUDA(launch_einsum<T>(en, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
+    } else if (need_den) {
+        NEF_CUDA(launch_einsum<T>(en, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
+        EinDesc ed = bind(p, pp.epi_den, factors);
+        ed.op[0] = sden;
+        NEF_CUDA(launch_einsum<T>(ed, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
     } else {
+        NEF_CUDA(launch_einsum<T>(en, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
         for (auto& r : pp.colsum) NEF_TRY(run_ein<T>(p, r, factors, st));
         NEF_TRY(run_ein<T>(p, pp.den_prod, factors, st));
         NEF_TRY(run_ein<T>(p, pp.epi_den_closed, factors, st));
@@ -1263,6 +1310,7 @@ template <typename T>
 nef_status sweep_once(nef_plan_t p, const T* y, const uint32_t* mbits, void* const* factors, const WeightSpec& w,
                       const UpdateSpec& u, const LossSpec* loss, double* trace, int only_l, cudaStream_t st) {
     bool first = true;
+    const long long c0 = kernel_launches();
     for (int l = 0; l < p->md.L; ++l) {
         if (only_l >= 0 && l != only_l) continue;
         const LossSpec* lp = first ? loss : nullptr;
@@ -1271,6 +1319,7 @@ nef_status sweep_once(nef_plan_t p, const T* y, const uint32_t* mbits, void* con
         NEF_TRY(run_pass<T>(p, p->pass[l], y, mbits, factors, w, u, st, lp, &n_part));
         if (lp) NEF_CUDA(launch_loss_append(p->loss_part, n_part, trace, p->loss_count, p->loss_out, st));
     }
+    if (only_l < 0 && !loss) p->sweep_launches[mbits ? 1 : 0] = (int)(kernel_launches() - c0);
     return NEF_OK;
 }
 
@@ -1916,7 +1965,35 @@ nef_status build_plan(nef_plan_t p) {
         const bool id_closed = !pp.den_closed ||
                                (pp.epi_den_closed.ops.size() == 1 && pp.epi_den_closed.free_let.empty());
         pp.finish_identity = id_num && id_den && id_closed && md.term[pp.l].size() <= (size_t)kMaxFacLet;
+        pp.dual_epi = dual_pair(pp.epi_num, pp.epi_den);
         p->max_ld = std::max<int64_t>(p->max_ld, pp.view.bond_pad);
+    }
+    // ---- contracted operands with one recipe (the same product of the same factors in
+    // the same layout, e.g. the column-side operand of several passes of one view) share
+    // the first one's buffer, so a sweep builds each of them once per change of its factors
+    for (int pi = 0; pi < (int)p->pass.size(); ++pi) {
+        PassPlan& pp = p->pass[pi];
+        if (pp.generic) continue;
+        for (int k = -1; k < (int)pp.Q.size(); ++k) {
+            SourcePlan& sp = source_ref(pp, k);
+            if (sp.copy_of >= 0) continue;
+            bool done = false;
+            for (int pj = 0; pj <= pi && !done; ++pj) {
+                PassPlan& po = p->pass[pj];
+                if (po.generic || po.view.bond_pad != pp.view.bond_pad) continue;
+                for (int k2 = -1; k2 < (int)po.Q.size() && !done; ++k2) {
+                    if (pj == pi && k2 >= k) break;
+                    const SourcePlan& so = source_ref(po, k2);
+                    if (so.copy_of >= 0 || so.shared || so.n_rows != sp.n_rows || so.desc.ld != sp.desc.ld ||
+                        !same_recipe(so.build, sp.build))
+                        continue;
+                    sp.buf = so.buf;
+                    sp.build.out_index = so.buf;
+                    sp.shared = true;
+                    done = true;
+                }
+            }
+        }
     }
     // ---- workspace
     size_t es = p->esz;
@@ -1948,11 +2025,13 @@ nef_status build_plan(nef_plan_t p) {
             if (q.cs_buf >= 0) NEF_TRY(alloc(p, q.cs_buf, (size_t)pp.view.bond_pad * es));
     }
     p->src_bf16.assign(next_buf + 1, nullptr);
+    p->src_built.assign(next_buf + 1, {});
     for (auto& pp : p->pass) {
         if (pp.generic) continue;
         std::vector<SourcePlan*> srcs{&pp.P};
         for (auto& q : pp.Q) srcs.push_back(&q);
         for (auto* sp : srcs) {
+            if (sp->shared) continue;  // the buffer of the operand it repeats
             size_t n = (size_t)sp->n_rows * pp.view.bond_pad;
             NEF_TRY(alloc(p, sp->buf, n * es));
             if (p->prec == NEF_BF16) {
@@ -2198,7 +2277,9 @@ int nef_plan_info(nef_plan_t plan, char* buf, int cap) {
 
 int nef_plan_launches(nef_plan_t plan, int has_mask) {
     if (!plan) return 0;
-    // one sweep inside a nef_fit call (the per-call start-up is not counted)
+    // one sweep inside a nef_fit call (the per-call start-up is not counted): as counted
+    // when a sweep was last recorded or run, else the planner's estimate
+    if (plan->sweep_launches[has_mask ? 1 : 0] > 0) return plan->sweep_launches[has_mask ? 1 : 0];
     int total = 0;
     for (auto& pp : plan->pass) {
         if (pp.generic) {
