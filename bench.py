@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", default="cp_kl",
-                    choices=["cp_kl", "cp_beta05", "custom4", "small", "batched", "uber", "icews", "losses"],
+                    choices=["cp_kl", "cp_beta05", "custom4", "small", "batched", "uber", "icews", "losses",
+                             "foldin", "uber_mesh"],
                     help="cp_kl: the benchmark line (default); the others print one measurement "
                          "line each for the other workloads")
     ap.add_argument("--batched-problems", type=int, default=48)
@@ -537,9 +538,13 @@ def time_fit(nef, torch, p, precision, sweeps, warmup, stream, eager=False, auto
     """Seconds per sweep of one nef_fit call of `sweeps` sweeps (after `warmup`
     sweeps), and the final loss, from p.inits[0]."""
     dt = torch.float64 if precision == "fp64" else torch.float32
-    Y = torch.from_numpy(p.y).cuda().to(dt)
-    M = None if p.mask is None else torch.from_numpy(p.mask).cuda()
-    fs = [torch.from_numpy(f).cuda().to(dt) for f in p.inits[0]]
+
+    def dev(a):
+        return a if torch.is_tensor(a) else torch.from_numpy(a).cuda()
+
+    Y = dev(p.y).to(dt)
+    M = None if p.mask is None else dev(p.mask)
+    fs = [dev(f).to(dt) for f in p.inits[0]]
     lk = dict(loss=getattr(p, "loss", "ab"), loss_par=getattr(p, "loss_par", 0.0))
     plan = nef.Plan(p.model_str, p.dims, precision=precision, stream=stream, eager=eager, **lk)
     if autotune:
@@ -566,6 +571,28 @@ def time_fit(nef, torch, p, precision, sweeps, warmup, stream, eager=False, auto
     return sec, loss, prof, info
 
 
+def uber_mesh_problem(torch, dims=(27, 7, 24, 400, 400), r=10, k=6, seed=0):
+    """The Uber model 'wr,dr,hr,irk,jrk->wdhij' at the 400 x 400 pick-up mesh of the
+    paper's largest Uber tensor (27 x 7 x 24 x 400 x 400 = 725.8 M entries), R = 10,
+    K = 6: the recipe of synth.config_uber (Gamma(0.3,1) truth, Poisson data, no mask,
+    KL, inits U(0.5,1.5)) drawn on the GPU with a seeded torch generator, since numpy
+    would take minutes at this size."""
+    from types import SimpleNamespace
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    w, d, h, i, j = dims
+    shapes = [(w, r), (d, r), (h, r), (i, r, k), (j, r, k)]
+    truth = [torch._standard_gamma(torch.full(s, 0.3, device="cuda"), generator=g) for s in shapes]
+    mean = torch.einsum("wr,dr,hr,irk,jrk->wdhij", *truth)
+    y = torch.poisson(mean, generator=g).contiguous()
+    del mean, truth
+    inits = [[(0.5 + torch.rand(s, device="cuda", generator=g)).contiguous() for s in shapes]]
+    return SimpleNamespace(model_str="wr,dr,hr,irk,jrk->wdhij",
+                           dims={"w": w, "d": d, "h": h, "i": i, "j": j, "r": r, "k": k}, y=y, mask=None,
+                           inits=inits, alpha=1.0, beta=0.0, factor_shapes=lambda: shapes,
+                           note=f"uber-mesh wr,dr,hr,irk,jrk->wdhij {dims} R{r} K{k} KL (data drawn on the GPU)")
+
+
 def run_workload(args):
     """Measurement lines for the workloads other than the benchmark line."""
     import numpy as np
@@ -575,6 +602,12 @@ def run_workload(args):
     hbm, _, src = load_peaks()
     stream = torch.cuda.current_stream()
     sweeps = max(3, args.steps)
+    if args.workload == "foldin":
+        # the learned fold-in workload alone (the benchmark line carries it as a variant)
+        out = foldin_variant(nef, torch, stream)
+        out["peak_source"] = f"hbm_gbs {hbm} of {src}"
+        print(json.dumps(out), flush=True)
+        return 0
     if args.workload == "losses":
         # the 512^3 rank-64 CP workload under each further loss family (App. B), BF16
         # and the plain FP32 sweep, the same sweeps from the same start
@@ -599,11 +632,12 @@ def run_workload(args):
         out["peak_source"] = f"hbm_gbs {hbm} of {src}"
         print(json.dumps(out), flush=True)
         return 0
-    if args.workload in ("cp_beta05", "custom4", "small", "uber", "icews"):
+    if args.workload in ("cp_beta05", "custom4", "small", "uber", "icews", "uber_mesh"):
         p = {"cp_beta05": lambda: synth.config2(beta=-0.5, n=args.n),
              "custom4": synth.config3, "small": synth.config1,
-             "uber": synth.config_uber, "icews": synth.config_icews}[args.workload]()
-        n_el = p.y.size
+             "uber": synth.config_uber, "icews": synth.config_icews,
+             "uber_mesh": lambda: uber_mesh_problem(torch)}[args.workload]()
+        n_el = p.y.numel() if torch.is_tensor(p.y) else p.y.size
         n_fac = len(p.factor_shapes())
         bytes_sweep = n_fac * (4.0 * n_el + (n_el / 8.0 if p.mask is not None else 0.0))
         out = {"workload": p.note, "alpha_beta": [p.alpha, p.beta], "entries": int(n_el),
@@ -661,9 +695,19 @@ def run_workload(args):
     facs = fresh()
     nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, args.warmup, losses=False)
     torch.cuda.synchronize()
+    # the fit: one call of `sweeps` sweeps (set-up included), no loss evaluation
     t0 = time.perf_counter()
-    losses = nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, sweeps)
+    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, sweeps, losses=False)
+    torch.cuda.synchronize()
     t_b = time.perf_counter() - t0
+    # the call's fixed cost, and the loss of every fit (0 sweeps: set-up + loss pass)
+    t0 = time.perf_counter()
+    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, 0, losses=False)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, 0)
+    t_loss = time.perf_counter() - t0 - t_setup
     # one plain FP32 plan per (problem, restart), the same sweeps (at most the first 48 problems)
     n_cmp = min(48, len(Ys))
     facs2 = fresh(n_cmp)
@@ -687,9 +731,12 @@ def run_workload(args):
            "batched_bf16": {"fit_sweeps_per_s": fits * sweeps / t_b, "seconds": t_b,
                             "ms_per_all_problem_sweep": t_b / sweeps * 1e3,
                             "hbm_frac": bytes_sweep * sweeps / t_b / 1e9 / hbm,
-                            "note": "wall clock of one nef_fit_batched call (one persistent launch per bond "
-                                    "width, graph-captured); bytes count Y and the mask bits once per problem "
-                                    "and mode, not once per restart"},
+                            "call_setup_ms": t_setup * 1e3, "loss_pass_ms": t_loss * 1e3,
+                            "note": "wall clock of one nef_fit_batched call of all the sweeps without the "
+                                    "final loss evaluation (one persistent launch per bond width, "
+                                    "graph-captured); call_setup_ms is a 0-sweep call, loss_pass_ms the "
+                                    "extra time of the losses of every fit; bytes count Y and the mask bits "
+                                    "once per problem and mode, not once per restart"},
            "per_fit_fp32": {"fit_sweeps_per_s": sweeps_fp32 / t_s, "seconds": t_s, "problems": n_cmp,
                             "note": "one NEF_FP32 plan per problem, restarts fitted one after another"},
            "speedup": (fits * sweeps / t_b) / (sweeps_fp32 / t_s),
