@@ -544,7 +544,7 @@ def time_fit(nef, torch, p, precision, sweeps, warmup, stream, eager=False, auto
 
     Y = dev(p.y).to(dt)
     M = None if p.mask is None else dev(p.mask)
-    fs = [dev(f).to(dt) for f in p.inits[0]]
+    fs = [dev(f).to(dt).clone() for f in p.inits[0]]  # every fit starts from the same inits
     lk = dict(loss=getattr(p, "loss", "ab"), loss_par=getattr(p, "loss_par", 0.0))
     plan = nef.Plan(p.model_str, p.dims, precision=precision, stream=stream, eager=eager, **lk)
     if autotune:

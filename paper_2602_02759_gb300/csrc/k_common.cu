@@ -18,46 +18,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <typename T>
-__global__ void k_einsum_part(EinDesc d, int64_t chunk, T* partial) {
-    pdl_wait();
-    pdl_trigger();
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int sp = blockIdx.y;
-    if (o >= d.n_out_el) return;
-    int64_t off[kMaxEinOps];
-    for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
-    int64_t rem = o;
-    for (int q = d.n_out - 1; q >= 0; --q) {
-        int64_t v = rem % d.dim[q];
-        rem /= d.dim[q];
-        for (int k = 0; k < d.n_ops; ++k) off[k] += v * d.ost[k][q];
-    }
-    const int64_t f0 = (int64_t)sp * chunk;
-    const int64_t f1 = min(f0 + chunk, d.n_free_el);
-    int64_t idx[kMaxEinLet];
-    rem = f0;
-    for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
-        idx[q] = rem % d.dim[q];
-        rem /= d.dim[q];
-        for (int k = 0; k < d.n_ops; ++k) off[k] += idx[q] * d.ost[k][q];
-    }
-    T acc = T(0);
-    for (int64_t f = f0; f < f1; ++f) {
-        T p = T(1);
-        for (int k = 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
-        acc += p;
-        for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
-            idx[q] += 1;
-            for (int k = 0; k < d.n_ops; ++k) off[k] += d.ost[k][q];
-            if (idx[q] < d.dim[q]) break;
-            for (int k = 0; k < d.n_ops; ++k) off[k] -= d.ost[k][q] * d.dim[q];
-            idx[q] = 0;
-        }
-    }
-    partial[(int64_t)sp * d.n_out_el + o] = acc;
-}
-
 // Destination write of a contraction: out (= or +=), and with out16 the BF16 copy
 // and the FP32 value rounded to it (round to nearest even).
 template <typename T>
@@ -75,18 +35,66 @@ __device__ __forceinline__ void ein_store(const EinDesc& d, void* outp, int64_t 
     out[dst] = d.accumulate ? out[dst] + acc : acc;
 }
 
+// Operand 0 at offset off: the value, or the sum of its split partials in split order.
+template <typename T>
+__device__ __forceinline__ T ein_op0(const EinDesc& d, const void* base, int64_t off) {
+    const T* p = static_cast<const T*>(base) + off;
+    T v = p[0];
+    for (int s = 1; s < d.op0_splits; ++s) v += p[(int64_t)s * d.op0_split_stride];
+    return v;
+}
+
 // Product of the operands at one free combination: all of them into acc, or (DUAL)
 // operand 0 times the rest into acc and operand 0b times the rest into accb.
 template <typename T, bool DUAL>
 __device__ __forceinline__ void ein_term(const EinDesc& d, const int64_t* off, T& acc, T& accb) {
     T p = T(1);
-    for (int k = DUAL ? 1 : 0; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
+    for (int k = 1; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
     if constexpr (DUAL) {
-        acc += static_cast<const T*>(d.op[0])[off[0]] * p;
-        accb += static_cast<const T*>(d.op0b)[off[0]] * p;
+        acc += ein_op0<T>(d, d.op[0], off[0]) * p;
+        accb += ein_op0<T>(d, d.op0b, off[0]) * p;
     } else {
-        acc += p;
+        acc += (d.n_ops > 0 ? ein_op0<T>(d, d.op[0], off[0]) : T(1)) * p;
     }
+}
+
+template <typename T>
+__global__ void k_einsum_part(EinDesc d, int64_t chunk, T* partial) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sp = blockIdx.y;
+    if (o >= d.n_out_el) return;
+    int64_t off[kMaxEinOps];
+    for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
+    uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
+    for (int q = d.n_out - 1; q >= 0; --q) {
+        const uint32_t dq = (uint32_t)d.dim[q];
+        const int64_t v = rem % dq;
+        rem /= dq;
+        for (int k = 0; k < d.n_ops; ++k) off[k] += v * d.ost[k][q];
+    }
+    const int64_t f0 = (int64_t)sp * chunk;
+    const int64_t f1 = min(f0 + chunk, d.n_free_el);
+    int64_t idx[kMaxEinLet];
+    int64_t frem = f0;
+    for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
+        idx[q] = frem % d.dim[q];
+        frem /= d.dim[q];
+        for (int k = 0; k < d.n_ops; ++k) off[k] += idx[q] * d.ost[k][q];
+    }
+    T acc = T(0), unused = T(0);
+    for (int64_t f = f0; f < f1; ++f) {
+        ein_term<T, false>(d, off, acc, unused);
+        for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
+            idx[q] += 1;
+            for (int k = 0; k < d.n_ops; ++k) off[k] += d.ost[k][q];
+            if (idx[q] < d.dim[q]) break;
+            for (int k = 0; k < d.n_ops; ++k) off[k] -= d.ost[k][q] * d.dim[q];
+            idx[q] = 0;
+        }
+    }
+    partial[(int64_t)sp * d.n_out_el + o] = acc;
 }
 
 // Single-split contraction written straight to the destination layout.
@@ -98,10 +106,12 @@ __global__ void k_einsum_direct(EinDesc d) {
     if (o >= d.n_out_el) return;
     int64_t off[kMaxEinOps];
     for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
-    int64_t dst = 0, rem = o;
+    int64_t dst = 0;
+    uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
     for (int q = d.n_out - 1; q >= 0; --q) {
-        const int64_t v = rem % d.dim[q];
-        rem /= d.dim[q];
+        const uint32_t dq = (uint32_t)d.dim[q];
+        const int64_t v = rem % dq;
+        rem /= dq;
         dst += v * d.out_st[q];
         for (int k = 0; k < d.n_ops; ++k) off[k] += v * d.ost[k][q];
     }
@@ -159,10 +169,11 @@ __global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
     if (ok) {
         int64_t base[kMaxEinOps];
         for (int k = 0; k < d.n_ops; ++k) base[k] = 0;
-        int64_t rem = o;
+        uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
         for (int q = d.n_out - 1; q >= 0; --q) {
-            const int64_t v = rem % d.dim[q];
-            rem /= d.dim[q];
+            const uint32_t dq = (uint32_t)d.dim[q];
+            const int64_t v = rem % dq;
+            rem /= dq;
             dst += v * d.out_st[q];
             for (int k = 0; k < d.n_ops; ++k) base[k] += v * d.ost[k][q];
         }
@@ -196,10 +207,12 @@ __global__ void k_einsum_final(EinDesc d, int n_split, const T* partial) {
     if (o >= d.n_out_el) return;
     T acc = T(0);
     for (int s = 0; s < n_split; ++s) acc += partial[(int64_t)s * d.n_out_el + o];
-    int64_t dst = 0, rem = o;
+    int64_t dst = 0;
+    uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
     for (int q = d.n_out - 1; q >= 0; --q) {
-        dst += (rem % d.dim[q]) * d.out_st[q];
-        rem /= d.dim[q];
+        const uint32_t dq = (uint32_t)d.dim[q];
+        dst += (int64_t)(rem % dq) * d.out_st[q];
+        rem /= dq;
     }
     ein_store<T>(d, d.out, dst, acc);
 }
@@ -550,9 +563,13 @@ inline unsigned blocks_for(int64_t n, int threads = kThreads) {
 template <typename T>
 cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cudaStream_t st) {
     if (d.n_out_el <= 0) return cudaSuccess;
+    if (d.n_out_el >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // 32-bit output decode
     const bool dual = d.op0b != nullptr && d.outb != nullptr && d.n_ops >= 1;
-    // few free combinations per output: a group of G threads per output
-    if (d.n_free_el > 4 && d.n_free_el < ((int64_t)1 << 31)) {
+    // few free combinations per output: a group of G threads per output, unless there are
+    // outputs enough for one thread each and few combinations (a short loop beats the
+    // group's idle threads and its reduction)
+    const bool short_loop = d.n_free_el <= 16 && d.n_out_el >= 32768;
+    if (d.n_free_el > 4 && !short_loop && d.n_free_el < ((int64_t)1 << 31)) {
         const int g = d.n_free_el <= 32 ? 8 : (d.n_free_el <= 128 ? 32 : kThreads);
         const bool part_ok = partial_cap >= 2 * d.n_out_el;
         if (d.n_free_el / g <= 64 || !part_ok) {

@@ -111,6 +111,10 @@ struct EinDesc {
     // and writes outb (the two share every other operand read)
     const void* op0b;
     void* outb;
+    // op0_splits > 1: operand 0 (and op0b) is the sum of that many partial copies
+    // op0_split_stride elements apart (read in split order at every access)
+    int op0_splits;
+    int64_t op0_split_stride;
 };
 
 // ----------------------------------------------------- finishing a pass

@@ -223,6 +223,7 @@ struct PassPlan {
     std::string desc;
     bool finish_identity = false;     // epilogue is a relabelling of S: fused finish kernel
     bool dual_epi = false;            // epi_num and epi_den differ only in the S they read
+    bool epi_s_once = false;          // the epilogue reads every element of S once
     // generic
     EinRecipe gen_num, gen_den;
 };
@@ -1199,14 +1200,20 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
     // S = the sum of the split partials (one split: the partials are S); numerator and
     // denominator reduced in one launch, and contracted by one dual epilogue where
     // their recipes differ only in which S they read
-    T* snum = n_split == 1 ? spn : static_cast<T*>(buf_ptr(p, B_SNUM));
-    T* sden = n_split == 1 ? spd : static_cast<T*>(buf_ptr(p, B_SDEN));
-    if (n_split > 1) {
+    // (an epilogue that reads each element of S once sums the partials as it reads them)
+    const bool in_place = n_split == 1 || (pp.epi_s_once && (!need_den || pp.dual_epi));
+    T* snum = in_place ? spn : static_cast<T*>(buf_ptr(p, B_SNUM));
+    T* sden = in_place ? spd : static_cast<T*>(buf_ptr(p, B_SDEN));
+    if (!in_place) {
         if (need_den) NEF_CUDA(launch_reduce_splits2<T>(spn, spd, n_split, sz, snum, sden, st));
         else NEF_CUDA(launch_reduce_splits<T>(spn, n_split, sz, snum, st));
     }
     EinDesc en = bind(p, pp.epi_num, factors);
     en.op[0] = snum;
+    if (in_place && n_split > 1) {
+        en.op0_splits = n_split;
+        en.op0_split_stride = sz;
+    }
     if (need_den && pp.dual_epi) {
         en.op0b = sden;
         en.outb = buf_ptr(p, B_DEN);
@@ -1966,6 +1973,11 @@ nef_status build_plan(nef_plan_t p) {
                                (pp.epi_den_closed.ops.size() == 1 && pp.epi_den_closed.free_let.empty());
         pp.finish_identity = id_num && id_den && id_closed && md.term[pp.l].size() <= (size_t)kMaxFacLet;
         pp.dual_epi = dual_pair(pp.epi_num, pp.epi_den);
+        // every letter of the epilogue moves its S operand: each S element is read once,
+        // so the split partials can be summed where they are read
+        pp.epi_s_once = !pp.epi_num.ops.empty() && pp.epi_num.ops[0].kind == 1;
+        for (int x : pp.epi_num.out_let) pp.epi_s_once = pp.epi_s_once && pp.epi_num.ops[0].st[x] != 0;
+        for (int x : pp.epi_num.free_let) pp.epi_s_once = pp.epi_s_once && pp.epi_num.ops[0].st[x] != 0;
         p->max_ld = std::max<int64_t>(p->max_ld, pp.view.bond_pad);
     }
     // ---- contracted operands with one recipe (the same product of the same factors in

@@ -45,7 +45,12 @@ cudaError_t launch_einsum(const EinDesc& d, T*, int64_t, cudaStream_t) {
                 for (int k = 0; k < d.n_ops; ++k) {
                     int64_t off = 0;
                     for (int q = 0; q < nl; ++q) off += idx[q] * d.ost[k][q];
-                    p *= static_cast<const T*>(k == 0 && pass == 1 ? d.op0b : d.op[k])[off];
+                    const T* base = static_cast<const T*>(k == 0 && pass == 1 ? d.op0b : d.op[k]);
+                    T v = base[off];
+                    // operand 0 as the sum of its split partials
+                    if (k == 0)
+                        for (int sp = 1; sp < d.op0_splits; ++sp) v += base[off + sp * d.op0_split_stride];
+                    p *= v;
                 }
                 acc += p;
             }
