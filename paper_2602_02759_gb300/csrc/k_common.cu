@@ -97,16 +97,14 @@ __global__ void k_einsum_part(EinDesc d, int64_t chunk, T* partial) {
     partial[(int64_t)sp * d.n_out_el + o] = acc;
 }
 
-// Single-split contraction written straight to the destination layout.
+// Single-split contraction: one thread per output element (false past the last).
 template <typename T, bool DUAL>
-__global__ void k_einsum_direct(EinDesc d) {
-    pdl_wait();
-    pdl_trigger();
+__device__ __forceinline__ bool ein_direct_eval(const EinDesc& d, int64_t& dst, T& acc, T& accb) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= d.n_out_el) return;
+    if (o >= d.n_out_el) return false;
     int64_t off[kMaxEinOps];
     for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
-    int64_t dst = 0;
+    dst = 0;
     uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
     for (int q = d.n_out - 1; q >= 0; --q) {
         const uint32_t dq = (uint32_t)d.dim[q];
@@ -117,7 +115,8 @@ __global__ void k_einsum_direct(EinDesc d) {
     }
     int64_t idx[kMaxEinLet];
     for (int q = d.n_out; q < d.n_out + d.n_free; ++q) idx[q] = 0;
-    T acc = T(0), accb = T(0);
+    acc = T(0);
+    accb = T(0);
     for (int64_t f = 0; f < d.n_free_el; ++f) {
         ein_term<T, DUAL>(d, off, acc, accb);
         for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
@@ -128,6 +127,17 @@ __global__ void k_einsum_direct(EinDesc d) {
             idx[q] = 0;
         }
     }
+    return true;
+}
+
+// Single-split contraction written straight to the destination layout.
+template <typename T, bool DUAL>
+__global__ void k_einsum_direct(EinDesc d) {
+    pdl_wait();
+    pdl_trigger();
+    int64_t dst;
+    T acc, accb;
+    if (!ein_direct_eval<T, DUAL>(d, dst, acc, accb)) return;
     ein_store<T>(d, d.out, dst, acc);
     if constexpr (DUAL) ein_store<T>(d, d.outb, dst, accb);
 }
@@ -156,16 +166,14 @@ __device__ __forceinline__ T group_sum(T acc, T* sh) {
 // sums its partials.  Used where G threads cover an output's free combinations in a
 // few steps (at most 4 for G = 8 and 32, 64 for G = 256).
 template <typename T, int G, bool DUAL>
-__global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
-    pdl_wait();
-    pdl_trigger();
+__device__ __forceinline__ bool ein_grouped_eval(const EinDesc& d, T* sh, int64_t& dst, T& acc, T& accb) {
     constexpr int kGroups = kThreads / G;
-    __shared__ T sh[kThreads / 32];
     const int sub = (int)(threadIdx.x % G);
     const int64_t o = (int64_t)blockIdx.x * kGroups + threadIdx.x / G;
     const bool ok = o < d.n_out_el;
-    T acc = T(0), accb = T(0);
-    int64_t dst = 0;
+    acc = T(0);
+    accb = T(0);
+    dst = 0;
     if (ok) {
         int64_t base[kMaxEinOps];
         for (int k = 0; k < d.n_ops; ++k) base[k] = 0;
@@ -193,7 +201,17 @@ __global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
     }
     acc = group_sum<T, G>(acc, sh);
     if constexpr (DUAL) accb = group_sum<T, G>(accb, sh);
-    if (ok && sub == 0) {
+    return ok && sub == 0;
+}
+
+template <typename T, int G, bool DUAL>
+__global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ T sh[kThreads / 32];
+    int64_t dst;
+    T acc, accb;
+    if (ein_grouped_eval<T, G, DUAL>(d, sh, dst, acc, accb)) {
         ein_store<T>(d, d.out, dst, acc);
         if constexpr (DUAL) ein_store<T>(d, d.outb, dst, accb);
     }
@@ -507,6 +525,40 @@ struct LetterDims {
     int64_t d[kMaxFacLet];
 };
 
+// The epilogue's last contraction with Eq. 3.4 applied to its outputs (EinUpdate).
+template <typename T, bool DUAL>
+__device__ __forceinline__ void ein_update_out(const EinDesc& d, const EinUpdate& up, int64_t dst, T acc, T accb) {
+    ein_store<T>(d, d.out, dst, acc);
+    if constexpr (DUAL) ein_store<T>(d, d.outb, dst, accb);
+    const T num = DUAL ? acc : static_cast<const T*>(up.num)[dst];
+    const T den = DUAL ? accb : acc;
+    T* th = static_cast<T*>(up.theta);
+    const T v = mu_update(th[dst], num, den, up.u);
+    th[dst] = v;
+    int64_t idx[kMaxFacLet];
+    decode_letters<T>(dst, up.nlet, up.dim, idx);
+    write_mirrors<T>(up.mir, idx, up.nlet, v);
+}
+
+template <typename T, bool DUAL>
+__global__ void k_einsum_direct_upd(EinDesc d, EinUpdate up) {
+    pdl_wait();
+    pdl_trigger();
+    int64_t dst;
+    T acc, accb;
+    if (ein_direct_eval<T, DUAL>(d, dst, acc, accb)) ein_update_out<T, DUAL>(d, up, dst, acc, accb);
+}
+
+template <typename T, int G, bool DUAL>
+__global__ void __launch_bounds__(kThreads) k_einsum_grouped_upd(EinDesc d, EinUpdate up) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ T sh[kThreads / 32];
+    int64_t dst;
+    T acc, accb;
+    if (ein_grouped_eval<T, G, DUAL>(d, sh, dst, acc, accb)) ein_update_out<T, DUAL>(d, up, dst, acc, accb);
+}
+
 template <typename T>
 __global__ void k_update_mirror(T* __restrict__ theta, const T* __restrict__ num, const T* __restrict__ den,
                                 int64_t n, UpdateSpec u, int nlet, LetterDims dim, MirrorDesc m) {
@@ -560,11 +612,10 @@ inline unsigned blocks_for(int64_t n, int threads = kThreads) {
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cudaStream_t st) {
-    if (d.n_out_el <= 0) return cudaSuccess;
-    if (d.n_out_el >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // 32-bit output decode
-    const bool dual = d.op0b != nullptr && d.outb != nullptr && d.n_ops >= 1;
+// How a contraction runs: a group of G threads per output (returns G), one thread per
+// output (1), or split over the free combinations with a partial buffer (0).
+static int ein_mode(const EinDesc& d, int64_t partial_cap, int64_t* n_split_out) {
+    *n_split_out = 1;
     // few free combinations per output: a group of G threads per output, unless there are
     // outputs enough for one thread each and few combinations (a short loop beats the
     // group's idle threads and its reduction)
@@ -573,20 +624,8 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
         const int g = d.n_free_el <= 32 ? 8 : (d.n_free_el <= 128 ? 32 : kThreads);
         const bool part_ok = partial_cap >= 2 * d.n_out_el;
         if (d.n_free_el / g <= 64 || !part_ok) {
-            const int64_t per = kThreads / g;
-            const int64_t blocks = (d.n_out_el + per - 1) / per;
-            if (blocks < ((int64_t)1 << 31)) {
-                if (dual) {
-                    if (g == 8) launch_pdl(k_einsum_grouped<T, 8, true>, (unsigned)blocks, kThreads, 0, st, d);
-                    else if (g == 32) launch_pdl(k_einsum_grouped<T, 32, true>, (unsigned)blocks, kThreads, 0, st, d);
-                    else launch_pdl(k_einsum_grouped<T, kThreads, true>, (unsigned)blocks, kThreads, 0, st, d);
-                } else {
-                    if (g == 8) launch_pdl(k_einsum_grouped<T, 8, false>, (unsigned)blocks, kThreads, 0, st, d);
-                    else if (g == 32) launch_pdl(k_einsum_grouped<T, 32, false>, (unsigned)blocks, kThreads, 0, st, d);
-                    else launch_pdl(k_einsum_grouped<T, kThreads, false>, (unsigned)blocks, kThreads, 0, st, d);
-                }
-                return cudaGetLastError();
-            }
+            const int64_t blocks = (d.n_out_el + kThreads / g - 1) / (kThreads / g);
+            if (blocks < ((int64_t)1 << 31)) return g;
         }
     }
     // split the free combinations so that the grid has enough threads
@@ -598,7 +637,31 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
         n_split = std::min<int64_t>(n_split, partial_cap / d.n_out_el);
         n_split = std::max<int64_t>(n_split, 1);
     }
-    if (n_split == 1) {
+    *n_split_out = n_split;
+    return n_split == 1 ? 1 : 0;
+}
+
+template <typename T>
+cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cudaStream_t st) {
+    if (d.n_out_el <= 0) return cudaSuccess;
+    if (d.n_out_el >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // 32-bit output decode
+    const bool dual = d.op0b != nullptr && d.outb != nullptr && d.n_ops >= 1;
+    int64_t n_split = 1;
+    const int mode = ein_mode(d, partial_cap, &n_split);
+    if (mode > 1) {
+        const unsigned blocks = (unsigned)((d.n_out_el + kThreads / mode - 1) / (kThreads / mode));
+        if (dual) {
+            if (mode == 8) launch_pdl(k_einsum_grouped<T, 8, true>, blocks, kThreads, 0, st, d);
+            else if (mode == 32) launch_pdl(k_einsum_grouped<T, 32, true>, blocks, kThreads, 0, st, d);
+            else launch_pdl(k_einsum_grouped<T, kThreads, true>, blocks, kThreads, 0, st, d);
+        } else {
+            if (mode == 8) launch_pdl(k_einsum_grouped<T, 8, false>, blocks, kThreads, 0, st, d);
+            else if (mode == 32) launch_pdl(k_einsum_grouped<T, 32, false>, blocks, kThreads, 0, st, d);
+            else launch_pdl(k_einsum_grouped<T, kThreads, false>, blocks, kThreads, 0, st, d);
+        }
+        return cudaGetLastError();
+    }
+    if (mode == 1) {
         // one pass straight into the destination
         if (dual) launch_pdl(k_einsum_direct<T, true>, blocks_for(d.n_out_el), kThreads, 0, st, d);
         else launch_pdl(k_einsum_direct<T, false>, blocks_for(d.n_out_el), kThreads, 0, st, d);
@@ -620,6 +683,45 @@ cudaError_t launch_einsum(const EinDesc& d, T* partial, int64_t partial_cap, cud
     dim3 grid(blocks_for(d.n_out_el), (unsigned)n_split);
     launch_pdl(k_einsum_part<T>, grid, kThreads, 0, st, d, chunk, partial);
     launch_pdl(k_einsum_final<T>, blocks_for(d.n_out_el), kThreads, 0, st, d, (int)n_split, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_einsum_update(const EinDesc& d, const EinUpdate& up, T* partial, int64_t partial_cap,
+                                 cudaStream_t st) {
+    if (d.n_out_el <= 0) return cudaSuccess;
+    if (d.n_out_el >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    const bool dual = d.op0b != nullptr && d.outb != nullptr && d.n_ops >= 1;
+    if (dual == (up.num != nullptr)) return cudaErrorInvalidValue;  // num from the dual form or from up.num
+    int64_t n_split = 1;
+    const int mode = ein_mode(d, partial_cap, &n_split);
+    if (mode > 1) {
+        const unsigned blocks = (unsigned)((d.n_out_el + kThreads / mode - 1) / (kThreads / mode));
+        if (dual) {
+            if (mode == 8) launch_pdl(k_einsum_grouped_upd<T, 8, true>, blocks, kThreads, 0, st, d, up);
+            else if (mode == 32) launch_pdl(k_einsum_grouped_upd<T, 32, true>, blocks, kThreads, 0, st, d, up);
+            else launch_pdl(k_einsum_grouped_upd<T, kThreads, true>, blocks, kThreads, 0, st, d, up);
+        } else {
+            if (mode == 8) launch_pdl(k_einsum_grouped_upd<T, 8, false>, blocks, kThreads, 0, st, d, up);
+            else if (mode == 32) launch_pdl(k_einsum_grouped_upd<T, 32, false>, blocks, kThreads, 0, st, d, up);
+            else launch_pdl(k_einsum_grouped_upd<T, kThreads, false>, blocks, kThreads, 0, st, d, up);
+        }
+        return cudaGetLastError();
+    }
+    if (mode == 1) {
+        if (dual) launch_pdl(k_einsum_direct_upd<T, true>, blocks_for(d.n_out_el), kThreads, 0, st, d, up);
+        else launch_pdl(k_einsum_direct_upd<T, false>, blocks_for(d.n_out_el), kThreads, 0, st, d, up);
+        return cudaGetLastError();
+    }
+    // split over the free combinations: the contraction(s), then the update on its own
+    cudaError_t e = launch_einsum<T>(d, partial, partial_cap, st);
+    if (e != cudaSuccess) return e;
+    LetterDims ld{};
+    for (int q = 0; q < up.nlet; ++q) ld.d[q] = up.dim[q];
+    const T* num = dual ? static_cast<const T*>(d.out) : static_cast<const T*>(up.num);
+    const T* den = dual ? static_cast<const T*>(d.outb) : static_cast<const T*>(d.out);
+    launch_pdl(k_update_mirror<T>, blocks_for(d.n_out_el), kThreads, 0, st, static_cast<T*>(up.theta), num, den,
+               d.n_out_el, up.u, up.nlet, ld, up.mir);
     return cudaGetLastError();
 }
 
@@ -751,6 +853,7 @@ cudaError_t launch_generic_weights(const GenericRecon& g, const T* y, const uint
 
 #define NEF_INST(T)                                                                          \
     template cudaError_t launch_einsum<T>(const EinDesc&, T*, int64_t, cudaStream_t);        \
+    template cudaError_t launch_einsum_update<T>(const EinDesc&, const EinUpdate&, T*, int64_t, cudaStream_t); \
     template cudaError_t launch_check_data<T>(const T*, int64_t, int*, cudaStream_t);        \
     template cudaError_t launch_reduce_splits<T>(const T*, int, int64_t, T*, cudaStream_t);  \
     template cudaError_t launch_reduce_splits2<T>(const T*, const T*, int, int64_t, T*, T*, cudaStream_t); \

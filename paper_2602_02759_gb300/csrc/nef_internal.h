@@ -163,6 +163,24 @@ struct ColsumDesc {
 template <typename T>
 cudaError_t launch_finish(const FinishDesc& d, const UpdateSpec& u, cudaStream_t st);
 
+// Eq. 3.4 applied by the contraction that completes a factor's numerator and
+// denominator (the epilogue's last einsum, whose outputs are the factor's elements in
+// term order): with num set, the contraction computes den and num is read there;
+// otherwise it is the dual form computing num (out) and den (outb).  The updated
+// element goes to theta and to the factor's canonical copies.
+struct EinUpdate {
+    void* theta;
+    const void* num;
+    int nlet;
+    int64_t dim[kMaxFacLet];
+    MirrorDesc mir;
+    UpdateSpec u;
+};
+
+template <typename T>
+cudaError_t launch_einsum_update(const EinDesc& d, const EinUpdate& up, T* partial, int64_t partial_cap,
+                                 cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n, const UpdateSpec& u,
                                  int nlet, const int64_t* dim, const MirrorDesc& m, cudaStream_t st);

@@ -1214,28 +1214,40 @@ nef_status run_pass(nef_plan_t p, PassPlan& pp, const T* y, const uint32_t* mbit
         en.op0_splits = n_split;
         en.op0_split_stride = sz;
     }
+    // the epilogue's last contraction also applies Eq. 3.4 to its outputs (the factor's
+    // elements) and writes the factor's copies, unless num and den are exported
+    EinUpdate up{};
+    up.theta = factors[pp.l];
+    up.nlet = (int)ldims.size();
+    for (int q = 0; q < up.nlet; ++q) up.dim[q] = ldims[q];
+    up.mir = mir;
+    up.u = u;
+    auto last = [&](const EinDesc& d, const void* num_in) -> cudaError_t {
+        if (export_num) return launch_einsum<T>(d, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st);
+        EinUpdate uu = up;
+        uu.num = num_in;
+        return launch_einsum_update<T>(d, uu, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st);
+    };
     if (need_den && pp.dual_epi) {
         en.op0b = sden;
         en.outb = buf_ptr(p, B_DEN);
-        NEF_CUDA(launch_einsum<T>(en, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
+        NEF_CUDA(last(en, nullptr));
     } else if (need_den) {
         NEF_CUDA(launch_einsum<T>(en, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
         EinDesc ed = bind(p, pp.epi_den, factors);
         ed.op[0] = sden;
-        NEF_CUDA(launch_einsum<T>(ed, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
+        NEF_CUDA(last(ed, num));
     } else {
         NEF_CUDA(launch_einsum<T>(en, static_cast<T*>(p->ein_partial), p->ein_partial_cap, st));
         for (auto& r : pp.colsum) NEF_TRY(run_ein<T>(p, r, factors, st));
         NEF_TRY(run_ein<T>(p, pp.den_prod, factors, st));
-        NEF_TRY(run_ein<T>(p, pp.epi_den_closed, factors, st));
+        NEF_CUDA(last(bind(p, pp.epi_den_closed, factors), num));
     }
     if (export_num) {
         NEF_CUDA(cudaMemcpyAsync(export_num, num, nl * sizeof(T), cudaMemcpyDeviceToDevice, st));
         NEF_CUDA(cudaMemcpyAsync(export_den, den, nl * sizeof(T), cudaMemcpyDeviceToDevice, st));
         return NEF_OK;
     }
-    NEF_CUDA(launch_update_mirror<T>(static_cast<T*>(factors[pp.l]), num, den, nl, u, (int)ldims.size(),
-                                     ldims.data(), mir, st));
     return after_update<T>(p, pp.l, st);
 }
 

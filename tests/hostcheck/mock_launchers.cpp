@@ -313,6 +313,19 @@ cudaError_t launch_update_mirror(T* theta, const T* num, const T* den, int64_t n
     });
 }
 
+// The contraction, then Eq. 3.4 over its outputs (num from the dual form or up.num).
+template <typename T>
+cudaError_t launch_einsum_update(const EinDesc& d, const EinUpdate& up, T* partial, int64_t cap, cudaStream_t st) {
+    const bool dual = d.op0b != nullptr && d.outb != nullptr;
+    if (dual == (up.num != nullptr)) return cudaErrorInvalidValue;
+    cudaError_t e = launch_einsum<T>(d, partial, cap, st);
+    if (e != cudaSuccess) return e;
+    const T* num = dual ? static_cast<const T*>(d.out) : static_cast<const T*>(up.num);
+    const T* den = dual ? static_cast<const T*>(d.outb) : static_cast<const T*>(d.out);
+    return launch_update_mirror<T>(static_cast<T*>(up.theta), num, den, d.n_out_el, up.u, up.nlet, up.dim, up.mir,
+                                   st);
+}
+
 template <typename T>
 cudaError_t launch_mirror_init(const T* theta, int64_t n, int nlet, const int64_t* dim_in,
                                const MirrorDesc& m, cudaStream_t) {
@@ -397,6 +410,7 @@ cudaError_t launch_loss_append(const double* part, int n, double* trace, int* co
                                                    const LossSpec*, double*, int, cudaStream_t);
 #define INST2(T)                                                                                 \
     template cudaError_t launch_finish<T>(const FinishDesc&, const UpdateSpec&, cudaStream_t);       \
+    template cudaError_t launch_einsum_update<T>(const EinDesc&, const EinUpdate&, T*, int64_t, cudaStream_t); \
     template cudaError_t launch_update_mirror<T>(T*, const T*, const T*, int64_t, const UpdateSpec&,  \
                                                  int, const int64_t*, const MirrorDesc&, cudaStream_t); \
     template cudaError_t launch_mirror_init<T>(const T*, int64_t, int, const int64_t*,                \

@@ -315,6 +315,35 @@ def test_uber_shape_sampled_update():
         np.testing.assert_allclose(got[elems], expect, rtol=2e-3)
 
 
+def test_uber_mesh_update_matches_oracle_and_fp32():
+    """The Uber model on a 200 x 200 pick-up mesh (27x7x24x200x200 = 181 M entries,
+    a quarter of the paper's largest Uber mesh), BF16: one update of each factor from
+    the same start, every element against the plain FP32 CUDA-core update (2e-3) and
+    sampled elements against the FP64 oracle (2e-3)."""
+    nef = _nef()
+    p = synth.config_uber(dims=(27, 7, 24, 200, 200))
+    m = OracleModel(p.model_str, p.dims)
+    init = [f.astype(np.float64) for f in p.inits[0]]
+    pb = nef.Plan(p.model_str, p.dims, precision="bf16")
+    pf = nef.Plan(p.model_str, p.dims, precision="fp32")
+    assert all("kernel=tcgen05" in ln for ln in pb.info().splitlines() if ln.startswith("factor")), pb.info()
+    Y = dev(p.y)
+    rng = np.random.default_rng(17)
+    for l in range(5):
+        fb = [dev(f) for f in init]
+        ff = [dev(f) for f in init]
+        pb.update(l, Y, None, fb, p.alpha, p.beta)
+        pf.update(l, Y, None, ff, p.alpha, p.beta)
+        pb.check()
+        pf.check()
+        gb = fb[l].cpu().numpy().reshape(-1)
+        np.testing.assert_allclose(gb, ff[l].cpu().numpy().reshape(-1), rtol=2e-3)
+        elems = rng.choice(gb.size, size=3, replace=False)
+        num, den = m.numden_sampled(l, elems, p.y, None, init, p.alpha, p.beta)
+        expect = m.apply_update(init[l].reshape(-1)[elems], num, den, p.alpha, p.beta)
+        np.testing.assert_allclose(gb[elems], expect, rtol=2e-3)
+
+
 # ------------------------------------------------------------------ autotune
 
 def test_autotune_bf16_then_fit(tmp_path):
