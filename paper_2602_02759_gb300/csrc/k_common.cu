@@ -35,6 +35,25 @@ __device__ __forceinline__ void ein_store(const EinDesc& d, void* outp, int64_t 
     out[dst] = d.accumulate ? out[dst] + acc : acc;
 }
 
+// The index arrays below are walked with loops unrolled over their fixed sizes (and
+// guarded by the descriptor's counts), so they stay in registers; the descriptor is a
+// __grid_constant__ parameter, read in place.
+
+// Adds the offsets of letters q_lo..q_hi-1 decoded from r (the last letter fastest) to
+// every operand's offset, and to *dst with the destination strides.
+__device__ __forceinline__ void ein_decode(const EinDesc& d, int q_lo, int q_hi, uint32_t r,
+                                           int64_t (&off)[kMaxEinOps], int64_t* dst) {
+    for (int q = q_hi - 1; q >= q_lo; --q) {
+        const uint32_t dq = (uint32_t)d.dim[q];
+        const int64_t v = r % dq;
+        r /= dq;
+        if (dst) *dst += v * d.out_st[q];
+#pragma unroll
+        for (int k = 0; k < kMaxEinOps; ++k)
+            if (k < d.n_ops) off[k] += v * d.ost[k][q];
+    }
+}
+
 // Operand 0 at offset off: the value, or the sum of its split partials in split order.
 template <typename T>
 __device__ __forceinline__ T ein_op0(const EinDesc& d, const void* base, int64_t off) {
@@ -47,52 +66,65 @@ __device__ __forceinline__ T ein_op0(const EinDesc& d, const void* base, int64_t
 // Product of the operands at one free combination: all of them into acc, or (DUAL)
 // operand 0 times the rest into acc and operand 0b times the rest into accb.
 template <typename T, bool DUAL>
-__device__ __forceinline__ void ein_term(const EinDesc& d, const int64_t* off, T& acc, T& accb) {
+__device__ __forceinline__ void ein_term(const EinDesc& d, const int64_t (&off)[kMaxEinOps], T& acc, T& accb) {
     T p = T(1);
-    for (int k = 1; k < d.n_ops; ++k) p *= static_cast<const T*>(d.op[k])[off[k]];
+#pragma unroll
+    for (int k = 1; k < kMaxEinOps; ++k)
+        if (k < d.n_ops) p *= static_cast<const T*>(d.op[k])[off[k]];
     if constexpr (DUAL) {
         acc += ein_op0<T>(d, d.op[0], off[0]) * p;
         accb += ein_op0<T>(d, d.op0b, off[0]) * p;
     } else {
-        acc += (d.n_ops > 0 ? ein_op0<T>(d, d.op[0], off[0]) : T(1)) * p;
+        acc += ein_op0<T>(d, d.op[0], off[0]) * p;
+    }
+}
+
+// Steps the free letters' multi-index (the last fastest) by one, moving the offsets.
+__device__ __forceinline__ void ein_step(const EinDesc& d, int32_t (&idx)[kMaxEinLet], int64_t (&off)[kMaxEinOps]) {
+#pragma unroll
+    for (int q = kMaxEinLet - 1; q >= 0; --q) {
+        if (q < d.n_out || q >= d.n_out + d.n_free) continue;
+        idx[q] += 1;
+#pragma unroll
+        for (int k = 0; k < kMaxEinOps; ++k)
+            if (k < d.n_ops) off[k] += d.ost[k][q];
+        if (idx[q] < d.dim[q]) break;
+#pragma unroll
+        for (int k = 0; k < kMaxEinOps; ++k)
+            if (k < d.n_ops) off[k] -= d.ost[k][q] * d.dim[q];
+        idx[q] = 0;
     }
 }
 
 template <typename T>
-__global__ void k_einsum_part(EinDesc d, int64_t chunk, T* partial) {
+__global__ void k_einsum_part(const __grid_constant__ EinDesc d, int64_t chunk, T* partial) {
     pdl_wait();
     pdl_trigger();
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int sp = blockIdx.y;
     if (o >= d.n_out_el) return;
     int64_t off[kMaxEinOps];
-    for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
-    uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
-    for (int q = d.n_out - 1; q >= 0; --q) {
-        const uint32_t dq = (uint32_t)d.dim[q];
-        const int64_t v = rem % dq;
-        rem /= dq;
-        for (int k = 0; k < d.n_ops; ++k) off[k] += v * d.ost[k][q];
-    }
+#pragma unroll
+    for (int k = 0; k < kMaxEinOps; ++k) off[k] = 0;
+    ein_decode(d, 0, d.n_out, (uint32_t)o, off, nullptr);  // n_out_el < 2^31 (checked at launch)
     const int64_t f0 = (int64_t)sp * chunk;
     const int64_t f1 = min(f0 + chunk, d.n_free_el);
-    int64_t idx[kMaxEinLet];
+    int32_t idx[kMaxEinLet];
     int64_t frem = f0;
-    for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
-        idx[q] = frem % d.dim[q];
+#pragma unroll
+    for (int q = kMaxEinLet - 1; q >= 0; --q) {
+        idx[q] = 0;
+        if (q < d.n_out || q >= d.n_out + d.n_free) continue;
+        idx[q] = (int32_t)(frem % d.dim[q]);
         frem /= d.dim[q];
-        for (int k = 0; k < d.n_ops; ++k) off[k] += idx[q] * d.ost[k][q];
+#pragma unroll
+        for (int k = 0; k < kMaxEinOps; ++k)
+            if (k < d.n_ops) off[k] += (int64_t)idx[q] * d.ost[k][q];
     }
     T acc = T(0), unused = T(0);
     for (int64_t f = f0; f < f1; ++f) {
         ein_term<T, false>(d, off, acc, unused);
-        for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
-            idx[q] += 1;
-            for (int k = 0; k < d.n_ops; ++k) off[k] += d.ost[k][q];
-            if (idx[q] < d.dim[q]) break;
-            for (int k = 0; k < d.n_ops; ++k) off[k] -= d.ost[k][q] * d.dim[q];
-            idx[q] = 0;
-        }
+        ein_step(d, idx, off);
     }
     partial[(int64_t)sp * d.n_out_el + o] = acc;
 }
@@ -103,36 +135,25 @@ __device__ __forceinline__ bool ein_direct_eval(const EinDesc& d, int64_t& dst, 
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= d.n_out_el) return false;
     int64_t off[kMaxEinOps];
-    for (int k = 0; k < d.n_ops; ++k) off[k] = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxEinOps; ++k) off[k] = 0;
     dst = 0;
-    uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
-    for (int q = d.n_out - 1; q >= 0; --q) {
-        const uint32_t dq = (uint32_t)d.dim[q];
-        const int64_t v = rem % dq;
-        rem /= dq;
-        dst += v * d.out_st[q];
-        for (int k = 0; k < d.n_ops; ++k) off[k] += v * d.ost[k][q];
-    }
-    int64_t idx[kMaxEinLet];
-    for (int q = d.n_out; q < d.n_out + d.n_free; ++q) idx[q] = 0;
+    ein_decode(d, 0, d.n_out, (uint32_t)o, off, &dst);  // n_out_el < 2^31 (checked at launch)
+    int32_t idx[kMaxEinLet];
+#pragma unroll
+    for (int q = 0; q < kMaxEinLet; ++q) idx[q] = 0;
     acc = T(0);
     accb = T(0);
     for (int64_t f = 0; f < d.n_free_el; ++f) {
         ein_term<T, DUAL>(d, off, acc, accb);
-        for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
-            idx[q] += 1;
-            for (int k = 0; k < d.n_ops; ++k) off[k] += d.ost[k][q];
-            if (idx[q] < d.dim[q]) break;
-            for (int k = 0; k < d.n_ops; ++k) off[k] -= d.ost[k][q] * d.dim[q];
-            idx[q] = 0;
-        }
+        ein_step(d, idx, off);
     }
     return true;
 }
 
 // Single-split contraction written straight to the destination layout.
 template <typename T, bool DUAL>
-__global__ void k_einsum_direct(EinDesc d) {
+__global__ void k_einsum_direct(const __grid_constant__ EinDesc d) {
     pdl_wait();
     pdl_trigger();
     int64_t dst;
@@ -164,7 +185,8 @@ __device__ __forceinline__ T group_sum(T acc, T* sh) {
 // Contraction with G threads per output element: the threads of a group take the
 // free combinations f = sub, sub + G, ... (each decodes its own f) and the group
 // sums its partials.  Used where G threads cover an output's free combinations in a
-// few steps (at most 4 for G = 8 and 32, 64 for G = 256).
+// few steps (at most 4 for G = 8 and 32, 64 for G = 256).  Returns true for the
+// thread that writes the output.
 template <typename T, int G, bool DUAL>
 __device__ __forceinline__ bool ein_grouped_eval(const EinDesc& d, T* sh, int64_t& dst, T& acc, T& accb) {
     constexpr int kGroups = kThreads / G;
@@ -176,26 +198,15 @@ __device__ __forceinline__ bool ein_grouped_eval(const EinDesc& d, T* sh, int64_
     dst = 0;
     if (ok) {
         int64_t base[kMaxEinOps];
-        for (int k = 0; k < d.n_ops; ++k) base[k] = 0;
-        uint32_t rem = (uint32_t)o;  // n_out_el < 2^31 (checked at launch)
-        for (int q = d.n_out - 1; q >= 0; --q) {
-            const uint32_t dq = (uint32_t)d.dim[q];
-            const int64_t v = rem % dq;
-            rem /= dq;
-            dst += v * d.out_st[q];
-            for (int k = 0; k < d.n_ops; ++k) base[k] += v * d.ost[k][q];
-        }
-#pragma unroll 4
+#pragma unroll
+        for (int k = 0; k < kMaxEinOps; ++k) base[k] = 0;
+        ein_decode(d, 0, d.n_out, (uint32_t)o, base, &dst);  // n_out_el < 2^31 (checked at launch)
+#pragma unroll 2
         for (int64_t f = sub; f < d.n_free_el; f += G) {
             int64_t off[kMaxEinOps];
-            for (int k = 0; k < d.n_ops; ++k) off[k] = base[k];
-            uint32_t r = (uint32_t)f;  // n_free_el < 2^31 on this path
-            for (int q = d.n_out + d.n_free - 1; q >= d.n_out; --q) {
-                const uint32_t dq = (uint32_t)d.dim[q];
-                const uint32_t v = r % dq;
-                r /= dq;
-                for (int k = 0; k < d.n_ops; ++k) off[k] += (int64_t)v * d.ost[k][q];
-            }
+#pragma unroll
+            for (int k = 0; k < kMaxEinOps; ++k) off[k] = base[k];
+            ein_decode(d, d.n_out, d.n_out + d.n_free, (uint32_t)f, off, nullptr);  // n_free_el < 2^31 here
             ein_term<T, DUAL>(d, off, acc, accb);
         }
     }
@@ -205,7 +216,7 @@ __device__ __forceinline__ bool ein_grouped_eval(const EinDesc& d, T* sh, int64_
 }
 
 template <typename T, int G, bool DUAL>
-__global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
+__global__ void __launch_bounds__(kThreads) k_einsum_grouped(const __grid_constant__ EinDesc d) {
     pdl_wait();
     pdl_trigger();
     __shared__ T sh[kThreads / 32];
@@ -218,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_einsum_grouped(EinDesc d) {
 }
 
 template <typename T>
-__global__ void k_einsum_final(EinDesc d, int n_split, const T* partial) {
+__global__ void k_einsum_final(const __grid_constant__ EinDesc d, int n_split, const T* partial) {
     pdl_wait();
     pdl_trigger();
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -445,8 +456,11 @@ __device__ __forceinline__ uint16_t bf16_bits(float x) {
 }
 
 template <typename T>
-__device__ __forceinline__ void decode_letters(int64_t e, int nlet, const int64_t* dim, int64_t* idx) {
-    for (int q = nlet - 1; q >= 0; --q) {
+__device__ __forceinline__ void decode_letters(int64_t e, int nlet, const int64_t* dim, int64_t (&idx)[kMaxFacLet]) {
+#pragma unroll
+    for (int q = kMaxFacLet - 1; q >= 0; --q) {
+        idx[q] = 0;
+        if (q >= nlet) continue;
         idx[q] = e % dim[q];
         e /= dim[q];
     }
@@ -458,10 +472,14 @@ __device__ __forceinline__ void decode_letters(int64_t e, int nlet, const int64_
 // tensor cores multiply (otherwise the rounding of a whole factor column biases
 // num/den of that column, and the exponential updates scale the bias by num/den).
 template <typename T>
-__device__ __forceinline__ void write_mirrors(const MirrorDesc& m, const int64_t* idx, int nlet, T v) {
-    for (int k = 0; k < m.n; ++k) {
+__device__ __forceinline__ void write_mirrors(const MirrorDesc& m, const int64_t (&idx)[kMaxFacLet], int nlet, T v) {
+#pragma unroll
+    for (int k = 0; k < kMaxMirror; ++k) {
+        if (k >= m.n) break;
         int64_t off = 0;
-        for (int q = 0; q < nlet; ++q) off += idx[q] * m.st[k][q];
+#pragma unroll
+        for (int q = 0; q < kMaxFacLet; ++q)
+            if (q < nlet) off += idx[q] * m.st[k][q];
         if (m.p16[k]) {
             const uint16_t b = bf16_bits((float)v);
             m.p16[k][off] = b;
@@ -478,7 +496,8 @@ __device__ __forceinline__ void write_mirrors(const MirrorDesc& m, const int64_t
 constexpr int kFinEl = 32;
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_finish(FinishDesc d, UpdateSpec u) {
+__global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ FinishDesc d,
+                                                     const __grid_constant__ UpdateSpec u) {
     pdl_wait();
     pdl_trigger();
     constexpr int kGrp = kThreads / kFinEl;
@@ -486,12 +505,14 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishDesc d, UpdateSpec u)
     const int lane = (int)(threadIdx.x % kFinEl), g = (int)(threadIdx.x / kFinEl);
     const int64_t e = (int64_t)blockIdx.x * kFinEl + lane;
     const bool ok = e < d.n;
-    int64_t idx[kMaxFacLet];
+    int64_t idx[kMaxFacLet] = {};
     int64_t soff = 0, boff = 0;
     T num = T(0), den = T(0);
     if (ok) {
         decode_letters<T>(e, d.nlet, d.dim, idx);
-        for (int q = 0; q < d.nlet; ++q) {
+#pragma unroll
+        for (int q = 0; q < kMaxFacLet; ++q) {
+            if (q >= d.nlet) continue;
             soff += idx[q] * d.s_st[q];
             boff += idx[q] * d.b_st[q];
         }
@@ -535,13 +556,37 @@ __device__ __forceinline__ void ein_update_out(const EinDesc& d, const EinUpdate
     T* th = static_cast<T*>(up.theta);
     const T v = mu_update(th[dst], num, den, up.u);
     th[dst] = v;
-    int64_t idx[kMaxFacLet];
-    decode_letters<T>(dst, up.nlet, up.dim, idx);
-    write_mirrors<T>(up.mir, idx, up.nlet, v);
+    // the element's letters (term order, the last fastest) and its place in each copy
+    // (unrolled over the fixed sizes, so the index stays in registers)
+    uint32_t idx[kMaxFacLet];
+    uint32_t rem = (uint32_t)dst;  // factors have < 2^31 elements
+#pragma unroll
+    for (int q = kMaxFacLet - 1; q >= 0; --q) {
+        idx[q] = 0;
+        if (q >= up.nlet) continue;
+        const uint32_t dq = (uint32_t)up.dim[q];
+        idx[q] = rem % dq;
+        rem /= dq;
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxMirror; ++k) {
+        if (k >= up.mir.n) break;
+        int64_t off = 0;
+#pragma unroll
+        for (int q = 0; q < kMaxFacLet; ++q)
+            if (q < up.nlet) off += (int64_t)idx[q] * up.mir.st[k][q];
+        if (up.mir.p16[k]) {
+            const uint16_t b = bf16_bits((float)v);
+            up.mir.p16[k][off] = b;
+            static_cast<T*>(up.mir.p32[k])[off] = (T)__uint_as_float((uint32_t)b << 16);
+        } else {
+            static_cast<T*>(up.mir.p32[k])[off] = v;
+        }
+    }
 }
 
 template <typename T, bool DUAL>
-__global__ void k_einsum_direct_upd(EinDesc d, EinUpdate up) {
+__global__ void k_einsum_direct_upd(const __grid_constant__ EinDesc d, const __grid_constant__ EinUpdate up) {
     pdl_wait();
     pdl_trigger();
     int64_t dst;
@@ -550,7 +595,8 @@ __global__ void k_einsum_direct_upd(EinDesc d, EinUpdate up) {
 }
 
 template <typename T, int G, bool DUAL>
-__global__ void __launch_bounds__(kThreads) k_einsum_grouped_upd(EinDesc d, EinUpdate up) {
+__global__ void __launch_bounds__(kThreads) k_einsum_grouped_upd(const __grid_constant__ EinDesc d,
+                                                                  const __grid_constant__ EinUpdate up) {
     pdl_wait();
     pdl_trigger();
     __shared__ T sh[kThreads / 32];
@@ -561,7 +607,8 @@ __global__ void __launch_bounds__(kThreads) k_einsum_grouped_upd(EinDesc d, EinU
 
 template <typename T>
 __global__ void k_update_mirror(T* __restrict__ theta, const T* __restrict__ num, const T* __restrict__ den,
-                                int64_t n, UpdateSpec u, int nlet, LetterDims dim, MirrorDesc m) {
+                                int64_t n, const __grid_constant__ UpdateSpec u, int nlet,
+                                const __grid_constant__ LetterDims dim, const __grid_constant__ MirrorDesc m) {
     pdl_wait();
     pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -574,7 +621,8 @@ __global__ void k_update_mirror(T* __restrict__ theta, const T* __restrict__ num
 }
 
 template <typename T>
-__global__ void k_mirror_init(const T* __restrict__ theta, int64_t n, int nlet, LetterDims dim, MirrorDesc m) {
+__global__ void k_mirror_init(const T* __restrict__ theta, int64_t n, int nlet, const __grid_constant__ LetterDims dim,
+                              const __grid_constant__ MirrorDesc m) {
     pdl_wait();
     pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -586,7 +634,7 @@ __global__ void k_mirror_init(const T* __restrict__ theta, int64_t n, int nlet, 
 
 // Column sums of canonical operands: block (job, column).
 template <typename T>
-__global__ void k_colsums(ColsumDesc d) {
+__global__ void k_colsums(const __grid_constant__ ColsumDesc d) {
     pdl_wait();
     pdl_trigger();
     const ColsumJob& j = d.job[blockIdx.x];
