@@ -644,7 +644,8 @@ def run_workload(args):
                "algorithmic_bytes_per_sweep": bytes_sweep, "sweeps": sweeps}
         precs = ["bf16", "fp32"] + (["fp64"] if args.workload == "small" else [])
         for prec in precs:
-            sec, loss, prof, info = time_fit(nef, torch, p, prec, sweeps, args.warmup, stream)
+            sec, loss, prof, info = time_fit(nef, torch, p, prec, sweeps, args.warmup, stream,
+                                             autotune=not args.no_autotune)
             if prec == "bf16":
                 out["plan"] = info.strip().splitlines()
             out[prec] = {"sweeps_per_s": 1.0 / sec, "ms_per_sweep": sec * 1e3,
