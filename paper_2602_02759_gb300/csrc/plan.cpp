@@ -840,15 +840,21 @@ bool plan_view(const nef_plan_s& p, int l, int s, int e, int assign, int qform, 
     const int64_t target = (p.prec == NEF_BF16) ? p.n_sm : p.n_sm * 4;
     int64_t ns = 1;
     {
+        // the fewest waves of CTAs that keep >= 90 % of the SMs busy (a CTA has a fixed
+        // start-up and drain, so one long CTA per SM beats several short ones), else the
+        // best-filled split over up to four waves
         const int64_t rbs = std::max<int64_t>(1, n_rb);
         const int64_t hi = std::max<int64_t>(1, std::min<int64_t>(tiles, 4 * ((target + rbs - 1) / rbs)));
         double best = -1.0;
+        int64_t best_waves = 0;
         for (int64_t c = 1; c <= hi; ++c) {
             const int64_t ctas = rbs * c;
             const int64_t waves = (ctas + target - 1) / target;
             const double eff = (double)ctas / (double)(waves * target);
-            if (eff > best + 1e-9) {
+            const bool settled = best >= 0.9 && waves > best_waves;  // a fuller, earlier wave count won
+            if (!settled && eff > best + 1e-9) {
                 best = eff;
+                best_waves = waves;
                 ns = c;
             }
         }
