@@ -68,36 +68,47 @@ __global__ void k_mirror_batched(const BatchFinish* __restrict__ fin, const int6
 
 // One problem, all restarts: thread per entry of the unpadded tensor.
 __global__ void k_loss_batched(const float* __restrict__ y, const uint8_t* __restrict__ mask, int64_t I,
-                               int64_t J, int64_t K, int rank, int restarts, BatchFactors fac, LossSpec L,
-                               double* __restrict__ part) {
-    __shared__ double sh[kMaxRestarts][kThreads / 32];
-    double acc[kMaxRestarts];
-    for (int k = 0; k < kMaxRestarts; ++k) acc[k] = 0.0;
-    const int64_t n = I * J * K;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        if (mask && !mask[e]) continue;
-        const int64_t k3 = e % K, ij = e / K;
-        const int64_t j = ij % J, i = ij / J;
-        const float yv = y[e];
-        for (int q = 0; q < restarts; ++q) {
-            const float* A = fac.f[q][0];
-            const float* B = fac.f[q][1];
-            const float* C = fac.f[q][2];
-            float yh = 0.f;
-            for (int r = 0; r < rank; ++r) yh = fmaf(A[i * rank + r] * B[j * rank + r], C[k3 * rank + r], yh);
-            acc[q] += (double)divergence(yv, yh, L);
-        }
-    }
+                               int64_t J, int64_t K, int rank, int restarts, const __grid_constant__ BatchFactors fac,
+                               const __grid_constant__ LossSpec L, double* __restrict__ part) {
+    // One restart at a time: C of that restart in shared memory as [rank][K] (lanes read
+    // consecutive k), each warp takes (i, j) pairs and its lanes the k of that row of Y;
+    // lane r holds A[i,r] B[j,r] and the rank-sum runs over shuffles of it (rank <= 32).
+    extern __shared__ float c_sh[];
+    __shared__ double sh[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n_ij = I * J;
+    const int64_t warps_total = (int64_t)gridDim.x * (kThreads / 32);
     for (int q = 0; q < restarts; ++q) {
-        double v = warp_sum(acc[q]);
-        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < restarts) {
-        double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += sh[threadIdx.x][w];
-        part[(int64_t)blockIdx.x * restarts + threadIdx.x] = t;
+        const float* A = fac.f[q][0];
+        const float* B = fac.f[q][1];
+        const float* C = fac.f[q][2];
+        __syncthreads();  // c_sh free from the previous restart
+        for (int64_t t = threadIdx.x; t < K * rank; t += kThreads) {
+            const int64_t k = t / rank, r = t - k * rank;
+            c_sh[r * K + k] = C[t];
+        }
+        __syncthreads();
+        double acc = 0.0;
+        for (int64_t ij = (int64_t)blockIdx.x * (kThreads / 32) + warp; ij < n_ij; ij += warps_total) {
+            const int64_t i = ij / J, j = ij - i * J;
+            const float ab = lane < rank ? A[i * rank + lane] * B[j * rank + lane] : 0.f;
+            for (int64_t k0 = 0; k0 < K; k0 += 32) {
+                const int64_t k = k0 + lane;
+                const int64_t kc = k < K ? k : K - 1;
+                float yh = 0.f;
+                for (int r = 0; r < rank; ++r) yh = fmaf(__shfl_sync(0xffffffffu, ab, r), c_sh[r * K + kc], yh);
+                const int64_t e = ij * K + k;
+                if (k < K && (!mask || mask[e])) acc += (double)divergence(y[e], yh, L);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sh[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tsum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) tsum += sh[w];
+            part[(int64_t)blockIdx.x * restarts + q] = tsum;
+        }
     }
 }
 
@@ -130,8 +141,14 @@ cudaError_t launch_mirror_batched(const BatchFinish* fin, const int64_t* prefix,
 cudaError_t launch_loss_batched(const float* y, const uint8_t* mask, const int64_t* dims, int rank, int restarts,
                                 const BatchFactors& fac, const LossSpec& L, double* part, int n_blocks,
                                 double* out, cudaStream_t st) {
-    k_loss_batched<<<n_blocks, kThreads, 0, st>>>(y, mask, dims[0], dims[1], dims[2], rank, restarts, fac, L,
-                                                  part);
+    const size_t smem = (size_t)dims[2] * rank * sizeof(float);  // C of one restart, [rank][K]
+    if (rank > 32 || smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_loss_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_loss_batched<<<n_blocks, kThreads, smem, st>>>(y, mask, dims[0], dims[1], dims[2], rank, restarts, fac, L,
+                                                     part);
     k_loss_reduce<<<1, 32, 0, st>>>(part, n_blocks, restarts, out);
     return cudaGetLastError();
 }
