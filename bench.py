@@ -694,20 +694,22 @@ def run_workload(args):
     bytes_sweep = 3 * n_sum * (4.0 + 1.0 / 8.0)
     fits = len(Ys) * restarts
     facs = fresh()
-    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, args.warmup, losses=False)
+    # the work-item size, tuned on this workload (outside the timed region)
+    tiles, tile_ms = nef.fit_batched_tune(Ys, Ms, facs, 1.0, 0.0)
+    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, args.warmup, losses=False, tiles=tiles)
     torch.cuda.synchronize()
     # the fit: one call of `sweeps` sweeps (set-up included), no loss evaluation
     t0 = time.perf_counter()
-    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, sweeps, losses=False)
+    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, sweeps, losses=False, tiles=tiles)
     torch.cuda.synchronize()
     t_b = time.perf_counter() - t0
     # the call's fixed cost, and the loss of every fit (0 sweeps: set-up + loss pass)
     t0 = time.perf_counter()
-    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, 0, losses=False)
+    nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, 0, losses=False, tiles=tiles)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
-    losses = nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, 0)
+    losses = nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, 0, tiles=tiles)
     t_loss = time.perf_counter() - t0 - t_setup
     # one plain FP32 plan per (problem, restart), the same sweeps (at most the first 48 problems)
     n_cmp = min(48, len(Ys))
@@ -733,6 +735,8 @@ def run_workload(args):
                             "ms_per_all_problem_sweep": t_b / sweeps * 1e3,
                             "hbm_frac": bytes_sweep * sweeps / t_b / 1e9 / hbm,
                             "call_setup_ms": t_setup * 1e3, "loss_pass_ms": t_loss * 1e3,
+                            "tiles_per_item": tiles,
+                            "tune_ms_2_sweeps": {str(k): v for k, v in tile_ms.items()},
                             "note": "wall clock of one nef_fit_batched call of all the sweeps without the "
                                     "final loss evaluation (one persistent launch per bond width, "
                                     "graph-captured); call_setup_ms is a 0-sweep call, loss_pass_ms the "

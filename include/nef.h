@@ -110,11 +110,14 @@ typedef struct {
                         /* tensor-core pass; 0 = the default 4e9 (about 2 s).  A wait that  */
                         /* runs out stops its kernel cleanly and nef_check then reports     */
                         /* NEF_ETIMEOUT (the results of that call are invalid)              */
+    int batch_tiles;    /* nef_fit_batched: 64-column tiles of Y per work item (one fused   */
+                        /* pass of a row block over that many tiles); 0 = the default 64;   */
+                        /* nef_fit_batched_tune picks one for a workload                    */
 } nef_options;
 
 /* Fill *opt with the defaults: NEF_FP32, eps = 1e-10, no data check, fused, no
  * profiling, stream NULL, tol 0, no loss trace, graph replay, NEF_LOSS_AB,
- * loss_par 0, default wait limit. */
+ * loss_par 0, default wait limit, default batched tiles per work item. */
 void nef_default_options(nef_options* opt);
 
 /*
@@ -358,6 +361,19 @@ nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_t* ranks, c
                            const uint8_t* const* masks, float* const* factors, int restarts,
                            double alpha, double beta, int iters, const nef_options* opt,
                            double* losses);
+
+/*
+ * nef_fit_batched_tune -- the autotuner of the batched engine's work-item size:
+ * times nef_fit_batched over two sweeps with each of 16, 32, 64, 128 and 256
+ * column tiles per work item (nef_options.batch_tiles), on copies of the
+ * factors (the caller's factors are left unchanged), and returns the fastest in
+ * *tiles; ms (host, 5 doubles, or NULL) receives each candidate's wall time in
+ * that order.  Arguments as nef_fit_batched.  Allocates the factor copies for
+ * the duration of the call; synchronises opt->stream.  Errors as nef_fit_batched.
+ */
+nef_status nef_fit_batched_tune(int n, const int64_t* shapes, const int64_t* ranks, const float* const* Y,
+                                const uint8_t* const* masks, float* const* factors, int restarts,
+                                double alpha, double beta, const nef_options* opt, int* tiles, double* ms);
 
 /*
  * nef_cp3_update_static -- update factor l of the 3-way CP model

@@ -20,6 +20,7 @@ from ._nef import (  # noqa: F401
     Plan,
     cp3_update_static,
     fit_batched,
+    fit_batched_tune,
     load,
     pack_params,
     split_model,

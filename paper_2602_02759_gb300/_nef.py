@@ -24,7 +24,7 @@ PRECISIONS = {"fp32": NEF_FP32, "bf16": NEF_BF16, "fp64": NEF_FP64}
 EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "nef_fit_ex", "nef_fit_ctl",
            "nef_plan_sweeps", "nef_plan_autotune", "nef_update", "nef_numden", "nef_apply_update", "nef_loss",
            "nef_plan_info", "nef_plan_launches",
-           "nef_plan_profile", "nef_tc_trace", "nef_check", "nef_fit_batched", "nef_cp3_update_static",
+           "nef_plan_profile", "nef_tc_trace", "nef_check", "nef_fit_batched", "nef_fit_batched_tune", "nef_cp3_update_static",
            "nef_last_error",
            "nef_foldin_num_params", "nef_foldin_create", "nef_foldin_destroy", "nef_foldin_grad",
            "nef_foldin_train_step", "nef_foldin_predict", "nef_foldin_params"]
@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("check_data", ctypes.c_int), ("force_generic", ctypes.c_int),
                 ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("tol", ctypes.c_double), ("loss_trace", ctypes.c_void_p), ("eager", ctypes.c_int),
-                ("loss", ctypes.c_int), ("loss_par", ctypes.c_double), ("wait_cycles", ctypes.c_int64)]
+                ("loss", ctypes.c_int), ("loss_par", ctypes.c_double), ("wait_cycles", ctypes.c_int64),
+                ("batch_tiles", ctypes.c_int)]
 
 
 class FitControl(ctypes.Structure):
@@ -105,6 +106,10 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(Options), dp]
     lib.nef_fit_batched.restype = ctypes.c_int
+    lib.nef_fit_batched_tune.argtypes = [ctypes.c_int, i64p, i64p, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_int), dp]
+    lib.nef_fit_batched_tune.restype = ctypes.c_int
     lib.nef_cp3_update_static.argtypes = [vp, i64p, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
     lib.nef_cp3_update_static.restype = ctypes.c_int
@@ -145,12 +150,7 @@ def split_model(model_str: str):
     return list(rhs), latent, lhs.split(",")
 
 
-def fit_batched(Ys, masks, factors, alpha, beta, iters, eps=1e-10, stream=None, losses=True):
-    """nef_fit_batched: fit many CP models 'ir,jr,kr->ijk', each with several restarts.
-
-    Ys: list of n CUDA float32 [I, J, K] tensors; masks: None or a list of n uint8
-    tensors; factors: list over problems of lists over restarts of [A, B, C]
-    (CUDA float32, updated in place).  Returns an n x restarts list of losses."""
+def _batched_args(Ys, masks, factors, eps, stream, tiles):
     import torch
     n = len(Ys)
     restarts = len(factors[0])
@@ -167,12 +167,36 @@ def fit_batched(Ys, masks, factors, alpha, beta, iters, eps=1e-10, stream=None, 
     opt.precision = NEF_BF16
     opt.eps = float(eps)
     opt.stream = ctypes.c_void_p(stream.cuda_stream)
+    opt.batch_tiles = int(tiles)
+    return n, restarts, shapes, ranks, ys, ms, fs, opt
+
+
+def fit_batched(Ys, masks, factors, alpha, beta, iters, eps=1e-10, stream=None, losses=True, tiles=0):
+    """nef_fit_batched: fit many CP models 'ir,jr,kr->ijk', each with several restarts.
+
+    Ys: list of n CUDA float32 [I, J, K] tensors; masks: None or a list of n uint8
+    tensors; factors: list over problems of lists over restarts of [A, B, C]
+    (CUDA float32, updated in place); tiles: column tiles per work item (0 = the
+    default; see fit_batched_tune).  Returns an n x restarts list of losses."""
+    n, restarts, shapes, ranks, ys, ms, fs, opt = _batched_args(Ys, masks, factors, eps, stream, tiles)
     out = (ctypes.c_double * (n * restarts))() if losses else None
     check(load().nef_fit_batched(n, shapes, ranks, ys, ms, fs, restarts, float(alpha), float(beta), int(iters),
                                  ctypes.byref(opt), out))
     if not losses:
         return None
     return [[out[p * restarts + k] for k in range(restarts)] for p in range(n)]
+
+
+def fit_batched_tune(Ys, masks, factors, alpha, beta, eps=1e-10, stream=None):
+    """nef_fit_batched_tune: the column tiles per work item (16 .. 256) with which
+    two sweeps of fit_batched run fastest on this workload (timed on copies of the
+    factors, which are left unchanged).  Returns (tiles, {tiles: ms})."""
+    n, restarts, shapes, ranks, ys, ms, fs, opt = _batched_args(Ys, masks, factors, eps, stream, 0)
+    best = ctypes.c_int()
+    times = (ctypes.c_double * 5)()
+    check(load().nef_fit_batched_tune(n, shapes, ranks, ys, ms, fs, restarts, float(alpha), float(beta),
+                                      ctypes.byref(opt), ctypes.byref(best), times))
+    return best.value, dict(zip((16, 32, 64, 128, 256), list(times)))
 
 
 def cp3_update_static(Y, factors, l, alpha, beta, eps=1e-10, stream=None):

@@ -14,6 +14,7 @@
 // are copied once per call into a zero-padded layout (dimensions rounded up to
 // multiples of 4, padding unobserved).
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <vector>
 
@@ -54,10 +55,7 @@ nef_status bfail(nef_status s, const char* msg) {
 
 int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-#ifndef NEF_BATCH_TILES
-#define NEF_BATCH_TILES 64
-#endif
-constexpr int64_t kTilesPerCta = NEF_BATCH_TILES;  // column tiles per CTA of one unit
+constexpr int64_t kDefaultTiles = 64;  // column tiles per work item unless opt->batch_tiles says
 
 struct Prob {
     int64_t d[3], pd[3];
@@ -83,6 +81,8 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
     else nef_default_options(&opt);
     if (opt.precision != NEF_BF16)
         return bfail(NEF_EUNSUPPORTED, "the batched engine runs on the tensor cores: use NEF_BF16");
+    if (opt.batch_tiles < 0 || opt.batch_tiles > 4096) return bfail(NEF_EINVAL, "batch_tiles must be in [0, 4096]");
+    const int64_t kTilesPerCta = opt.batch_tiles > 0 ? opt.batch_tiles : kDefaultTiles;
     cudaStream_t st = static_cast<cudaStream_t>(opt.stream);
     const WeightSpec w = weight_spec(alpha, beta);
     const UpdateSpec u = update_spec(alpha, beta, opt.eps);
@@ -374,5 +374,56 @@ extern "C" nef_status nef_fit_batched(int n, const int64_t* shapes, const int64_
     B_CUDA(cudaMemcpyAsync(&herr, errf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     B_CUDA(cudaStreamSynchronize(st));
     if (herr) return bfail(NEF_ETIMEOUT, "a bounded wait in the batched tensor-core pass gave up");
+    return NEF_OK;
+}
+
+extern "C" nef_status nef_fit_batched_tune(int n, const int64_t* shapes, const int64_t* ranks,
+                                           const float* const* Y, const uint8_t* const* masks,
+                                           float* const* factors, int restarts, double alpha, double beta,
+                                           const nef_options* opt_in, int* tiles, double* ms) {
+    set_last_error("");
+    if (n < 1 || !shapes || !ranks || !factors || !tiles) return bfail(NEF_EINVAL, "NULL argument or n < 1");
+    if (restarts < 1 || restarts > kMaxRestarts) return bfail(NEF_EINVAL, "restarts must be in [1, 16]");
+    nef_options opt;
+    if (opt_in) opt = *opt_in;
+    else nef_default_options(&opt);
+    cudaStream_t st = static_cast<cudaStream_t>(opt.stream);
+    // copies of every factor: each candidate fits from the caller's starting point
+    const size_t nf = (size_t)n * restarts * 3;
+    std::vector<size_t> off(nf + 1, 0);
+    for (int p = 0; p < n; ++p)
+        for (int k = 0; k < restarts; ++k)
+            for (int m = 0; m < 3; ++m) {
+                const size_t f = ((size_t)p * restarts + k) * 3 + m;
+                off[f + 1] = off[f] + (size_t)rup(shapes[3 * p + m] * ranks[p], 4);
+            }
+    DevBuf work;
+    B_CUDA(work.alloc(off[nf] * sizeof(float)));
+    std::vector<float*> copies(nf);
+    for (size_t f = 0; f < nf; ++f) copies[f] = work.as<float>() + off[f];
+    static const int kCand[5] = {16, 32, 64, 128, 256};
+    double best = 1e300;
+    int best_t = (int)kDefaultTiles;
+    for (int c = 0; c < 5; ++c) {
+        for (size_t f = 0; f < nf; ++f) {
+            const int p = (int)(f / (3 * (size_t)restarts)), m = (int)(f % 3);
+            if (!factors[f]) return bfail(NEF_EINVAL, "factor pointer is NULL");
+            B_CUDA(cudaMemcpyAsync(copies[f], factors[f], (size_t)shapes[3 * p + m] * ranks[p] * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, st));
+        }
+        B_CUDA(cudaStreamSynchronize(st));
+        opt.batch_tiles = kCand[c];
+        const auto t0 = std::chrono::steady_clock::now();
+        const nef_status rc = nef_fit_batched(n, shapes, ranks, Y, masks, copies.data(), restarts, alpha, beta, 2,
+                                              &opt, nullptr);
+        const double t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (rc != NEF_OK) return rc;
+        if (ms) ms[c] = t;
+        if (t < best) {
+            best = t;
+            best_t = kCand[c];
+        }
+    }
+    *tiles = best_t;
     return NEF_OK;
 }

@@ -2126,6 +2126,7 @@ void nef_default_options(nef_options* opt) {
     opt->loss = NEF_LOSS_AB;
     opt->loss_par = 0.0;
     opt->wait_cycles = 0;
+    opt->batch_tiles = 0;
 }
 
 nef_status nef_plan(const char* model_str, const int64_t* shapes, int n_obs, const int64_t* ranks,

@@ -88,3 +88,38 @@ def test_batched_restarts_independent():
     for pi in range(3):
         for q in range(3):
             assert torch.equal(full[pi][1][q], single[pi][0][q])
+
+
+def test_batched_tune_then_fit_matches_oracle():
+    """nef_fit_batched_tune picks the column tiles per work item on the GPU and leaves
+    the factors unchanged; fits with the smallest candidate (16 tiles: many work items
+    and partials per row block) and with the tuned value both reach the FP64 oracle's
+    loss within 1e-3 after 60 sweeps."""
+    import paper_2602_02759_gb300 as nef
+    restarts, iters = 2, 60
+    probs = _batch(4, 300, 40, 150, 4, 32, restarts, 0.1)
+    Ys = [torch.from_numpy(p.y).cuda() for p in probs]
+    Ms = [torch.from_numpy(p.mask).cuda() for p in probs]
+
+    def fresh():
+        return [[[torch.from_numpy(f).cuda() for f in p.inits[k]] for k in range(restarts)] for p in probs]
+
+    facs = fresh()
+    tiles, times = nef.fit_batched_tune(Ys, Ms, facs, 1.0, 0.0)
+    torch.cuda.synchronize()
+    assert tiles in (16, 32, 64, 128, 256) and all(t > 0 for t in times.values())
+    for pi, p in enumerate(probs):
+        for k in range(restarts):
+            for f, g in zip(facs[pi][k], p.inits[k]):
+                assert np.array_equal(f.cpu().numpy(), g)
+    for t in sorted({16, tiles}):
+        facs = fresh()
+        nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, iters, losses=False, tiles=t)
+        torch.cuda.synchronize()
+        for pi, p in enumerate(probs):
+            m = OracleModel(p.model_str, p.dims)
+            for k in range(restarts):
+                _, tr = m.fit(p.y, p.mask, [f.astype(np.float64) for f in p.inits[k]], 1.0, 0.0, iters, trace=True)
+                got = [f.cpu().numpy().astype(np.float64) for f in facs[pi][k]]
+                lo, _ = m.loss(p.y, p.mask, got, 1.0, 0.0)
+                assert lo == pytest.approx(tr[-1], rel=1e-3), (t, pi, k, p.dims)

@@ -32,6 +32,10 @@ def lib():
     lib.nef_fit_batched.argtypes = [ctypes.c_int, i64p, i64p, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(Opt), ctypes.POINTER(ctypes.c_double)]
+    lib.nef_fit_batched_tune.argtypes = [ctypes.c_int, i64p, i64p, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(Opt), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double)]
     lib.nef_default_options.argtypes = [ctypes.POINTER(Opt)]
     lib.nef_last_error.restype = ctypes.c_char_p
     return lib
@@ -49,7 +53,7 @@ def problems(seed, shapes, ranks, restarts, missing):
     return out
 
 
-def call(lib, shapes, ranks, probs, restarts, a, b, iters, prec=NEF_BF16):
+def call(lib, shapes, ranks, probs, restarts, a, b, iters, prec=NEF_BF16, tiles=0):
     n = len(shapes)
     sh = (ctypes.c_int64 * (3 * n))(*[d for s in shapes for d in s])
     rk = (ctypes.c_int64 * n)(*ranks)
@@ -61,6 +65,7 @@ def call(lib, shapes, ranks, probs, restarts, a, b, iters, prec=NEF_BF16):
     o = Opt()
     lib.nef_default_options(ctypes.byref(o))
     o.precision = prec
+    o.batch_tiles = tiles
     rc = lib.nef_fit_batched(n, sh, rk, ys, ms, fs, restarts, a, b, iters, ctypes.byref(o), losses)
     return rc, work, list(losses)
 
@@ -101,3 +106,53 @@ def test_batched_argument_errors(lib):
     assert rc != 0 and b"restarts" in lib.nef_last_error()
     rc, _, _ = call(lib, shapes, [3], probs, 1, 0.0, 0.5, 1)
     assert rc != 0
+    rc, _, _ = call(lib, shapes, [3], probs, 1, 1.0, 0.0, 1, tiles=-1)
+    assert rc != 0 and b"batch_tiles" in lib.nef_last_error()
+
+
+@pytest.mark.parametrize("tiles", [1, 3, 4096])
+def test_batched_tiles_per_item(lib, tiles):
+    """Work items of 1 and 3 column tiles (views of up to 66 tiles then split into
+    many partials) and of 4096 (one item per row block): the fit still matches the
+    FP64 oracle."""
+    shapes = [(5, 7, 9), (70, 9, 66)]
+    ranks = [3, 17]
+    probs = problems(5, shapes, ranks, 1, 0.1)
+    rc, work, _ = call(lib, shapes, ranks, probs, 1, 1.0, 0.0, 2, tiles=tiles)
+    assert rc == 0, lib.nef_last_error()
+    for p, ((I, J, K), R) in enumerate(zip(shapes, ranks)):
+        m = OracleModel(MODEL, dict(i=I, j=J, k=K, r=R))
+        y, mask, inits = probs[p]
+        ref = m.fit(y.astype(np.float64), mask, [f.astype(np.float64) for f in inits[0]], 1.0, 0.0, 2)
+        for q in range(3):
+            assert np.linalg.norm(work[p][q] - ref[q]) / np.linalg.norm(ref[q]) < 1e-2, (tiles, p, q)
+
+
+def test_batched_tune_leaves_factors(lib):
+    """nef_fit_batched_tune returns one of its candidates, reports a time for each,
+    and leaves the caller's factors as they were."""
+    shapes = [(6, 10, 13), (30, 8, 20)]
+    ranks = [4, 20]
+    restarts = 2
+    probs = problems(6, shapes, ranks, restarts, 0.1)
+    n = len(shapes)
+    sh = (ctypes.c_int64 * (3 * n))(*[d for t in shapes for d in t])
+    rk = (ctypes.c_int64 * n)(*ranks)
+    ys = (ctypes.c_void_p * n)(*[p[0].ctypes.data for p in probs])
+    ms = (ctypes.c_void_p * n)(*[p[1].ctypes.data for p in probs])
+    work = [[f.copy() for f in p[2][k]] for p in probs for k in range(restarts)]
+    before = [[f.copy() for f in u] for u in work]
+    fs = (ctypes.c_void_p * (3 * n * restarts))(*[f.ctypes.data for u in work for f in u])
+    o = Opt()
+    lib.nef_default_options(ctypes.byref(o))
+    o.precision = NEF_BF16
+    best = ctypes.c_int()
+    times = (ctypes.c_double * 5)()
+    rc = lib.nef_fit_batched_tune(n, sh, rk, ys, ms, fs, restarts, 1.0, 0.0, ctypes.byref(o), ctypes.byref(best),
+                                  times)
+    assert rc == 0, lib.nef_last_error()
+    assert best.value in (16, 32, 64, 128, 256)
+    assert all(t > 0 for t in times)
+    for u, v in zip(work, before):
+        for f, g in zip(u, v):
+            assert np.array_equal(f, g)
