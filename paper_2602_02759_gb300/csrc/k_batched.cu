@@ -67,12 +67,14 @@ __global__ void k_mirror_batched(const BatchFinish* __restrict__ fin, const int6
 }
 
 // One problem, all restarts: thread per entry of the unpadded tensor.
+template <bool SMEM>
 __global__ void k_loss_batched(const float* __restrict__ y, const uint8_t* __restrict__ mask, int64_t I,
                                int64_t J, int64_t K, int rank, int restarts, const __grid_constant__ BatchFactors fac,
                                const __grid_constant__ LossSpec L, double* __restrict__ part) {
     // One restart at a time: C of that restart in shared memory as [rank][K] (lanes read
-    // consecutive k), each warp takes (i, j) pairs and its lanes the k of that row of Y;
-    // lane r holds A[i,r] B[j,r] and the rank-sum runs over shuffles of it (rank <= 32).
+    // consecutive k; SMEM = false for a C too large for it: read from global memory),
+    // each warp takes (i, j) pairs and its lanes the k of that row of Y; lane r holds
+    // A[i,r] B[j,r] and the rank-sum runs over shuffles of it (rank <= 32).
     extern __shared__ float c_sh[];
     __shared__ double sh[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -82,12 +84,14 @@ __global__ void k_loss_batched(const float* __restrict__ y, const uint8_t* __res
         const float* A = fac.f[q][0];
         const float* B = fac.f[q][1];
         const float* C = fac.f[q][2];
-        __syncthreads();  // c_sh free from the previous restart
-        for (int64_t t = threadIdx.x; t < K * rank; t += kThreads) {
-            const int64_t k = t / rank, r = t - k * rank;
-            c_sh[r * K + k] = C[t];
+        if constexpr (SMEM) {
+            __syncthreads();  // c_sh free from the previous restart
+            for (int64_t t = threadIdx.x; t < K * rank; t += kThreads) {
+                const int64_t k = t / rank, r = t - k * rank;
+                c_sh[r * K + k] = C[t];
+            }
+            __syncthreads();
         }
-        __syncthreads();
         double acc = 0.0;
         for (int64_t ij = (int64_t)blockIdx.x * (kThreads / 32) + warp; ij < n_ij; ij += warps_total) {
             const int64_t i = ij / J, j = ij - i * J;
@@ -96,7 +100,8 @@ __global__ void k_loss_batched(const float* __restrict__ y, const uint8_t* __res
                 const int64_t k = k0 + lane;
                 const int64_t kc = k < K ? k : K - 1;
                 float yh = 0.f;
-                for (int r = 0; r < rank; ++r) yh = fmaf(__shfl_sync(0xffffffffu, ab, r), c_sh[r * K + kc], yh);
+                for (int r = 0; r < rank; ++r)
+                    yh = fmaf(__shfl_sync(0xffffffffu, ab, r), SMEM ? c_sh[r * K + kc] : C[kc * rank + r], yh);
                 const int64_t e = ij * K + k;
                 if (k < K && (!mask || mask[e])) acc += (double)divergence(y[e], yh, L);
             }
@@ -109,6 +114,7 @@ __global__ void k_loss_batched(const float* __restrict__ y, const uint8_t* __res
             for (int w = 0; w < kThreads / 32; ++w) tsum += sh[w];
             part[(int64_t)blockIdx.x * restarts + q] = tsum;
         }
+        __syncthreads();  // sh read before the next restart writes it
     }
 }
 
@@ -141,14 +147,20 @@ cudaError_t launch_mirror_batched(const BatchFinish* fin, const int64_t* prefix,
 cudaError_t launch_loss_batched(const float* y, const uint8_t* mask, const int64_t* dims, int rank, int restarts,
                                 const BatchFactors& fac, const LossSpec& L, double* part, int n_blocks,
                                 double* out, cudaStream_t st) {
+    if (rank > 32) return cudaErrorInvalidValue;
     const size_t smem = (size_t)dims[2] * rank * sizeof(float);  // C of one restart, [rank][K]
-    if (rank > 32 || smem > 200 * 1024) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_loss_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    if (smem <= 96 * 1024) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_loss_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_loss_batched<true><<<n_blocks, kThreads, smem, st>>>(y, mask, dims[0], dims[1], dims[2], rank, restarts,
+                                                               fac, L, part);
+    } else {
+        k_loss_batched<false><<<n_blocks, kThreads, 0, st>>>(y, mask, dims[0], dims[1], dims[2], rank, restarts, fac,
+                                                             L, part);
     }
-    k_loss_batched<<<n_blocks, kThreads, smem, st>>>(y, mask, dims[0], dims[1], dims[2], rank, restarts, fac, L,
-                                                     part);
     k_loss_reduce<<<1, 32, 0, st>>>(part, n_blocks, restarts, out);
     return cudaGetLastError();
 }

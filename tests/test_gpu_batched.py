@@ -142,3 +142,26 @@ def test_batched_tune_leaves_factors_and_tiles_agree():
         for pi in range(len(probs)):
             for k in range(restarts):
                 assert losses[t][pi][k] == pytest.approx(losses[0][pi][k], rel=5e-4), (t, pi, k)
+
+
+def test_batched_losses_long_third_mode():
+    """The per-fit losses when C of a restart does not fit in shared memory
+    (K x R x 4 bytes > 96 KB: K = 800, R = 32) next to one that does: each loss
+    equals the FP64 oracle's loss at the returned factors within 1e-5."""
+    import paper_2602_02759_gb300 as nef
+    restarts = 2
+    probs = [synth.make_problem("ir,jr,kr->ijk", dict(i=20, j=24, k=800, r=32), 901, gamma=(0.3, 1.0),
+                                missing=0.1, restarts=restarts),
+             synth.make_problem("ir,jr,kr->ijk", dict(i=30, j=28, k=36, r=12), 902, gamma=(0.3, 1.0),
+                                missing=0.1, restarts=restarts)]
+    Ys = [torch.from_numpy(p.y).cuda() for p in probs]
+    Ms = [torch.from_numpy(p.mask).cuda() for p in probs]
+    facs = [[[torch.from_numpy(f).cuda() for f in p.inits[k]] for k in range(restarts)] for p in probs]
+    losses = nef.fit_batched(Ys, Ms, facs, 1.0, 0.0, 5)
+    torch.cuda.synchronize()
+    for pi, p in enumerate(probs):
+        m = OracleModel(p.model_str, p.dims)
+        for k in range(restarts):
+            got = [f.cpu().numpy().astype(np.float64) for f in facs[pi][k]]
+            lo, _ = m.loss(p.y, p.mask, got, 1.0, 0.0)
+            assert losses[pi][k] == pytest.approx(lo, rel=1e-5), (pi, k)
