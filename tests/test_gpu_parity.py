@@ -394,3 +394,18 @@ def test_autotune_bf16_then_fit(tmp_path):
         assert forced.profile(reset=True)["tcgen05"][1] >= iters
         lo, _ = forced.loss(Y, None, fs, 1.0, 0.0)
         assert lo == pytest.approx(trace[-1], rel=1e-3), (ring, gather)
+
+
+def test_launch_count_of_a_recorded_sweep():
+    """nef_plan_launches reports the kernels a sweep launched, as counted by the
+    launchers: for the CP model on the tensor cores, three per factor update (fused
+    pass, finish, column sums of the updated factor's copies)."""
+    nef = _nef()
+    model_str, dims = "ir,jr,kr->ijk", dict(i=256, j=160, k=288, r=32)
+    rng = np.random.default_rng(5)
+    y = rng.poisson(2.0, (256, 160, 288)).astype(np.float32)
+    fs = [dev(rng.uniform(0.5, 1.5, (n, 32))) for n in (256, 160, 288)]
+    plan = nef.Plan(model_str, dims, precision="bf16")
+    plan.fit(dev(y), None, fs, 1.0, 0.0, 3)
+    plan.check()
+    assert plan.launches(False) == 9, plan.launches(False)
