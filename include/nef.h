@@ -446,7 +446,8 @@ void nef_foldin_destroy(nef_foldin_t enc);
 
 /*
  * nef_foldin_grad -- gradient of L at the current parameters for one batch.
- *   slices  : device [n x d_in] FP32 (raw nonnegative values; log1p is applied inside)
+ *   slices  : device [n x d_in] FP32 (raw nonnegative values; log1p is applied inside),
+ *             or NULL for the batch kept by nef_foldin_load_batch
  *   targets : device [n x d_out] FP32 loadings
  *   grads   : device, packed like the parameters, receives dL/dparams
  *   loss    : host, receives L (synchronises), or NULL
@@ -457,10 +458,23 @@ nef_status nef_foldin_grad(nef_foldin_t enc, const float* slices, const float* t
                            double* loss);
 
 /*
+ * nef_foldin_load_batch -- compute the input features (log1p of the slices, in
+ * BF16, and their transposed copy) of one batch of n slices once and keep them
+ * in the encoder, for full-batch training: nef_foldin_grad and
+ * nef_foldin_train_step with slices == NULL then use them instead of recomputing
+ * them on every step (the same values, so the same results).  The kept batch
+ * is dropped by any call that passes slices (including nef_foldin_predict);
+ * slices == NULL without a kept batch of the same n is NEF_EINVAL.
+ * Errors: NEF_EINVAL (n outside [1, max_batch], NULL pointer), NEF_ECUDA.
+ */
+nef_status nef_foldin_load_batch(nef_foldin_t enc, const float* slices, int n);
+
+/*
  * nef_foldin_train_step -- forward, backward and one Adam step (Kingma & Ba,
- * bias-corrected with the encoder's step count) on one batch; loss (host, or
- * NULL) receives L before the step.  Errors as nef_foldin_grad, plus NEF_EINVAL
- * for lr <= 0, beta outside [0, 1) or eps <= 0.
+ * bias-corrected with the encoder's step count) on one batch (slices, or NULL
+ * for the batch kept by nef_foldin_load_batch); loss (host, or NULL) receives L
+ * before the step.  Errors as nef_foldin_grad, plus NEF_EINVAL for lr <= 0, beta
+ * outside [0, 1) or eps <= 0.
  */
 nef_status nef_foldin_train_step(nef_foldin_t enc, const float* slices, const float* targets, int n, double lr,
                                  double beta1, double beta2, double eps, double* loss);

@@ -27,7 +27,7 @@ EXPORTS = ["nef_default_options", "nef_plan", "nef_plan_destroy", "nef_fit", "ne
            "nef_plan_profile", "nef_tc_trace", "nef_check", "nef_fit_batched", "nef_fit_batched_tune", "nef_cp3_update_static",
            "nef_last_error",
            "nef_foldin_num_params", "nef_foldin_create", "nef_foldin_destroy", "nef_foldin_grad",
-           "nef_foldin_train_step", "nef_foldin_predict", "nef_foldin_params"]
+           "nef_foldin_train_step", "nef_foldin_predict", "nef_foldin_load_batch", "nef_foldin_params"]
 
 
 class Options(ctypes.Structure):
@@ -124,6 +124,8 @@ def load(path: str = LIB_PATH):
     lib.nef_foldin_train_step.argtypes = [vp, vp, vp, ci, dbl, dbl, dbl, dbl, dp]
     lib.nef_foldin_train_step.restype = ci
     lib.nef_foldin_predict.argtypes = [vp, vp, ci, vp]
+    lib.nef_foldin_load_batch.argtypes = [vp, vp, ci]
+    lib.nef_foldin_load_batch.restype = ctypes.c_int
     lib.nef_foldin_predict.restype = ci
     lib.nef_foldin_params.argtypes = [vp, vp]
     lib.nef_foldin_params.restype = ci
@@ -464,23 +466,34 @@ class FoldIn:
             raise ValueError(f"expected a contiguous float32 CUDA tensor [n, {cols}]")
 
     def grad(self, slices, targets):
-        """(packed gradient tensor, loss) at the current parameters."""
+        """(packed gradient tensor, loss) at the current parameters, on `slices` or, when
+        slices is None, on the batch kept by load_batch."""
         import torch
-        self._check(slices, self.d_in)
+        if slices is not None:
+            self._check(slices, self.d_in)
         self._check(targets, self.d_out)
-        g = torch.empty(self.n_params, dtype=torch.float32, device=slices.device)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=targets.device)
         loss = ctypes.c_double(0.0)
-        check(load().nef_foldin_grad(self._h, ctypes.c_void_p(slices.data_ptr()),
-                                     ctypes.c_void_p(targets.data_ptr()), int(slices.shape[0]),
+        check(load().nef_foldin_grad(self._h, ctypes.c_void_p(None if slices is None else slices.data_ptr()),
+                                     ctypes.c_void_p(targets.data_ptr()), int(targets.shape[0]),
                                      ctypes.c_void_p(g.data_ptr()), ctypes.byref(loss)))
         return g, float(loss.value)
 
-    def train_step(self, slices, targets, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=True):
+    def load_batch(self, slices):
+        """nef_foldin_load_batch: keep the features of this batch for full-batch steps
+        (train_step / grad with slices=None)."""
         self._check(slices, self.d_in)
+        self._kept = int(slices.shape[0])
+        check(load().nef_foldin_load_batch(self._h, ctypes.c_void_p(slices.data_ptr()), self._kept))
+
+    def train_step(self, slices, targets, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=True):
+        """One Adam step on `slices`, or on the batch kept by load_batch when slices is None."""
+        if slices is not None:
+            self._check(slices, self.d_in)
         self._check(targets, self.d_out)
         loss = ctypes.c_double(0.0)
-        check(load().nef_foldin_train_step(self._h, ctypes.c_void_p(slices.data_ptr()),
-                                           ctypes.c_void_p(targets.data_ptr()), int(slices.shape[0]),
+        check(load().nef_foldin_train_step(self._h, ctypes.c_void_p(None if slices is None else slices.data_ptr()),
+                                           ctypes.c_void_p(targets.data_ptr()), int(targets.shape[0]),
                                            float(lr), float(beta1), float(beta2), float(eps),
                                            ctypes.byref(loss) if want_loss else None))
         return float(loss.value) if want_loss else None

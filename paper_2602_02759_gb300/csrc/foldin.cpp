@@ -41,6 +41,7 @@ struct nef_foldin_s {
     int64_t ws_floats = 0;
     int n_sm = 152;
     int64_t t = 0;
+    int loaded_n = 0;          // slices whose features X, Xt hold (nef_foldin_load_batch), or 0
     std::vector<void*> allocs;
 };
 
@@ -104,7 +105,12 @@ nef_status gemm(nef_foldin_t f, const uint16_t* A, int64_t lda, const uint16_t* 
 // Forward pass of n samples; with `train`, also the transposed copies the backward pass needs.
 nef_status forward(nef_foldin_t f, const float* slices, int n, bool train) {
     const int d = f->d, h = f->h, o = f->o, ldn = f->ldn;
-    FI_CUDA(nef::launch_fi_features(slices, n, d, f->X, train ? f->Xt : nullptr, ldn, f->st));
+    if (slices) {
+        FI_CUDA(nef::launch_fi_features(slices, n, d, f->X, train ? f->Xt : nullptr, ldn, f->st));
+        f->loaded_n = 0;  // X (and Xt) no longer hold the kept batch
+    } else if (f->loaded_n != n) {
+        return fi_fail(NEF_EINVAL, "slices is NULL and no batch of this size is kept (nef_foldin_load_batch)");
+    }
     FI_TRY(gemm(f, f->X, d, f->W1t, d, f->Z1, h, n, h, d));
     FI_CUDA(nef::launch_fi_bias_act(f->Z1, f->p + f->ob1, n, h, 1, f->H1, train ? f->H1t : nullptr, ldn, nullptr,
                                     f->st));
@@ -261,7 +267,7 @@ nef_status nef_foldin_grad(nef_foldin_t f, const float* slices, const float* tar
                            double* loss) {
     set_last_error("");
     FI_TRY(check_batch(f, n));
-    if (!slices || !targets || !grads) return fi_fail(NEF_EINVAL, "NULL argument");
+    if (!targets || !grads) return fi_fail(NEF_EINVAL, "NULL argument");
     FI_TRY(forward(f, slices, n, true));
     FI_TRY(backward(f, targets, n));
     FI_CUDA(cudaMemcpyAsync(grads, f->g, f->np * sizeof(float), cudaMemcpyDeviceToDevice, f->st));
@@ -273,7 +279,7 @@ nef_status nef_foldin_train_step(nef_foldin_t f, const float* slices, const floa
                                  double beta1, double beta2, double eps, double* loss) {
     set_last_error("");
     FI_TRY(check_batch(f, n));
-    if (!slices || !targets) return fi_fail(NEF_EINVAL, "NULL argument");
+    if (!targets) return fi_fail(NEF_EINVAL, "NULL argument");
     if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
         return fi_fail(NEF_EINVAL, "Adam hyper-parameters out of range");
     FI_TRY(forward(f, slices, n, true));
@@ -288,6 +294,15 @@ nef_status nef_foldin_train_step(nef_foldin_t f, const float* slices, const floa
                                 (float)lr, (float)beta1, (float)beta2, (float)eps, (float)bc1, (float)bc2, f->st));
     FI_TRY(refresh_weights(f, false));
     if (loss) FI_TRY(read_loss(f, n, loss));
+    return NEF_OK;
+}
+
+nef_status nef_foldin_load_batch(nef_foldin_t f, const float* slices, int n) {
+    set_last_error("");
+    FI_TRY(check_batch(f, n));
+    if (!slices) return fi_fail(NEF_EINVAL, "NULL argument");
+    FI_CUDA(nef::launch_fi_features(slices, n, f->d, f->X, f->Xt, f->ldn, f->st));
+    f->loaded_n = n;
     return NEF_OK;
 }
 

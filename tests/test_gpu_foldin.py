@@ -261,3 +261,23 @@ def test_foldin_gain_at_benchmark_size():
         gaps[k] = ((le - full) / full, (lp - full) / full)
         assert le - full < lp - full, (k, gaps)
     print("fold-in gaps (encoder, plain) by passes:", gaps)
+
+
+def test_foldin_kept_batch_steps_equal_passed_batch():
+    """Full-batch training on the GPU: five Adam steps on a batch kept by
+    nef_foldin_load_batch give bit for bit the parameters of five steps that pass
+    the slices each time (the same features, products and reductions)."""
+    nef = _nef()
+    d, h, o, n = 1024, 256, 32, 384
+    rng = np.random.default_rng(11)
+    xs = torch.as_tensor(rng.poisson(0.4, (n, d)).astype(np.float32)).cuda()
+    tg = torch.as_tensor(rng.gamma(0.5, 1.0, (n, o)).astype(np.float32)).cuda()
+    flat = torch.as_tensor(nef.pack_params(synth.mlp_params((d, h, h, o), 4))).cuda()
+    a = nef.FoldIn(d, h, o, n, flat.clone())
+    b = nef.FoldIn(d, h, o, n, flat.clone())
+    b.load_batch(xs)
+    for _ in range(5):
+        a.train_step(xs, tg, 1e-3, want_loss=False)
+        b.train_step(None, tg, 1e-3, want_loss=False)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params(), b.params())

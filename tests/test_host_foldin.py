@@ -36,6 +36,7 @@ def lib():
     lib.nef_foldin_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, dp]
     lib.nef_foldin_predict.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.nef_foldin_load_batch.argtypes = [vp, vp, ctypes.c_int]
     lib.nef_foldin_params.argtypes = [vp, vp]
     lib.nef_foldin_num_params.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.nef_foldin_num_params.restype = ctypes.c_int64
@@ -137,3 +138,31 @@ def test_foldin_argument_errors(lib):
                                          None) != 0
     finally:
         lib.nef_foldin_destroy(f)
+
+
+def test_foldin_kept_batch_steps_equal_passed_batch(lib):
+    """Three Adam steps on a batch kept by nef_foldin_load_batch give exactly the
+    parameters of three steps that pass the slices each time; a call that passes
+    slices drops the kept batch, after which slices == NULL is rejected."""
+    d, h, o, n = 64, 32, 8, 12
+    _, slices, targets, flat = setup(d, h, o, n, seed=2)
+    a = create(lib, d, h, o, n, flat)
+    b = create(lib, d, h, o, n, flat)
+    try:
+        assert lib.nef_foldin_load_batch(b, slices.ctypes.data, n) == 0
+        for _ in range(3):
+            assert lib.nef_foldin_train_step(a, slices.ctypes.data, targets.ctypes.data, n, 1e-3, 0.9, 0.999,
+                                             1e-8, None) == 0
+            assert lib.nef_foldin_train_step(b, None, targets.ctypes.data, n, 1e-3, 0.9, 0.999, 1e-8, None) == 0
+        pa = np.zeros(flat.size, np.float32)
+        pb = np.zeros(flat.size, np.float32)
+        assert lib.nef_foldin_params(a, pa.ctypes.data) == 0 and lib.nef_foldin_params(b, pb.ctypes.data) == 0
+        assert np.array_equal(pa, pb)
+        assert lib.nef_foldin_train_step(b, None, targets.ctypes.data, n - 1, 1e-3, 0.9, 0.999, 1e-8, None) != 0
+        out = np.zeros((n, o), np.float32)
+        assert lib.nef_foldin_predict(b, slices.ctypes.data, n, out.ctypes.data) == 0
+        assert lib.nef_foldin_train_step(b, None, targets.ctypes.data, n, 1e-3, 0.9, 0.999, 1e-8, None) != 0
+        assert b"kept" in lib.nef_last_error()
+    finally:
+        lib.nef_foldin_destroy(a)
+        lib.nef_foldin_destroy(b)
