@@ -15,7 +15,6 @@
 // so no clearing is needed between calls.
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 
 #include "../../include/nef.h"
 #include "nef_internal.h"
@@ -27,26 +26,15 @@ namespace {
 constexpr int64_t kStaticScratchFloats = (int64_t)4 << 20;
 static __device__ __align__(256) float g_nef_static_scratch[kStaticScratchFloats];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float* g_scratch_ptr[kMaxDevices] = {};
-
 // Device address of the scratch array on the current device.  In host code the
 // array's name only stands for the host-side shadow symbol, so the address is
-// looked up once per device with that device current.
+// looked up with the device current, on every call: after a device reset the
+// module is loaded again and the array may move, so no address is kept.
 cudaError_t scratch_on_current_device(float** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_nef_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_nef_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<float*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<float*>(p);
     return cudaSuccess;
 }
 
