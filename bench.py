@@ -748,6 +748,17 @@ def run_workload(args):
     t_s = time.perf_counter() - t1
     sweeps_fp32 = n_cmp * restarts * (args.warmup + sweeps)
     rel = [abs(losses[a][b] - loss_fp32[a][b]) / loss_fp32[a][b] for a in range(n_cmp) for b in range(restarts)]
+    # the issue side: every restart's epilogue work runs per entry, so the engine is bound by
+    # instruction issue, not by HBM; the instructions per entry-update are the ncu count of
+    # k_batched_persistent on the first 8 problems (36.3 warp instructions per 32)
+    eu_per_s = 3.0 * n_sum * restarts * sweeps / t_b
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    issue_peak = n_sm * 4 * 2070e6  # 4 schedulers per SM, one warp instruction per clock, 2070 MHz
+    issue = {"entry_updates_per_s": eu_per_s, "warp_instructions_per_32_entry_updates": 36.3,
+             "achieved_warp_instructions_per_s": eu_per_s * 36.3 / 32, "peak_warp_instructions_per_s": issue_peak,
+             "frac": eu_per_s * 36.3 / 32 / issue_peak,
+             "note": "instruction count per entry-update from one ncu capture of the first 8 problems; "
+                     "peak = SMs x 4 issue slots x 2070 MHz"}
     out = {"workload": f"batched CP: {'all' if len(Ys) == 512 else 'first ' + str(len(Ys)) + ' of the'} 512 "
                        f"problems (dims U{{20..300}}^3, ranks U{{4..32}}, 10% missing), {restarts} restarts each, KL",
            "data": gen_note, "entries": int(n_sum), "fits": fits, "sweeps": sweeps,
@@ -755,7 +766,7 @@ def run_workload(args):
                             "ms_per_all_problem_sweep": t_b / sweeps * 1e3,
                             "hbm_frac": bytes_sweep * sweeps / t_b / 1e9 / hbm,
                             "call_setup_ms": t_setup * 1e3, "loss_pass_ms": t_loss * 1e3,
-                            "tiles_per_item": tiles,
+                            "tiles_per_item": tiles, "issue": issue,
                             "tune_ms_2_sweeps": {str(k): v for k, v in tile_ms.items()},
                             "note": "wall clock of one nef_fit_batched call of all the sweeps without the "
                                     "final loss evaluation (one persistent launch per bond width, "
