@@ -301,6 +301,7 @@ nef_status nef_foldin_load_batch(nef_foldin_t f, const float* slices, int n) {
     set_last_error("");
     FI_TRY(check_batch(f, n));
     if (!slices) return fi_fail(NEF_EINVAL, "NULL argument");
+    f->loaded_n = 0;  // X and Xt are rewritten: no batch is kept unless this one is
     FI_CUDA(nef::launch_fi_features(slices, n, f->d, f->X, f->Xt, f->ldn, f->st));
     f->loaded_n = n;
     return NEF_OK;
