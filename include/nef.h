@@ -394,11 +394,10 @@ nef_status nef_fit_batched_tune(int n, const int64_t* shapes, const int64_t* ran
  * factor must satisfy rows x R <= 1,048,576 (rows = I, J or K); larger sizes
  * return NEF_EINVAL.  Every call shares that array: calls that can overlap on
  * the GPU (other streams or host threads) race and must be serialised by the
- * caller.  The first call on each device looks up the array's device address
- * (and keeps it for later calls), so make it before any stream capture.  A
- * cudaDeviceReset discards the array's device memory: the kept address is then
- * stale, so do not call this entry point on a device after resetting it in the
- * same process.  The launch grid is sized from the device's SM count.  Returns
+ * caller.  Every call looks up the array's device address (so a device reset,
+ * after which the array may move, is followed); the first call on a device
+ * loads the library's device code there, so make it before any stream
+ * capture.  The launch grid is sized from the device's SM count.  Returns
  * once the work is enqueued.
  * Errors: NEF_EINVAL (null pointer, bad rank, factor index or size, alpha or
  * beta not finite, eps negative or not finite), NEF_EUNSUPPORTED (alpha == 0
